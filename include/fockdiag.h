@@ -1,0 +1,178 @@
+/*
+ * fockdiag.h -- C ABI of the GB300 (sm_103a) Fock-amplitude library.
+ *
+ * The library computes photon-number probabilities and conditional density
+ * matrices of a noisy M-mode Gaussian state from its Bargmann triple
+ * (A, b, c), by the recurrence of arXiv 2303.08879 eq. (recrel) walked as in
+ * Algorithm 1 (all modes detected, Sec. 3.1) and Algorithm 2 (conditional
+ * states, Sec. 3.2), plus vector-Jacobian products with respect to A, b and
+ * c (Sec. 2.5, eqs. dL_dB and dL_dA).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Complex numbers are fk_c128 = {re, im} (same layout as C99 double
+ *    complex, cuDoubleComplex and torch.complex128).
+ *  - A is D x D row-major and b has D entries, D = 2M.  Lattice index 2j is
+ *    the row m and 2j+1 the column n of <m|rho|n> for mode j (the Fock-index
+ *    pairing of Sec. 2.1).  A is used through its symmetric part
+ *    (A + A^T)/2; amplitudes are the Taylor coefficients of
+ *    c exp(z^T A z / 2 + b^T z) scaled by sqrt(k!).
+ *  - cutoffs[j] = C_j >= 1: photon numbers 0 <= k < C_j (eq.
+ *    local_boundary_conditions, Sec. 2.2).
+ *  - Pointers named d_* are DEVICE pointers owned by the caller; host_*
+ *    are host pointers.  Compute calls are stream-ordered: they enqueue work
+ *    on `stream` (a cudaStream_t; NULL = legacy default stream), never
+ *    synchronise it and never allocate device memory.  The caller supplies
+ *    a device workspace of at least fk_workspace_size() bytes, 256-byte
+ *    aligned, used by one call at a time.
+ *  - Errors are returned as fk_status; no exception crosses the ABI.  A
+ *    failure detected on the device after launch (a barrier wait that ran
+ *    out of time, inconsistent flags) is recorded in the workspace status
+ *    word and read back with fk_workspace_status().
+ *  - Gradients follow PyTorch's convention for a real loss L:
+ *    grad z = dL/dRe z + i dL/dIm z.  For holomorphic amplitudes this is
+ *    grad xi = sum_k gbar_k conj(dG_k / dxi), the chain rule of Sec. 2.5.
+ *    grad_A is symmetric (A enters only through its symmetric part).
+ */
+#ifndef FOCKDIAG_H
+#define FOCKDIAG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { double re, im; } fk_c128;
+
+typedef enum {
+    FK_OK = 0,
+    FK_EINVAL = 1,         /* bad argument: M < 1, cutoff < 1, NULL pointer, no detected mode ... */
+    FK_EUNSUPPORTED = 2,   /* beyond compiled limits (see FK_MAX_*) */
+    FK_EWORKSPACE = 3,     /* workspace smaller than fk_workspace_size() or misaligned */
+    FK_ENOMEM = 4,         /* host allocation failed */
+    FK_ECUDA = 5,          /* a CUDA runtime call or launch failed */
+    FK_ETIMEOUT = 6,       /* a device-side barrier wait exceeded its time limit */
+    FK_ENONFINITE = 7,     /* reserved: NaN/Inf in the inputs */
+    FK_EBZERO = 8          /* FK_FLAG_B_ZERO was given but b has a nonzero entry */
+} fk_status;
+
+/* Compiled limits. */
+#define FK_MAX_MODES 12        /* M after dropping modes with C_j = 1 */
+#define FK_MAX_CUTOFF 64       /* any single C_j */
+#define FK_MAX_LEVELS 512      /* sum_j (C_j - 1) */
+
+/* Operation codes for fk_workspace_size(). */
+#define FK_OP_DIAG      1      /* fock_diag_probs[_batched]                  */
+#define FK_OP_DIAG_VJP  2      /* fock_diag_probs then fock_diag_probs_vjp   */
+#define FK_OP_COND      3      /* fock_conditional_dm[_batched]              */
+#define FK_OP_COND_VJP  4      /* fock_conditional_dm then its VJP           */
+
+/* Flags. */
+#define FK_FLAG_B_ZERO    1u   /* caller guarantees b == 0 for every circuit:
+                                  the odd-weight amplitudes vanish (eq.
+                                  recrel_noB, Sec. 2.4), their storage is
+                                  omitted and the diagonal pivots of
+                                  Algorithm 1 are skipped.  Checked on the
+                                  device (FK_EBZERO). */
+#define FK_FLAG_RECOMPUTE 2u   /* VJP: run the forward walk first instead of
+                                  reusing the state left in the workspace */
+
+/* Human-readable text for a status code (static storage). */
+const char *fk_status_string(int status);
+
+/* Library version, major*10000 + minor*100 + patch. */
+int fk_version(void);
+
+/*
+ * Bargmann triple of a Gaussian state (host computation).
+ * Sec. 2.1, eqs. (A_rho), (b_rho) and Sec. 2.2 (vacuum amplitude):
+ *   A = P_M sigma_- sigma_+^{-1},  b = P_M sigma_+^{-1} mu,
+ *   c = exp(-mu^dagger sigma_+^{-1} mu / 2) / sqrt(det sigma_+),
+ *   sigma_pm = sigma +- I/2, sigma and mu the complex covariance and mean in
+ *   the (a_1..a_M, a^dag_1..a^dag_M) basis, hbar = 1.
+ * host_V: 2M x 2M real quadrature covariance, ordering (x_1..x_M, p_1..p_M),
+ * row-major; host_mean: 2M real quadrature means.  Outputs (host): A (D x D),
+ * b (D), c (1) in the library's interleaved lattice order.
+ * Returns FK_EINVAL for M < 1 or M > 64 or a singular sigma_+.
+ */
+int fk_gaussian_to_triple(int M, const double *host_V, const double *host_mean,
+                          fk_c128 *host_A, fk_c128 *host_b, fk_c128 *host_c);
+
+/*
+ * Workspace bytes for `op` on `batch` circuits of one shape (M, cutoffs,
+ * detected_mask; mask may be NULL = all detected, ignored by the DIAG ops).
+ * Depends on the current CUDA device (its SM count sizes per-block partial
+ * sums).  Writes *bytes; no device work.
+ */
+int fk_workspace_size(int M, const int *host_cutoffs, const unsigned char *host_detected_mask,
+                      int batch, int op, unsigned flags, size_t *bytes);
+
+/*
+ * Detection probabilities, all modes detected (Algorithm 1, Sec. 3.1):
+ * p(n) = G_{n1 n1 n2 n2 ...} for every 0 <= n < cutoffs.
+ *   d_A [batch][D][D], d_b [batch][D], d_c [batch]   inputs (read only)
+ *   d_probs [batch][prod C_j]   output, row-major over modes (mode 0
+ *                               slowest); the imaginary part is round-off.
+ * The walk's amplitudes stay in the workspace for a following
+ * fock_diag_probs_vjp() on the same inputs.
+ */
+int fock_diag_probs(const fk_c128 *d_A, const fk_c128 *d_b, const fk_c128 *d_c, int M,
+                    const int *host_cutoffs, fk_c128 *d_probs, void *d_ws, size_t ws_bytes,
+                    void *stream);
+int fock_diag_probs_batched(int batch, const fk_c128 *d_A, const fk_c128 *d_b, const fk_c128 *d_c,
+                            int M, const int *host_cutoffs, fk_c128 *d_probs, unsigned flags,
+                            void *d_ws, size_t ws_bytes, void *stream);
+
+/*
+ * Vector-Jacobian product of fock_diag_probs (Sec. 2.5) by a reverse walk.
+ *   d_grad_probs [batch][prod C_j]   upstream gradient (PyTorch convention)
+ *   d_grad_A [batch][D][D], d_grad_b [batch][D], d_grad_c [batch]  outputs
+ * Unless FK_FLAG_RECOMPUTE is set, d_ws must hold the state of a
+ * fock_diag_probs[_batched] call with the same inputs, shape and flags.
+ */
+int fock_diag_probs_vjp(const fk_c128 *d_A, const fk_c128 *d_b, const fk_c128 *d_c, int M,
+                        const int *host_cutoffs, const fk_c128 *d_grad_probs, fk_c128 *d_grad_A,
+                        fk_c128 *d_grad_b, fk_c128 *d_grad_c, void *d_ws, size_t ws_bytes,
+                        void *stream);
+int fock_diag_probs_vjp_batched(int batch, const fk_c128 *d_A, const fk_c128 *d_b,
+                                const fk_c128 *d_c, int M, const int *host_cutoffs,
+                                const fk_c128 *d_grad_probs, fk_c128 *d_grad_A,
+                                fk_c128 *d_grad_b, fk_c128 *d_grad_c, unsigned flags,
+                                void *d_ws, size_t ws_bytes, void *stream);
+
+/*
+ * Reads the device-side status word of a workspace after the calls queued
+ * on `stream` (synchronises the stream).  *status = FK_OK or the first error
+ * a kernel recorded; the word is cleared by the next compute call.
+ */
+int fk_workspace_status(const void *d_ws, void *stream, int *status);
+
+/*
+ * Self-test of the bounded device-side wait: launches one block that waits
+ * for a flag in the workspace that nothing sets, giving up after
+ * timeout_ns; the status word then reads FK_ETIMEOUT.  Needs 256 bytes of
+ * workspace.  Used by the failure-detection tests; no GPU fault involved.
+ */
+int fk_selftest_wait_timeout(void *d_ws, size_t ws_bytes, unsigned long long timeout_ns,
+                             void *stream);
+
+/*
+ * Schedule description (host only, no device work): for the all-detected
+ * walk of one circuit writes
+ *   out[0] = amplitudes stored, out[1] = pivots applied, out[2] = levels,
+ *   out[3 + 6*s .. 3 + 6*s + 5] for level s = number of
+ *   {diagonal, offset_1, offset_2, offset_1010, offset_1001, pivots}:
+ *   amplitudes of total weight 2s (diagonal, 2, 1010, 1001) or 2s + 1
+ *   (offset_1) and the pivots applied at level s (digit sum s),
+ * for at most out_len entries.  flags as in fock_diag_probs_batched.
+ */
+int fk_describe_diag_schedule(int M, const int *host_cutoffs, unsigned flags, int64_t *out,
+                              int out_len);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FOCKDIAG_H */

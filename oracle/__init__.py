@@ -73,6 +73,8 @@ def _load():
             lib.or_walk_all_conditional.restype = I
             lib.or_walk_stats.argtypes = [P, P]
             lib.or_walk_stats.restype = None
+            lib.or_walk_level_hist.argtypes = [P, P, I]
+            lib.or_walk_level_hist.restype = None
             _lib = lib
     return _lib
 
@@ -222,6 +224,14 @@ class Walk:
         if rc:
             raise RuntimeError(f"walk failed ({rc})")
         return (out, od) if with_tangent else out
+
+    def level_hist(self, nlev):
+        """[nlev, 6] counts of stored amplitudes per level and type (diag,
+        offset_1 ket, offset_1 bra, offset_2, offset_1010, offset_1001); level
+        s holds total weight 2s (2s+1 for offset_1)."""
+        h = np.zeros(6 * nlev, np.int64)
+        self._lib.or_walk_level_hist(self._h, _ptr(h), nlev)
+        return h.reshape(nlev, 6)
 
     def stats(self):
         s = np.zeros(9, np.int64)

@@ -491,3 +491,29 @@ void or_walk_stats(const walk_t *w, int64_t *stats)
     stats[7] = (int64_t)w->used;
     stats[8] = (int64_t)w->used - s;
 }
+
+/*
+ * Per-level histogram of the stored amplitudes: hist[6*s + t] counts the
+ * amplitudes of detected-part type t (as in or_walk_stats) whose total
+ * weight is 2s (even types) or 2s+1 (offset_1 types); nlev rows.
+ */
+void or_walk_level_hist(const walk_t *w, int64_t *hist, int nlev)
+{
+    memset(hist, 0, sizeof(int64_t) * 6 * nlev);
+    int x[OR_MAXD];
+    for (uint64_t i = 0; i < w->cap; ++i) {
+        if (!w->tab[i].key) continue;
+        uint64_t code = w->tab[i].key - 1;
+        int wsum = 0;
+        for (int d = 0; d < w->D; ++d) {
+            x[d] = (int)((code / w->radix[d]) % (uint64_t)w->dims[d]);
+            wsum += x[d];
+        }
+        int type = 0;
+        if (code != 0 && parent_index((walk_t *)w, x, &type) < 0) continue;
+        if (code == 0) type = 0;
+        if (type < 0) continue;
+        const int s = wsum / 2;
+        if (s < nlev) hist[6 * s + type]++;
+    }
+}

@@ -1,0 +1,414 @@
+// api.cpp -- host side of the C ABI declared in include/fockdiag.h:
+// argument checking, storage geometry, workspace layout, the Gaussian ->
+// Bargmann triple map, and dispatch to the CUDA launchers.
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "fk_internal.h"
+#include "../../include/fockdiag.h"
+
+namespace fk {
+
+int build_diag_shape(int M, const int *cutoffs, bool has_b, DiagShape *sh)
+{
+    if (M < 1 || !cutoffs || !sh) return FK_EINVAL;
+    std::memset(sh, 0, sizeof(*sh));
+    sh->M_orig = M;
+    sh->D_orig = 2 * M;
+    int k = 0;
+    int64_t nd = 1;
+    for (int j = 0; j < M; ++j) {
+        if (cutoffs[j] < 1) return FK_EINVAL;
+        if (cutoffs[j] > FK_MAX_CUTOFF) return FK_EUNSUPPORTED;
+        if (cutoffs[j] == 1) continue;          // index always 0: never read or written
+        if (k >= FK_MAXM) return FK_EUNSUPPORTED;
+        sh->C[k] = cutoffs[j];
+        sh->mode_map[k] = j;
+        nd *= cutoffs[j];
+        if (nd >= (int64_t(1) << 31)) return FK_EUNSUPPORTED;
+        ++k;
+    }
+    sh->M = k;
+    sh->n_diag = nd;
+    sh->has_b = has_b ? 1 : 0;
+    int L = 0;
+    for (int i = 0; i < k; ++i) L += sh->C[i] - 1;
+    if (L > FK_MAX_LEVELS) return FK_EUNSUPPORTED;
+    sh->L = L;
+    int64_t st = 1;
+    for (int i = k - 1; i >= 0; --i) {
+        sh->stride[i] = st;
+        st *= sh->C[i];
+    }
+    // amplitude boxes, concatenated: DIAG, T2(K), P1010/P1001(K,m), T1K/T1B(j)
+    int64_t off = nd;
+    for (int K = 0; K < k; ++K) {
+        sh->off_t2[K] = off;
+        off += box_size(*sh, K, K, 2, -1, 0);
+    }
+    for (int K = 0; K < k; ++K)
+        for (int m = K + 1; m < k; ++m) {
+            const int64_t n = box_size(*sh, K, K, 1, m, 1);
+            sh->off_1010[K][m] = off;
+            off += n;
+            sh->off_1001[K][m] = off;
+            off += n;
+        }
+    if (has_b) {
+        for (int j = 0; j < k; ++j) {
+            sh->off_t1k[j] = off;
+            off += box_size(*sh, 0, 0, 1, j > 0 ? j : -1, 1);
+            sh->off_t1b[j] = off;
+            off += (j == 0) ? box_size(*sh, 0, 0, 2, -1, 0) : box_size(*sh, 0, 0, 1, j, 1);
+        }
+    }
+    sh->circ_size = off;
+    int64_t ap = 0;
+    for (int K = 0; K < k; ++K) {
+        sh->off_ap[K] = ap;
+        ap += box_size(*sh, K, K, 1, -1, 0);
+    }
+    sh->n_ap = ap;
+    return FK_OK;
+}
+
+int diag_layout(const DiagShape &sh, int batch, bool vjp, DiagLayout *lay)
+{
+    const size_t B = (size_t)batch, D = 2 * (size_t)sh.M;
+    const size_t c16 = 16;
+    size_t o = 0;
+    lay->ctl = o; o = align_up(o + sizeof(Control));
+    lay->As = o; o = align_up(o + B * D * D * c16);
+    lay->bs = o; o = align_up(o + B * D * c16);
+    lay->F = o; o = align_up(o + B * (size_t)sh.circ_size * c16);
+    lay->grid_vjp = 0;
+    if (vjp) {
+        int grid = 1;
+        if (sh.M > 0) {
+            int rc = diag_grid_size(sh, true, &grid);
+            if (rc) return rc;
+        }
+        lay->grid_vjp = grid;
+        lay->Fbar = o; o = align_up(o + B * (size_t)sh.circ_size * c16);
+        lay->scratch = o; o = align_up(o + B * (size_t)sh.n_ap * c16);
+        lay->partA = o; o = align_up(o + B * (size_t)grid * D * D * c16);
+        lay->partb = o; o = align_up(o + B * (size_t)grid * D * c16);
+    } else {
+        lay->Fbar = lay->scratch = lay->partA = lay->partb = o;
+    }
+    lay->total = o;
+    return FK_OK;
+}
+
+// Number of digit vectors with the given extents summing to each s.
+static std::vector<int64_t> level_hist(const std::vector<int> &ext, int L)
+{
+    std::vector<int64_t> h(L + 1, 0), n(L + 1, 0);
+    h[0] = 1;
+    for (int e : ext) {
+        std::fill(n.begin(), n.end(), 0);
+        for (int s = 0; s <= L; ++s)
+            if (h[s])
+                for (int v = 0; v < e && s + v <= L; ++v) n[s + v] += h[s];
+        h.swap(n);
+    }
+    return h;
+}
+
+static std::vector<int> extents(const DiagShape &sh, int k0, int a, int da, int m, int dm)
+{
+    std::vector<int> e;
+    for (int i = k0; i < sh.M; ++i) e.push_back(sh.C[i] - (i == a ? da : 0) - (i == m ? dm : 0));
+    for (int &v : e) if (v < 0) v = 0;
+    return e;
+}
+
+// ------------------------------------------------------------------- a0
+// Gaussian state -> (A, b, c); see fk_gaussian_to_triple in fockdiag.h.
+using cd = std::complex<double>;
+
+static bool invert_and_det(int n, std::vector<cd> &a, std::vector<cd> &inv, cd *det)
+{
+    inv.assign((size_t)n * n, cd(0, 0));
+    for (int i = 0; i < n; ++i) inv[(size_t)i * n + i] = 1.0;
+    cd d = 1.0;
+    for (int col = 0; col < n; ++col) {
+        int piv = col;
+        double best = std::abs(a[(size_t)col * n + col]);
+        for (int r = col + 1; r < n; ++r) {
+            const double v = std::abs(a[(size_t)r * n + col]);
+            if (v > best) { best = v; piv = r; }
+        }
+        if (!(best > 0.0)) return false;
+        if (piv != col) {
+            for (int c = 0; c < n; ++c) {
+                std::swap(a[(size_t)piv * n + c], a[(size_t)col * n + c]);
+                std::swap(inv[(size_t)piv * n + c], inv[(size_t)col * n + c]);
+            }
+            d = -d;
+        }
+        const cd p = a[(size_t)col * n + col];
+        d *= p;
+        for (int c = 0; c < n; ++c) {
+            a[(size_t)col * n + c] /= p;
+            inv[(size_t)col * n + c] /= p;
+        }
+        for (int r = 0; r < n; ++r) {
+            if (r == col) continue;
+            const cd f = a[(size_t)r * n + col];
+            if (f == cd(0, 0)) continue;
+            for (int c = 0; c < n; ++c) {
+                a[(size_t)r * n + c] -= f * a[(size_t)col * n + c];
+                inv[(size_t)r * n + c] -= f * inv[(size_t)col * n + c];
+            }
+        }
+    }
+    *det = d;
+    return true;
+}
+
+static int gaussian_to_triple(int M, const double *V, const double *mean, fk_c128 *Aout,
+                              fk_c128 *bout, fk_c128 *cout)
+{
+    const int n = 2 * M;
+    // a_j = (x_j + i p_j)/sqrt2, a^dag_j = (x_j - i p_j)/sqrt2:
+    // sigma = W V W^dagger, mu = W mean with W = [[I, iI], [I, -iI]]/sqrt2.
+    const double r2 = 1.0 / std::sqrt(2.0);
+    std::vector<cd> W((size_t)n * n, cd(0, 0));
+    for (int j = 0; j < M; ++j) {
+        W[(size_t)j * n + j] = r2;
+        W[(size_t)j * n + M + j] = cd(0, r2);
+        W[(size_t)(M + j) * n + j] = r2;
+        W[(size_t)(M + j) * n + M + j] = cd(0, -r2);
+    }
+    std::vector<cd> WV((size_t)n * n, 0.0), sig((size_t)n * n, 0.0), mu(n, 0.0);
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < n; ++k) {
+            cd s = 0;
+            for (int l = 0; l < n; ++l) s += W[(size_t)i * n + l] * V[(size_t)l * n + k];
+            WV[(size_t)i * n + k] = s;
+        }
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < n; ++k) {
+            cd s = 0;
+            for (int l = 0; l < n; ++l) s += WV[(size_t)i * n + l] * std::conj(W[(size_t)k * n + l]);
+            sig[(size_t)i * n + k] = s;
+        }
+    for (int i = 0; i < n; ++i) {
+        cd s = 0;
+        for (int l = 0; l < n; ++l) s += W[(size_t)i * n + l] * mean[l];
+        mu[i] = s;
+    }
+    std::vector<cd> sp = sig, sm = sig, spi;
+    for (int i = 0; i < n; ++i) {
+        sp[(size_t)i * n + i] += 0.5;
+        sm[(size_t)i * n + i] -= 0.5;
+    }
+    cd det;
+    std::vector<cd> tmp = sp;
+    if (!invert_and_det(n, tmp, spi, &det)) return FK_EINVAL;
+    // A_blk = P sm spi, b_blk = P spi mu; (P X)_{i,.} = X_{(i + M) mod 2M, .}
+    std::vector<cd> Ablk((size_t)n * n, 0.0), bblk(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        const int pi = (i + M) % n;
+        for (int k = 0; k < n; ++k) {
+            cd s = 0;
+            for (int l = 0; l < n; ++l) s += sm[(size_t)pi * n + l] * spi[(size_t)l * n + k];
+            Ablk[(size_t)i * n + k] = s;
+        }
+        cd s = 0;
+        for (int l = 0; l < n; ++l) s += spi[(size_t)pi * n + l] * mu[l];
+        bblk[i] = s;
+    }
+    cd q = 0;
+    for (int i = 0; i < n; ++i) {
+        cd s = 0;
+        for (int l = 0; l < n; ++l) s += spi[(size_t)i * n + l] * mu[l];
+        q += std::conj(mu[i]) * s;
+    }
+    const cd c = std::exp(-0.5 * q) / std::sqrt(det);
+    // lattice order: index 2j <- a^dag_j (block M + j), 2j+1 <- a_j (block j),
+    // so that index 2j is the row m of <m|rho|n>.
+    std::vector<int> perm(n);
+    for (int j = 0; j < M; ++j) {
+        perm[2 * j] = M + j;
+        perm[2 * j + 1] = j;
+    }
+    for (int i = 0; i < n; ++i) {
+        for (int k = 0; k < n; ++k) {
+            const cd v = Ablk[(size_t)perm[i] * n + perm[k]];
+            Aout[(size_t)i * n + k] = {v.real(), v.imag()};
+        }
+        bout[i] = {bblk[perm[i]].real(), bblk[perm[i]].imag()};
+    }
+    *cout = {c.real(), c.imag()};
+    return FK_OK;
+}
+
+static bool aligned(const void *p) { return ((uintptr_t)p % kAlign) == 0; }
+
+}  // namespace fk
+
+using namespace fk;
+
+extern "C" {
+
+const char *fk_status_string(int status)
+{
+    switch (status) {
+    case FK_OK: return "ok";
+    case FK_EINVAL: return "invalid argument";
+    case FK_EUNSUPPORTED: return "size beyond compiled limits";
+    case FK_EWORKSPACE: return "workspace too small or misaligned";
+    case FK_ENOMEM: return "host allocation failed";
+    case FK_ECUDA: return "CUDA runtime error";
+    case FK_ETIMEOUT: return "device barrier wait timed out";
+    case FK_ENONFINITE: return "non-finite input";
+    case FK_EBZERO: return "FK_FLAG_B_ZERO given but b is nonzero";
+    default: return "unknown status";
+    }
+}
+
+int fk_version(void) { return 100; }
+
+int fk_gaussian_to_triple(int M, const double *V, const double *mean, fk_c128 *A, fk_c128 *b,
+                          fk_c128 *c)
+{
+    if (M < 1 || M > 64 || !V || !mean || !A || !b || !c) return FK_EINVAL;
+    try {
+        return gaussian_to_triple(M, V, mean, A, b, c);
+    } catch (...) {
+        return FK_ENOMEM;
+    }
+}
+
+int fk_workspace_size(int M, const int *cutoffs, const unsigned char *mask, int batch, int op,
+                      unsigned flags, size_t *bytes)
+{
+    (void)mask;
+    if (!bytes || batch < 1) return FK_EINVAL;
+    if (op == FK_OP_DIAG || op == FK_OP_DIAG_VJP) {
+        DiagShape sh;
+        int rc = build_diag_shape(M, cutoffs, !(flags & FK_FLAG_B_ZERO), &sh);
+        if (rc) return rc;
+        DiagLayout lay;
+        rc = diag_layout(sh, batch, op == FK_OP_DIAG_VJP, &lay);
+        if (rc) return rc;
+        *bytes = lay.total;
+        return FK_OK;
+    }
+    return FK_EUNSUPPORTED;
+}
+
+int fock_diag_probs_batched(int batch, const fk_c128 *A, const fk_c128 *b, const fk_c128 *c,
+                            int M, const int *cutoffs, fk_c128 *probs, unsigned flags, void *ws,
+                            size_t ws_bytes, void *stream)
+{
+    if (batch < 1 || !A || !b || !c || !probs || !ws) return FK_EINVAL;
+    DiagShape sh;
+    int rc = build_diag_shape(M, cutoffs, !(flags & FK_FLAG_B_ZERO), &sh);
+    if (rc) return rc;
+    DiagLayout lay;
+    rc = diag_layout(sh, batch, false, &lay);
+    if (rc) return rc;
+    if (ws_bytes < lay.total || !aligned(ws)) return FK_EWORKSPACE;
+    return launch_diag_forward(sh, batch, flags, A, b, c, probs, ws, lay, stream);
+}
+
+int fock_diag_probs(const fk_c128 *A, const fk_c128 *b, const fk_c128 *c, int M,
+                    const int *cutoffs, fk_c128 *probs, void *ws, size_t ws_bytes, void *stream)
+{
+    return fock_diag_probs_batched(1, A, b, c, M, cutoffs, probs, 0u, ws, ws_bytes, stream);
+}
+
+int fock_diag_probs_vjp_batched(int batch, const fk_c128 *A, const fk_c128 *b, const fk_c128 *c,
+                                int M, const int *cutoffs, const fk_c128 *gprobs, fk_c128 *gA,
+                                fk_c128 *gb, fk_c128 *gc, unsigned flags, void *ws,
+                                size_t ws_bytes, void *stream)
+{
+    if (batch < 1 || !A || !b || !c || !gprobs || !gA || !gb || !gc || !ws) return FK_EINVAL;
+    DiagShape sh;
+    int rc = build_diag_shape(M, cutoffs, !(flags & FK_FLAG_B_ZERO), &sh);
+    if (rc) return rc;
+    DiagLayout lay;
+    rc = diag_layout(sh, batch, true, &lay);
+    if (rc) return rc;
+    if (ws_bytes < lay.total || !aligned(ws)) return FK_EWORKSPACE;
+    if (flags & FK_FLAG_RECOMPUTE) {
+        // the forward's probabilities land in the adjoint region, cleared next
+        void *tmp = (char *)ws + lay.Fbar;
+        rc = launch_diag_forward(sh, batch, flags, A, b, c, tmp, ws, lay, stream);
+        if (rc) return rc;
+    }
+    return launch_diag_vjp(sh, batch, flags, A, b, c, gprobs, gA, gb, gc, ws, lay, stream);
+}
+
+int fock_diag_probs_vjp(const fk_c128 *A, const fk_c128 *b, const fk_c128 *c, int M,
+                        const int *cutoffs, const fk_c128 *gprobs, fk_c128 *gA, fk_c128 *gb,
+                        fk_c128 *gc, void *ws, size_t ws_bytes, void *stream)
+{
+    return fock_diag_probs_vjp_batched(1, A, b, c, M, cutoffs, gprobs, gA, gb, gc, 0u, ws,
+                                       ws_bytes, stream);
+}
+
+int fk_workspace_status(const void *ws, void *stream, int *status)
+{
+    if (!ws || !status) return FK_EINVAL;
+    return read_status(ws, stream, status);
+}
+
+int fk_selftest_wait_timeout(void *ws, size_t ws_bytes, unsigned long long timeout_ns, void *stream)
+{
+    if (!ws || ws_bytes < sizeof(Control) || !aligned(ws)) return FK_EWORKSPACE;
+    return launch_wait_selftest(ws, timeout_ns, stream);
+}
+
+int fk_describe_diag_schedule(int M, const int *cutoffs, unsigned flags, int64_t *out, int out_len)
+{
+    if (!out || out_len < 3) return FK_EINVAL;
+    DiagShape sh;
+    int rc = build_diag_shape(M, cutoffs, !(flags & FK_FLAG_B_ZERO), &sh);
+    if (rc) return rc;
+    const int L = sh.L;
+    std::vector<int64_t> rows((size_t)6 * (L + 1), 0);
+    auto add = [&](int col, const std::vector<int64_t> &h, int shift) {
+        for (int s = 0; s <= L; ++s) {
+            const int lev = s + shift;
+            if (lev >= 0 && lev <= L) rows[(size_t)6 * lev + col] += h[s];
+        }
+    };
+    int64_t pivots = 0;
+    const int k = sh.M;
+    add(0, level_hist(extents(sh, 0, -1, 0, -1, 0), L), 0);
+    for (int K = 0; K < k; ++K) {
+        add(2, level_hist(extents(sh, K, K, 2, -1, 0), L), 1);
+        for (int m = K + 1; m < k; ++m) {
+            const auto h = level_hist(extents(sh, K, K, 1, m, 1), L);
+            add(3, h, 1);
+            add(4, h, 1);
+        }
+        const auto hp = level_hist(extents(sh, K, K, 1, -1, 0), L);
+        add(5, hp, 0);
+        for (auto v : hp) pivots += v;
+    }
+    if (sh.has_b && k > 0) {
+        for (int j = 0; j < k; ++j) {
+            add(1, level_hist(extents(sh, 0, 0, 1, j > 0 ? j : -1, 1), L), 0);
+            add(1, level_hist(j == 0 ? extents(sh, 0, 0, 2, -1, 0) : extents(sh, 0, 0, 1, j, 1), L), 0);
+        }
+        const auto hd = level_hist(extents(sh, 0, 0, 1, -1, 0), L);
+        add(5, hd, 0);
+        for (auto v : hd) pivots += v;
+    }
+    out[0] = sh.circ_size;
+    out[1] = pivots;
+    out[2] = L + 1;
+    for (int i = 0; i < (int)rows.size() && 3 + i < out_len; ++i) out[3 + i] = rows[i];
+    return FK_OK;
+}
+
+}  // extern "C"

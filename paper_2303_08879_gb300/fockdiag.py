@@ -1,0 +1,219 @@
+"""Thin Python binding of the C ABI (include/fockdiag.h).
+
+Argument marshalling only: every step of the walk runs in libfockdiag.so.
+PyTorch provides device memory, streams and the autograd hook; no fallback
+exists -- a missing or unloadable library raises ``FockError``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfockdiag.so")
+
+FK_OK = 0
+FK_ETIMEOUT = 6
+FK_EBZERO = 8
+FK_OP_DIAG, FK_OP_DIAG_VJP, FK_OP_COND, FK_OP_COND_VJP = 1, 2, 3, 4
+FK_FLAG_B_ZERO = 1
+FK_FLAG_RECOMPUTE = 2
+
+# every symbol the header declares
+EXPORTS = [
+    "fk_status_string", "fk_version", "fk_gaussian_to_triple", "fk_workspace_size",
+    "fock_diag_probs", "fock_diag_probs_batched", "fock_diag_probs_vjp",
+    "fock_diag_probs_vjp_batched", "fk_workspace_status", "fk_selftest_wait_timeout",
+    "fk_describe_diag_schedule",
+]
+
+
+class FockError(RuntimeError):
+    def __init__(self, status, where=""):
+        self.status = status
+        msg = _status_text(status)
+        super().__init__(f"{where}: {msg} (status {status})" if where else msg)
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def _status_text(st):
+    try:
+        return lib().fk_status_string(int(st)).decode()
+    except Exception:
+        return f"status {st}"
+
+
+def lib():
+    """Load libfockdiag.so (raises FockError if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise FockError(-1, f"{LIB_PATH} is not built (run paper_2303_08879_gb300.build)")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, U, Z = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint, ctypes.c_size_t
+        L.fk_status_string.argtypes = [I]
+        L.fk_status_string.restype = ctypes.c_char_p
+        L.fk_version.restype = I
+        L.fk_gaussian_to_triple.argtypes = [I, P, P, P, P, P]
+        L.fk_workspace_size.argtypes = [I, P, P, I, I, U, ctypes.POINTER(Z)]
+        L.fock_diag_probs.argtypes = [P, P, P, I, P, P, P, Z, P]
+        L.fock_diag_probs_batched.argtypes = [I, P, P, P, I, P, P, U, P, Z, P]
+        L.fock_diag_probs_vjp.argtypes = [P, P, P, I, P, P, P, P, P, P, Z, P]
+        L.fock_diag_probs_vjp_batched.argtypes = [I, P, P, P, I, P, P, P, P, P, U, P, Z, P]
+        L.fk_workspace_status.argtypes = [P, P, ctypes.POINTER(I)]
+        L.fk_selftest_wait_timeout.argtypes = [P, Z, ctypes.c_ulonglong, P]
+        L.fk_describe_diag_schedule.argtypes = [I, P, U, P, I]
+        for name in EXPORTS:           # fail here, not at first use, if one is missing
+            getattr(L, name)
+        _lib = L
+        return L
+
+
+def _check(st, where):
+    if st != FK_OK:
+        raise FockError(st, where)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _cut(cutoffs):
+    return (ctypes.c_int * len(cutoffs))(*[int(c) for c in cutoffs])
+
+
+def _need_cuda_c128(name, t):
+    if not isinstance(t, torch.Tensor) or t.device.type != "cuda" or t.dtype != torch.complex128:
+        raise TypeError(f"{name} must be a CUDA complex128 tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+# ----------------------------------------------------------------- host side
+def fk_gaussian_to_triple(V, mean):
+    """Bargmann triple (A, b, c) of a Gaussian state (numpy in, numpy out)."""
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    mean = np.ascontiguousarray(mean, dtype=np.float64)
+    M = V.shape[0] // 2
+    A = np.zeros((2 * M, 2 * M), np.complex128)
+    b = np.zeros(2 * M, np.complex128)
+    c = np.zeros(1, np.complex128)
+    st = lib().fk_gaussian_to_triple(M, V.ctypes.data, mean.ctypes.data, A.ctypes.data,
+                                     b.ctypes.data, c.ctypes.data)
+    _check(st, "fk_gaussian_to_triple")
+    return A, b, complex(c[0])
+
+
+def fk_workspace_size(M, cutoffs, batch=1, op=FK_OP_DIAG, flags=0, detected_mask=None):
+    n = ctypes.c_size_t(0)
+    mask = None
+    if detected_mask is not None:
+        mask = (ctypes.c_ubyte * M)(*[1 if v else 0 for v in detected_mask])
+    st = lib().fk_workspace_size(M, _cut(cutoffs), mask, batch, op, flags, ctypes.byref(n))
+    _check(st, "fk_workspace_size")
+    return int(n.value)
+
+
+def fk_describe_diag_schedule(M, cutoffs, flags=0):
+    L = sum(max(int(c) - 1, 0) for c in cutoffs)
+    n = 3 + 6 * (L + 1)
+    out = np.zeros(n, np.int64)
+    st = lib().fk_describe_diag_schedule(M, _cut(cutoffs), flags, out.ctypes.data, n)
+    _check(st, "fk_describe_diag_schedule")
+    lev = int(out[2])
+    rows = out[3:3 + 6 * lev].reshape(lev, 6)
+    return {"stored": int(out[0]), "pivots": int(out[1]), "levels": lev,
+            "per_level": rows}
+
+
+def workspace(nbytes, device=None):
+    """A 256-byte aligned device workspace (torch allocations are)."""
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8,
+                       device=device or torch.device("cuda"))
+
+
+# --------------------------------------------------------------- device side
+def fock_diag_probs_batched(A, b, c, cutoffs, probs=None, flags=0, ws=None, stream=None,
+                            for_vjp=True):
+    """p(n) for a batch of circuits of one shape (Algorithm 1).
+
+    A [B, D, D], b [B, D], c [B] complex128 CUDA tensors.  Returns
+    (probs [B, *cutoffs], ws); ``ws`` keeps the walk for a following VJP.
+    """
+    for n, t in (("A", A), ("b", b), ("c", c)):
+        _need_cuda_c128(n, t)
+    B, M = A.shape[0], len(cutoffs)
+    if A.shape != (B, 2 * M, 2 * M) or b.shape != (B, 2 * M) or c.shape != (B,):
+        raise ValueError("shapes must be A[B,2M,2M], b[B,2M], c[B]")
+    if probs is None:
+        probs = torch.empty((B,) + tuple(int(x) for x in cutoffs), dtype=torch.complex128,
+                            device=A.device)
+    _need_cuda_c128("probs", probs)
+    need = fk_workspace_size(M, cutoffs, B, FK_OP_DIAG_VJP if for_vjp else FK_OP_DIAG, flags)
+    if ws is None:
+        ws = workspace(need, A.device)
+    st = lib().fock_diag_probs_batched(B, _ptr(A), _ptr(b), _ptr(c), M, _cut(cutoffs), _ptr(probs),
+                                       flags, _ptr(ws), ws.numel(), _stream(stream))
+    _check(st, "fock_diag_probs_batched")
+    return probs, ws
+
+
+def fock_diag_probs(A, b, c, cutoffs, probs=None, ws=None, stream=None):
+    """Single-circuit form: A [D, D], b [D], c [] -> probs [*cutoffs]."""
+    p, ws = fock_diag_probs_batched(A.unsqueeze(0), b.unsqueeze(0), c.reshape(1), cutoffs,
+                                    None if probs is None else probs.unsqueeze(0), 0, ws, stream)
+    return p[0], ws
+
+
+def fock_diag_probs_vjp_batched(A, b, c, cutoffs, grad_probs, ws, flags=0, stream=None,
+                                out=None):
+    """(grad_A, grad_b, grad_c) of a batch (PyTorch complex-gradient convention)."""
+    for n, t in (("A", A), ("b", b), ("c", c), ("grad_probs", grad_probs)):
+        _need_cuda_c128(n, t)
+    B, M = A.shape[0], len(cutoffs)
+    if out is None:
+        gA = torch.empty_like(A); gb = torch.empty_like(b); gc = torch.empty_like(c)
+    else:
+        gA, gb, gc = out
+    need = fk_workspace_size(M, cutoffs, B, FK_OP_DIAG_VJP, flags)
+    if ws is None:
+        ws = workspace(need, A.device)
+        flags |= FK_FLAG_RECOMPUTE
+    st = lib().fock_diag_probs_vjp_batched(B, _ptr(A), _ptr(b), _ptr(c), M, _cut(cutoffs),
+                                           _ptr(grad_probs), _ptr(gA), _ptr(gb), _ptr(gc), flags,
+                                           _ptr(ws), ws.numel(), _stream(stream))
+    _check(st, "fock_diag_probs_vjp_batched")
+    return gA, gb, gc
+
+
+def fk_workspace_status(ws, stream=None):
+    v = ctypes.c_int(0)
+    st = lib().fk_workspace_status(_ptr(ws), _stream(stream), ctypes.byref(v))
+    _check(st, "fk_workspace_status")
+    return int(v.value)
+
+
+def check_workspace(ws, stream=None, where="device"):
+    st = fk_workspace_status(ws, stream)
+    if st != FK_OK:
+        raise FockError(st, where)
+
+
+def fk_selftest_wait_timeout(ws, timeout_ns, stream=None):
+    st = lib().fk_selftest_wait_timeout(_ptr(ws), ws.numel(), int(timeout_ns), _stream(stream))
+    _check(st, "fk_selftest_wait_timeout")

@@ -1,0 +1,274 @@
+"""GPU parity of the all-detected walk (Algorithm 1) and its VJP against the
+CPU oracle, through the C ABI.
+
+Tolerances (from the accuracy requirement on this path): amplitudes agree
+to 1e-10 relative where |G| > 1e-12 and 1e-12 absolute below; VJPs to 1e-8
+relative (to the largest entry of each gradient).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import gradients as ograd
+from oracle import triple as otriple
+from paper_2303_08879_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+RTOL, ATOL, VJP_RTOL = 1e-10, 1e-12, 1e-8
+
+
+@pytest.fixture(scope="module")
+def fd():
+    from paper_2303_08879_gb300 import build
+    build.build()
+    from paper_2303_08879_gb300 import fockdiag
+    return fockdiag
+
+
+def cuda(x):
+    return torch.as_tensor(np.asarray(x), dtype=torch.complex128).cuda()
+
+
+def assert_amp_close(got, ref):
+    got = np.asarray(got); ref = np.asarray(ref)
+    assert got.shape == ref.shape
+    err = np.abs(got - ref)
+    big = np.abs(ref) > ATOL
+    if big.any():
+        worst = np.max(err[big] / np.abs(ref[big]))
+        assert worst <= RTOL, f"max relative error {worst:.3e}"
+    if (~big).any():
+        assert np.max(err[~big]) <= ATOL, f"max absolute error {np.max(err[~big]):.3e}"
+
+
+def assert_grad_close(got, ref, what):
+    got = np.asarray(got); ref = np.asarray(ref)
+    scale = max(np.max(np.abs(ref)), 1e-300)
+    err = np.max(np.abs(got - ref)) / scale
+    assert err <= VJP_RTOL, f"{what}: relative error {err:.3e}"
+
+
+def gpu_probs(fd, A, b, c, cut, flags=0):
+    A = cuda(np.asarray(A)[None] if np.ndim(A) == 2 else A)
+    b = cuda(np.asarray(b)[None] if np.ndim(b) == 1 else b)
+    c = cuda(np.atleast_1d(c))
+    p, ws = fd.fock_diag_probs_batched(A, b, c, cut, flags=flags)
+    fd.check_workspace(ws)
+    return p.cpu().numpy(), (A, b, c, ws)
+
+
+CASES = [((5, 4), True), ((3, 4, 3), True), ((4, 4, 4), False), ((2, 5, 1), True),
+         ((1, 3), False), ((6,), True), ((3, 3, 2, 3), False), ((2, 2, 2, 2), True),
+         ((1, 1), True), ((7, 2, 5), True), ((4, 1, 3, 2), True), ((2,), False)]
+
+
+@pytest.mark.parametrize("cut,withb", CASES)
+def test_forward_matches_full_density_matrix(fd, cut, withb):
+    rng = np.random.default_rng(7 * sum(cut) + len(cut))
+    D = 2 * len(cut)
+    A, b = inputs.random_symmetric(D, rng, with_b=withb)
+    c = 0.6 + 0.1j
+    ref = oracle.full_dm_probs(A, b, c, cut)
+    got, _ = gpu_probs(fd, A, b, c, cut)
+    assert_amp_close(got[0], ref)
+    if not withb:
+        got0, _ = gpu_probs(fd, A, b, c, cut, flags=fd.FK_FLAG_B_ZERO)
+        assert_amp_close(got0[0], ref)
+
+
+def test_gbs_m2_c10_full_density_matrix(fd):
+    """1 circuit, M = 2, C = 10 (squeezed, Haar 2x2, loss): all 100 probabilities."""
+    circ = inputs.workload("gbs_m2_c10")[0]
+    Ao, bo, co = otriple.gaussian_to_triple(circ.V, circ.mean)
+    ref = oracle.full_dm_probs(Ao, bo, co, circ.cutoffs)
+    A, b, c = fd.fk_gaussian_to_triple(circ.V, circ.mean)
+    for flags in (0, fd.FK_FLAG_B_ZERO):
+        got, _ = gpu_probs(fd, A, b, c, circ.cutoffs, flags)
+        assert_amp_close(got[0], ref)
+
+
+def test_many_tiles_ragged_levels(fd):
+    """M = 5, C = 6 and uneven cutoffs: several 128-pivot tiles per level, ragged tails."""
+    rng = np.random.default_rng(3)
+    for cut, withb in (((6, 6, 6, 6, 6), False), ((7, 5, 6, 4, 6), True)):
+        A, b = inputs.random_symmetric(2 * len(cut), rng, scale=0.15, with_b=withb)
+        ref = oracle.Walk(A, b, 0.7, cut).all_probs()
+        got, _ = gpu_probs(fd, A, b, 0.7, cut)
+        assert_amp_close(got[0], ref)
+
+
+def test_batched_matches_single(fd):
+    circs = inputs.workload("gbs_m8_c6_batch16", 5)
+    cut = (3, 4, 3, 2, 3, 2, 3, 3)
+    trip = [fd.fk_gaussian_to_triple(c.V, c.mean) for c in circs]
+    A = np.stack([t[0] for t in trip]); b = np.stack([t[1] for t in trip])
+    c = np.array([t[2] for t in trip])
+    got, _ = gpu_probs(fd, A, b, c, cut, flags=fd.FK_FLAG_B_ZERO)
+    for i, circ in enumerate(circs):
+        Ao, bo, co = otriple.gaussian_to_triple(circ.V, circ.mean)
+        ref = oracle.Walk(Ao, bo, co, cut).all_probs()
+        assert_amp_close(got[i], ref)
+
+
+def test_gbs_m8_c6_batch16_full_size_sampled(fd):
+    """The benchmark workload at full size (16 circuits, M = 8, C = 6, b = 0) in
+    the launch configuration the benchmark uses; sampled outputs computed one
+    by one by the oracle, plus properties of every output."""
+    circs = inputs.workload("gbs_m8_c6_batch16")
+    cut = circs[0].cutoffs
+    trip = [fd.fk_gaussian_to_triple(c.V, c.mean) for c in circs]
+    A = np.stack([t[0] for t in trip]); b = np.stack([t[1] for t in trip])
+    c = np.array([t[2] for t in trip])
+    got, _ = gpu_probs(fd, A, b, c, cut, flags=fd.FK_FLAG_B_ZERO)
+    assert got.shape == (16,) + cut
+    re = got.real.reshape(16, -1)
+    assert np.all(re > -1e-15)
+    s = re.sum(axis=1)
+    assert np.all(s <= 1 + 1e-12) and np.all(s > 0.2)
+    assert np.max(np.abs(got.imag)) < 1e-14
+    rng = np.random.default_rng(11)
+    for ci in (0, 9, 15):
+        Ao, bo, co = otriple.gaussian_to_triple(circs[ci].V, circs[ci].mean)
+        w = oracle.Walk(Ao, bo, co, cut)
+        pats = [tuple(rng.integers(0, 6, size=8)) for _ in range(40)]
+        pats += [(0,) * 8, (5,) * 8, (5, 0, 0, 0, 0, 0, 0, 0), (0,) * 7 + (5,)]
+        for n in pats:
+            ref, _ = w.prob(n)
+            assert_amp_close(got[ci][n], ref)
+
+
+# ---------------------------------------------------------------------- VJP
+def oracle_vjp(A, b, c, cut, gbar_probs):
+    G = oracle.full_lattice(A, b, c, oracle.dm_dims(cut))
+    gfull = np.zeros_like(G)
+    for n in np.ndindex(*cut):
+        gfull[tuple(v for a in n for v in (a, a))] = gbar_probs[n]
+    return ograd.vjp(G, gfull, c)
+
+
+VJP_CASES = [((4, 3), True), ((3, 3, 3), False), ((3, 4, 2), True), ((2, 1, 3), True),
+             ((5,), True), ((2, 2, 2, 2), False), ((4, 4), False)]
+
+
+@pytest.mark.parametrize("cut,withb", VJP_CASES)
+def test_vjp_matches_oracle_gradient(fd, cut, withb):
+    rng = np.random.default_rng(100 + sum(cut))
+    D = 2 * len(cut)
+    A, b = inputs.random_symmetric(D, rng, with_b=withb)
+    c = 0.8 - 0.1j
+    gbar = rng.normal(size=cut) + 1j * rng.normal(size=cut)
+    rA, rb, rc = oracle_vjp(A, b, c, cut, gbar)
+    for flags in ((0, fd.FK_FLAG_B_ZERO) if not withb else (0,)):
+        p, (Ad, bd, cd, ws) = gpu_probs(fd, A, b, c, cut, flags)
+        gA, gb, gc = fd.fock_diag_probs_vjp_batched(Ad, bd, cd, cut, cuda(gbar[None]), ws, flags=flags)
+        fd.check_workspace(ws)
+        assert_grad_close(gA[0].cpu().numpy(), rA, "grad_A")
+        if withb:
+            assert_grad_close(gb[0].cpu().numpy(), rb, "grad_b")
+        else:
+            assert np.max(np.abs(gb[0].cpu().numpy())) < 1e-12 * max(1, np.max(np.abs(rA)))
+        assert abs(gc[0].item() - rc) <= VJP_RTOL * max(abs(rc), 1e-300)
+
+
+def test_vjp_recompute_flag_and_autograd(fd):
+    from paper_2303_08879_gb300 import autograd as fag
+    rng = np.random.default_rng(5)
+    cut = (3, 4, 3)
+    A, b = inputs.random_symmetric(6, rng)
+    c = 0.9
+    gbar = rng.normal(size=cut)
+    rA, rb, rc = oracle_vjp(A, b, c, cut, gbar)
+    Ad, bd, cd = cuda(A[None]), cuda(b[None]), cuda([c])
+    gA, gb, gc = fd.fock_diag_probs_vjp_batched(Ad, bd, cd, cut, cuda(gbar[None]), None)
+    assert_grad_close(gA[0].cpu().numpy(), rA, "grad_A (recompute)")
+    assert_grad_close(gb[0].cpu().numpy(), rb, "grad_b (recompute)")
+    # autograd: L = sum_n w_n Re p_n
+    At = Ad.clone().requires_grad_(True); bt = bd.clone().requires_grad_(True)
+    ct = cd.clone().requires_grad_(True)
+    P = fag.diag_probs(At, bt, ct, cut)
+    L = (torch.as_tensor(gbar, device="cuda") * P[0].real).sum()
+    L.backward()
+    assert_grad_close(At.grad[0].cpu().numpy(), rA, "autograd grad_A")
+    assert_grad_close(bt.grad[0].cpu().numpy(), rb, "autograd grad_b")
+
+
+def test_vjp_full_size_homogeneity_and_adjoint(fd):
+    """Benchmark workload (16 x M=8, C=6) at full size: Euler homogeneity
+    G_k(t^2 A, t b, c) = t^|k| G_k and c conj(grad_c) = sum conj(gbar) p hold
+    exactly for the VJP; a dot-product test against the oracle's forward-mode
+    tangent on sampled outputs checks it along random directions."""
+    circs = inputs.workload("gbs_m8_c6_batch16")
+    cut = circs[0].cutoffs
+    trip = [fd.fk_gaussian_to_triple(c.V, c.mean) for c in circs]
+    A = np.stack([t[0] for t in trip]); b = np.stack([t[1] for t in trip])
+    c = np.array([t[2] for t in trip])
+    flags = fd.FK_FLAG_B_ZERO
+    p, (Ad, bd, cd, ws) = gpu_probs(fd, A, b, c, cut, flags)
+    rng = np.random.default_rng(2)
+    w = rng.normal(size=(16,) + cut)
+    gA, gb, gc = fd.fock_diag_probs_vjp_batched(Ad, bd, cd, cut, cuda(w), ws, flags=flags)
+    fd.check_workspace(ws)
+    gA = gA.cpu().numpy(); gc = gc.cpu().numpy()
+    wsum = np.zeros(cut)
+    for n in np.ndindex(*cut):
+        wsum[n] = 2 * sum(n)
+    for i in range(16):
+        lhs = np.sum(w[i] * wsum * p[i])
+        rhs = np.sum(2 * A[i] * np.conj(gA[i]))
+        assert abs(lhs - rhs) <= 1e-9 * np.sum(np.abs(w[i] * wsum * p[i]))
+        lc = np.sum(w[i] * p[i])
+        assert abs(c[i] * np.conj(gc[i]) - lc) <= 1e-10 * np.sum(np.abs(w[i] * p[i]))
+        assert np.max(np.abs(gA[i] - gA[i].T)) <= 1e-14 * np.max(np.abs(gA[i]))
+    # dot-product test on a sparse upstream gradient supported on sampled patterns
+    ci = 3
+    pats = sorted(set(tuple(rng.integers(0, 4, size=8)) for _ in range(30)))
+    gs = np.zeros((1,) + cut, complex)
+    for n in pats:
+        gs[(0,) + n] = rng.normal() + 1j * rng.normal()
+    gA1, gb1, gc1 = fd.fock_diag_probs_vjp_batched(Ad[ci:ci + 1].contiguous(), bd[ci:ci + 1].contiguous(),
+                                                   cd[ci:ci + 1].contiguous(), cut, cuda(gs), None,
+                                                   flags=flags)
+    Ao, bo, co = otriple.gaussian_to_triple(circs[ci].V, circs[ci].mean)
+    for _ in range(2):
+        dA = rng.normal(size=(16, 16)) + 1j * rng.normal(size=(16, 16))
+        dc = rng.normal() + 1j * rng.normal()
+        wt = oracle.Walk(Ao, bo, co, cut, tangent=(dA, np.zeros(16), dc))
+        lhs = 0.0
+        for n in pats:
+            _, t = wt.prob(n)
+            lhs += np.real(np.conj(gs[(0,) + n]) * t)
+        rhs = np.real(np.vdot(gA1[0].cpu().numpy(), dA) + np.conj(gc1[0].item()) * dc)
+        assert abs(lhs - rhs) <= 1e-8 * max(abs(lhs), 1e-12)
+
+
+# ----------------------------------------------------- failure detection
+def test_b_zero_flag_violation_is_reported(fd):
+    rng = np.random.default_rng(1)
+    A, b = inputs.random_symmetric(4, rng)
+    Ad, bd, cd = cuda(A[None]), cuda(b[None]), cuda([0.5])
+    p, ws = fd.fock_diag_probs_batched(Ad, bd, cd, (3, 3), flags=fd.FK_FLAG_B_ZERO)
+    assert fd.fk_workspace_status(ws) == fd.FK_EBZERO
+    # the context stays usable
+    p, ws = fd.fock_diag_probs_batched(Ad, bd, cd, (3, 3))
+    assert fd.fk_workspace_status(ws) == fd.FK_OK
+
+
+def test_bounded_wait_times_out(fd):
+    ws = fd.workspace(256)
+    fd.fk_selftest_wait_timeout(ws, 2_000_000)      # 2 ms; nothing sets the flag
+    assert fd.fk_workspace_status(ws) == fd.FK_ETIMEOUT
+    torch.cuda.synchronize()
+    x = torch.ones(4, device="cuda") * 2
+    assert x.sum().item() == 8.0
+
+
+def test_small_workspace_rejected(fd):
+    rng = np.random.default_rng(1)
+    A, b = inputs.random_symmetric(4, rng)
+    Ad, bd, cd = cuda(A[None]), cuda(b[None]), cuda([0.5])
+    ws = fd.workspace(256)
+    with pytest.raises(fd.FockError) as e:
+        fd.fock_diag_probs_batched(Ad, bd, cd, (3, 3), ws=ws)
+    assert e.value.status == 3
