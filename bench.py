@@ -1,0 +1,368 @@
+"""Benchmark of the all-detected Fock walk (Algorithm 1) forward + VJP.
+
+Workload: 16 synthetic noisy GBS circuits, M = 8 modes, all PNR-detected,
+cutoff C = 6 per mode (6^8 = 1.68 M probabilities each), squeezing
+r ~ U[0.3, 1], Haar 8x8 interferometer, loss eta ~ U[0.6, 1], no
+displacement (b = 0).  One step = the forward walk of all 16 circuits plus
+the VJP of L = sum_n w_n Re p_n (w ~ N(0, 1)) with respect to A, b and c.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  ``value`` = probabilities (diagonal Fock amplitudes)
+per second over the whole job, inputs resident on the device; ``e2e`` = the
+same through the public API with pinned host buffers (host<->device copies
+inside the timed region).  Under torchrun each rank runs its own 16
+circuits (weak scaling, no collective on the data path).
+``--impl reference`` times the CPU oracle (naive Algorithm 1) instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "gbs_m8_c6_batch16"
+METRIC = "Fock diag amplitudes/s (c128); fwd+VJP circuits/s vs plain, rel err<=1e-10"
+UNIT = "amplitudes/s"
+NCIRC = 16
+
+# DRAM traffic of the dominant kernel (diag_vjp_kernel) per launch, from one
+# ncu capture of this workload; valid only for the kernel source it was
+# measured on (sha256 prefix of csrc/walk_diag.cu).  None until captured.
+TRAFFIC = {"kernel_sha": None, "bytes_per_launch": None}
+
+
+def kernel_sha():
+    with open(os.path.join(ROOT, "paper_2303_08879_gb300", "csrc", "walk_diag.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+# --------------------------------------------------------------- counting
+def algorithmic_flops(cut):
+    """8 x sum over written amplitudes of their complex terms (b = 0 walk).
+
+    An amplitude written from the off-diagonal pivot e + 1_{2K} has one term
+    per read P - 1_l with P_l >= 1: l = 2K always, l = 2K+1 if e_K >= 1, and
+    l = 2m, 2m+1 for each m > K with e_m >= 1.  The pivot writes the diagonal
+    e + 1_K, offset_2 if e_K <= C_K - 3, and offset_1010/1001 at every m > K
+    with e_m <= C_m - 2.
+    """
+    M = len(cut)
+    total = 0
+    for K in range(M):
+        ext = [cut[K] - 1] + [cut[m] for m in range(K + 1, M)]
+        grids = np.meshgrid(*[np.arange(x) for x in ext], indexing="ij")
+        e = np.stack([g.ravel() for g in grids], axis=1)
+        eK = e[:, 0]
+        rest = e[:, 1:]
+        terms = 1 + (eK >= 1) + 2 * (rest >= 1).sum(axis=1)
+        outs = 1 + (eK <= cut[K] - 3) + 2 * (rest <= np.array(cut[K + 1:]) - 2).sum(axis=1)
+        total += int((terms * outs).sum())
+    return 8 * total
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1])); smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------- CPU oracle
+def oracle_sample(budget_s, first_circuit=0):
+    """Time the oracle's naive Algorithm 1 walk on a sub-box of one circuit's
+    probabilities sized to ~budget_s seconds (forward only)."""
+    import oracle
+    from oracle import triple as ot
+    from paper_2303_08879_gb300 import inputs
+    circ = inputs.workload(WORKLOAD, 1, start=first_circuit)[0]
+    A, b, c = ot.gaussian_to_triple(circ.V, circ.mean)
+    cut = list(circ.cutoffs)
+    rate_guess = 6.0e4                     # probabilities per second, one core
+    while np.prod(cut) > rate_guess * budget_s and min(cut) > 1:
+        j = max(i for i in range(len(cut)) if cut[i] == max(cut))
+        cut[j] -= 1
+    t0 = time.perf_counter()
+    w = oracle.Walk(A, b, c, tuple(cut))
+    P = w.all_probs()
+    dt = time.perf_counter() - t0
+    w.close()
+    return int(P.size), dt, tuple(cut)
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    budget = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    for i in range(args.warmup):
+        oracle_sample(budget, i % NCIRC)
+    n_tot, t_tot, cut = 0, 0.0, None
+    for i in range(args.steps):
+        n, dt, cut = oracle_sample(budget, (args.warmup + i) % NCIRC)
+        n_tot += n
+        t_tot += dt
+    value = n_tot / t_tot
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_tot / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+        "config": config_block(),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"naive Algorithm 1 walk (forward only), probabilities of the "
+                                   f"sub-box n < {list(cut)} of one circuit per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+def config_block():
+    return {"workload": f"{WORKLOAD}: {NCIRC} circuits, M=8 modes all PNR-detected, cutoff 6 "
+                        "(6^8 probabilities each), b=0, forward + VJP of sum_n w_n Re p_n",
+            "circuits_per_gpu": NCIRC, "modes": 8, "cutoff": 6,
+            "l2": "walk state per step 5.6 GB > 129 MB L2 (no flush needed)"}
+
+
+# ------------------------------------------------------------------- GPU
+def measure_fp64_peak(torch):
+    """FP64 roof: the larger of the library's FMA-chain probe and cuBLAS
+    DGEMM (8192^3, best of 5), both measured live (TFLOP/s)."""
+    from paper_2303_08879_gb300 import fockdiag as fd
+    fma = fd.fk_measure_fp64_fma_rate()
+    n = 8192
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        a @ a
+    torch.cuda.synchronize()
+    best = 0.0
+    for _ in range(5):
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(); a @ a; e1.record(); torch.cuda.synchronize()
+        best = max(best, 2.0 * n ** 3 / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+    del a
+    torch.cuda.empty_cache()
+    return max(fma, best), {"fma_probe": fma, "dgemm": best}
+
+
+def run_gpu(args):
+    if not args.no_cpu_baseline and int(os.environ.get("WORLD_SIZE", "1")) == 1:
+        import oracle                  # compile the oracle before any CUDA work
+        oracle.build()
+    import torch
+    import torch.distributed as dist
+    from paper_2303_08879_gb300 import fockdiag as fd
+    from paper_2303_08879_gb300 import inputs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    circs = inputs.workload(WORKLOAD, NCIRC, start=rank * NCIRC)
+    cut = circs[0].cutoffs
+    M = len(cut)
+    trip = [fd.fk_gaussian_to_triple(c.V, c.mean) for c in circs]
+    pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+    A_h = pin(np.stack([t[0] for t in trip]))
+    b_h = pin(np.stack([t[1] for t in trip]))
+    c_h = pin(np.array([t[2] for t in trip], np.complex128))
+    rng = np.random.default_rng(1000 + rank)
+    w_h = pin(rng.normal(size=(NCIRC,) + cut).astype(np.complex128))
+    dev = torch.device("cuda", local)
+    A, b, c, w = (x.to(dev) for x in (A_h, b_h, c_h, w_h))
+    flags = fd.FK_FLAG_B_ZERO
+    probs = torch.empty((NCIRC,) + cut, dtype=torch.complex128, device=dev)
+    gA, gb, gc = torch.empty_like(A), torch.empty_like(b), torch.empty_like(c)
+    ws = fd.workspace(fd.fk_workspace_size(M, cut, NCIRC, fd.FK_OP_DIAG_VJP, flags), dev)
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def step(tk=None):
+        if tk is not None:
+            tk[0].record(stream)
+        fd.fock_diag_probs_batched(A, b, c, cut, probs=probs, flags=flags, ws=ws)
+        if tk is not None:
+            tk[1].record(stream)
+        fd.fock_diag_probs_vjp_batched(A, b, c, cut, w, ws, flags=flags, out=(gA, gb, gc))
+        if tk is not None:
+            tk[2].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    fd.check_workspace(ws, where="warm-up")
+    barrier(); torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    marks = [[ev(), ev(), ev()] for _ in range(args.steps)]
+    t0, t1 = ev(), ev()
+    t0.record(stream)
+    for i in range(args.steps):
+        step(marks[i])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    barrier()
+    fd.check_workspace(ws, where="timed steps")
+    ms = t0.elapsed_time(t1) / args.steps
+    fwd_ms = statistics.mean(m[0].elapsed_time(m[1]) for m in marks)
+    vjp_ms = statistics.mean(m[1].elapsed_time(m[2]) for m in marks)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # end to end through the public API, pinned host buffers in and out
+    gA_h, gb_h, gc_h = (torch.empty_like(x, device="cpu").pin_memory() for x in (A_h, b_h, c_h))
+
+    def e2e_step():
+        A.copy_(A_h, non_blocking=True); b.copy_(b_h, non_blocking=True)
+        c.copy_(c_h, non_blocking=True); w.copy_(w_h, non_blocking=True)
+        step()
+        gA_h.copy_(gA, non_blocking=True); gb_h.copy_(gb, non_blocking=True)
+        gc_h.copy_(gc, non_blocking=True)
+
+    e2e_step(); torch.cuda.synchronize()
+    barrier()
+    u0, u1 = ev(), ev()
+    u0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    u1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = u0.elapsed_time(u1) / args.steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    fd.check_workspace(ws, where="e2e steps")
+
+    h2d = sum(x.numel() * x.element_size() for x in (A_h, b_h, c_h, w_h))
+    d2h = sum(x.numel() * x.element_size() for x in (gA_h, gb_h, gc_h))
+    amps = world * NCIRC * int(np.prod(cut))
+    out = None
+    if rank == 0:
+        flops_fwd = NCIRC * algorithmic_flops(cut)
+        flops_vjp = 2 * flops_fwd
+        peak, peaks = measure_fp64_peak(torch)
+        achieved = flops_vjp / (vjp_ms * 1e-3) / 1e12
+        sha = kernel_sha()
+        traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["kernel_sha"] == sha else None
+        out = {
+            "metric": METRIC, "value": amps / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+            "data": "synthetic", "config": config_block(),
+            "circuits_per_s": world * NCIRC / (ms * 1e-3),
+            "kernel_ms": {"diag_forward_kernel": fwd_ms, "diag_vjp_kernel": vjp_ms},
+            "e2e": {"value": amps / (e2e_ms * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": 2 * args.steps,
+            "roofline": {"bound": "alu", "kernel": "diag_vjp_kernel", "achieved": achieved,
+                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": traffic,
+                         "peak_source": "measured live: max of FP64 FMA-chain probe and cuBLAS DGEMM",
+                         "peaks_measured": peaks, "peak_nominal": 1.25,
+                         "forward": {"achieved": flops_fwd / (fwd_ms * 1e-3) / 1e12,
+                                     "frac": flops_fwd / (fwd_ms * 1e-3) / 1e12 / peak}},
+            "clocks": clocks,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            n, dt, scut = oracle_sample(20.0)
+            out["cpu_baseline"] = {
+                "value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"naive Algorithm 1 walk (forward only) of one circuit, probabilities "
+                          f"of the sub-box n < {list(scut)}, {dt:.1f} s"}
+    if world > 1:
+        dist.destroy_process_group()
+    if out is not None:
+        print(json.dumps(out))
+
+
+def main():
+    global NCIRC
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--circuits", type=int, default=NCIRC,
+                    help="circuits per GPU (default 16; smaller only for profiler captures)")
+    args = ap.parse_args()
+    NCIRC = args.circuits
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

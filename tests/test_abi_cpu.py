@@ -22,7 +22,7 @@ from paper_2303_08879_gb300 import build as pbuild
 from paper_2303_08879_gb300 import inputs
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "fockdiag.h")
+HEADERS = [os.path.join(ROOT, "include", h) for h in ("fockdiag.h", "fockdiag_probe.h")]
 
 
 @pytest.fixture(scope="module")
@@ -34,7 +34,7 @@ def fd():
 
 
 def declared_functions():
-    src = open(HEADER).read()
+    src = "".join(open(h).read() for h in HEADERS)
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     names = re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(\w+)\s*\(", src, flags=re.M)
     return sorted(set(n for n in names if n not in ("if", "while")))
