@@ -28,7 +28,7 @@ EXPORTS = [
     "fk_status_string", "fk_version", "fk_gaussian_to_triple", "fk_workspace_size",
     "fock_diag_probs", "fock_diag_probs_batched", "fock_diag_probs_vjp",
     "fock_diag_probs_vjp_batched", "fk_workspace_status", "fk_selftest_wait_timeout",
-    "fk_describe_diag_schedule",
+    "fk_describe_diag_schedule", "fk_measure_fp64_fma_rate",
 ]
 
 
@@ -72,6 +72,7 @@ def lib():
         L.fk_workspace_status.argtypes = [P, P, ctypes.POINTER(I)]
         L.fk_selftest_wait_timeout.argtypes = [P, Z, ctypes.c_ulonglong, P]
         L.fk_describe_diag_schedule.argtypes = [I, P, U, P, I]
+        L.fk_measure_fp64_fma_rate.argtypes = [P, Z, ctypes.POINTER(ctypes.c_double), P]
         for name in EXPORTS:           # fail here, not at first use, if one is missing
             getattr(L, name)
         _lib = L
@@ -217,3 +218,12 @@ def check_workspace(ws, stream=None, where="device"):
 def fk_selftest_wait_timeout(ws, timeout_ns, stream=None):
     st = lib().fk_selftest_wait_timeout(_ptr(ws), ws.numel(), int(timeout_ns), _stream(stream))
     _check(st, "fk_selftest_wait_timeout")
+
+
+def fk_measure_fp64_fma_rate(device=None, stream=None):
+    """FP64 FMA throughput of the device in TFLOP/s (roofline denominator)."""
+    ws = workspace(256, device)
+    v = ctypes.c_double(0.0)
+    st = lib().fk_measure_fp64_fma_rate(_ptr(ws), ws.numel(), ctypes.byref(v), _stream(stream))
+    _check(st, "fk_measure_fp64_fma_rate")
+    return float(v.value)
