@@ -37,10 +37,13 @@ METRIC = "Fock diag amplitudes/s (c128); fwd+VJP circuits/s vs plain, rel err<=1
 UNIT = "amplitudes/s"
 NCIRC = 16
 
-# DRAM traffic of the dominant kernel (diag_vjp_kernel) per launch, from one
-# ncu capture of this workload; valid only for the kernel source it was
-# measured on (sha256 prefix of csrc/walk_diag.cu).  None until captured.
-TRAFFIC = {"kernel_sha": None, "bytes_per_launch": None}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant
+# kernel (diag_vjp_kernel) per launch of this 16-circuit workload.  Captured
+# with ncu on a 2-circuit launch (9.990 GB read + 1.553 GB written) and scaled
+# by 8: circuits share no data, so traffic grows in proportion to them.  Valid
+# only for the kernel source it was measured on (sha256 prefix of
+# csrc/walk_diag.cu); reported as null once the kernel changes.
+TRAFFIC = {"kernel_sha": "bbee46fa125744b9", "bytes_per_launch": 8 * (9.990473e9 + 1.552535e9)}
 
 
 def kernel_sha():
