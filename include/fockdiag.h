@@ -143,6 +143,35 @@ int fock_diag_probs_vjp_batched(int batch, const fk_c128 *d_A, const fk_c128 *d_
                                 void *d_ws, size_t ws_bytes, void *stream);
 
 /*
+ * Allocation-free variant of fock_diag_probs_batched.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory themselves -- for example code running where the CUDA
+ * allocator is unavailable or forbidden (a plugin host that owns all device
+ * memory, a real-time loop that must not allocate, a binding without access
+ * to cudaMalloc).  The walk's scratch then lives in one device array of
+ * FK_STATIC_WORKSPACE_BYTES that the library reserves on every GPU it is
+ * loaded on and keeps until the process exits.  The caller still passes the
+ * inputs and the probabilities output (device pointers, as above).
+ *   - Calls whose workspace would exceed FK_STATIC_WORKSPACE_BYTES return
+ *     FK_EWORKSPACE (fk_workspace_size with FK_OP_DIAG gives the need).
+ *   - The first call on a GPU looks up the array's device address (with that
+ *     GPU current); make that first call before any stream capture.
+ *   - Every call on a GPU shares the one array: calls that overlap on the
+ *     GPU (different streams or threads without ordering) race and corrupt
+ *     each other.  Calls are otherwise stream-ordered like the others.
+ *   - The call clears what must start at zero (the status word and barrier
+ *     counters); the array keeps the previous call's amplitudes otherwise.
+ *   - host_status may be NULL.  If not, the call waits for the walk to
+ *     finish (synchronising `stream`) and stores the device-side status
+ *     there (FK_OK, FK_ETIMEOUT, FK_EBZERO).
+ * No cudaMalloc, cudaFree or other allocating routine is called.
+ */
+#define FK_STATIC_WORKSPACE_BYTES (16u << 20)   /* 16 MiB per GPU */
+int fock_diag_probs_static(int batch, const fk_c128 *d_A, const fk_c128 *d_b, const fk_c128 *d_c,
+                           int M, const int *host_cutoffs, fk_c128 *d_probs, unsigned flags,
+                           void *stream, int *host_status);
+
+/*
  * Reads the device-side status word of a workspace after the calls queued
  * on `stream` (synchronises the stream).  *status = FK_OK or the first error
  * a kernel recorded; the word is cleared by the next compute call.

@@ -1,0 +1,69 @@
+// static_ws.cu -- fock_diag_probs_static: the all-detected forward walk with
+// its scratch in a fixed device array owned by the library, for callers that
+// cannot allocate device memory themselves.
+//
+// The array below is device memory reserved when the library is loaded onto a
+// GPU and kept until the process exits.  Host code must not use its name as a
+// pointer: on the host that name only stands in for the device symbol.  The
+// device address is looked up once per GPU with cudaGetSymbolAddress (with
+// that GPU current) and cached; the walk kernel then receives that address
+// exactly as it would receive a caller-supplied workspace.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "fk_internal.h"
+#include "../../include/fockdiag.h"
+
+namespace {
+
+constexpr size_t kStaticBytes = (size_t)FK_STATIC_WORKSPACE_BYTES;
+
+static __device__ __align__(256) unsigned char g_static_ws[kStaticBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void *g_addr[kMaxDevices] = {nullptr};
+
+// Device address of g_static_ws on the current GPU (looked up on first use).
+int static_workspace(void **out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FK_ECUDA;
+    if (dev < 0 || dev >= kMaxDevices) return FK_EUNSUPPORTED;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_addr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_static_ws) != cudaSuccess || !p) return FK_ECUDA;
+        g_addr[dev] = p;
+    }
+    *out = g_addr[dev];
+    return FK_OK;
+}
+
+}  // namespace
+
+extern "C" int fock_diag_probs_static(int batch, const fk_c128 *A, const fk_c128 *b,
+                                      const fk_c128 *c, int M, const int *cutoffs,
+                                      fk_c128 *probs, unsigned flags, void *stream,
+                                      int *host_status)
+{
+    using namespace fk;
+    if (batch < 1 || !A || !b || !c || !probs) return FK_EINVAL;
+    DiagShape sh;
+    int rc = build_diag_shape(M, cutoffs, !(flags & FK_FLAG_B_ZERO), &sh);
+    if (rc) return rc;
+    DiagLayout lay;
+    rc = diag_layout(sh, batch, false, &lay);
+    if (rc) return rc;
+    if (lay.total > kStaticBytes) return FK_EWORKSPACE;
+    void *ws = nullptr;
+    rc = static_workspace(&ws);
+    if (rc) return rc;
+    // The launcher clears the control block (barrier counters, status word)
+    // with cudaMemsetAsync before the kernel; the rest of the array needs no
+    // initial value (every amplitude is written before it is read).
+    rc = launch_diag_forward(sh, batch, flags, A, b, c, probs, ws, lay, stream);
+    if (rc || !host_status) return rc;
+    return read_status(ws, stream, host_status);
+}

@@ -28,7 +28,7 @@ EXPORTS = [
     "fk_status_string", "fk_version", "fk_gaussian_to_triple", "fk_workspace_size",
     "fock_diag_probs", "fock_diag_probs_batched", "fock_diag_probs_vjp",
     "fock_diag_probs_vjp_batched", "fk_workspace_status", "fk_selftest_wait_timeout",
-    "fk_describe_diag_schedule", "fk_measure_fp64_fma_rate",
+    "fk_describe_diag_schedule", "fk_measure_fp64_fma_rate", "fock_diag_probs_static",
 ]
 
 
@@ -73,6 +73,7 @@ def lib():
         L.fk_selftest_wait_timeout.argtypes = [P, Z, ctypes.c_ulonglong, P]
         L.fk_describe_diag_schedule.argtypes = [I, P, U, P, I]
         L.fk_measure_fp64_fma_rate.argtypes = [P, Z, ctypes.POINTER(ctypes.c_double), P]
+        L.fock_diag_probs_static.argtypes = [I, P, P, P, I, P, P, U, P, ctypes.POINTER(I)]
         for name in EXPORTS:           # fail here, not at first use, if one is missing
             getattr(L, name)
         _lib = L
