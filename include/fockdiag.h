@@ -101,8 +101,9 @@ int fk_gaussian_to_triple(int M, const double *host_V, const double *host_mean,
                           fk_c128 *host_A, fk_c128 *host_b, fk_c128 *host_c);
 
 /*
- * Workspace bytes for `op` on `batch` circuits of one shape (M, cutoffs,
- * detected_mask; mask may be NULL = all detected, ignored by the DIAG ops).
+ * Workspace bytes for `op` on `batch` circuits of one shape (M cutoffs,
+ * detected_mask; the mask is ignored by the DIAG ops and required by the COND
+ * ops; circuits with differing cutoffs use fk_conditional_workspace_size).
  * Depends on the current CUDA device (its SM count sizes per-block partial
  * sums).  Writes *bytes; no device work.
  */
@@ -141,6 +142,49 @@ int fock_diag_probs_vjp_batched(int batch, const fk_c128 *d_A, const fk_c128 *d_
                                 const fk_c128 *d_grad_probs, fk_c128 *d_grad_A,
                                 fk_c128 *d_grad_b, fk_c128 *d_grad_c, unsigned flags,
                                 void *d_ws, size_t ws_bytes, void *stream);
+
+/*
+ * Conditional states (Algorithm 2, Sec. 3.2): for every detection pattern n
+ * of the detected modes (host_mask[j] != 0), the unnormalised density matrix
+ * of the undetected modes, rho(n) = the diagonal block G_{..n_j n_j..} of the
+ * state (Sec. 3.2: "each detection outcome corresponds with one such block").
+ * Undetected modes keep both Fock indices; detected modes are walked only
+ * along the diagonal, for O(M^2 prod_U C^2 prod_D C) work.
+ *   host_cutoffs [batch][M]   each circuit's cutoffs (they may differ)
+ *   host_mask [M]             1 = detected, shared by the batch
+ *   d_rho                     output, circuits packed back to back; circuit i
+ *                             starts at element offset rho_offsets[i] and holds
+ *                             [pattern][ket][bra]: patterns row-major over the
+ *                             detected modes, ket and bra row-major over the
+ *                             undetected modes (mode order)
+ * At most 1024 circuits per call, FK_MAX_MODES detected and 4 undetected
+ * modes with cutoff > 1.  The walk stays in the workspace for the VJP.
+ */
+int fk_conditional_workspace_size(int batch, int M, const int *host_cutoffs,
+                                  const unsigned char *host_mask, int op, unsigned flags,
+                                  size_t *bytes, int64_t *rho_offsets /* [batch + 1] or NULL */);
+int fock_conditional_dm(const fk_c128 *d_A, const fk_c128 *d_b, const fk_c128 *d_c, int M,
+                        const int *host_cutoffs, const unsigned char *host_mask, fk_c128 *d_rho,
+                        void *d_ws, size_t ws_bytes, void *stream);
+int fock_conditional_dm_batched(int batch, const fk_c128 *d_A, const fk_c128 *d_b,
+                                const fk_c128 *d_c, int M, const int *host_cutoffs,
+                                const unsigned char *host_mask, fk_c128 *d_rho, unsigned flags,
+                                void *d_ws, size_t ws_bytes, void *stream);
+
+/*
+ * Vector-Jacobian product of fock_conditional_dm (Sec. 2.5 by a reverse
+ * walk); d_grad_rho has the layout of d_rho.  Unless FK_FLAG_RECOMPUTE is
+ * set, d_ws must hold the state of the forward call with the same inputs.
+ */
+int fock_conditional_dm_vjp(const fk_c128 *d_A, const fk_c128 *d_b, const fk_c128 *d_c, int M,
+                            const int *host_cutoffs, const unsigned char *host_mask,
+                            const fk_c128 *d_grad_rho, fk_c128 *d_grad_A, fk_c128 *d_grad_b,
+                            fk_c128 *d_grad_c, void *d_ws, size_t ws_bytes, void *stream);
+int fock_conditional_dm_vjp_batched(int batch, const fk_c128 *d_A, const fk_c128 *d_b,
+                                    const fk_c128 *d_c, int M, const int *host_cutoffs,
+                                    const unsigned char *host_mask, const fk_c128 *d_grad_rho,
+                                    fk_c128 *d_grad_A, fk_c128 *d_grad_b, fk_c128 *d_grad_c,
+                                    unsigned flags, void *d_ws, size_t ws_bytes, void *stream);
 
 /*
  * Allocation-free variant of fock_diag_probs_batched.  The paper has no

@@ -301,7 +301,102 @@ int fk_workspace_size(int M, const int *cutoffs, const unsigned char *mask, int 
         *bytes = lay.total;
         return FK_OK;
     }
+    if (op == FK_OP_COND || op == FK_OP_COND_VJP) {
+        if (!cutoffs || !mask) return FK_EINVAL;
+        std::vector<int> cut((size_t)batch * M);
+        for (int i = 0; i < batch; ++i)
+            for (int j = 0; j < M; ++j) cut[(size_t)i * M + j] = cutoffs[j];
+        return fk_conditional_workspace_size(batch, M, cut.data(), mask, op, flags, bytes, nullptr);
+    }
     return FK_EUNSUPPORTED;
+}
+
+int fk_conditional_workspace_size(int batch, int M, const int *cutoffs, const unsigned char *mask,
+                                  int op, unsigned flags, size_t *bytes, int64_t *rho_offsets)
+{
+    (void)flags;
+    if (!bytes || (op != FK_OP_COND && op != FK_OP_COND_VJP)) return FK_EINVAL;
+    const CondPlan *plan = nullptr;
+    int rc = get_cond_plan(batch, M, cutoffs, mask, &plan);
+    if (rc) return rc;
+    CondLayout lay;
+    if (op == FK_OP_COND_VJP) {
+        rc = cond_layout(*plan, true, &lay);
+    } else {
+        rc = cond_layout(*plan, false, &lay);
+    }
+    if (rc) return rc;
+    *bytes = lay.total;
+    if (rho_offsets) {
+        int64_t off = 0;
+        for (int i = 0; i < batch; ++i) {
+            rho_offsets[i] = off;
+            int64_t np = 1, nu = 1;
+            for (int j = 0; j < M; ++j) {
+                const int C = cutoffs[(size_t)i * M + j];
+                if (mask[j]) np *= C; else nu *= C;
+            }
+            off += np * nu * nu;
+        }
+        rho_offsets[batch] = off;
+    }
+    return FK_OK;
+}
+
+int fock_conditional_dm_batched(int batch, const fk_c128 *A, const fk_c128 *b, const fk_c128 *c,
+                                int M, const int *cutoffs, const unsigned char *mask, fk_c128 *rho,
+                                unsigned flags, void *ws, size_t ws_bytes, void *stream)
+{
+    if (batch < 1 || !A || !b || !c || !rho || !ws || !cutoffs || !mask) return FK_EINVAL;
+    const CondPlan *plan = nullptr;
+    int rc = get_cond_plan(batch, M, cutoffs, mask, &plan);
+    if (rc) return rc;
+    CondLayout lay;
+    rc = cond_layout(*plan, false, &lay);
+    if (rc) return rc;
+    if (ws_bytes < lay.total || !aligned(ws)) return FK_EWORKSPACE;
+    return launch_cond_forward(*plan, flags, A, b, c, rho, ws, lay, stream);
+}
+
+int fock_conditional_dm(const fk_c128 *A, const fk_c128 *b, const fk_c128 *c, int M,
+                        const int *cutoffs, const unsigned char *mask, fk_c128 *rho, void *ws,
+                        size_t ws_bytes, void *stream)
+{
+    return fock_conditional_dm_batched(1, A, b, c, M, cutoffs, mask, rho, 0u, ws, ws_bytes, stream);
+}
+
+int fock_conditional_dm_vjp_batched(int batch, const fk_c128 *A, const fk_c128 *b,
+                                    const fk_c128 *c, int M, const int *cutoffs,
+                                    const unsigned char *mask, const fk_c128 *grho, fk_c128 *gA,
+                                    fk_c128 *gb, fk_c128 *gc, unsigned flags, void *ws,
+                                    size_t ws_bytes, void *stream)
+{
+    if (batch < 1 || !A || !b || !c || !grho || !gA || !gb || !gc || !ws || !cutoffs || !mask)
+        return FK_EINVAL;
+    const CondPlan *plan = nullptr;
+    int rc = get_cond_plan(batch, M, cutoffs, mask, &plan);
+    if (rc) return rc;
+    CondLayout lay;
+    rc = cond_layout(*plan, true, &lay);
+    if (rc) return rc;
+    if (ws_bytes < lay.total || !aligned(ws)) return FK_EWORKSPACE;
+    if (flags & FK_FLAG_RECOMPUTE) {
+        // the forward's output lands in the adjoint region, cleared next
+        void *tmp = (char *)ws + lay.Fbar;
+        if ((size_t)plan->rho_total * 16 > lay.partA - lay.Fbar) return FK_EWORKSPACE;
+        rc = launch_cond_forward(*plan, flags, A, b, c, tmp, ws, lay, stream);
+        if (rc) return rc;
+    }
+    return launch_cond_vjp(*plan, flags, A, b, c, grho, gA, gb, gc, ws, lay, stream);
+}
+
+int fock_conditional_dm_vjp(const fk_c128 *A, const fk_c128 *b, const fk_c128 *c, int M,
+                            const int *cutoffs, const unsigned char *mask, const fk_c128 *grho,
+                            fk_c128 *gA, fk_c128 *gb, fk_c128 *gc, void *ws, size_t ws_bytes,
+                            void *stream)
+{
+    return fock_conditional_dm_vjp_batched(1, A, b, c, M, cutoffs, mask, grho, gA, gb, gc, 0u, ws,
+                                           ws_bytes, stream);
 }
 
 int fock_diag_probs_batched(int batch, const fk_c128 *A, const fk_c128 *b, const fk_c128 *c,

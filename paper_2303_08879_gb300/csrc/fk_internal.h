@@ -34,6 +34,60 @@ struct DiagLayout {
 };
 int diag_layout(const DiagShape &sh, int batch, bool vjp, DiagLayout *lay);
 
+// ------------------------------------------------------- conditional walk
+// Algorithm 2 (Sec. 3.2): undetected modes keep their full (ket, bra) index
+// pairs, the detected modes follow the Algorithm-1 structure (with the
+// offset_1 types, which the undetected reads need even when b = 0).  The
+// amplitude at (u, y) -- u a point of the undetected sub-lattice, y a
+// position of the detected structure -- is stored at F[y * U2 + u].
+constexpr int FK_MAXU = 4;            // undetected modes with cutoff > 1
+constexpr int kCondTPB = 128;
+
+struct CondCirc {
+    DiagShape dsh;                    // detected sub-problem (kept modes, offset_1 boxes)
+    int nU;                           // undetected modes with C > 1
+    int CU[FK_MAXU];                  // their cutoffs
+    int U2;                           // prod CU^2 (u-block size)
+    int ustride[2 * FK_MAXU];         // u-block strides of the undetected lattice indices
+    int Lu;                           // sum 2 (CU - 1): levels of the undetected sub-lattice
+    int nchunk;                       // ceil(U2 / kCondTPB)
+    int NUo;                          // prod CU: ket (= bra) extent of the output
+    int Dred;                         // 2 (dsh.M + nU): detected indices first, then undetected
+    int red_to_orig[2 * FK_MAXM + 2 * FK_MAXU];
+    int W_off;                        // this circuit's level table in the plan (unsigned words)
+    int Wn;                           // its row length (dsh.L + 2)
+    int64_t off_F;                    // amplitudes of this circuit in F (elements)
+    int64_t off_rho;                  // its block of the output (elements)
+    int64_t off_scratch;              // its VJP scratch (elements): dsh.n_ap * U2
+    int64_t n_patterns;               // detected patterns (= dsh.n_diag)
+};
+
+struct CondPlan {
+    int B, M, Md;                     // circuits, caller's modes, detected modes in the mask
+    int Dmax;                         // 2 M
+    int Lmax;                         // max detected levels over circuits
+    int64_t F_total, scratch_total, rho_total;
+    size_t plan_bytes;                // CondCirc[B] followed by the level tables
+    const void *host_plan;            // pinned host copy (kept for the life of the process)
+};
+
+struct CondLayout {
+    size_t ctl, plan, Ar, br, F, Fbar, scratch, partA, partb, total;
+    int grid_vjp;
+};
+
+// Returns the cached plan of (batch, M, cutoffs[batch][M], mask); the pinned
+// host copy stays valid for the life of the process (graph replays copy it).
+int get_cond_plan(int batch, int M, const int *cutoffs, const unsigned char *mask,
+                  const CondPlan **plan);
+int cond_layout(const CondPlan &plan, bool vjp, CondLayout *lay);
+int cond_grid_size(const CondPlan &plan, bool vjp, int *grid);
+int launch_cond_forward(const CondPlan &plan, unsigned flags, const void *A, const void *b,
+                        const void *c, void *rho, void *ws, const CondLayout &lay, void *stream);
+int launch_cond_vjp(const CondPlan &plan, unsigned flags, const void *A, const void *b,
+                    const void *c, const void *grho, void *gA, void *gb, void *gc, void *ws,
+                    const CondLayout &lay, void *stream);
+
 // Launchers (walk_diag.cu).  All pointers are device pointers.
 int diag_grid_size(const DiagShape &sh, bool vjp, int *grid);
 int launch_diag_forward(const DiagShape &sh, int batch, unsigned flags, const void *A,

@@ -5,7 +5,7 @@
 // Arithmetic.  The kernels carry F_k = G_k / sqrt(k!) instead of G_k.  Eq.
 // (recrel) then reads
 //     F_{P+1_w} = (b_w F_P + sum_l A_wl F_{P-1_l}) / (P_w + 1),
-// the rescaled matrix-vector form the paper mentions in Sec. 3.3: every term
+// the rescaled matrix-vector form the paper mentions in Sec. 4: every term
 // of a sum carries the same factor sqrt(P!) relative to the original form,
 // so no read needs its own sqrt weight and each write is one complex
 // matrix-vector row times a reciprocal from a table.  Probabilities are
@@ -26,6 +26,7 @@
 #include <mutex>
 
 #include "fk_internal.h"
+#include "walk_common.cuh"
 #include "../../include/fockdiag.h"
 
 namespace fk {
@@ -35,7 +36,7 @@ namespace {
 constexpr int TPB = 128;          // pivots per tile = threads per block
 constexpr int RS = TPB + 1;       // padded row stride of per-thread smem columns
 constexpr int CH = 8;             // output rows per register chunk
-constexpr int TABN = FK_MAX_CUTOFF + 2;
+constexpr int TABN = kTabN;
 
 struct DiagArgs {
     DiagShape sh;
@@ -51,107 +52,6 @@ struct DiagArgs {
     double2 *gA, *gb, *gc;
     unsigned long long timeout_ns;
 };
-
-// ---------------------------------------------------------------- helpers --
-struct Dig {
-    uint64_t lo = 0, hi = 0;
-    __device__ __forceinline__ int operator()(int i) const
-    {
-        const uint64_t w = i < 8 ? lo : hi;
-        return (int)((w >> (8 * (i & 7))) & 0xffu);
-    }
-    __device__ __forceinline__ void set(int i, int v)
-    {
-        if (i < 8) lo |= (uint64_t)v << (8 * i);
-        else hi |= (uint64_t)v << (8 * (i - 8));
-    }
-};
-
-__device__ __forceinline__ double2 cfma(double2 a, double2 x, double2 acc)
-{   // acc + a * x
-    acc.x = fma(a.x, x.x, acc.x);
-    acc.x = fma(-a.y, x.y, acc.x);
-    acc.y = fma(a.x, x.y, acc.y);
-    acc.y = fma(a.y, x.x, acc.y);
-    return acc;
-}
-
-__device__ __forceinline__ double2 cfma_conj(double2 a, double2 x, double2 acc)
-{   // acc + conj(a) * x
-    acc.x = fma(a.x, x.x, acc.x);
-    acc.x = fma(a.y, x.y, acc.x);
-    acc.y = fma(a.x, x.y, acc.y);
-    acc.y = fma(-a.y, x.x, acc.y);
-    return acc;
-}
-
-__device__ __forceinline__ double2 cmul(double2 a, double2 x)
-{
-    return make_double2(a.x * x.x - a.y * x.y, a.x * x.y + a.y * x.x);
-}
-
-__device__ __forceinline__ double2 rscale(double2 a, double s)
-{
-    return make_double2(a.x * s, a.y * s);
-}
-
-__device__ __forceinline__ double2 cadd(double2 a, double2 b)
-{
-    return make_double2(a.x + b.x, a.y + b.y);
-}
-
-__device__ __forceinline__ unsigned long long gtimer()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
-{
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ int ld_status(const Control *ctl)
-{
-    return *(volatile const int *)&ctl->status;
-}
-
-// Grid-wide barrier of a cooperative launch.  Every wait is bounded by
-// `timeout_ns`; on expiry the status word becomes FK_ETIMEOUT and all blocks
-// leave.  Returns false once any error is recorded.
-__device__ bool grid_sync(Control *ctl, unsigned nblocks, unsigned long long timeout_ns)
-{
-    __shared__ int s_ok;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned gen = ld_acquire(&ctl->bar_gen);
-        __threadfence();
-        const unsigned prev = atomicAdd(&ctl->bar_count, 1u);
-        if (prev == nblocks - 1) {
-            atomicExch(&ctl->bar_count, 0u);
-            __threadfence();
-            atomicAdd(&ctl->bar_gen, 1u);
-        } else {
-            const unsigned long long t0 = gtimer();
-            while (ld_acquire(&ctl->bar_gen) == gen) {
-                if (ld_status(ctl) != 0) break;
-                if (gtimer() - t0 > timeout_ns) {
-                    atomicCAS(&ctl->status, 0, (int)FK_ETIMEOUT);
-                    break;
-                }
-                __nanosleep(64);
-            }
-        }
-        __threadfence();
-        s_ok = (ld_status(ctl) == 0);
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
 
 // ------------------------------------------------------------ shared memory
 struct Smem {
@@ -211,61 +111,26 @@ __device__ Smem carve_smem(const DiagShape &sh, bool vjp)
     return s;
 }
 
-// Level-count table, reciprocal and factorial tables (every block builds its
-// own copy; they depend on the cutoffs only).
+// Level-count, reciprocal and factorial tables (every block builds its own
+// copy; they depend on the cutoffs only).
 __device__ void build_tables(const DiagShape &sh, Smem &s)
 {
-    const int M = sh.M, Wn = s.Wn;
-    for (int t = threadIdx.x; t < Wn; t += blockDim.x) s.W[M * Wn + t] = (t == 0) ? 1u : 0u;
-    for (int v = threadIdx.x; v < TABN; v += blockDim.x) {
-        s.inv[v] = v > 0 ? 1.0 / (double)v : 0.0;
-        double f = 1.0;
-        for (int u = 2; u <= v; ++u) f *= (double)u;
-        s.fact[v] = f;
-    }
-    __syncthreads();
-    for (int i = M - 1; i >= 0; --i) {
-        for (int t = threadIdx.x; t < Wn; t += blockDim.x) {
-            unsigned acc = 0;
-            for (int v = 0; v < sh.C[i] && v <= t; ++v) acc += s.W[(i + 1) * Wn + t - v];
-            s.W[i * Wn + t] = acc;
-        }
-        __syncthreads();
-    }
+    build_scalar_tables(s.inv, s.fact);
+    build_level_table(s.W, s.Wn, sh.C, sh.M);
 }
 
-__device__ __forceinline__ unsigned Wat(const Smem &s, int i, int t)
-{
-    return (t < 0 || t >= s.Wn) ? 0u : s.W[i * s.Wn + t];
-}
+__device__ __forceinline__ LevelTab ltab(const Smem &s) { return LevelTab{s.W, s.Wn}; }
 
-// Number of digit vectors over modes k0..M-1 with digit k0 in [0, C_k0 - dk0)
-// and the rest in [0, C_i), summing to s.
 __device__ __forceinline__ unsigned level_count(const DiagShape &sh, const Smem &sm, int k0,
                                                 int dk0, int s)
 {
-    unsigned n = 0;
-    for (int v = 0; v < sh.C[k0] - dk0; ++v) n += Wat(sm, k0 + 1, s - v);
-    return n;
+    return level_count(sh.C, ltab(sm), k0, dk0, s);
 }
 
-// The rank-th such vector in lexicographic order (mode k0 slowest).
-__device__ Dig unrank(const DiagShape &sh, const Smem &sm, int k0, int dk0, int s, unsigned rank)
+__device__ __forceinline__ Dig unrank(const DiagShape &sh, const Smem &sm, int k0, int dk0, int s,
+                                      unsigned rank)
 {
-    Dig d;
-    int rem = s;
-    for (int i = k0; i < sh.M; ++i) {
-        const int ext = sh.C[i] - (i == k0 ? dk0 : 0);
-        int v = 0;
-        for (; v < ext - 1; ++v) {
-            const unsigned c = Wat(sm, i + 1, rem - v);
-            if (rank < c) break;
-            rank -= c;
-        }
-        d.set(i, v);
-        rem -= v;
-    }
-    return d;
+    return unrank(sh.C, sh.M, ltab(sm), k0, dk0, s, rank);
 }
 
 __device__ __forceinline__ int64_t diag_index(const DiagShape &sh, const Dig &d, int k0)
@@ -796,7 +661,7 @@ __device__ void diag_reverse_tile(const DiagArgs &a, Smem &s, const TileId &tl, 
 }
 
 // ------------------------------------------------------------------ kernels
-__global__ void __launch_bounds__(TPB) diag_forward_kernel(DiagArgs a)
+__global__ void __launch_bounds__(TPB) diag_forward_kernel(const __grid_constant__ DiagArgs a)
 {
     const DiagShape &sh = a.sh;
     Smem s = carve_smem(sh, false);
@@ -827,7 +692,7 @@ __global__ void __launch_bounds__(TPB) diag_forward_kernel(DiagArgs a)
     }
 }
 
-__global__ void __launch_bounds__(TPB) diag_vjp_kernel(DiagArgs a)
+__global__ void __launch_bounds__(TPB) diag_vjp_kernel(const __grid_constant__ DiagArgs a)
 {
     const DiagShape &sh = a.sh;
     Smem s = carve_smem(sh, true);

@@ -29,6 +29,8 @@ EXPORTS = [
     "fock_diag_probs", "fock_diag_probs_batched", "fock_diag_probs_vjp",
     "fock_diag_probs_vjp_batched", "fk_workspace_status", "fk_selftest_wait_timeout",
     "fk_describe_diag_schedule", "fk_measure_fp64_fma_rate", "fock_diag_probs_static",
+    "fk_conditional_workspace_size", "fock_conditional_dm", "fock_conditional_dm_batched",
+    "fock_conditional_dm_vjp", "fock_conditional_dm_vjp_batched",
 ]
 
 
@@ -74,6 +76,11 @@ def lib():
         L.fk_describe_diag_schedule.argtypes = [I, P, U, P, I]
         L.fk_measure_fp64_fma_rate.argtypes = [P, Z, ctypes.POINTER(ctypes.c_double), P]
         L.fock_diag_probs_static.argtypes = [I, P, P, P, I, P, P, U, P, ctypes.POINTER(I)]
+        L.fk_conditional_workspace_size.argtypes = [I, I, P, P, I, U, ctypes.POINTER(Z), P]
+        L.fock_conditional_dm.argtypes = [P, P, P, I, P, P, P, P, Z, P]
+        L.fock_conditional_dm_batched.argtypes = [I, P, P, P, I, P, P, P, U, P, Z, P]
+        L.fock_conditional_dm_vjp.argtypes = [P, P, P, I, P, P, P, P, P, P, P, Z, P]
+        L.fock_conditional_dm_vjp_batched.argtypes = [I, P, P, P, I, P, P, P, P, P, P, U, P, Z, P]
         for name in EXPORTS:           # fail here, not at first use, if one is missing
             getattr(L, name)
         _lib = L
@@ -228,3 +235,78 @@ def fk_measure_fp64_fma_rate(device=None, stream=None):
     st = lib().fk_measure_fp64_fma_rate(_ptr(ws), ws.numel(), ctypes.byref(v), _stream(stream))
     _check(st, "fk_measure_fp64_fma_rate")
     return float(v.value)
+
+
+# ------------------------------------------------------ conditional states
+def _cond_args(cutoffs, mask):
+    cut = np.ascontiguousarray(np.asarray(cutoffs, dtype=np.int32))
+    if cut.ndim == 1:
+        cut = cut[None, :]
+    B, M = cut.shape
+    msk = (ctypes.c_ubyte * M)(*[1 if v else 0 for v in mask])
+    return cut, B, M, msk
+
+
+def fk_conditional_workspace_size(cutoffs, mask, op=FK_OP_COND_VJP, flags=0):
+    """(workspace bytes, rho offsets [B + 1]) for circuits cutoffs[B][M]."""
+    cut, B, M, msk = _cond_args(cutoffs, mask)
+    n = ctypes.c_size_t(0)
+    offs = np.zeros(B + 1, np.int64)
+    st = lib().fk_conditional_workspace_size(B, M, cut.ctypes.data, msk, op, flags,
+                                             ctypes.byref(n), offs.ctypes.data)
+    _check(st, "fk_conditional_workspace_size")
+    return int(n.value), offs
+
+
+def conditional_blocks(rho, cutoffs, mask):
+    """Split the packed output into per-circuit [patterns, ket, bra] views."""
+    cut, B, M, _ = _cond_args(cutoffs, mask)
+    out, off = [], 0
+    for i in range(B):
+        npat = int(np.prod([cut[i, j] for j in range(M) if mask[j]]))
+        nu = int(np.prod([cut[i, j] for j in range(M) if not mask[j]]))
+        out.append(rho[off:off + npat * nu * nu].view(npat, nu, nu))
+        off += npat * nu * nu
+    return out
+
+
+def fock_conditional_dm_batched(A, b, c, cutoffs, mask, rho=None, flags=0, ws=None, stream=None,
+                                for_vjp=True):
+    """Conditional states (Algorithm 2) of a batch; cutoffs[B][M] may differ
+    per circuit.  Returns (rho packed, offsets, ws)."""
+    for n, t in (("A", A), ("b", b), ("c", c)):
+        _need_cuda_c128(n, t)
+    cut, B, M, msk = _cond_args(cutoffs, mask)
+    if A.shape != (B, 2 * M, 2 * M) or b.shape != (B, 2 * M) or c.shape != (B,):
+        raise ValueError("shapes must be A[B,2M,2M], b[B,2M], c[B]")
+    need, offs = fk_conditional_workspace_size(cut, mask, FK_OP_COND_VJP if for_vjp else FK_OP_COND,
+                                               flags)
+    if rho is None:
+        rho = torch.empty(int(offs[-1]), dtype=torch.complex128, device=A.device)
+    _need_cuda_c128("rho", rho)
+    if ws is None:
+        ws = workspace(need, A.device)
+    st = lib().fock_conditional_dm_batched(B, _ptr(A), _ptr(b), _ptr(c), M, cut.ctypes.data, msk,
+                                           _ptr(rho), flags, _ptr(ws), ws.numel(), _stream(stream))
+    _check(st, "fock_conditional_dm_batched")
+    return rho, offs, ws
+
+
+def fock_conditional_dm_vjp_batched(A, b, c, cutoffs, mask, grad_rho, ws, flags=0, stream=None,
+                                    out=None):
+    for n, t in (("A", A), ("b", b), ("c", c), ("grad_rho", grad_rho)):
+        _need_cuda_c128(n, t)
+    cut, B, M, msk = _cond_args(cutoffs, mask)
+    if out is None:
+        gA = torch.empty_like(A); gb = torch.empty_like(b); gc = torch.empty_like(c)
+    else:
+        gA, gb, gc = out
+    need, _ = fk_conditional_workspace_size(cut, mask, FK_OP_COND_VJP, flags)
+    if ws is None:
+        ws = workspace(need, A.device)
+        flags |= FK_FLAG_RECOMPUTE
+    st = lib().fock_conditional_dm_vjp_batched(B, _ptr(A), _ptr(b), _ptr(c), M, cut.ctypes.data,
+                                               msk, _ptr(grad_rho), _ptr(gA), _ptr(gb), _ptr(gc),
+                                               flags, _ptr(ws), ws.numel(), _stream(stream))
+    _check(st, "fock_conditional_dm_vjp_batched")
+    return gA, gb, gc

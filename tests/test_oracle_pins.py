@@ -184,7 +184,7 @@ def test_alg2_matches_full_density_matrix(cut, det):
     w = oracle.Walk(A, b, 0.6, cut, det)
     R2 = w.all_conditional()
     assert rel(R2, R1) < 1e-12
-    # Sec. 3.3: the block walk stores prod_U C^2 x |Algorithm-1 closure over D|
+    # Sec. 4 (complexity of Algorithm 2): the block walk stores prod_U C^2 x |Algorithm-1 closure over D|
     dcut = tuple(c for c, d in zip(cut, det) if d)
     ucut = tuple(c for c, d in zip(cut, det) if not d)
     A1, b1 = inputs.random_symmetric(2 * len(dcut), rng)
