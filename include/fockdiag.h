@@ -101,6 +101,26 @@ int fk_gaussian_to_triple(int M, const double *host_V, const double *host_mean,
                           fk_c128 *host_A, fk_c128 *host_b, fk_c128 *host_c);
 
 /*
+ * Parameterised noisy circuit -> Bargmann triple and its Jacobian (host).
+ * M squeezed vacua (squeezing r_j of the x quadrature), real displacements
+ * x_j, a triangle of M(M-1)/2 beam splitters on neighbouring modes (k, k+1)
+ * for k = 0..M-2-i, i = 0..M-2, each [[cos t, -e^{-i p} sin t],
+ * [e^{i p} sin t, cos t]], then output phases e^{i psi_j}, then pure loss
+ * eta on every mode.  host_theta has M^2 + 2M entries
+ *   [r_0..r_{M-1}, x_0..x_{M-1}, (t_1, p_1)..(t_nbs, p_nbs), psi_0..psi_{M-1}].
+ * Outputs (A, b, c) as fk_gaussian_to_triple (Sec. 2.1 eqs. A_rho, b_rho;
+ * Sec. 2.2 vacuum amplitude) and, if the pointers are not NULL, the
+ * derivatives with respect to every parameter: dA [P][D][D], db [P][D],
+ * dc [P] (P = M^2 + 2M), from A = P_M (I - sigma_+^{-1}):
+ * dA = P_M sigma_+^{-1} dsigma sigma_+^{-1}, and so on.  The paper leaves the
+ * circuit ansatz open (Sec. 1); this one serves the gradient-based circuit
+ * optimisation of Sec. 2.5 (the chain rule through (A, b, c)).
+ */
+int fk_circuit_triple(int M, const double *host_theta, double eta, fk_c128 *host_A,
+                      fk_c128 *host_b, fk_c128 *host_c, fk_c128 *host_dA, fk_c128 *host_db,
+                      fk_c128 *host_dc);
+
+/*
  * Workspace bytes for `op` on `batch` circuits of one shape (M cutoffs,
  * detected_mask; the mask is ignored by the DIAG ops and required by the COND
  * ops; circuits with differing cutoffs use fk_conditional_workspace_size).

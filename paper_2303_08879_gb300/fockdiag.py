@@ -31,6 +31,8 @@ EXPORTS = [
     "fk_describe_diag_schedule", "fk_measure_fp64_fma_rate", "fock_diag_probs_static",
     "fk_conditional_workspace_size", "fock_conditional_dm", "fock_conditional_dm_batched",
     "fock_conditional_dm_vjp", "fock_conditional_dm_vjp_batched",
+    "fk_circuit_triple", "fk_mlp_sizes", "fk_mlp_load", "fk_mlp_forward", "fk_mlp_backward", "fk_mlp_train_step",
+    "fk_herald_scores",
 ]
 
 
@@ -76,6 +78,8 @@ def lib():
         L.fk_describe_diag_schedule.argtypes = [I, P, U, P, I]
         L.fk_measure_fp64_fma_rate.argtypes = [P, Z, ctypes.POINTER(ctypes.c_double), P]
         L.fock_diag_probs_static.argtypes = [I, P, P, P, I, P, P, U, P, ctypes.POINTER(I)]
+        L.fk_herald_scores.argtypes = [I, P, P, I, P, ctypes.c_double, P, P, P, P]
+        L.fk_circuit_triple.argtypes = [I, P, ctypes.c_double, P, P, P, P, P, P]
         L.fk_conditional_workspace_size.argtypes = [I, I, P, P, I, U, ctypes.POINTER(Z), P]
         L.fock_conditional_dm.argtypes = [P, P, P, I, P, P, P, P, Z, P]
         L.fock_conditional_dm_batched.argtypes = [I, P, P, P, I, P, P, P, U, P, Z, P]
@@ -125,6 +129,28 @@ def fk_gaussian_to_triple(V, mean):
     st = lib().fk_gaussian_to_triple(M, V.ctypes.data, mean.ctypes.data, A.ctypes.data,
                                      b.ctypes.data, c.ctypes.data)
     _check(st, "fk_gaussian_to_triple")
+    return A, b, complex(c[0])
+
+
+def fk_circuit_triple(theta, eta, M=3, jacobian=False):
+    """(A, b, c[, dA, db, dc]) of the parameterised circuit (numpy, host)."""
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    D = 2 * M
+    P = M * M + 2 * M
+    assert th.shape == (P,)
+    A = np.zeros((D, D), np.complex128); b = np.zeros(D, np.complex128)
+    c = np.zeros(1, np.complex128)
+    if jacobian:
+        dA = np.zeros((P, D, D), np.complex128); db = np.zeros((P, D), np.complex128)
+        dc = np.zeros(P, np.complex128)
+        ptrs = (dA.ctypes.data, db.ctypes.data, dc.ctypes.data)
+    else:
+        ptrs = (None, None, None)
+    st = lib().fk_circuit_triple(M, th.ctypes.data, float(eta), A.ctypes.data, b.ctypes.data,
+                                 c.ctypes.data, *ptrs)
+    _check(st, "fk_circuit_triple")
+    if jacobian:
+        return A, b, complex(c[0]), dA, db, dc
     return A, b, complex(c[0])
 
 
