@@ -242,6 +242,12 @@ def run_gpu(args):
     flags = fd.FK_FLAG_B_ZERO
     probs = torch.empty((NCIRC,) + cut, dtype=torch.complex128, device=dev)
     gA, gb, gc = torch.empty_like(A), torch.empty_like(b), torch.empty_like(c)
+    tuning = None
+    if not args.no_autotune:
+        from paper_2303_08879_gb300 import autotune
+        best, times = autotune.tune_diag(A, b, c, cut, w, flags=flags)
+        tuning = {"tile_pivots": best[0], "chunk_rows": best[1], "blocks_per_sm_cap": best[2],
+                  "ms_per_candidate": times}
     ws = fd.workspace(fd.fk_workspace_size(M, cut, NCIRC, fd.FK_OP_DIAG_VJP, flags), dev)
     stream = torch.cuda.current_stream()
     ev = lambda: torch.cuda.Event(enable_timing=True)
@@ -334,6 +340,7 @@ def run_gpu(args):
                          "forward": {"achieved": flops_fwd / (fwd_ms * 1e-3) / 1e12,
                                      "frac": flops_fwd / (fwd_ms * 1e-3) / 1e12 / peak}},
             "clocks": clocks,
+            "autotune": tuning,
         }
         if world == 1 and not args.no_cpu_baseline:
             n, dt, scut = oracle_sample(20.0)
@@ -355,6 +362,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--circuits", type=int, default=NCIRC,
                     help="circuits per GPU (default 16; smaller only for profiler captures)")
     args = ap.parse_args()

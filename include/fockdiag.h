@@ -236,6 +236,19 @@ int fock_diag_probs_static(int batch, const fk_c128 *d_A, const fk_c128 *d_b, co
                            void *stream, int *host_status);
 
 /*
+ * Tile shape of the all-detected walk kernels, process-wide (the paper has
+ * no counterpart: the autotuner in paper_2303_08879_gb300/autotune.py times
+ * the shapes on the caller's workload and sets the fastest).  tpb = pivots
+ * per tile (64, 128 or 256), ch = output rows per register chunk (4 or 8;
+ * compiled pairs: 128/8, 128/4, 64/8, 64/4, 256/8), blocks_per_sm = cap on
+ * resident blocks per SM (0 = as many as fit).  tpb = ch = 0 restores the
+ * default 128/8.  Workspaces must be sized (fk_workspace_size) after the
+ * setting they run with; a VJP launched with a different setting returns
+ * FK_EWORKSPACE.
+ */
+int fk_diag_set_tuning(int tpb, int ch, int blocks_per_sm);
+
+/*
  * Reads the device-side status word of a workspace after the calls queued
  * on `stream` (synchronises the stream).  *status = FK_OK or the first error
  * a kernel recorded; the word is cleared by the next compute call.

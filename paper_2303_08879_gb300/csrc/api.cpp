@@ -450,6 +450,11 @@ int fock_diag_probs_vjp(const fk_c128 *A, const fk_c128 *b, const fk_c128 *c, in
                                        ws_bytes, stream);
 }
 
+int fk_diag_set_tuning(int tpb, int ch, int blocks_per_sm)
+{
+    return set_diag_tuning(tpb, ch, blocks_per_sm);
+}
+
 int fk_workspace_status(const void *ws, void *stream, int *status)
 {
     if (!ws || !status) return FK_EINVAL;

@@ -88,6 +88,10 @@ int launch_cond_vjp(const CondPlan &plan, unsigned flags, const void *A, const v
                     const void *c, const void *grho, void *gA, void *gb, void *gc, void *ws,
                     const CondLayout &lay, void *stream);
 
+// Tile shape of the all-detected walk (pivots per tile, output rows per
+// register chunk, blocks per SM; 0 = as many as fit).  Process-wide.
+int set_diag_tuning(int tpb, int ch, int blocks_per_sm);
+
 // Launchers (walk_diag.cu).  All pointers are device pointers.
 int diag_grid_size(const DiagShape &sh, bool vjp, int *grid);
 int launch_diag_forward(const DiagShape &sh, int batch, unsigned flags, const void *A,

@@ -33,9 +33,6 @@ namespace fk {
 
 namespace {
 
-constexpr int TPB = 128;          // pivots per tile = threads per block
-constexpr int RS = TPB + 1;       // padded row stride of per-thread smem columns
-constexpr int CH = 8;             // output rows per register chunk
 constexpr int TABN = kTabN;
 
 struct DiagArgs {
@@ -69,140 +66,12 @@ struct Smem {
     int loaded_circ;
 };
 
-__host__ __device__ inline size_t smem_bytes(int M, int L, bool vjp)
-{
-    const int D = 2 * M;
-    size_t n = 0;
-    n += (size_t)(M + 1) * (L + 2) * sizeof(unsigned);
-    n = (n + 15) & ~(size_t)15;
-    n += 2 * TABN * sizeof(double);
-    n += (size_t)D * D * sizeof(double2) + (size_t)D * sizeof(double2);
-    n += (size_t)D * RS * sizeof(double2);
-    if (vjp) n += (size_t)D * RS * sizeof(double2) + RS * sizeof(double2);
-    n += (size_t)M * TPB * sizeof(int) + (M + 2) * sizeof(int);
-    return n + 64;
-}
-
-__device__ Smem carve_smem(const DiagShape &sh, bool vjp)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem s;
-    const int M = sh.M, D = 2 * M;
-    unsigned char *p = smem_raw;
-    s.W = (unsigned *)p;
-    s.Wn = sh.L + 2;
-    p += (size_t)(M + 1) * s.Wn * sizeof(unsigned);
-    p = (unsigned char *)(((uintptr_t)p + 15) & ~(uintptr_t)15);
-    s.inv = (double *)p; p += TABN * sizeof(double);
-    s.fact = (double *)p; p += TABN * sizeof(double);
-    s.As = (double2 *)p; p += (size_t)D * D * sizeof(double2);
-    s.bs = (double2 *)p; p += (size_t)D * sizeof(double2);
-    s.R = (double2 *)p; p += (size_t)D * RS * sizeof(double2);
-    if (vjp) {
-        s.Y = (double2 *)p; p += (size_t)D * RS * sizeof(double2);
-        s.FP = (double2 *)p; p += RS * sizeof(double2);
-    } else {
-        s.Y = nullptr;
-        s.FP = nullptr;
-    }
-    s.idx = (int *)p; p += (size_t)M * TPB * sizeof(int);
-    s.tiles = (int *)p;
-    s.loaded_circ = -1;
-    return s;
-}
-
-// Level-count, reciprocal and factorial tables (every block builds its own
-// copy; they depend on the cutoffs only).
-__device__ void build_tables(const DiagShape &sh, Smem &s)
-{
-    build_scalar_tables(s.inv, s.fact);
-    build_level_table(s.W, s.Wn, sh.C, sh.M);
-}
-
-__device__ __forceinline__ LevelTab ltab(const Smem &s) { return LevelTab{s.W, s.Wn}; }
-
-__device__ __forceinline__ unsigned level_count(const DiagShape &sh, const Smem &sm, int k0,
-                                                int dk0, int s)
-{
-    return level_count(sh.C, ltab(sm), k0, dk0, s);
-}
-
-__device__ __forceinline__ Dig unrank(const DiagShape &sh, const Smem &sm, int k0, int dk0, int s,
-                                      unsigned rank)
-{
-    return unrank(sh.C, sh.M, ltab(sm), k0, dk0, s, rank);
-}
-
-__device__ __forceinline__ int64_t diag_index(const DiagShape &sh, const Dig &d, int k0)
-{
-    int64_t idx = 0;
-    for (int i = k0; i < sh.M; ++i) idx += (int64_t)d(i) * sh.stride[i];
-    return idx;
-}
-
-// Load A_s (symmetric part, kept modes) and b of one circuit into smem.
-__device__ void load_circuit(const DiagArgs &a, Smem &s, int circ)
-{
-    if (s.loaded_circ == circ) return;
-    __syncthreads();
-    const int D = 2 * a.sh.M;
-    const double2 *As = a.As + (size_t)circ * D * D;
-    for (int e = threadIdx.x; e < D * D; e += blockDim.x) s.As[e] = As[e];
-    for (int e = threadIdx.x; e < D; e += blockDim.x) s.bs[e] = a.bs[(size_t)circ * D + e];
-    __syncthreads();
-    s.loaded_circ = circ;
-}
-
-// Tile bookkeeping for one phase: segment k (anchor K for AP, 0 for DP and
-// DIAG) x circuit, ceil(count / TPB) tiles each; tiles[k] = prefix over k.
-// kind: 0 = AP, 1 = DP, 2 = DIAG.
-__device__ int phase_tiles(const DiagArgs &a, Smem &s, int kind, int lev)
-{
-    const DiagShape &sh = a.sh;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int acc = 0;
-        const int nseg = (kind == 0) ? sh.M : 1;
-        for (int k = 0; k < nseg; ++k) {
-            s.tiles[k] = acc;
-            unsigned cnt;
-            if (kind == 0) cnt = level_count(sh, s, k, 1, lev);
-            else if (kind == 1) cnt = level_count(sh, s, 0, 1, lev);
-            else cnt = level_count(sh, s, 0, 0, lev);
-            acc += a.B * (int)((cnt + TPB - 1) / TPB);
-        }
-        s.tiles[nseg] = acc;
-    }
-    __syncthreads();
-    return s.tiles[(kind == 0) ? sh.M : 1];
-}
-
+// ---------------------------------------------------------------- geometry
 struct TileId {
     int seg, circ;
     unsigned rank0, count;
 };
 
-__device__ TileId decode_tile(const DiagArgs &a, const Smem &s, int kind, int lev, int tile)
-{
-    const DiagShape &sh = a.sh;
-    TileId t;
-    const int nseg = (kind == 0) ? sh.M : 1;
-    int k = 0;
-    while (k + 1 < nseg && tile >= s.tiles[k + 1]) ++k;
-    t.seg = k;
-    unsigned cnt;
-    if (kind == 0) cnt = level_count(sh, s, k, 1, lev);
-    else if (kind == 1) cnt = level_count(sh, s, 0, 1, lev);
-    else cnt = level_count(sh, s, 0, 0, lev);
-    const int per = (int)((cnt + TPB - 1) / TPB);
-    const int rem = tile - s.tiles[k];
-    t.circ = rem / per;
-    t.rank0 = (unsigned)(rem % per) * TPB;
-    t.count = cnt;
-    return t;
-}
-
-// ------------------------------------------------------- per-pivot geometry
 // AP(K) pivot with base e: read column j / write row i addresses and masks.
 struct ApGeom {
     int64_t diag;    // DIAG index of e
@@ -212,49 +81,6 @@ struct ApGeom {
     unsigned nmask;  // needed writes
 };
 
-__device__ __forceinline__ ApGeom ap_geom(const DiagShape &sh, const Dig &e, int K, Smem &s,
-                                          bool hasb)
-{
-    ApGeom g;
-    const int eK = e(K);
-    g.diag = diag_index(sh, e, K);
-    g.t2 = box_index(sh, e, K, K, 2, -1, 0);
-    g.t1k = hasb ? box_index(sh, e, 0, 0, 1, K > 0 ? K : -1, 1) : 0;
-    g.vmask = 1u | (eK >= 1 ? 2u : 0u);
-    g.nmask = 2u | (eK <= sh.C[K] - 3 ? 1u : 0u);
-    for (int m = K + 1; m < sh.M; ++m) {
-        s.idx[m * TPB + threadIdx.x] = (int)box_index(sh, e, K, K, 1, m, 1);
-        const int em = e(m);
-        if (em >= 1) g.vmask |= 3u << (2 * (m - K));
-        if (em <= sh.C[m] - 2) g.nmask |= 3u << (2 * (m - K));
-    }
-    return g;
-}
-
-// Flat address (within the circuit's amplitude array) of AP read column j.
-__device__ __forceinline__ int64_t ap_read_addr(const DiagShape &sh, const ApGeom &g, int K,
-                                                int j, const Smem &s)
-{
-    if (j == 0) return g.diag;
-    if (j == 1) return sh.off_t2[K] + g.t2 - sh.stride[K];
-    const int m = K + j / 2;
-    const int64_t ip = s.idx[m * TPB + threadIdx.x];
-    return ((j & 1) ? sh.off_1010[K][m] : sh.off_1001[K][m]) + ip - sh.stride[m];
-}
-
-// Flat address of AP write row i and its scale index P_w + 1.
-__device__ __forceinline__ int64_t ap_write_addr(const DiagShape &sh, const ApGeom &g,
-                                                 const Dig &e, int K, int i, const Smem &s,
-                                                 int *den)
-{
-    if (i == 0) { *den = e(K) + 2; return sh.off_t2[K] + g.t2; }
-    if (i == 1) { *den = e(K) + 1; return g.diag + sh.stride[K]; }
-    const int m = K + i / 2;
-    *den = e(m) + 1;
-    const int64_t ip = s.idx[m * TPB + threadIdx.x];
-    return ((i & 1) ? sh.off_1001[K][m] : sh.off_1010[K][m]) + ip;
-}
-
 // DP pivot d (b != 0): read column j = 2q -> T1B(q)[d-1_q], 2q+1 -> T1K(q)[d-1_q];
 // write row i = 2q -> T1K(q)[d], 2q+1 -> T1B(q)[d].
 struct DpGeom {
@@ -263,505 +89,700 @@ struct DpGeom {
     unsigned vmask, nmask;
 };
 
-__device__ __forceinline__ DpGeom dp_geom(const DiagShape &sh, const Dig &d, Smem &s)
-{
-    DpGeom g;
-    g.diag = diag_index(sh, d, 0);
-    g.t1b0 = box_index(sh, d, 0, 0, 2, -1, 0);
-    g.vmask = 0;
-    g.nmask = 0;
-    for (int q = 0; q < sh.M; ++q) {
-        s.idx[q * TPB + threadIdx.x] = (int)box_index(sh, d, 0, 0, 1, q > 0 ? q : -1, 1);
-        const int dq = d(q);
-        if (dq >= 1) g.vmask |= 3u << (2 * q);
-        if (q == 0) {
-            g.nmask |= 1u;
-            if (dq <= sh.C[0] - 3) g.nmask |= 2u;
-        } else if (dq <= sh.C[q] - 2) {
-            g.nmask |= 3u << (2 * q);
+// The walk for one tile shape: TPB pivots per tile (= threads per block) and
+// CH output rows per register chunk; the autotuner picks the instantiation.
+template <int TPB, int CH>
+struct Walk {
+    static constexpr int RS = TPB + 1;   // padded row stride of per-thread smem columns
+
+    static __host__ __device__ size_t smem_bytes(int M, int L, bool vjp)
+    {
+        const int D = 2 * M;
+        size_t n = 0;
+        n += (size_t)(M + 1) * (L + 2) * sizeof(unsigned);
+        n = (n + 15) & ~(size_t)15;
+        n += 2 * TABN * sizeof(double);
+        n += (size_t)D * D * sizeof(double2) + (size_t)D * sizeof(double2);
+        n += (size_t)D * RS * sizeof(double2);
+        if (vjp) n += (size_t)D * RS * sizeof(double2) + RS * sizeof(double2);
+        n += (size_t)M * TPB * sizeof(int) + (M + 2) * sizeof(int);
+        return n + 64;
+    }
+
+    static __device__ Smem carve_smem(const DiagShape &sh, bool vjp)
+    {
+        extern __shared__ __align__(16) unsigned char smem_raw[];
+        Smem s;
+        const int M = sh.M, D = 2 * M;
+        unsigned char *p = smem_raw;
+        s.W = (unsigned *)p;
+        s.Wn = sh.L + 2;
+        p += (size_t)(M + 1) * s.Wn * sizeof(unsigned);
+        p = (unsigned char *)(((uintptr_t)p + 15) & ~(uintptr_t)15);
+        s.inv = (double *)p; p += TABN * sizeof(double);
+        s.fact = (double *)p; p += TABN * sizeof(double);
+        s.As = (double2 *)p; p += (size_t)D * D * sizeof(double2);
+        s.bs = (double2 *)p; p += (size_t)D * sizeof(double2);
+        s.R = (double2 *)p; p += (size_t)D * RS * sizeof(double2);
+        if (vjp) {
+            s.Y = (double2 *)p; p += (size_t)D * RS * sizeof(double2);
+            s.FP = (double2 *)p; p += RS * sizeof(double2);
+        } else {
+            s.Y = nullptr;
+            s.FP = nullptr;
+        }
+        s.idx = (int *)p; p += (size_t)M * TPB * sizeof(int);
+        s.tiles = (int *)p;
+        s.loaded_circ = -1;
+        return s;
+    }
+
+    // Level-count, reciprocal and factorial tables (every block builds its own
+    // copy; they depend on the cutoffs only).
+    static __device__ void build_tables(const DiagShape &sh, Smem &s)
+    {
+        build_scalar_tables(s.inv, s.fact);
+        build_level_table(s.W, s.Wn, sh.C, sh.M);
+    }
+
+    static __device__ __forceinline__ LevelTab ltab(const Smem &s) { return LevelTab{s.W, s.Wn}; }
+
+    static __device__ __forceinline__ unsigned level_count(const DiagShape &sh, const Smem &sm, int k0,
+                                                    int dk0, int s)
+    {
+        return fk::level_count(sh.C, ltab(sm), k0, dk0, s);
+    }
+
+    static __device__ __forceinline__ Dig unrank(const DiagShape &sh, const Smem &sm, int k0, int dk0, int s,
+                                          unsigned rank)
+    {
+        return fk::unrank(sh.C, sh.M, ltab(sm), k0, dk0, s, rank);
+    }
+
+    static __device__ __forceinline__ int64_t diag_index(const DiagShape &sh, const Dig &d, int k0)
+    {
+        int64_t idx = 0;
+        for (int i = k0; i < sh.M; ++i) idx += (int64_t)d(i) * sh.stride[i];
+        return idx;
+    }
+
+    // Load A_s (symmetric part, kept modes) and b of one circuit into smem.
+    static __device__ void load_circuit(const DiagArgs &a, Smem &s, int circ)
+    {
+        if (s.loaded_circ == circ) return;
+        __syncthreads();
+        const int D = 2 * a.sh.M;
+        const double2 *As = a.As + (size_t)circ * D * D;
+        for (int e = threadIdx.x; e < D * D; e += blockDim.x) s.As[e] = As[e];
+        for (int e = threadIdx.x; e < D; e += blockDim.x) s.bs[e] = a.bs[(size_t)circ * D + e];
+        __syncthreads();
+        s.loaded_circ = circ;
+    }
+
+    // Tile bookkeeping for one phase: segment k (anchor K for AP, 0 for DP and
+    // DIAG) x circuit, ceil(count / TPB) tiles each; tiles[k] = prefix over k.
+    // kind: 0 = AP, 1 = DP, 2 = DIAG.
+    static __device__ int phase_tiles(const DiagArgs &a, Smem &s, int kind, int lev)
+    {
+        const DiagShape &sh = a.sh;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int acc = 0;
+            const int nseg = (kind == 0) ? sh.M : 1;
+            for (int k = 0; k < nseg; ++k) {
+                s.tiles[k] = acc;
+                unsigned cnt;
+                if (kind == 0) cnt = level_count(sh, s, k, 1, lev);
+                else if (kind == 1) cnt = level_count(sh, s, 0, 1, lev);
+                else cnt = level_count(sh, s, 0, 0, lev);
+                acc += a.B * (int)((cnt + TPB - 1) / TPB);
+            }
+            s.tiles[nseg] = acc;
+        }
+        __syncthreads();
+        return s.tiles[(kind == 0) ? sh.M : 1];
+    }
+
+
+    static __device__ TileId decode_tile(const DiagArgs &a, const Smem &s, int kind, int lev, int tile)
+    {
+        const DiagShape &sh = a.sh;
+        TileId t;
+        const int nseg = (kind == 0) ? sh.M : 1;
+        int k = 0;
+        while (k + 1 < nseg && tile >= s.tiles[k + 1]) ++k;
+        t.seg = k;
+        unsigned cnt;
+        if (kind == 0) cnt = level_count(sh, s, k, 1, lev);
+        else if (kind == 1) cnt = level_count(sh, s, 0, 1, lev);
+        else cnt = level_count(sh, s, 0, 0, lev);
+        const int per = (int)((cnt + TPB - 1) / TPB);
+        const int rem = tile - s.tiles[k];
+        t.circ = rem / per;
+        t.rank0 = (unsigned)(rem % per) * TPB;
+        t.count = cnt;
+        return t;
+    }
+
+    // ------------------------------------------------------- per-pivot geometry
+
+    static __device__ __forceinline__ ApGeom ap_geom(const DiagShape &sh, const Dig &e, int K, Smem &s,
+                                              bool hasb)
+    {
+        ApGeom g;
+        const int eK = e(K);
+        g.diag = diag_index(sh, e, K);
+        g.t2 = box_index(sh, e, K, K, 2, -1, 0);
+        g.t1k = hasb ? box_index(sh, e, 0, 0, 1, K > 0 ? K : -1, 1) : 0;
+        g.vmask = 1u | (eK >= 1 ? 2u : 0u);
+        g.nmask = 2u | (eK <= sh.C[K] - 3 ? 1u : 0u);
+        for (int m = K + 1; m < sh.M; ++m) {
+            s.idx[m * TPB + threadIdx.x] = (int)box_index(sh, e, K, K, 1, m, 1);
+            const int em = e(m);
+            if (em >= 1) g.vmask |= 3u << (2 * (m - K));
+            if (em <= sh.C[m] - 2) g.nmask |= 3u << (2 * (m - K));
+        }
+        return g;
+    }
+
+    // Flat address (within the circuit's amplitude array) of AP read column j.
+    static __device__ __forceinline__ int64_t ap_read_addr(const DiagShape &sh, const ApGeom &g, int K,
+                                                    int j, const Smem &s)
+    {
+        if (j == 0) return g.diag;
+        if (j == 1) return sh.off_t2[K] + g.t2 - sh.stride[K];
+        const int m = K + j / 2;
+        const int64_t ip = s.idx[m * TPB + threadIdx.x];
+        return ((j & 1) ? sh.off_1010[K][m] : sh.off_1001[K][m]) + ip - sh.stride[m];
+    }
+
+    // Flat address of AP write row i and its scale index P_w + 1.
+    static __device__ __forceinline__ int64_t ap_write_addr(const DiagShape &sh, const ApGeom &g,
+                                                     const Dig &e, int K, int i, const Smem &s,
+                                                     int *den)
+    {
+        if (i == 0) { *den = e(K) + 2; return sh.off_t2[K] + g.t2; }
+        if (i == 1) { *den = e(K) + 1; return g.diag + sh.stride[K]; }
+        const int m = K + i / 2;
+        *den = e(m) + 1;
+        const int64_t ip = s.idx[m * TPB + threadIdx.x];
+        return ((i & 1) ? sh.off_1001[K][m] : sh.off_1010[K][m]) + ip;
+    }
+
+
+    static __device__ __forceinline__ DpGeom dp_geom(const DiagShape &sh, const Dig &d, Smem &s)
+    {
+        DpGeom g;
+        g.diag = diag_index(sh, d, 0);
+        g.t1b0 = box_index(sh, d, 0, 0, 2, -1, 0);
+        g.vmask = 0;
+        g.nmask = 0;
+        for (int q = 0; q < sh.M; ++q) {
+            s.idx[q * TPB + threadIdx.x] = (int)box_index(sh, d, 0, 0, 1, q > 0 ? q : -1, 1);
+            const int dq = d(q);
+            if (dq >= 1) g.vmask |= 3u << (2 * q);
+            if (q == 0) {
+                g.nmask |= 1u;
+                if (dq <= sh.C[0] - 3) g.nmask |= 2u;
+            } else if (dq <= sh.C[q] - 2) {
+                g.nmask |= 3u << (2 * q);
+            }
+        }
+        return g;
+    }
+
+    static __device__ __forceinline__ int64_t dp_read_addr(const DiagShape &sh, const DpGeom &g, int j,
+                                                    const Smem &s)
+    {
+        const int q = j / 2;
+        if (j & 1) return sh.off_t1k[q] + s.idx[q * TPB + threadIdx.x] - sh.stride[q];
+        const int64_t ib = (q == 0) ? g.t1b0 : (int64_t)s.idx[q * TPB + threadIdx.x];
+        return sh.off_t1b[q] + ib - sh.stride[q];
+    }
+
+    static __device__ __forceinline__ int64_t dp_write_addr(const DiagShape &sh, const DpGeom &g,
+                                                     const Dig &d, int i, const Smem &s, int *den)
+    {
+        const int q = i / 2;
+        *den = d(q) + 1;
+        if ((i & 1) == 0) return sh.off_t1k[q] + s.idx[q * TPB + threadIdx.x];
+        const int64_t ib = (q == 0) ? g.t1b0 : (int64_t)s.idx[q * TPB + threadIdx.x];
+        return sh.off_t1b[q] + ib;
+    }
+
+    // ---------------------------------------------------------------- prologue
+    // A_s = (A + A^T)/2 restricted to kept modes, b restricted, vacuum seeds.
+    static __device__ void prologue(const DiagArgs &a, bool seed)
+    {
+        const DiagShape &sh = a.sh;
+        const int D = 2 * sh.M, Do = sh.D_orig;
+        const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+        int nz = 0;
+        for (int64_t e = gtid; e < (int64_t)a.B * D * D; e += gsz) {
+            const int c = (int)(e / (D * D));
+            const int w = (int)((e / D) % D), l = (int)(e % D);
+            const int ow = 2 * sh.mode_map[w / 2] + (w & 1), ol = 2 * sh.mode_map[l / 2] + (l & 1);
+            const double2 x = a.A[(size_t)c * Do * Do + (size_t)ow * Do + ol];
+            const double2 y = a.A[(size_t)c * Do * Do + (size_t)ol * Do + ow];
+            a.As[e] = make_double2(0.5 * (x.x + y.x), 0.5 * (x.y + y.y));
+        }
+        for (int64_t e = gtid; e < (int64_t)a.B * D; e += gsz) {
+            const int c = (int)(e / D), w = (int)(e % D);
+            const int ow = 2 * sh.mode_map[w / 2] + (w & 1);
+            const double2 v = a.b[(size_t)c * Do + ow];
+            a.bs[e] = v;
+            if (v.x != 0.0 || v.y != 0.0) nz = 1;
+        }
+        if (__syncthreads_or(nz) && threadIdx.x == 0) atomicOr(&a.ctl->has_b, 1);
+        if (seed) {
+            for (int64_t c = gtid; c < a.B; c += gsz) {
+                const double2 v = a.c[c];
+                a.F[(size_t)c * sh.circ_size] = v;
+                a.probs[(size_t)c * sh.n_diag] = v;
+            }
         }
     }
-    return g;
-}
 
-__device__ __forceinline__ int64_t dp_read_addr(const DiagShape &sh, const DpGeom &g, int j,
-                                                const Smem &s)
-{
-    const int q = j / 2;
-    if (j & 1) return sh.off_t1k[q] + s.idx[q * TPB + threadIdx.x] - sh.stride[q];
-    const int64_t ib = (q == 0) ? g.t1b0 : (int64_t)s.idx[q * TPB + threadIdx.x];
-    return sh.off_t1b[q] + ib - sh.stride[q];
-}
-
-__device__ __forceinline__ int64_t dp_write_addr(const DiagShape &sh, const DpGeom &g,
-                                                 const Dig &d, int i, const Smem &s, int *den)
-{
-    const int q = i / 2;
-    *den = d(q) + 1;
-    if ((i & 1) == 0) return sh.off_t1k[q] + s.idx[q * TPB + threadIdx.x];
-    const int64_t ib = (q == 0) ? g.t1b0 : (int64_t)s.idx[q * TPB + threadIdx.x];
-    return sh.off_t1b[q] + ib;
-}
-
-// ---------------------------------------------------------------- prologue
-// A_s = (A + A^T)/2 restricted to kept modes, b restricted, vacuum seeds.
-__device__ void prologue(const DiagArgs &a, bool seed)
-{
-    const DiagShape &sh = a.sh;
-    const int D = 2 * sh.M, Do = sh.D_orig;
-    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
-    int nz = 0;
-    for (int64_t e = gtid; e < (int64_t)a.B * D * D; e += gsz) {
-        const int c = (int)(e / (D * D));
-        const int w = (int)((e / D) % D), l = (int)(e % D);
-        const int ow = 2 * sh.mode_map[w / 2] + (w & 1), ol = 2 * sh.mode_map[l / 2] + (l & 1);
-        const double2 x = a.A[(size_t)c * Do * Do + (size_t)ow * Do + ol];
-        const double2 y = a.A[(size_t)c * Do * Do + (size_t)ol * Do + ow];
-        a.As[e] = make_double2(0.5 * (x.x + y.x), 0.5 * (x.y + y.y));
-    }
-    for (int64_t e = gtid; e < (int64_t)a.B * D; e += gsz) {
-        const int c = (int)(e / D), w = (int)(e % D);
-        const int ow = 2 * sh.mode_map[w / 2] + (w & 1);
-        const double2 v = a.b[(size_t)c * Do + ow];
-        a.bs[e] = v;
-        if (v.x != 0.0 || v.y != 0.0) nz = 1;
-    }
-    if (__syncthreads_or(nz) && threadIdx.x == 0) atomicOr(&a.ctl->has_b, 1);
-    if (seed) {
-        for (int64_t c = gtid; c < a.B; c += gsz) {
-            const double2 v = a.c[c];
-            a.F[(size_t)c * sh.circ_size] = v;
-            a.probs[(size_t)c * sh.n_diag] = v;
+    // ------------------------------------------------------------- forward AP
+    template <bool HASB>
+    static __device__ void ap_forward_tile(const DiagArgs &a, Smem &s, const TileId &tl, int K, int lev)
+    {
+        const DiagShape &sh = a.sh;
+        const int t = threadIdx.x, D = 2 * sh.M, N = 2 * (sh.M - K);
+        load_circuit(a, s, tl.circ);
+        double2 *F = a.F + (size_t)tl.circ * sh.circ_size;
+        const unsigned r = tl.rank0 + t;
+        const bool act = r < tl.count;
+        Dig e;
+        ApGeom g{};
+        double2 FP = make_double2(0, 0);
+        double fe = 1.0;
+        if (act) {
+            e = unrank(sh, s, K, 1, lev, r);
+            g = ap_geom(sh, e, K, s, HASB);
+            for (int j = 0; j < N; ++j) {
+                double2 v = make_double2(0, 0);
+                if ((g.vmask >> j) & 1u) v = __ldcg(F + ap_read_addr(sh, g, K, j, s));
+                s.R[j * RS + t] = v;
+            }
+            if (HASB) FP = __ldcg(F + sh.off_t1k[K] + g.t1k);
+            for (int i = K; i < sh.M; ++i) fe *= s.fact[e(i)];
+        } else {
+            for (int j = 0; j < N; ++j) s.R[j * RS + t] = make_double2(0, 0);
         }
-    }
-}
-
-// ------------------------------------------------------------- forward AP
-template <bool HASB>
-__device__ void ap_forward_tile(const DiagArgs &a, Smem &s, const TileId &tl, int K, int lev)
-{
-    const DiagShape &sh = a.sh;
-    const int t = threadIdx.x, D = 2 * sh.M, N = 2 * (sh.M - K);
-    load_circuit(a, s, tl.circ);
-    double2 *F = a.F + (size_t)tl.circ * sh.circ_size;
-    const unsigned r = tl.rank0 + t;
-    const bool act = r < tl.count;
-    Dig e;
-    ApGeom g{};
-    double2 FP = make_double2(0, 0);
-    double fe = 1.0;
-    if (act) {
-        e = unrank(sh, s, K, 1, lev, r);
-        g = ap_geom(sh, e, K, s, HASB);
-        for (int j = 0; j < N; ++j) {
-            double2 v = make_double2(0, 0);
-            if ((g.vmask >> j) & 1u) v = __ldcg(F + ap_read_addr(sh, g, K, j, s));
-            s.R[j * RS + t] = v;
-        }
-        if (HASB) FP = __ldcg(F + sh.off_t1k[K] + g.t1k);
-        for (int i = K; i < sh.M; ++i) fe *= s.fact[e(i)];
-    } else {
-        for (int j = 0; j < N; ++j) s.R[j * RS + t] = make_double2(0, 0);
-    }
-    const unsigned vm = __reduce_or_sync(0xffffffffu, g.vmask);
-    const unsigned nm = __reduce_or_sync(0xffffffffu, g.nmask);
-    const double2 *Ab = s.As + (size_t)(2 * K) * D + 2 * K;
-    for (int i0 = 0; i0 < N; i0 += CH) {
-        if (((nm >> i0) & 0xffu) == 0) continue;
-        double2 acc[CH];
-#pragma unroll
-        for (int ii = 0; ii < CH; ++ii)
-            acc[ii] = HASB && (i0 + ii < N) ? cmul(s.bs[2 * K + i0 + ii], FP) : make_double2(0, 0);
-        for (int j = 0; j < N; ++j) {
-            if (!((vm >> j) & 1u)) continue;
-            const double2 x = s.R[j * RS + t];
-#pragma unroll
+        const unsigned vm = __reduce_or_sync(0xffffffffu, g.vmask);
+        const unsigned nm = __reduce_or_sync(0xffffffffu, g.nmask);
+        const double2 *Ab = s.As + (size_t)(2 * K) * D + 2 * K;
+        for (int i0 = 0; i0 < N; i0 += CH) {
+            if (((nm >> i0) & ((1u << CH) - 1u)) == 0) continue;
+            double2 acc[CH];
+    #pragma unroll
             for (int ii = 0; ii < CH; ++ii)
-                if (i0 + ii < N && ((nm >> (i0 + ii)) & 1u))
-                    acc[ii] = cfma(Ab[(size_t)(i0 + ii) * D + j], x, acc[ii]);
-        }
-#pragma unroll
-        for (int ii = 0; ii < CH; ++ii) {
-            const int i = i0 + ii;
-            if (i < N && act && ((g.nmask >> i) & 1u)) {
-                int den;
-                const int64_t addr = ap_write_addr(sh, g, e, K, i, s, &den);
-                const double2 v = rscale(acc[ii], s.inv[den]);
-                F[addr] = v;
-                if (i == 1)
-                    a.probs[(size_t)tl.circ * sh.n_diag + addr] = rscale(v, fe * (double)(e(K) + 1));
+                acc[ii] = HASB && (i0 + ii < N) ? cmul(s.bs[2 * K + i0 + ii], FP) : make_double2(0, 0);
+            for (int j = 0; j < N; ++j) {
+                if (!((vm >> j) & 1u)) continue;
+                const double2 x = s.R[j * RS + t];
+    #pragma unroll
+                for (int ii = 0; ii < CH; ++ii)
+                    if (i0 + ii < N && ((nm >> (i0 + ii)) & 1u))
+                        acc[ii] = cfma(Ab[(size_t)(i0 + ii) * D + j], x, acc[ii]);
             }
-        }
-    }
-}
-
-// ------------------------------------------------------------- forward DP
-__device__ void dp_forward_tile(const DiagArgs &a, Smem &s, const TileId &tl, int lev)
-{
-    const DiagShape &sh = a.sh;
-    const int t = threadIdx.x, D = 2 * sh.M, N = D;
-    load_circuit(a, s, tl.circ);
-    double2 *F = a.F + (size_t)tl.circ * sh.circ_size;
-    const unsigned r = tl.rank0 + t;
-    const bool act = r < tl.count;
-    Dig d;
-    DpGeom g{};
-    double2 FP = make_double2(0, 0);
-    if (act) {
-        d = unrank(sh, s, 0, 1, lev, r);
-        g = dp_geom(sh, d, s);
-        for (int j = 0; j < N; ++j) {
-            double2 v = make_double2(0, 0);
-            if ((g.vmask >> j) & 1u) v = __ldcg(F + dp_read_addr(sh, g, j, s));
-            s.R[j * RS + t] = v;
-        }
-        FP = __ldcg(F + g.diag);
-    } else {
-        for (int j = 0; j < N; ++j) s.R[j * RS + t] = make_double2(0, 0);
-    }
-    const unsigned vm = __reduce_or_sync(0xffffffffu, g.vmask);
-    const unsigned nm = __reduce_or_sync(0xffffffffu, g.nmask);
-    for (int i0 = 0; i0 < N; i0 += CH) {
-        if (((nm >> i0) & 0xffu) == 0) continue;
-        double2 acc[CH];
-#pragma unroll
-        for (int ii = 0; ii < CH; ++ii)
-            acc[ii] = (i0 + ii < N) ? cmul(s.bs[i0 + ii], FP) : make_double2(0, 0);
-        for (int j = 0; j < N; ++j) {
-            if (!((vm >> j) & 1u)) continue;
-            const double2 x = s.R[j * RS + t];
-#pragma unroll
-            for (int ii = 0; ii < CH; ++ii)
-                if (i0 + ii < N && ((nm >> (i0 + ii)) & 1u))
-                    acc[ii] = cfma(s.As[(size_t)(i0 + ii) * D + j], x, acc[ii]);
-        }
-#pragma unroll
-        for (int ii = 0; ii < CH; ++ii) {
-            const int i = i0 + ii;
-            if (i < N && act && ((g.nmask >> i) & 1u)) {
-                int den;
-                const int64_t addr = dp_write_addr(sh, g, d, i, s, &den);
-                F[addr] = rscale(acc[ii], s.inv[den]);
-            }
-        }
-    }
-}
-
-// ------------------------------------------------- reverse-walk reductions
-// Accumulate sum_t Y[w][t] conj(R[j][t]) into the block's partial dL/dA and
-// sum_t Y[w][t] conj(FP[t]) into its partial dL/db (rows/cols from 2*k0).
-__device__ void reduce_partials(const DiagArgs &a, Smem &s, int circ, int k0, int N, bool hasb,
-                                unsigned wm, unsigned jm)
-{
-    __shared__ unsigned s_m[2];
-    if (threadIdx.x == 0) s_m[0] = s_m[1] = 0u;
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) {   // wm, jm arrive OR-reduced over each warp
-        atomicOr(&s_m[0], wm);
-        atomicOr(&s_m[1], jm);
-    }
-    __syncthreads();
-    wm = s_m[0];
-    jm = s_m[1];
-    const int D = 2 * a.sh.M;
-    double2 *pA = a.partA + ((size_t)circ * a.grid + blockIdx.x) * D * D;
-    for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-        const int w = e / N, j = e % N;
-        if (!((wm >> w) & 1u) || !((jm >> j) & 1u)) continue;
-        double2 acc = make_double2(0, 0);
-        for (int tt = 0; tt < TPB; ++tt) acc = cfma_conj(s.R[j * RS + tt], s.Y[w * RS + tt], acc);
-        double2 &dst = pA[(size_t)(2 * k0 + w) * D + 2 * k0 + j];
-        dst = cadd(dst, acc);
-    }
-    if (hasb) {
-        double2 *pb = a.partb + ((size_t)circ * a.grid + blockIdx.x) * D;
-        for (int w = threadIdx.x; w < N; w += blockDim.x) {
-            if (!((wm >> w) & 1u)) continue;
-            double2 acc = make_double2(0, 0);
-            for (int tt = 0; tt < TPB; ++tt) acc = cfma_conj(s.FP[tt], s.Y[w * RS + tt], acc);
-            pb[2 * k0 + w] = cadd(pb[2 * k0 + w], acc);
-        }
-    }
-    __syncthreads();
-}
-
-// --------------------------------------------------------- reverse AP
-template <bool HASB>
-__device__ void ap_reverse_tile(const DiagArgs &a, Smem &s, const TileId &tl, int K, int lev)
-{
-    const DiagShape &sh = a.sh;
-    const int t = threadIdx.x, D = 2 * sh.M, N = 2 * (sh.M - K);
-    load_circuit(a, s, tl.circ);
-    const double2 *F = a.F + (size_t)tl.circ * sh.circ_size;
-    double2 *Fb = a.Fbar + (size_t)tl.circ * sh.circ_size;
-    const unsigned r = tl.rank0 + t;
-    const bool act = r < tl.count;
-    Dig e;
-    ApGeom g{};
-    if (act) {
-        e = unrank(sh, s, K, 1, lev, r);
-        g = ap_geom(sh, e, K, s, HASB);
-        for (int j = 0; j < N; ++j) {
-            double2 v = make_double2(0, 0);
-            if ((g.vmask >> j) & 1u) v = __ldcg(F + ap_read_addr(sh, g, K, j, s));
-            s.R[j * RS + t] = v;
-        }
-        for (int i = 0; i < N; ++i) {
-            double2 v = make_double2(0, 0);
-            if ((g.nmask >> i) & 1u) {
-                int den;
-                const int64_t addr = ap_write_addr(sh, g, e, K, i, s, &den);
-                v = rscale(__ldcg(Fb + addr), s.inv[den]);
-            }
-            s.Y[i * RS + t] = v;
-        }
-        s.FP[t] = HASB ? __ldcg(F + sh.off_t1k[K] + g.t1k) : make_double2(0, 0);
-    } else {
-        for (int j = 0; j < N; ++j) {
-            s.R[j * RS + t] = make_double2(0, 0);
-            s.Y[j * RS + t] = make_double2(0, 0);
-        }
-        s.FP[t] = make_double2(0, 0);
-    }
-    const unsigned vm = __reduce_or_sync(0xffffffffu, g.vmask);
-    const unsigned nm = __reduce_or_sync(0xffffffffu, g.nmask);
-    const double2 *Ab = s.As + (size_t)(2 * K) * D + 2 * K;
-    // adjoint of the reads: Rbar_j = sum_i conj(A_{w_i l_j}) Y_i
-    for (int j0 = 0; j0 < N; j0 += CH) {
-        if (((vm >> j0) & 0xffu) == 0) continue;
-        double2 acc[CH];
-#pragma unroll
-        for (int jj = 0; jj < CH; ++jj) acc[jj] = make_double2(0, 0);
-        for (int i = 0; i < N; ++i) {
-            if (!((nm >> i) & 1u)) continue;
-            const double2 y = s.Y[i * RS + t];
-#pragma unroll
-            for (int jj = 0; jj < CH; ++jj)
-                if (j0 + jj < N && ((vm >> (j0 + jj)) & 1u))
-                    acc[jj] = cfma_conj(Ab[(size_t)i * D + j0 + jj], y, acc[jj]);
-        }
-#pragma unroll
-        for (int jj = 0; jj < CH; ++jj) {
-            const int j = j0 + jj;
-            if (j < N && act && ((g.vmask >> j) & 1u)) {
-                if (j == 0) {
-                    const int64_t ia = box_index(sh, e, K, K, 1, -1, 0);
-                    a.scratch[(size_t)tl.circ * sh.n_ap + sh.off_ap[K] + ia] = acc[jj];
-                } else {
-                    const int64_t addr = ap_read_addr(sh, g, K, j, s);
-                    Fb[addr] = cadd(__ldcg(Fb + addr), acc[jj]);
+    #pragma unroll
+            for (int ii = 0; ii < CH; ++ii) {
+                const int i = i0 + ii;
+                if (i < N && act && ((g.nmask >> i) & 1u)) {
+                    int den;
+                    const int64_t addr = ap_write_addr(sh, g, e, K, i, s, &den);
+                    const double2 v = rscale(acc[ii], s.inv[den]);
+                    F[addr] = v;
+                    if (i == 1)
+                        a.probs[(size_t)tl.circ * sh.n_diag + addr] = rscale(v, fe * (double)(e(K) + 1));
                 }
             }
         }
     }
-    if (HASB && act) {
-        double2 fpb = make_double2(0, 0);
-        for (int i = 0; i < N; ++i)
-            if ((g.nmask >> i) & 1u) fpb = cfma_conj(s.bs[2 * K + i], s.Y[i * RS + t], fpb);
-        const int64_t addr = sh.off_t1k[K] + g.t1k;
-        Fb[addr] = cadd(__ldcg(Fb + addr), fpb);
-    }
-    reduce_partials(a, s, tl.circ, K, N, HASB, nm, vm);
-}
 
-// --------------------------------------------------------- reverse DP
-__device__ void dp_reverse_tile(const DiagArgs &a, Smem &s, const TileId &tl, int lev)
-{
-    const DiagShape &sh = a.sh;
-    const int t = threadIdx.x, D = 2 * sh.M, N = D;
-    load_circuit(a, s, tl.circ);
-    const double2 *F = a.F + (size_t)tl.circ * sh.circ_size;
-    double2 *Fb = a.Fbar + (size_t)tl.circ * sh.circ_size;
-    const unsigned r = tl.rank0 + t;
-    const bool act = r < tl.count;
-    Dig d;
-    DpGeom g{};
-    if (act) {
-        d = unrank(sh, s, 0, 1, lev, r);
-        g = dp_geom(sh, d, s);
-        for (int j = 0; j < N; ++j) {
-            double2 v = make_double2(0, 0);
-            if ((g.vmask >> j) & 1u) v = __ldcg(F + dp_read_addr(sh, g, j, s));
-            s.R[j * RS + t] = v;
-        }
-        for (int i = 0; i < N; ++i) {
-            double2 v = make_double2(0, 0);
-            if ((g.nmask >> i) & 1u) {
-                int den;
-                const int64_t addr = dp_write_addr(sh, g, d, i, s, &den);
-                v = rscale(__ldcg(Fb + addr), s.inv[den]);
+    // ------------------------------------------------------------- forward DP
+    static __device__ void dp_forward_tile(const DiagArgs &a, Smem &s, const TileId &tl, int lev)
+    {
+        const DiagShape &sh = a.sh;
+        const int t = threadIdx.x, D = 2 * sh.M, N = D;
+        load_circuit(a, s, tl.circ);
+        double2 *F = a.F + (size_t)tl.circ * sh.circ_size;
+        const unsigned r = tl.rank0 + t;
+        const bool act = r < tl.count;
+        Dig d;
+        DpGeom g{};
+        double2 FP = make_double2(0, 0);
+        if (act) {
+            d = unrank(sh, s, 0, 1, lev, r);
+            g = dp_geom(sh, d, s);
+            for (int j = 0; j < N; ++j) {
+                double2 v = make_double2(0, 0);
+                if ((g.vmask >> j) & 1u) v = __ldcg(F + dp_read_addr(sh, g, j, s));
+                s.R[j * RS + t] = v;
             }
-            s.Y[i * RS + t] = v;
+            FP = __ldcg(F + g.diag);
+        } else {
+            for (int j = 0; j < N; ++j) s.R[j * RS + t] = make_double2(0, 0);
         }
-        s.FP[t] = __ldcg(F + g.diag);
-    } else {
-        for (int j = 0; j < N; ++j) {
-            s.R[j * RS + t] = make_double2(0, 0);
-            s.Y[j * RS + t] = make_double2(0, 0);
-        }
-        s.FP[t] = make_double2(0, 0);
-    }
-    const unsigned vm = __reduce_or_sync(0xffffffffu, g.vmask);
-    const unsigned nm = __reduce_or_sync(0xffffffffu, g.nmask);
-    for (int j0 = 0; j0 < N; j0 += CH) {
-        if (((vm >> j0) & 0xffu) == 0) continue;
-        double2 acc[CH];
-#pragma unroll
-        for (int jj = 0; jj < CH; ++jj) acc[jj] = make_double2(0, 0);
-        for (int i = 0; i < N; ++i) {
-            if (!((nm >> i) & 1u)) continue;
-            const double2 y = s.Y[i * RS + t];
-#pragma unroll
-            for (int jj = 0; jj < CH; ++jj)
-                if (j0 + jj < N && ((vm >> (j0 + jj)) & 1u))
-                    acc[jj] = cfma_conj(s.As[(size_t)i * D + j0 + jj], y, acc[jj]);
-        }
-#pragma unroll
-        for (int jj = 0; jj < CH; ++jj) {
-            const int j = j0 + jj;
-            if (j < N && act && ((g.vmask >> j) & 1u)) {
-                const int64_t addr = dp_read_addr(sh, g, j, s);
-                Fb[addr] = cadd(__ldcg(Fb + addr), acc[jj]);
+        const unsigned vm = __reduce_or_sync(0xffffffffu, g.vmask);
+        const unsigned nm = __reduce_or_sync(0xffffffffu, g.nmask);
+        for (int i0 = 0; i0 < N; i0 += CH) {
+            if (((nm >> i0) & ((1u << CH) - 1u)) == 0) continue;
+            double2 acc[CH];
+    #pragma unroll
+            for (int ii = 0; ii < CH; ++ii)
+                acc[ii] = (i0 + ii < N) ? cmul(s.bs[i0 + ii], FP) : make_double2(0, 0);
+            for (int j = 0; j < N; ++j) {
+                if (!((vm >> j) & 1u)) continue;
+                const double2 x = s.R[j * RS + t];
+    #pragma unroll
+                for (int ii = 0; ii < CH; ++ii)
+                    if (i0 + ii < N && ((nm >> (i0 + ii)) & 1u))
+                        acc[ii] = cfma(s.As[(size_t)(i0 + ii) * D + j], x, acc[ii]);
+            }
+    #pragma unroll
+            for (int ii = 0; ii < CH; ++ii) {
+                const int i = i0 + ii;
+                if (i < N && act && ((g.nmask >> i) & 1u)) {
+                    int den;
+                    const int64_t addr = dp_write_addr(sh, g, d, i, s, &den);
+                    F[addr] = rscale(acc[ii], s.inv[den]);
+                }
             }
         }
     }
-    if (act) {
-        double2 fpb = make_double2(0, 0);
-        for (int i = 0; i < N; ++i)
-            if ((g.nmask >> i) & 1u) fpb = cfma_conj(s.bs[i], s.Y[i * RS + t], fpb);
-        Fb[g.diag] = cadd(__ldcg(Fb + g.diag), fpb);
-    }
-    reduce_partials(a, s, tl.circ, 0, N, true, nm, vm);
-}
 
-// ------------------------------------------------------ reverse DIAGSUM
-// Adjoint of every diagonal amplitude of level `lev`: upstream seed plus the
-// read contributions the AP(K) pivots with base d left in scratch.
-__device__ void diag_reverse_tile(const DiagArgs &a, Smem &s, const TileId &tl, int lev)
-{
-    const DiagShape &sh = a.sh;
-    const unsigned r = tl.rank0 + threadIdx.x;
-    if (r >= tl.count) return;
-    const Dig d = unrank(sh, s, 0, 0, lev, r);
-    const int64_t idx = diag_index(sh, d, 0);
-    double f = 1.0;
-    int fnz = sh.M;
-    for (int i = 0; i < sh.M; ++i) {
-        const int v = d(i);
-        f *= s.fact[v];
-        if (v > 0 && fnz == sh.M) fnz = i;
-    }
-    double2 acc = rscale(a.gprobs[(size_t)tl.circ * sh.n_diag + idx], f);
-    const double2 *sc = a.scratch + (size_t)tl.circ * sh.n_ap;
-    const int kmax = fnz < sh.M ? fnz : sh.M - 1;
-    for (int K = 0; K <= kmax; ++K)
-        if (d(K) <= sh.C[K] - 2) acc = cadd(acc, __ldcg(sc + sh.off_ap[K] + box_index(sh, d, K, K, 1, -1, 0)));
-    a.Fbar[(size_t)tl.circ * sh.circ_size + idx] = acc;
-}
-
-// ------------------------------------------------------------------ kernels
-__global__ void __launch_bounds__(TPB) diag_forward_kernel(const __grid_constant__ DiagArgs a)
-{
-    const DiagShape &sh = a.sh;
-    Smem s = carve_smem(sh, false);
-    build_tables(sh, s);
-    prologue(a, true);
-    if (!grid_sync(a.ctl, gridDim.x, a.timeout_ns)) return;
-    const int hb = *(volatile int *)&a.ctl->has_b;
-    if (hb && !sh.has_b) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&a.ctl->status, 0, (int)FK_EBZERO);
-        return;
-    }
-    for (int lev = 0; lev < sh.L; ++lev) {
-        if (hb) {
-            const int nt = phase_tiles(a, s, 1, lev);
-            for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
-                const TileId tl = decode_tile(a, s, 1, lev, tile);
-                dp_forward_tile(a, s, tl, lev);
+    // ------------------------------------------------- reverse-walk reductions
+    // Accumulate sum_t Y[w][t] conj(R[j][t]) into the block's partial dL/dA and
+    // sum_t Y[w][t] conj(FP[t]) into its partial dL/db (rows/cols from 2*k0).
+    static __device__ void reduce_partials(const DiagArgs &a, Smem &s, int circ, int k0, int N, bool hasb,
+                                    unsigned wm, unsigned jm)
+    {
+        __shared__ unsigned s_m[2];
+        if (threadIdx.x == 0) s_m[0] = s_m[1] = 0u;
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) {   // wm, jm arrive OR-reduced over each warp
+            atomicOr(&s_m[0], wm);
+            atomicOr(&s_m[1], jm);
+        }
+        __syncthreads();
+        wm = s_m[0];
+        jm = s_m[1];
+        const int D = 2 * a.sh.M;
+        double2 *pA = a.partA + ((size_t)circ * a.grid + blockIdx.x) * D * D;
+        for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+            const int w = e / N, j = e % N;
+            if (!((wm >> w) & 1u) || !((jm >> j) & 1u)) continue;
+            double2 acc = make_double2(0, 0);
+            for (int tt = 0; tt < TPB; ++tt) acc = cfma_conj(s.R[j * RS + tt], s.Y[w * RS + tt], acc);
+            double2 &dst = pA[(size_t)(2 * k0 + w) * D + 2 * k0 + j];
+            dst = cadd(dst, acc);
+        }
+        if (hasb) {
+            double2 *pb = a.partb + ((size_t)circ * a.grid + blockIdx.x) * D;
+            for (int w = threadIdx.x; w < N; w += blockDim.x) {
+                if (!((wm >> w) & 1u)) continue;
+                double2 acc = make_double2(0, 0);
+                for (int tt = 0; tt < TPB; ++tt) acc = cfma_conj(s.FP[tt], s.Y[w * RS + tt], acc);
+                pb[2 * k0 + w] = cadd(pb[2 * k0 + w], acc);
             }
-            if (!grid_sync(a.ctl, gridDim.x, a.timeout_ns)) return;
         }
-        const int nt = phase_tiles(a, s, 0, lev);
-        for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
-            const TileId tl = decode_tile(a, s, 0, lev, tile);
-            if (hb) ap_forward_tile<true>(a, s, tl, tl.seg, lev);
-            else ap_forward_tile<false>(a, s, tl, tl.seg, lev);
-        }
-        if (lev + 1 < sh.L && !grid_sync(a.ctl, gridDim.x, a.timeout_ns)) return;
+        __syncthreads();
     }
-}
 
-__global__ void __launch_bounds__(TPB) diag_vjp_kernel(const __grid_constant__ DiagArgs a)
-{
-    const DiagShape &sh = a.sh;
-    Smem s = carve_smem(sh, true);
-    build_tables(sh, s);
-    prologue(a, false);
-    if (!grid_sync(a.ctl, gridDim.x, a.timeout_ns)) return;
-    const int hb = *(volatile int *)&a.ctl->has_b;
-    if (hb && !sh.has_b) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&a.ctl->status, 0, (int)FK_EBZERO);
-        return;
+    // --------------------------------------------------------- reverse AP
+    template <bool HASB>
+    static __device__ void ap_reverse_tile(const DiagArgs &a, Smem &s, const TileId &tl, int K, int lev)
+    {
+        const DiagShape &sh = a.sh;
+        const int t = threadIdx.x, D = 2 * sh.M, N = 2 * (sh.M - K);
+        load_circuit(a, s, tl.circ);
+        const double2 *F = a.F + (size_t)tl.circ * sh.circ_size;
+        double2 *Fb = a.Fbar + (size_t)tl.circ * sh.circ_size;
+        const unsigned r = tl.rank0 + t;
+        const bool act = r < tl.count;
+        Dig e;
+        ApGeom g{};
+        if (act) {
+            e = unrank(sh, s, K, 1, lev, r);
+            g = ap_geom(sh, e, K, s, HASB);
+            for (int j = 0; j < N; ++j) {
+                double2 v = make_double2(0, 0);
+                if ((g.vmask >> j) & 1u) v = __ldcg(F + ap_read_addr(sh, g, K, j, s));
+                s.R[j * RS + t] = v;
+            }
+            for (int i = 0; i < N; ++i) {
+                double2 v = make_double2(0, 0);
+                if ((g.nmask >> i) & 1u) {
+                    int den;
+                    const int64_t addr = ap_write_addr(sh, g, e, K, i, s, &den);
+                    v = rscale(__ldcg(Fb + addr), s.inv[den]);
+                }
+                s.Y[i * RS + t] = v;
+            }
+            s.FP[t] = HASB ? __ldcg(F + sh.off_t1k[K] + g.t1k) : make_double2(0, 0);
+        } else {
+            for (int j = 0; j < N; ++j) {
+                s.R[j * RS + t] = make_double2(0, 0);
+                s.Y[j * RS + t] = make_double2(0, 0);
+            }
+            s.FP[t] = make_double2(0, 0);
+        }
+        const unsigned vm = __reduce_or_sync(0xffffffffu, g.vmask);
+        const unsigned nm = __reduce_or_sync(0xffffffffu, g.nmask);
+        const double2 *Ab = s.As + (size_t)(2 * K) * D + 2 * K;
+        // adjoint of the reads: Rbar_j = sum_i conj(A_{w_i l_j}) Y_i
+        for (int j0 = 0; j0 < N; j0 += CH) {
+            if (((vm >> j0) & ((1u << CH) - 1u)) == 0) continue;
+            double2 acc[CH];
+    #pragma unroll
+            for (int jj = 0; jj < CH; ++jj) acc[jj] = make_double2(0, 0);
+            for (int i = 0; i < N; ++i) {
+                if (!((nm >> i) & 1u)) continue;
+                const double2 y = s.Y[i * RS + t];
+    #pragma unroll
+                for (int jj = 0; jj < CH; ++jj)
+                    if (j0 + jj < N && ((vm >> (j0 + jj)) & 1u))
+                        acc[jj] = cfma_conj(Ab[(size_t)i * D + j0 + jj], y, acc[jj]);
+            }
+    #pragma unroll
+            for (int jj = 0; jj < CH; ++jj) {
+                const int j = j0 + jj;
+                if (j < N && act && ((g.vmask >> j) & 1u)) {
+                    if (j == 0) {
+                        const int64_t ia = box_index(sh, e, K, K, 1, -1, 0);
+                        a.scratch[(size_t)tl.circ * sh.n_ap + sh.off_ap[K] + ia] = acc[jj];
+                    } else {
+                        const int64_t addr = ap_read_addr(sh, g, K, j, s);
+                        Fb[addr] = cadd(__ldcg(Fb + addr), acc[jj]);
+                    }
+                }
+            }
+        }
+        if (HASB && act) {
+            double2 fpb = make_double2(0, 0);
+            for (int i = 0; i < N; ++i)
+                if ((g.nmask >> i) & 1u) fpb = cfma_conj(s.bs[2 * K + i], s.Y[i * RS + t], fpb);
+            const int64_t addr = sh.off_t1k[K] + g.t1k;
+            Fb[addr] = cadd(__ldcg(Fb + addr), fpb);
+        }
+        reduce_partials(a, s, tl.circ, K, N, HASB, nm, vm);
     }
-    for (int lev = sh.L; lev >= 0; --lev) {
-        if (lev < sh.L) {
+
+    // --------------------------------------------------------- reverse DP
+    static __device__ void dp_reverse_tile(const DiagArgs &a, Smem &s, const TileId &tl, int lev)
+    {
+        const DiagShape &sh = a.sh;
+        const int t = threadIdx.x, D = 2 * sh.M, N = D;
+        load_circuit(a, s, tl.circ);
+        const double2 *F = a.F + (size_t)tl.circ * sh.circ_size;
+        double2 *Fb = a.Fbar + (size_t)tl.circ * sh.circ_size;
+        const unsigned r = tl.rank0 + t;
+        const bool act = r < tl.count;
+        Dig d;
+        DpGeom g{};
+        if (act) {
+            d = unrank(sh, s, 0, 1, lev, r);
+            g = dp_geom(sh, d, s);
+            for (int j = 0; j < N; ++j) {
+                double2 v = make_double2(0, 0);
+                if ((g.vmask >> j) & 1u) v = __ldcg(F + dp_read_addr(sh, g, j, s));
+                s.R[j * RS + t] = v;
+            }
+            for (int i = 0; i < N; ++i) {
+                double2 v = make_double2(0, 0);
+                if ((g.nmask >> i) & 1u) {
+                    int den;
+                    const int64_t addr = dp_write_addr(sh, g, d, i, s, &den);
+                    v = rscale(__ldcg(Fb + addr), s.inv[den]);
+                }
+                s.Y[i * RS + t] = v;
+            }
+            s.FP[t] = __ldcg(F + g.diag);
+        } else {
+            for (int j = 0; j < N; ++j) {
+                s.R[j * RS + t] = make_double2(0, 0);
+                s.Y[j * RS + t] = make_double2(0, 0);
+            }
+            s.FP[t] = make_double2(0, 0);
+        }
+        const unsigned vm = __reduce_or_sync(0xffffffffu, g.vmask);
+        const unsigned nm = __reduce_or_sync(0xffffffffu, g.nmask);
+        for (int j0 = 0; j0 < N; j0 += CH) {
+            if (((vm >> j0) & ((1u << CH) - 1u)) == 0) continue;
+            double2 acc[CH];
+    #pragma unroll
+            for (int jj = 0; jj < CH; ++jj) acc[jj] = make_double2(0, 0);
+            for (int i = 0; i < N; ++i) {
+                if (!((nm >> i) & 1u)) continue;
+                const double2 y = s.Y[i * RS + t];
+    #pragma unroll
+                for (int jj = 0; jj < CH; ++jj)
+                    if (j0 + jj < N && ((vm >> (j0 + jj)) & 1u))
+                        acc[jj] = cfma_conj(s.As[(size_t)i * D + j0 + jj], y, acc[jj]);
+            }
+    #pragma unroll
+            for (int jj = 0; jj < CH; ++jj) {
+                const int j = j0 + jj;
+                if (j < N && act && ((g.vmask >> j) & 1u)) {
+                    const int64_t addr = dp_read_addr(sh, g, j, s);
+                    Fb[addr] = cadd(__ldcg(Fb + addr), acc[jj]);
+                }
+            }
+        }
+        if (act) {
+            double2 fpb = make_double2(0, 0);
+            for (int i = 0; i < N; ++i)
+                if ((g.nmask >> i) & 1u) fpb = cfma_conj(s.bs[i], s.Y[i * RS + t], fpb);
+            Fb[g.diag] = cadd(__ldcg(Fb + g.diag), fpb);
+        }
+        reduce_partials(a, s, tl.circ, 0, N, true, nm, vm);
+    }
+
+    // ------------------------------------------------------ reverse DIAGSUM
+    // Adjoint of every diagonal amplitude of level `lev`: upstream seed plus the
+    // read contributions the AP(K) pivots with base d left in scratch.
+    static __device__ void diag_reverse_tile(const DiagArgs &a, Smem &s, const TileId &tl, int lev)
+    {
+        const DiagShape &sh = a.sh;
+        const unsigned r = tl.rank0 + threadIdx.x;
+        if (r >= tl.count) return;
+        const Dig d = unrank(sh, s, 0, 0, lev, r);
+        const int64_t idx = diag_index(sh, d, 0);
+        double f = 1.0;
+        int fnz = sh.M;
+        for (int i = 0; i < sh.M; ++i) {
+            const int v = d(i);
+            f *= s.fact[v];
+            if (v > 0 && fnz == sh.M) fnz = i;
+        }
+        double2 acc = rscale(a.gprobs[(size_t)tl.circ * sh.n_diag + idx], f);
+        const double2 *sc = a.scratch + (size_t)tl.circ * sh.n_ap;
+        const int kmax = fnz < sh.M ? fnz : sh.M - 1;
+        for (int K = 0; K <= kmax; ++K)
+            if (d(K) <= sh.C[K] - 2) acc = cadd(acc, __ldcg(sc + sh.off_ap[K] + box_index(sh, d, K, K, 1, -1, 0)));
+        a.Fbar[(size_t)tl.circ * sh.circ_size + idx] = acc;
+    }
+
+    // ------------------------------------------------------------------ kernels
+    static __device__ void forward(const DiagArgs &a)
+    {
+        const DiagShape &sh = a.sh;
+        Smem s = carve_smem(sh, false);
+        build_tables(sh, s);
+        prologue(a, true);
+        if (!grid_sync(a.ctl, gridDim.x, a.timeout_ns)) return;
+        const int hb = *(volatile int *)&a.ctl->has_b;
+        if (hb && !sh.has_b) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&a.ctl->status, 0, (int)FK_EBZERO);
+            return;
+        }
+        for (int lev = 0; lev < sh.L; ++lev) {
+            if (hb) {
+                const int nt = phase_tiles(a, s, 1, lev);
+                for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+                    const TileId tl = decode_tile(a, s, 1, lev, tile);
+                    dp_forward_tile(a, s, tl, lev);
+                }
+                if (!grid_sync(a.ctl, gridDim.x, a.timeout_ns)) return;
+            }
             const int nt = phase_tiles(a, s, 0, lev);
             for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
                 const TileId tl = decode_tile(a, s, 0, lev, tile);
-                if (hb) ap_reverse_tile<true>(a, s, tl, tl.seg, lev);
-                else ap_reverse_tile<false>(a, s, tl, tl.seg, lev);
+                if (hb) ap_forward_tile<true>(a, s, tl, tl.seg, lev);
+                else ap_forward_tile<false>(a, s, tl, tl.seg, lev);
             }
-            if (!grid_sync(a.ctl, gridDim.x, a.timeout_ns)) return;
-        }
-        {
-            const int nt = phase_tiles(a, s, 2, lev);
-            for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
-                const TileId tl = decode_tile(a, s, 2, lev, tile);
-                diag_reverse_tile(a, s, tl, lev);
-            }
-            if (!grid_sync(a.ctl, gridDim.x, a.timeout_ns)) return;
-        }
-        if (hb && lev < sh.L) {
-            const int nt = phase_tiles(a, s, 1, lev);
-            for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
-                const TileId tl = decode_tile(a, s, 1, lev, tile);
-                dp_reverse_tile(a, s, tl, lev);
-            }
-            if (!grid_sync(a.ctl, gridDim.x, a.timeout_ns)) return;
+            if (lev + 1 < sh.L && !grid_sync(a.ctl, gridDim.x, a.timeout_ns)) return;
         }
     }
-    // Final reduction of the per-block partials (fixed order -> deterministic),
-    // symmetrisation dL/dA <- (dL/dA + dL/dA^T)/2, scatter to the caller's modes.
-    const int D = 2 * sh.M, Do = sh.D_orig;
-    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t e = gtid; e < (int64_t)a.B * Do * Do; e += gsz) a.gA[e] = make_double2(0, 0);
-    for (int64_t e = gtid; e < (int64_t)a.B * Do; e += gsz) a.gb[e] = make_double2(0, 0);
-    if (!grid_sync(a.ctl, gridDim.x, a.timeout_ns)) return;
-    for (int64_t e = gtid; e < (int64_t)a.B * D * D; e += gsz) {
-        const int c = (int)(e / (D * D));
-        const int w = (int)((e / D) % D), l = (int)(e % D);
-        double2 x = make_double2(0, 0), y = make_double2(0, 0);
-        for (int blk = 0; blk < a.grid; ++blk) {
-            const double2 *pA = a.partA + ((size_t)c * a.grid + blk) * D * D;
-            x = cadd(x, pA[(size_t)w * D + l]);
-            y = cadd(y, pA[(size_t)l * D + w]);
+
+    static __device__ void vjp(const DiagArgs &a)
+    {
+        const DiagShape &sh = a.sh;
+        Smem s = carve_smem(sh, true);
+        build_tables(sh, s);
+        prologue(a, false);
+        if (!grid_sync(a.ctl, gridDim.x, a.timeout_ns)) return;
+        const int hb = *(volatile int *)&a.ctl->has_b;
+        if (hb && !sh.has_b) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&a.ctl->status, 0, (int)FK_EBZERO);
+            return;
         }
-        const int ow = 2 * sh.mode_map[w / 2] + (w & 1), ol = 2 * sh.mode_map[l / 2] + (l & 1);
-        a.gA[(size_t)c * Do * Do + (size_t)ow * Do + ol] = make_double2(0.5 * (x.x + y.x), 0.5 * (x.y + y.y));
+        for (int lev = sh.L; lev >= 0; --lev) {
+            if (lev < sh.L) {
+                const int nt = phase_tiles(a, s, 0, lev);
+                for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+                    const TileId tl = decode_tile(a, s, 0, lev, tile);
+                    if (hb) ap_reverse_tile<true>(a, s, tl, tl.seg, lev);
+                    else ap_reverse_tile<false>(a, s, tl, tl.seg, lev);
+                }
+                if (!grid_sync(a.ctl, gridDim.x, a.timeout_ns)) return;
+            }
+            {
+                const int nt = phase_tiles(a, s, 2, lev);
+                for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+                    const TileId tl = decode_tile(a, s, 2, lev, tile);
+                    diag_reverse_tile(a, s, tl, lev);
+                }
+                if (!grid_sync(a.ctl, gridDim.x, a.timeout_ns)) return;
+            }
+            if (hb && lev < sh.L) {
+                const int nt = phase_tiles(a, s, 1, lev);
+                for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+                    const TileId tl = decode_tile(a, s, 1, lev, tile);
+                    dp_reverse_tile(a, s, tl, lev);
+                }
+                if (!grid_sync(a.ctl, gridDim.x, a.timeout_ns)) return;
+            }
+        }
+        // Final reduction of the per-block partials (fixed order -> deterministic),
+        // symmetrisation dL/dA <- (dL/dA + dL/dA^T)/2, scatter to the caller's modes.
+        const int D = 2 * sh.M, Do = sh.D_orig;
+        const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+        for (int64_t e = gtid; e < (int64_t)a.B * Do * Do; e += gsz) a.gA[e] = make_double2(0, 0);
+        for (int64_t e = gtid; e < (int64_t)a.B * Do; e += gsz) a.gb[e] = make_double2(0, 0);
+        if (!grid_sync(a.ctl, gridDim.x, a.timeout_ns)) return;
+        for (int64_t e = gtid; e < (int64_t)a.B * D * D; e += gsz) {
+            const int c = (int)(e / (D * D));
+            const int w = (int)((e / D) % D), l = (int)(e % D);
+            double2 x = make_double2(0, 0), y = make_double2(0, 0);
+            for (int blk = 0; blk < a.grid; ++blk) {
+                const double2 *pA = a.partA + ((size_t)c * a.grid + blk) * D * D;
+                x = cadd(x, pA[(size_t)w * D + l]);
+                y = cadd(y, pA[(size_t)l * D + w]);
+            }
+            const int ow = 2 * sh.mode_map[w / 2] + (w & 1), ol = 2 * sh.mode_map[l / 2] + (l & 1);
+            a.gA[(size_t)c * Do * Do + (size_t)ow * Do + ol] = make_double2(0.5 * (x.x + y.x), 0.5 * (x.y + y.y));
+        }
+        for (int64_t e = gtid; e < (int64_t)a.B * D; e += gsz) {
+            const int c = (int)(e / D), w = (int)(e % D);
+            double2 x = make_double2(0, 0);
+            for (int blk = 0; blk < a.grid; ++blk) x = cadd(x, a.partb[((size_t)c * a.grid + blk) * D + w]);
+            const int ow = 2 * sh.mode_map[w / 2] + (w & 1);
+            a.gb[(size_t)c * Do + ow] = x;
+        }
+        for (int64_t c = gtid; c < a.B; c += gsz) a.gc[c] = a.Fbar[(size_t)c * sh.circ_size];
     }
-    for (int64_t e = gtid; e < (int64_t)a.B * D; e += gsz) {
-        const int c = (int)(e / D), w = (int)(e % D);
-        double2 x = make_double2(0, 0);
-        for (int blk = 0; blk < a.grid; ++blk) x = cadd(x, a.partb[((size_t)c * a.grid + blk) * D + w]);
-        const int ow = 2 * sh.mode_map[w / 2] + (w & 1);
-        a.gb[(size_t)c * Do + ow] = x;
-    }
-    for (int64_t c = gtid; c < a.B; c += gsz) a.gc[c] = a.Fbar[(size_t)c * sh.circ_size];
+
+    // Vacuum-only problem (every cutoff is 1): p = c.
+};
+
+template <int TPB, int CH>
+__global__ void __launch_bounds__(TPB) diag_forward_kernel(const __grid_constant__ DiagArgs a)
+{
+    Walk<TPB, CH>::forward(a);
 }
 
-// Vacuum-only problem (every cutoff is 1): p = c.
+template <int TPB, int CH>
+__global__ void __launch_bounds__(TPB) diag_vjp_kernel(const __grid_constant__ DiagArgs a)
+{
+    Walk<TPB, CH>::vjp(a);
+}
+
 __global__ void copy_c_kernel(const double2 *c, double2 *probs, int B, int64_t stride)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -812,28 +833,76 @@ int device_sms(int *sms)
     return FK_OK;
 }
 
+// Compiled tile shapes (pivots per tile, output rows per register chunk).
+struct Variant {
+    int tpb, ch;
+    const void *fwd, *vjp;
+    size_t (*smem)(int, int, bool);
+};
+
+template <int T, int C>
+Variant variant()
+{
+    return Variant{T, C, (const void *)diag_forward_kernel<T, C>, (const void *)diag_vjp_kernel<T, C>,
+                   &Walk<T, C>::smem_bytes};
+}
+
+const Variant kVariants[] = {variant<128, 8>(), variant<128, 4>(), variant<64, 8>(),
+                             variant<64, 4>(), variant<256, 8>()};
+
+std::mutex g_tune_mu;
+int g_tpb = 128, g_ch = 8, g_bps = 0;
+
+const Variant &current_variant(int *bps)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    *bps = g_bps;
+    for (const Variant &v : kVariants)
+        if (v.tpb == g_tpb && v.ch == g_ch) return v;
+    return kVariants[0];
+}
+
 }  // namespace
+
+int set_diag_tuning(int tpb, int ch, int bps)
+{
+    if (tpb == 0 && ch == 0) {
+        tpb = 128;
+        ch = 8;
+    }
+    bool ok = false;
+    for (const Variant &v : kVariants) ok |= (v.tpb == tpb && v.ch == ch);
+    if (!ok || bps < 0 || bps > 32) return FK_EINVAL;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tpb = tpb;
+    g_ch = ch;
+    g_bps = bps;
+    return FK_OK;
+}
 
 int diag_grid_size(const DiagShape &sh, bool vjp, int *grid)
 {
     int sms = 0;
     int rc = device_sms(&sms);
     if (rc) return rc;
-    const size_t smem = smem_bytes(sh.M, sh.L, vjp);
-    const void *fn = vjp ? (const void *)diag_vjp_kernel : (const void *)diag_forward_kernel;
+    int bps = 0;
+    const Variant &v = current_variant(&bps);
+    const size_t smem = v.smem(sh.M, sh.L, vjp);
+    const void *fn = vjp ? v.vjp : v.fwd;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return FK_ECUDA;
     int per = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, TPB, smem) != cudaSuccess) return FK_ECUDA;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, v.tpb, smem) != cudaSuccess) return FK_ECUDA;
     if (per < 1) return FK_EUNSUPPORTED;
+    if (bps > 0 && bps < per) per = bps;
     *grid = per * sms;
     return FK_OK;
 }
 
-static int launch_coop(const void *fn, int grid, size_t smem, DiagArgs *args, cudaStream_t st)
+static int launch_coop(const void *fn, int grid, int tpb, size_t smem, DiagArgs *args, cudaStream_t st)
 {
     void *params[] = {args};
-    cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(TPB), params, smem, st);
+    cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(tpb), params, smem, st);
     return e == cudaSuccess ? FK_OK : FK_ECUDA;
 }
 
@@ -872,7 +941,9 @@ int launch_diag_forward(const DiagShape &sh, int batch, unsigned flags, const vo
     int rc = diag_grid_size(sh, false, &grid);
     if (rc) return rc;
     a.grid = grid;
-    return launch_coop((const void *)diag_forward_kernel, grid, smem_bytes(sh.M, sh.L, false), &a, st);
+    int bps = 0;
+    const Variant &v = current_variant(&bps);
+    return launch_coop(v.fwd, grid, v.tpb, v.smem(sh.M, sh.L, false), &a, st);
 }
 
 int launch_diag_vjp(const DiagShape &sh, int batch, unsigned flags, const void *A, const void *b,
@@ -900,7 +971,13 @@ int launch_diag_vjp(const DiagShape &sh, int batch, unsigned flags, const void *
     a.gb = (double2 *)gb;
     a.gc = (double2 *)gc;
     a.grid = lay.grid_vjp;
-    return launch_coop((const void *)diag_vjp_kernel, lay.grid_vjp, smem_bytes(sh.M, sh.L, true), &a, st);
+    int bps = 0;
+    const Variant &v = current_variant(&bps);
+    int grid = 0;
+    int rc = diag_grid_size(sh, true, &grid);
+    if (rc) return rc;
+    if (grid != lay.grid_vjp) return FK_EWORKSPACE;   // tuning changed since the layout was sized
+    return launch_coop(v.vjp, lay.grid_vjp, v.tpb, v.smem(sh.M, sh.L, true), &a, st);
 }
 
 int launch_wait_selftest(void *ws, unsigned long long timeout_ns, void *stream)

@@ -32,7 +32,7 @@ EXPORTS = [
     "fk_conditional_workspace_size", "fock_conditional_dm", "fock_conditional_dm_batched",
     "fock_conditional_dm_vjp", "fock_conditional_dm_vjp_batched",
     "fk_circuit_triple", "fk_mlp_sizes", "fk_mlp_load", "fk_mlp_forward", "fk_mlp_backward", "fk_mlp_train_step",
-    "fk_herald_scores",
+    "fk_herald_scores", "fk_diag_set_tuning",
 ]
 
 
@@ -78,6 +78,7 @@ def lib():
         L.fk_describe_diag_schedule.argtypes = [I, P, U, P, I]
         L.fk_measure_fp64_fma_rate.argtypes = [P, Z, ctypes.POINTER(ctypes.c_double), P]
         L.fock_diag_probs_static.argtypes = [I, P, P, P, I, P, P, U, P, ctypes.POINTER(I)]
+        L.fk_diag_set_tuning.argtypes = [I, I, I]
         L.fk_herald_scores.argtypes = [I, P, P, I, P, ctypes.c_double, P, P, P, P]
         L.fk_circuit_triple.argtypes = [I, P, ctypes.c_double, P, P, P, P, P, P]
         L.fk_conditional_workspace_size.argtypes = [I, I, P, P, I, U, ctypes.POINTER(Z), P]
@@ -336,3 +337,7 @@ def fock_conditional_dm_vjp_batched(A, b, c, cutoffs, mask, grad_rho, ws, flags=
                                                flags, _ptr(ws), ws.numel(), _stream(stream))
     _check(st, "fock_conditional_dm_vjp_batched")
     return gA, gb, gc
+
+
+def fk_diag_set_tuning(tpb=0, ch=0, blocks_per_sm=0):
+    _check(lib().fk_diag_set_tuning(int(tpb), int(ch), int(blocks_per_sm)), "fk_diag_set_tuning")

@@ -22,7 +22,7 @@ from paper_2303_08879_gb300 import build as pbuild
 from paper_2303_08879_gb300 import inputs
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADERS = [os.path.join(ROOT, "include", h) for h in ("fockdiag.h", "fockdiag_probe.h")]
+HEADERS = [os.path.join(ROOT, "include", h) for h in sorted(os.listdir(os.path.join(ROOT, "include")))]
 
 
 @pytest.fixture(scope="module")

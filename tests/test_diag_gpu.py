@@ -272,3 +272,29 @@ def test_small_workspace_rejected(fd):
     with pytest.raises(fd.FockError) as e:
         fd.fock_diag_probs_batched(Ad, bd, cd, (3, 3), ws=ws)
     assert e.value.status == 3
+
+
+@pytest.mark.parametrize("cand", [(128, 8, 0), (128, 4, 0), (64, 8, 0), (64, 4, 0), (256, 8, 0),
+                                  (128, 8, 2), (64, 8, 4)])
+def test_every_tile_shape_matches_oracle(fd, cand):
+    """Each compiled tile shape the autotuner may pick gives the oracle's
+    probabilities and gradients (b != 0 and b = 0, several tiles per level)."""
+    try:
+        fd.fk_diag_set_tuning(*cand)
+        rng = np.random.default_rng(77)
+        for cut, withb in (((7, 5, 6, 4), True), ((5, 5, 5, 5, 4), False)):
+            A, b = inputs.random_symmetric(2 * len(cut), rng, scale=0.15, with_b=withb)
+            ref = oracle.Walk(A, b, 0.7, cut).all_probs()
+            got, (Ad, bd, cd, ws) = gpu_probs(fd, A, b, 0.7, cut)
+            assert_amp_close(got[0], ref)
+        cut = (4, 3, 3)
+        A, b = inputs.random_symmetric(6, rng)
+        gbar = rng.normal(size=cut) + 1j * rng.normal(size=cut)
+        rA, rb, rc = oracle_vjp(A, b, 0.8, cut, gbar)
+        _, (Ad, bd, cd, ws) = gpu_probs(fd, A, b, 0.8, cut)
+        gA, gb, gc = fd.fock_diag_probs_vjp_batched(Ad, bd, cd, cut, cuda(gbar[None]), ws)
+        fd.check_workspace(ws)
+        assert_grad_close(gA[0].cpu().numpy(), rA, "grad_A")
+        assert_grad_close(gb[0].cpu().numpy(), rb, "grad_b")
+    finally:
+        fd.fk_diag_set_tuning(0, 0, 0)
