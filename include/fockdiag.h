@@ -120,6 +120,12 @@ int fk_circuit_triple(int M, const double *host_theta, double eta, fk_c128 *host
                       fk_c128 *host_b, fk_c128 *host_c, fk_c128 *host_dA, fk_c128 *host_db,
                       fk_c128 *host_dc);
 
+/* The same for n parameter rows host_theta[n][M^2 + 2M] (outputs stacked
+ * along a leading n axis), on `threads` host threads (0 = all cores). */
+int fk_circuit_triple_batched(int n, int M, const double *host_theta, double eta,
+                              fk_c128 *host_A, fk_c128 *host_b, fk_c128 *host_c, fk_c128 *host_dA,
+                              fk_c128 *host_db, fk_c128 *host_dc, int threads);
+
 /*
  * Workspace bytes for `op` on `batch` circuits of one shape (M cutoffs,
  * detected_mask; the mask is ignored by the DIAG ops and required by the COND

@@ -20,6 +20,7 @@
 #include <cmath>
 #include <complex>
 #include <cstring>
+#include <thread>
 #include <vector>
 
 #include "fk_internal.h"
@@ -324,4 +325,33 @@ extern "C" int fk_circuit_triple(int M, const double *theta, double eta, fk_c128
     } catch (...) {
         return FK_ENOMEM;
     }
+}
+
+extern "C" int fk_circuit_triple_batched(int n, int M, const double *theta, double eta, fk_c128 *A,
+                                         fk_c128 *b, fk_c128 *c, fk_c128 *dA, fk_c128 *db,
+                                         fk_c128 *dc, int threads)
+{
+    if (n < 1 || M < 1 || M > 16 || !theta || !A || !b || !c) return FK_EINVAL;
+    const int D = 2 * M, P = M * M + 2 * M;
+    if (threads < 1) threads = (int)std::thread::hardware_concurrency();
+    if (threads < 1) threads = 1;
+    if (threads > n) threads = n;
+    std::vector<int> status(threads, FK_OK);
+    auto work = [&](int t) {
+        for (int i = t; i < n; i += threads) {
+            const int rc = fk_circuit_triple(M, theta + (size_t)i * P, eta, A + (size_t)i * D * D,
+                                             b + (size_t)i * D, c + i,
+                                             dA ? dA + (size_t)i * P * D * D : nullptr,
+                                             db ? db + (size_t)i * P * D : nullptr,
+                                             dc ? dc + (size_t)i * P : nullptr);
+            if (rc) { status[t] = rc; return; }
+        }
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < threads; ++t) pool.emplace_back(work, t);
+    work(0);
+    for (auto &th : pool) th.join();
+    for (int rc : status)
+        if (rc) return rc;
+    return FK_OK;
 }

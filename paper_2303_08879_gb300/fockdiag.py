@@ -31,7 +31,7 @@ EXPORTS = [
     "fk_describe_diag_schedule", "fk_measure_fp64_fma_rate", "fock_diag_probs_static",
     "fk_conditional_workspace_size", "fock_conditional_dm", "fock_conditional_dm_batched",
     "fock_conditional_dm_vjp", "fock_conditional_dm_vjp_batched",
-    "fk_circuit_triple", "fk_mlp_sizes", "fk_mlp_load", "fk_mlp_forward", "fk_mlp_backward", "fk_mlp_train_step",
+    "fk_circuit_triple", "fk_circuit_triple_batched", "fk_mlp_sizes", "fk_mlp_load", "fk_mlp_forward", "fk_mlp_backward", "fk_mlp_train_step",
     "fk_herald_scores", "fk_diag_set_tuning",
 ]
 
@@ -81,6 +81,7 @@ def lib():
         L.fk_diag_set_tuning.argtypes = [I, I, I]
         L.fk_herald_scores.argtypes = [I, P, P, I, P, ctypes.c_double, P, P, P, P]
         L.fk_circuit_triple.argtypes = [I, P, ctypes.c_double, P, P, P, P, P, P]
+        L.fk_circuit_triple_batched.argtypes = [I, I, P, ctypes.c_double, P, P, P, P, P, P, I]
         L.fk_conditional_workspace_size.argtypes = [I, I, P, P, I, U, ctypes.POINTER(Z), P]
         L.fock_conditional_dm.argtypes = [P, P, P, I, P, P, P, P, Z, P]
         L.fock_conditional_dm_batched.argtypes = [I, P, P, P, I, P, P, P, U, P, Z, P]
@@ -153,6 +154,26 @@ def fk_circuit_triple(theta, eta, M=3, jacobian=False):
     if jacobian:
         return A, b, complex(c[0]), dA, db, dc
     return A, b, complex(c[0])
+
+
+def fk_circuit_triple_batched(theta, eta, M=3, jacobian=False, threads=0):
+    """Stacked (A, b, c[, dA, db, dc]) for parameter rows theta [n, M^2 + 2M]."""
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    n, P = th.shape
+    D = 2 * M
+    assert P == M * M + 2 * M
+    A = np.zeros((n, D, D), np.complex128); b = np.zeros((n, D), np.complex128)
+    c = np.zeros(n, np.complex128)
+    if jacobian:
+        dA = np.zeros((n, P, D, D), np.complex128); db = np.zeros((n, P, D), np.complex128)
+        dc = np.zeros((n, P), np.complex128)
+        ptrs = (dA.ctypes.data, db.ctypes.data, dc.ctypes.data)
+    else:
+        ptrs = (None, None, None)
+    st = lib().fk_circuit_triple_batched(n, M, th.ctypes.data, float(eta), A.ctypes.data,
+                                         b.ctypes.data, c.ctypes.data, *ptrs, int(threads))
+    _check(st, "fk_circuit_triple_batched")
+    return (A, b, c, dA, db, dc) if jacobian else (A, b, c)
 
 
 def fk_workspace_size(M, cutoffs, batch=1, op=FK_OP_DIAG, flags=0, detected_mask=None):
