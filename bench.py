@@ -42,8 +42,10 @@ NCIRC = 16
 # with ncu on a 2-circuit launch (9.990 GB read + 1.553 GB written) and scaled
 # by 8: circuits share no data, so traffic grows in proportion to them.  Valid
 # only for the kernel source it was measured on (sha256 prefix of
-# csrc/walk_diag.cu); reported as null once the kernel changes.
-TRAFFIC = {"kernel_sha": "bbee46fa125744b9", "bytes_per_launch": 8 * (9.990473e9 + 1.552535e9)}
+# csrc/walk_diag.cu) and tile shape (pivots per tile / rows per chunk /
+# blocks-per-SM cap); reported as null once either differs.
+TRAFFIC = {"kernel_sha": "bbee46fa125744b9", "tuning": None,
+           "bytes_per_launch": 8 * (9.990473e9 + 1.552535e9)}
 
 
 def kernel_sha():
@@ -243,7 +245,12 @@ def run_gpu(args):
     probs = torch.empty((NCIRC,) + cut, dtype=torch.complex128, device=dev)
     gA, gb, gc = torch.empty_like(A), torch.empty_like(b), torch.empty_like(c)
     tuning = None
-    if not args.no_autotune:
+    if args.tuning:
+        best = tuple(int(v) for v in args.tuning.split("/"))
+        fd.fk_diag_set_tuning(*best)
+        tuning = {"tile_pivots": best[0], "chunk_rows": best[1], "blocks_per_sm_cap": best[2],
+                  "ms_per_candidate": None}
+    elif not args.no_autotune:
         from paper_2303_08879_gb300 import autotune
         best, times = autotune.tune_diag(A, b, c, cut, w, flags=flags)
         tuning = {"tile_pivots": best[0], "chunk_rows": best[1], "blocks_per_sm_cap": best[2],
@@ -321,7 +328,10 @@ def run_gpu(args):
         peak, peaks = measure_fp64_peak(torch)
         achieved = flops_vjp / (vjp_ms * 1e-3) / 1e12
         sha = kernel_sha()
-        traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["kernel_sha"] == sha else None
+        shape = None if tuning is None else [tuning["tile_pivots"], tuning["chunk_rows"],
+                                             tuning["blocks_per_sm_cap"]]
+        traffic = (TRAFFIC["bytes_per_launch"]
+                   if TRAFFIC["kernel_sha"] == sha and TRAFFIC["tuning"] == shape else None)
         out = {
             "metric": METRIC, "value": amps / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -363,6 +373,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tuning", default=None,
+                    help="fixed tile shape 'pivots/rows/cap' instead of the autotuner")
     ap.add_argument("--circuits", type=int, default=NCIRC,
                     help="circuits per GPU (default 16; smaller only for profiler captures)")
     args = ap.parse_args()

@@ -56,10 +56,10 @@ struct Smem {
     int Wn;           // row length
     double *inv;      // 1/v
     double *fact;     // v!
-    double2 *As;      // D x D of the tile's circuit
+    double *A3;       // [3][D][D]: Re A, Re A + Im A, Im A - Re A of the tile's circuit
     double2 *bs;      // D
-    double2 *R;       // [D][RS] forward reads per pivot
-    double2 *Y;       // [D][RS] scaled output adjoints per pivot (VJP)
+    double *R3;       // [3][D][RS] reads per pivot (three planes, see store_read)
+    double *Y3;       // [3][D][RS] scaled output adjoints per pivot (VJP)
     double2 *FP;      // [RS] pivot values (VJP, b != 0)
     int *idx;         // [M][TPB] box indices per pivot
     int *tiles;       // [M + 2] tile prefix sums of the current phase
@@ -102,9 +102,10 @@ struct Walk {
         n += (size_t)(M + 1) * (L + 2) * sizeof(unsigned);
         n = (n + 15) & ~(size_t)15;
         n += 2 * TABN * sizeof(double);
-        n += (size_t)D * D * sizeof(double2) + (size_t)D * sizeof(double2);
-        n += (size_t)D * RS * sizeof(double2);
-        if (vjp) n += (size_t)D * RS * sizeof(double2) + RS * sizeof(double2);
+        n += 3 * (size_t)D * D * sizeof(double) + (size_t)D * sizeof(double2);
+        n += 3 * (size_t)D * RS * sizeof(double);
+        if (vjp) n += 3 * (size_t)D * RS * sizeof(double) + RS * sizeof(double2);
+        n = (n + 15) & ~(size_t)15;
         n += (size_t)M * TPB * sizeof(int) + (M + 2) * sizeof(int);
         return n + 64;
     }
@@ -121,16 +122,17 @@ struct Walk {
         p = (unsigned char *)(((uintptr_t)p + 15) & ~(uintptr_t)15);
         s.inv = (double *)p; p += TABN * sizeof(double);
         s.fact = (double *)p; p += TABN * sizeof(double);
-        s.As = (double2 *)p; p += (size_t)D * D * sizeof(double2);
+        s.A3 = (double *)p; p += 3 * (size_t)D * D * sizeof(double);
         s.bs = (double2 *)p; p += (size_t)D * sizeof(double2);
-        s.R = (double2 *)p; p += (size_t)D * RS * sizeof(double2);
+        s.R3 = (double *)p; p += 3 * (size_t)D * RS * sizeof(double);
         if (vjp) {
-            s.Y = (double2 *)p; p += (size_t)D * RS * sizeof(double2);
+            s.Y3 = (double *)p; p += 3 * (size_t)D * RS * sizeof(double);
             s.FP = (double2 *)p; p += RS * sizeof(double2);
         } else {
-            s.Y = nullptr;
+            s.Y3 = nullptr;
             s.FP = nullptr;
         }
+        p = (unsigned char *)(((uintptr_t)p + 15) & ~(uintptr_t)15);
         s.idx = (int *)p; p += (size_t)M * TPB * sizeof(int);
         s.tiles = (int *)p;
         s.loaded_circ = -1;
@@ -167,16 +169,124 @@ struct Walk {
     }
 
     // Load A_s (symmetric part, kept modes) and b of one circuit into smem.
+    // A is kept as three real planes for Gauss's three-multiplication complex
+    // product: Re A, Re A + Im A and Im A - Re A.
     static __device__ void load_circuit(const DiagArgs &a, Smem &s, int circ)
     {
         if (s.loaded_circ == circ) return;
         __syncthreads();
-        const int D = 2 * a.sh.M;
-        const double2 *As = a.As + (size_t)circ * D * D;
-        for (int e = threadIdx.x; e < D * D; e += blockDim.x) s.As[e] = As[e];
+        const int D = 2 * a.sh.M, DD = D * D;
+        const double2 *As = a.As + (size_t)circ * DD;
+        for (int e = threadIdx.x; e < DD; e += blockDim.x) {
+            const double2 v = As[e];
+            s.A3[e] = v.x;
+            s.A3[DD + e] = v.x + v.y;
+            s.A3[2 * DD + e] = v.y - v.x;
+        }
         for (int e = threadIdx.x; e < D; e += blockDim.x) s.bs[e] = a.bs[(size_t)circ * D + e];
         __syncthreads();
         s.loaded_circ = circ;
+    }
+
+    // Three planes of a read x: forward (Re x, Im x, Re x + Im x); reverse
+    // (Re x, Re x - Im x, Re x + Im x).
+    static __device__ __forceinline__ void store_read(Smem &s, int D, int j, int t, double2 x,
+                                                      bool reverse)
+    {
+        s.R3[(size_t)j * RS + t] = x.x;
+        s.R3[(size_t)(D + j) * RS + t] = reverse ? x.x - x.y : x.y;
+        s.R3[(size_t)(2 * D + j) * RS + t] = x.x + x.y;
+    }
+
+    // Three planes of a scaled output adjoint y: (Re y, Im y, Re y + Im y).
+    static __device__ __forceinline__ void store_adj(Smem &s, int D, int i, int t, double2 y)
+    {
+        s.Y3[(size_t)i * RS + t] = y.x;
+        s.Y3[(size_t)(D + i) * RS + t] = y.y;
+        s.Y3[(size_t)(2 * D + i) * RS + t] = y.x + y.y;
+    }
+
+    static __device__ __forceinline__ double2 load_adj(const Smem &s, int D, int i, int t)
+    {
+        return make_double2(s.Y3[(size_t)i * RS + t], s.Y3[(size_t)(D + i) * RS + t]);
+    }
+
+    // Rows row0 + i (i in [0, N)) of A x for this thread's reads, CH rows at a
+    // time: with x = xr + i xi and s = xr + xi,
+    //   Re = sum Ar s - sum (Ar + Ai) xi,  Im = sum Ar s + sum (Ai - Ar) xr,
+    // three DFMA per complex term.  `emit(i, value)` receives each row.
+    template <bool HASB, class Emit>
+    static __device__ __forceinline__ void matvec(const Smem &s, int D, int row0, int N,
+                                                  unsigned vm, unsigned nm, double2 pv, Emit emit)
+    {
+        const int t = threadIdx.x, DD = D * D;
+        const double *Ar = s.A3 + (size_t)row0 * D + row0;
+        const double *Ap = Ar + DD, *Am = Ar + 2 * DD;
+        for (int i0 = 0; i0 < N; i0 += CH) {
+            if (((nm >> i0) & ((1u << CH) - 1u)) == 0) continue;
+            double p1[CH], p2[CH], p3[CH];
+#pragma unroll
+            for (int ii = 0; ii < CH; ++ii) p1[ii] = p2[ii] = p3[ii] = 0.0;
+            for (int j = 0; j < N; ++j) {
+                if (!((vm >> j) & 1u)) continue;
+                const double xr = s.R3[(size_t)j * RS + t];
+                const double xi = s.R3[(size_t)(D + j) * RS + t];
+                const double xs = s.R3[(size_t)(2 * D + j) * RS + t];
+#pragma unroll
+                for (int ii = 0; ii < CH; ++ii)
+                    if (i0 + ii < N && ((nm >> (i0 + ii)) & 1u)) {
+                        const size_t o = (size_t)(i0 + ii) * D + j;
+                        p1[ii] = fma(Ar[o], xs, p1[ii]);
+                        p2[ii] = fma(Ap[o], xi, p2[ii]);
+                        p3[ii] = fma(Am[o], xr, p3[ii]);
+                    }
+            }
+#pragma unroll
+            for (int ii = 0; ii < CH; ++ii) {
+                const int i = i0 + ii;
+                if (i < N && ((nm >> i) & 1u)) {
+                    double2 v = make_double2(p1[ii] - p2[ii], p1[ii] + p3[ii]);
+                    if (HASB) v = cadd(v, cmul(s.bs[row0 + i], pv));
+                    emit(i, v);
+                }
+            }
+        }
+    }
+
+    // Columns row0 + j of A^H y for this thread's scaled output adjoints:
+    //   Re = sum Ar ys + sum (Ai - Ar) yi,  Im = sum Ar ys - sum (Ar + Ai) yr.
+    template <class Emit>
+    static __device__ __forceinline__ void matvec_adj(const Smem &s, int D, int row0, int N,
+                                                      unsigned vm, unsigned nm, Emit emit)
+    {
+        const int t = threadIdx.x, DD = D * D;
+        const double *Ar = s.A3 + (size_t)row0 * D + row0;
+        const double *Ap = Ar + DD, *Am = Ar + 2 * DD;
+        for (int j0 = 0; j0 < N; j0 += CH) {
+            if (((vm >> j0) & ((1u << CH) - 1u)) == 0) continue;
+            double p1[CH], q2[CH], q3[CH];
+#pragma unroll
+            for (int jj = 0; jj < CH; ++jj) p1[jj] = q2[jj] = q3[jj] = 0.0;
+            for (int i = 0; i < N; ++i) {
+                if (!((nm >> i) & 1u)) continue;
+                const double yr = s.Y3[(size_t)i * RS + t];
+                const double yi = s.Y3[(size_t)(D + i) * RS + t];
+                const double ys = s.Y3[(size_t)(2 * D + i) * RS + t];
+#pragma unroll
+                for (int jj = 0; jj < CH; ++jj)
+                    if (j0 + jj < N && ((vm >> (j0 + jj)) & 1u)) {
+                        const size_t o = (size_t)i * D + j0 + jj;
+                        p1[jj] = fma(Ar[o], ys, p1[jj]);
+                        q2[jj] = fma(Am[o], yi, q2[jj]);
+                        q3[jj] = fma(Ap[o], yr, q3[jj]);
+                    }
+            }
+#pragma unroll
+            for (int jj = 0; jj < CH; ++jj) {
+                const int j = j0 + jj;
+                if (j < N && ((vm >> j) & 1u)) emit(j, make_double2(p1[jj] + q2[jj], p1[jj] - q3[jj]));
+            }
+        }
     }
 
     // Tile bookkeeping for one phase: segment k (anchor K for AP, 0 for DP and
@@ -364,43 +474,23 @@ struct Walk {
             for (int j = 0; j < N; ++j) {
                 double2 v = make_double2(0, 0);
                 if ((g.vmask >> j) & 1u) v = __ldcg(F + ap_read_addr(sh, g, K, j, s));
-                s.R[j * RS + t] = v;
+                store_read(s, D, j, t, v, false);
             }
             if (HASB) FP = __ldcg(F + sh.off_t1k[K] + g.t1k);
             for (int i = K; i < sh.M; ++i) fe *= s.fact[e(i)];
         } else {
-            for (int j = 0; j < N; ++j) s.R[j * RS + t] = make_double2(0, 0);
+            for (int j = 0; j < N; ++j) store_read(s, D, j, t, make_double2(0, 0), false);
         }
         const unsigned vm = __reduce_or_sync(0xffffffffu, g.vmask);
         const unsigned nm = __reduce_or_sync(0xffffffffu, g.nmask);
-        const double2 *Ab = s.As + (size_t)(2 * K) * D + 2 * K;
-        for (int i0 = 0; i0 < N; i0 += CH) {
-            if (((nm >> i0) & ((1u << CH) - 1u)) == 0) continue;
-            double2 acc[CH];
-    #pragma unroll
-            for (int ii = 0; ii < CH; ++ii)
-                acc[ii] = HASB && (i0 + ii < N) ? cmul(s.bs[2 * K + i0 + ii], FP) : make_double2(0, 0);
-            for (int j = 0; j < N; ++j) {
-                if (!((vm >> j) & 1u)) continue;
-                const double2 x = s.R[j * RS + t];
-    #pragma unroll
-                for (int ii = 0; ii < CH; ++ii)
-                    if (i0 + ii < N && ((nm >> (i0 + ii)) & 1u))
-                        acc[ii] = cfma(Ab[(size_t)(i0 + ii) * D + j], x, acc[ii]);
-            }
-    #pragma unroll
-            for (int ii = 0; ii < CH; ++ii) {
-                const int i = i0 + ii;
-                if (i < N && act && ((g.nmask >> i) & 1u)) {
-                    int den;
-                    const int64_t addr = ap_write_addr(sh, g, e, K, i, s, &den);
-                    const double2 v = rscale(acc[ii], s.inv[den]);
-                    F[addr] = v;
-                    if (i == 1)
-                        a.probs[(size_t)tl.circ * sh.n_diag + addr] = rscale(v, fe * (double)(e(K) + 1));
-                }
-            }
-        }
+        matvec<HASB>(s, D, 2 * K, N, vm, nm, FP, [&](int i, double2 acc) {
+            if (!act || !((g.nmask >> i) & 1u)) return;
+            int den;
+            const int64_t addr = ap_write_addr(sh, g, e, K, i, s, &den);
+            const double2 v = rscale(acc, s.inv[den]);
+            F[addr] = v;
+            if (i == 1) a.probs[(size_t)tl.circ * sh.n_diag + addr] = rscale(v, fe * (double)(e(K) + 1));
+        });
     }
 
     // ------------------------------------------------------------- forward DP
@@ -421,45 +511,30 @@ struct Walk {
             for (int j = 0; j < N; ++j) {
                 double2 v = make_double2(0, 0);
                 if ((g.vmask >> j) & 1u) v = __ldcg(F + dp_read_addr(sh, g, j, s));
-                s.R[j * RS + t] = v;
+                store_read(s, D, j, t, v, false);
             }
             FP = __ldcg(F + g.diag);
         } else {
-            for (int j = 0; j < N; ++j) s.R[j * RS + t] = make_double2(0, 0);
+            for (int j = 0; j < N; ++j) store_read(s, D, j, t, make_double2(0, 0), false);
         }
         const unsigned vm = __reduce_or_sync(0xffffffffu, g.vmask);
         const unsigned nm = __reduce_or_sync(0xffffffffu, g.nmask);
-        for (int i0 = 0; i0 < N; i0 += CH) {
-            if (((nm >> i0) & ((1u << CH) - 1u)) == 0) continue;
-            double2 acc[CH];
-    #pragma unroll
-            for (int ii = 0; ii < CH; ++ii)
-                acc[ii] = (i0 + ii < N) ? cmul(s.bs[i0 + ii], FP) : make_double2(0, 0);
-            for (int j = 0; j < N; ++j) {
-                if (!((vm >> j) & 1u)) continue;
-                const double2 x = s.R[j * RS + t];
-    #pragma unroll
-                for (int ii = 0; ii < CH; ++ii)
-                    if (i0 + ii < N && ((nm >> (i0 + ii)) & 1u))
-                        acc[ii] = cfma(s.As[(size_t)(i0 + ii) * D + j], x, acc[ii]);
-            }
-    #pragma unroll
-            for (int ii = 0; ii < CH; ++ii) {
-                const int i = i0 + ii;
-                if (i < N && act && ((g.nmask >> i) & 1u)) {
-                    int den;
-                    const int64_t addr = dp_write_addr(sh, g, d, i, s, &den);
-                    F[addr] = rscale(acc[ii], s.inv[den]);
-                }
-            }
-        }
+        matvec<true>(s, D, 0, N, vm, nm, FP, [&](int i, double2 acc) {
+            if (!act || !((g.nmask >> i) & 1u)) return;
+            int den;
+            const int64_t addr = dp_write_addr(sh, g, d, i, s, &den);
+            F[addr] = rscale(acc, s.inv[den]);
+        });
     }
 
     // ------------------------------------------------- reverse-walk reductions
     // Accumulate sum_t Y[w][t] conj(R[j][t]) into the block's partial dL/dA and
     // sum_t Y[w][t] conj(FP[t]) into its partial dL/db (rows/cols from 2*k0).
-    static __device__ void reduce_partials(const DiagArgs &a, Smem &s, int circ, int k0, int N, bool hasb,
-                                    unsigned wm, unsigned jm)
+    // With planes y = (yr, yi, yr + yi) and R = (Rr, Rr - Ri, Rr + Ri):
+    //   Re = sum (yr + yi) Rr - sum yi (Rr - Ri),
+    //   Im = sum (yr + yi) Rr - sum yr (Rr + Ri)   (three DFMA per term).
+    static __device__ void reduce_partials(const DiagArgs &a, Smem &s, int circ, int k0, int N,
+                                           bool hasb, unsigned wm, unsigned jm)
     {
         __shared__ unsigned s_m[2];
         if (threadIdx.x == 0) s_m[0] = s_m[1] = 0u;
@@ -476,17 +551,25 @@ struct Walk {
         for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
             const int w = e / N, j = e % N;
             if (!((wm >> w) & 1u) || !((jm >> j) & 1u)) continue;
-            double2 acc = make_double2(0, 0);
-            for (int tt = 0; tt < TPB; ++tt) acc = cfma_conj(s.R[j * RS + tt], s.Y[w * RS + tt], acc);
+            const double *ys = s.Y3 + (size_t)(2 * D + w) * RS, *yi = s.Y3 + (size_t)(D + w) * RS;
+            const double *yr = s.Y3 + (size_t)w * RS;
+            const double *rr = s.R3 + (size_t)j * RS, *rd = s.R3 + (size_t)(D + j) * RS;
+            const double *rp = s.R3 + (size_t)(2 * D + j) * RS;
+            double P = 0.0, Q = 0.0, T = 0.0;
+            for (int tt = 0; tt < TPB; ++tt) {
+                P = fma(ys[tt], rr[tt], P);
+                Q = fma(yi[tt], rd[tt], Q);
+                T = fma(yr[tt], rp[tt], T);
+            }
             double2 &dst = pA[(size_t)(2 * k0 + w) * D + 2 * k0 + j];
-            dst = cadd(dst, acc);
+            dst = cadd(dst, make_double2(P - Q, P - T));
         }
         if (hasb) {
             double2 *pb = a.partb + ((size_t)circ * a.grid + blockIdx.x) * D;
             for (int w = threadIdx.x; w < N; w += blockDim.x) {
                 if (!((wm >> w) & 1u)) continue;
                 double2 acc = make_double2(0, 0);
-                for (int tt = 0; tt < TPB; ++tt) acc = cfma_conj(s.FP[tt], s.Y[w * RS + tt], acc);
+                for (int tt = 0; tt < TPB; ++tt) acc = cfma_conj(s.FP[tt], load_adj(s, D, w, tt), acc);
                 pb[2 * k0 + w] = cadd(pb[2 * k0 + w], acc);
             }
         }
@@ -512,7 +595,7 @@ struct Walk {
             for (int j = 0; j < N; ++j) {
                 double2 v = make_double2(0, 0);
                 if ((g.vmask >> j) & 1u) v = __ldcg(F + ap_read_addr(sh, g, K, j, s));
-                s.R[j * RS + t] = v;
+                store_read(s, D, j, t, v, true);
             }
             for (int i = 0; i < N; ++i) {
                 double2 v = make_double2(0, 0);
@@ -521,51 +604,33 @@ struct Walk {
                     const int64_t addr = ap_write_addr(sh, g, e, K, i, s, &den);
                     v = rscale(__ldcg(Fb + addr), s.inv[den]);
                 }
-                s.Y[i * RS + t] = v;
+                store_adj(s, D, i, t, v);
             }
             s.FP[t] = HASB ? __ldcg(F + sh.off_t1k[K] + g.t1k) : make_double2(0, 0);
         } else {
             for (int j = 0; j < N; ++j) {
-                s.R[j * RS + t] = make_double2(0, 0);
-                s.Y[j * RS + t] = make_double2(0, 0);
+                store_read(s, D, j, t, make_double2(0, 0), true);
+                store_adj(s, D, j, t, make_double2(0, 0));
             }
             s.FP[t] = make_double2(0, 0);
         }
         const unsigned vm = __reduce_or_sync(0xffffffffu, g.vmask);
         const unsigned nm = __reduce_or_sync(0xffffffffu, g.nmask);
-        const double2 *Ab = s.As + (size_t)(2 * K) * D + 2 * K;
         // adjoint of the reads: Rbar_j = sum_i conj(A_{w_i l_j}) Y_i
-        for (int j0 = 0; j0 < N; j0 += CH) {
-            if (((vm >> j0) & ((1u << CH) - 1u)) == 0) continue;
-            double2 acc[CH];
-    #pragma unroll
-            for (int jj = 0; jj < CH; ++jj) acc[jj] = make_double2(0, 0);
-            for (int i = 0; i < N; ++i) {
-                if (!((nm >> i) & 1u)) continue;
-                const double2 y = s.Y[i * RS + t];
-    #pragma unroll
-                for (int jj = 0; jj < CH; ++jj)
-                    if (j0 + jj < N && ((vm >> (j0 + jj)) & 1u))
-                        acc[jj] = cfma_conj(Ab[(size_t)i * D + j0 + jj], y, acc[jj]);
+        matvec_adj(s, D, 2 * K, N, vm, nm, [&](int j, double2 acc) {
+            if (!act || !((g.vmask >> j) & 1u)) return;
+            if (j == 0) {
+                const int64_t ia = box_index(sh, e, K, K, 1, -1, 0);
+                a.scratch[(size_t)tl.circ * sh.n_ap + sh.off_ap[K] + ia] = acc;
+            } else {
+                const int64_t addr = ap_read_addr(sh, g, K, j, s);
+                Fb[addr] = cadd(__ldcg(Fb + addr), acc);
             }
-    #pragma unroll
-            for (int jj = 0; jj < CH; ++jj) {
-                const int j = j0 + jj;
-                if (j < N && act && ((g.vmask >> j) & 1u)) {
-                    if (j == 0) {
-                        const int64_t ia = box_index(sh, e, K, K, 1, -1, 0);
-                        a.scratch[(size_t)tl.circ * sh.n_ap + sh.off_ap[K] + ia] = acc[jj];
-                    } else {
-                        const int64_t addr = ap_read_addr(sh, g, K, j, s);
-                        Fb[addr] = cadd(__ldcg(Fb + addr), acc[jj]);
-                    }
-                }
-            }
-        }
+        });
         if (HASB && act) {
             double2 fpb = make_double2(0, 0);
             for (int i = 0; i < N; ++i)
-                if ((g.nmask >> i) & 1u) fpb = cfma_conj(s.bs[2 * K + i], s.Y[i * RS + t], fpb);
+                if ((g.nmask >> i) & 1u) fpb = cfma_conj(s.bs[2 * K + i], load_adj(s, D, i, t), fpb);
             const int64_t addr = sh.off_t1k[K] + g.t1k;
             Fb[addr] = cadd(__ldcg(Fb + addr), fpb);
         }
@@ -590,7 +655,7 @@ struct Walk {
             for (int j = 0; j < N; ++j) {
                 double2 v = make_double2(0, 0);
                 if ((g.vmask >> j) & 1u) v = __ldcg(F + dp_read_addr(sh, g, j, s));
-                s.R[j * RS + t] = v;
+                store_read(s, D, j, t, v, true);
             }
             for (int i = 0; i < N; ++i) {
                 double2 v = make_double2(0, 0);
@@ -599,44 +664,27 @@ struct Walk {
                     const int64_t addr = dp_write_addr(sh, g, d, i, s, &den);
                     v = rscale(__ldcg(Fb + addr), s.inv[den]);
                 }
-                s.Y[i * RS + t] = v;
+                store_adj(s, D, i, t, v);
             }
             s.FP[t] = __ldcg(F + g.diag);
         } else {
             for (int j = 0; j < N; ++j) {
-                s.R[j * RS + t] = make_double2(0, 0);
-                s.Y[j * RS + t] = make_double2(0, 0);
+                store_read(s, D, j, t, make_double2(0, 0), true);
+                store_adj(s, D, j, t, make_double2(0, 0));
             }
             s.FP[t] = make_double2(0, 0);
         }
         const unsigned vm = __reduce_or_sync(0xffffffffu, g.vmask);
         const unsigned nm = __reduce_or_sync(0xffffffffu, g.nmask);
-        for (int j0 = 0; j0 < N; j0 += CH) {
-            if (((vm >> j0) & ((1u << CH) - 1u)) == 0) continue;
-            double2 acc[CH];
-    #pragma unroll
-            for (int jj = 0; jj < CH; ++jj) acc[jj] = make_double2(0, 0);
-            for (int i = 0; i < N; ++i) {
-                if (!((nm >> i) & 1u)) continue;
-                const double2 y = s.Y[i * RS + t];
-    #pragma unroll
-                for (int jj = 0; jj < CH; ++jj)
-                    if (j0 + jj < N && ((vm >> (j0 + jj)) & 1u))
-                        acc[jj] = cfma_conj(s.As[(size_t)i * D + j0 + jj], y, acc[jj]);
-            }
-    #pragma unroll
-            for (int jj = 0; jj < CH; ++jj) {
-                const int j = j0 + jj;
-                if (j < N && act && ((g.vmask >> j) & 1u)) {
-                    const int64_t addr = dp_read_addr(sh, g, j, s);
-                    Fb[addr] = cadd(__ldcg(Fb + addr), acc[jj]);
-                }
-            }
-        }
+        matvec_adj(s, D, 0, N, vm, nm, [&](int j, double2 acc) {
+            if (!act || !((g.vmask >> j) & 1u)) return;
+            const int64_t addr = dp_read_addr(sh, g, j, s);
+            Fb[addr] = cadd(__ldcg(Fb + addr), acc);
+        });
         if (act) {
             double2 fpb = make_double2(0, 0);
             for (int i = 0; i < N; ++i)
-                if ((g.nmask >> i) & 1u) fpb = cfma_conj(s.bs[i], s.Y[i * RS + t], fpb);
+                if ((g.nmask >> i) & 1u) fpb = cfma_conj(s.bs[i], load_adj(s, D, i, t), fpb);
             Fb[g.diag] = cadd(__ldcg(Fb + g.diag), fpb);
         }
         reduce_partials(a, s, tl.circ, 0, N, true, nm, vm);
