@@ -255,6 +255,26 @@ int fock_diag_probs_static(int batch, const fk_c128 *d_A, const fk_c128 *d_b, co
 int fk_diag_set_tuning(int tpb, int ch, int blocks_per_sm);
 
 /*
+ * Product engine of the all-detected forward walk, process-wide.  Each write
+ * of Algorithm 1 is a row of A (restricted to the pivot's modes) times the
+ * pivot's reads (eq. recrel with F = G / sqrt(k!)).
+ *   FK_ENGINE_FP64:   complex128 DFMA (three real products per term).
+ *   FK_ENGINE_TENSOR: the same sums on the bf16 tensor cores: every value is
+ *     cut to a 56-bit fixed-point integer relative to a power of two shared
+ *     by a row of A or by one pivot's reads, split into seven balanced
+ *     base-256 digits (exact in bf16), and the digit products with digit
+ *     index sum <= 6 are accumulated exactly (integer partial sums below
+ *     2^23 in fp32), recombined in int64 and scaled back with one rounding.
+ *     The error is of the order of 2^-53 times the largest term of a sum,
+ *     like FP64; values below 2^-997 count as zero.  Shapes with M > 8 use
+ *     FP64.  The VJP always runs in FP64.
+ * Returns FK_EINVAL for another value.  Default FK_ENGINE_FP64.
+ */
+#define FK_ENGINE_FP64 0
+#define FK_ENGINE_TENSOR 1
+int fk_diag_set_engine(int engine);
+
+/*
  * Reads the device-side status word of a workspace after the calls queued
  * on `stream` (synchronises the stream).  *status = FK_OK or the first error
  * a kernel recorded; the word is cleared by the next compute call.

@@ -455,6 +455,11 @@ int fk_diag_set_tuning(int tpb, int ch, int blocks_per_sm)
     return set_diag_tuning(tpb, ch, blocks_per_sm);
 }
 
+int fk_diag_set_engine(int engine)
+{
+    return set_diag_engine(engine);
+}
+
 int fk_workspace_status(const void *ws, void *stream, int *status)
 {
     if (!ws || !status) return FK_EINVAL;

@@ -91,6 +91,8 @@ int launch_cond_vjp(const CondPlan &plan, unsigned flags, const void *A, const v
 // Tile shape of the all-detected walk (pivots per tile, output rows per
 // register chunk, blocks per SM; 0 = as many as fit).  Process-wide.
 int set_diag_tuning(int tpb, int ch, int blocks_per_sm);
+// Product engine of the all-detected forward walk (FK_ENGINE_*).  Process-wide.
+int set_diag_engine(int engine);
 
 // Launchers (walk_diag.cu).  All pointers are device pointers.
 int diag_grid_size(const DiagShape &sh, bool vjp, int *grid);

@@ -61,6 +61,11 @@ struct Smem {
     double *R3;       // [3][D][RS] reads per pivot (three planes, see store_read)
     double *Y3;       // [3][D][RS] scaled output adjoints per pivot (VJP)
     double2 *FP;      // [RS] pivot values (VJP, b != 0)
+    uint16_t *Ad;     // tensor-core engine: [7][2D][AS] bf16 digit slices of the real form of A
+    double *sA;       // tensor-core engine: [2D] row scales 2^(e_r - 1048)
+    int *fA;          // tensor-core engine: [2D] row exponent fields e_r
+    double *wb;       // tensor-core engine: per-warp [16 KS][WBS] reads in, products out
+    int AS;           // row stride of Ad (bf16 elements)
     int *idx;         // [M][TPB] box indices per pivot
     int *tiles;       // [M + 2] tile prefix sums of the current phase
     int loaded_circ;
@@ -89,21 +94,47 @@ struct DpGeom {
     unsigned vmask, nmask;
 };
 
+// Row stride (bf16 elements) of a digit slice of the 2D x 2D real form of A:
+// at least 2D, and a word stride of 4 mod 8 so the eight rows one fragment
+// load touches fall in distinct banks.
+__host__ __device__ inline int digit_row_stride(int D2)
+{
+    int w = D2 / 2;
+    w += (12 - w % 8) % 8;
+    return 2 * w;
+}
+
 // The walk for one tile shape: TPB pivots per tile (= threads per block) and
-// CH output rows per register chunk; the autotuner picks the instantiation.
-template <int TPB, int CH>
+// either CH output rows per FP64 register chunk (KS = 0) or, for KS > 0, the
+// tensor-core digit engine with up to 16 KS real rows (M <= 4 KS); the
+// autotuner picks the instantiation.
+template <int TPB, int CH, int KS = 0>
 struct Walk {
     static constexpr int RS = TPB + 1;   // padded row stride of per-thread smem columns
+    static constexpr bool TC = KS > 0;   // forward products on the tensor cores
+    static constexpr int XS = 16 * (KS > 0 ? KS : 1);   // rows of a per-warp buffer
+    static constexpr int WBS = 34;       // column stride (doubles) of a per-warp buffer
+    static constexpr int NDIG = 7;       // base-256 digits per value (Sec. 2.1 accuracy)
 
     static __host__ __device__ size_t smem_bytes(int M, int L, bool vjp)
     {
         const int D = 2 * M;
+        const bool tc = TC && !vjp;
         size_t n = 0;
         n += (size_t)(M + 1) * (L + 2) * sizeof(unsigned);
         n = (n + 15) & ~(size_t)15;
         n += 2 * TABN * sizeof(double);
-        n += 3 * (size_t)D * D * sizeof(double) + (size_t)D * sizeof(double2);
-        n += 3 * (size_t)D * RS * sizeof(double);
+        if (tc) {
+            const int D2 = 2 * D;
+            n += (size_t)D * sizeof(double2);
+            n += (size_t)D2 * (sizeof(double) + sizeof(int));
+            n = (n + 15) & ~(size_t)15;
+            n += (size_t)(TPB / 32) * XS * WBS * sizeof(double);
+            n += (size_t)NDIG * D2 * digit_row_stride(D2) * sizeof(uint16_t);
+        } else {
+            n += 3 * (size_t)D * D * sizeof(double) + (size_t)D * sizeof(double2);
+            n += 3 * (size_t)D * RS * sizeof(double);
+        }
         if (vjp) n += 3 * (size_t)D * RS * sizeof(double) + RS * sizeof(double2);
         n = (n + 15) & ~(size_t)15;
         n += (size_t)M * TPB * sizeof(int) + (M + 2) * sizeof(int);
@@ -122,9 +153,27 @@ struct Walk {
         p = (unsigned char *)(((uintptr_t)p + 15) & ~(uintptr_t)15);
         s.inv = (double *)p; p += TABN * sizeof(double);
         s.fact = (double *)p; p += TABN * sizeof(double);
-        s.A3 = (double *)p; p += 3 * (size_t)D * D * sizeof(double);
-        s.bs = (double2 *)p; p += (size_t)D * sizeof(double2);
-        s.R3 = (double *)p; p += 3 * (size_t)D * RS * sizeof(double);
+        s.Ad = nullptr;
+        s.sA = nullptr;
+        s.fA = nullptr;
+        s.wb = nullptr;
+        s.AS = 0;
+        if (TC && !vjp) {
+            const int D2 = 2 * D;
+            s.A3 = nullptr;
+            s.R3 = nullptr;
+            s.bs = (double2 *)p; p += (size_t)D * sizeof(double2);
+            s.sA = (double *)p; p += (size_t)D2 * sizeof(double);
+            s.fA = (int *)p; p += (size_t)D2 * sizeof(int);
+            p = (unsigned char *)(((uintptr_t)p + 15) & ~(uintptr_t)15);
+            s.wb = (double *)p; p += (size_t)(TPB / 32) * XS * WBS * sizeof(double);
+            s.AS = digit_row_stride(D2);
+            s.Ad = (uint16_t *)p; p += (size_t)NDIG * D2 * s.AS * sizeof(uint16_t);
+        } else {
+            s.A3 = (double *)p; p += 3 * (size_t)D * D * sizeof(double);
+            s.bs = (double2 *)p; p += (size_t)D * sizeof(double2);
+            s.R3 = (double *)p; p += 3 * (size_t)D * RS * sizeof(double);
+        }
         if (vjp) {
             s.Y3 = (double *)p; p += 3 * (size_t)D * RS * sizeof(double);
             s.FP = (double2 *)p; p += RS * sizeof(double2);
@@ -177,6 +226,13 @@ struct Walk {
         __syncthreads();
         const int D = 2 * a.sh.M, DD = D * D;
         const double2 *As = a.As + (size_t)circ * DD;
+        if (TC && s.Ad != nullptr) {
+            load_circuit_digits(s, As, D);
+            for (int e = threadIdx.x; e < D; e += blockDim.x) s.bs[e] = a.bs[(size_t)circ * D + e];
+            __syncthreads();
+            s.loaded_circ = circ;
+            return;
+        }
         for (int e = threadIdx.x; e < DD; e += blockDim.x) {
             const double2 v = As[e];
             s.A3[e] = v.x;
@@ -193,6 +249,12 @@ struct Walk {
     static __device__ __forceinline__ void store_read(Smem &s, int D, int j, int t, double2 x,
                                                       bool reverse)
     {
+        if (TC && !reverse) {
+            double *w = s.wb + (size_t)(t >> 5) * XS * WBS + (t & 31);
+            w[(2 * j) * WBS] = x.x;
+            w[(2 * j + 1) * WBS] = x.y;
+            return;
+        }
         s.R3[(size_t)j * RS + t] = x.x;
         s.R3[(size_t)(D + j) * RS + t] = reverse ? x.x - x.y : x.y;
         s.R3[(size_t)(2 * D + j) * RS + t] = x.x + x.y;
@@ -251,6 +313,193 @@ struct Walk {
                 }
             }
         }
+    }
+
+    // ------------------------------------------------- tensor-core engine
+    // A real product sum_c R[r][c] x[c] is computed exactly on the bf16 tensor
+    // cores (an Ozaki-type split): each value is turned into a 56-bit fixed
+    // point integer relative to a power of two shared along the contraction
+    // (per row r of R, per pivot for x), written as seven balanced base-256
+    // digits in [-128, 127] (exact in bf16), and the digit products are summed
+    // in fp32 per digit diagonal d = s + u <= 6.  Every partial sum is an
+    // integer below 2^23 (|digit product| <= 2^14, at most 7 x 2D terms), so
+    // fp32 holds it exactly; the diagonals are recombined in int64 and scaled
+    // back in one rounding.  Dropped diagonals and the fixed-point cut leave a
+    // relative error near 2^-53 of the largest term, like FP64.
+
+    static __device__ __forceinline__ int fexp(double v) { return (__double2hiint(v) >> 20) & 0x7ff; }
+
+    // 2^(f - 1048) (the scale of a value whose largest exponent field is f), 0
+    // for f < 26 (values below 2^-997 are flushed to zero).
+    static __device__ __forceinline__ double digit_scale(int f)
+    {
+        return f >= 26 ? __longlong_as_double((long long)(f - 25) << 52) : 0.0;
+    }
+
+    // Biased fixed point U = round(v * 2^(1076 - fmax)) + 0x0080808080808080:
+    // |round(...)| < 2^54, so 0 < U < 2^56 and byte k of U minus 128 is the
+    // k-th balanced base-256 digit.
+    static __device__ __forceinline__ uint64_t to_fixed(double v, int fmax)
+    {
+        const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
+        const int f = (hi >> 20) & 0x7ff;
+        long long X = 0;
+        if (f != 0 && fmax >= 26) {
+            const unsigned long long m =
+                ((unsigned long long)((hi & 0xfffffu) | 0x100000u) << 32) | lo;
+            const int q = min(fmax - f, 63);
+            X = (long long)((((m << 2) >> q) + 1ull) >> 1);
+            if (hi >> 31) X = -X;
+        }
+        return (uint64_t)(X + 0x0080808080808080ll);
+    }
+
+    // bf16 bits of digit s (0 = most significant) of a biased fixed point U.
+    static __device__ __forceinline__ uint32_t digit_bits(uint64_t U, int sl)
+    {
+        const int k = NDIG - 1 - sl;
+        const uint32_t w = (k >= 4) ? (uint32_t)(U >> 32) : (uint32_t)U;
+        const uint32_t byte = (w >> (8 * (k & 3))) & 0xffu;
+        const float d = __uint_as_float(0x4B000000u | byte) - 8388736.0f;   // byte - 128, exact
+        return __float_as_uint(d) >> 16;                                      // exact in bf16
+    }
+
+    // Digit slices of the real form R of A_s (row 2i: Re, col 2j -> Re A_ij,
+    // col 2j+1 -> -Im A_ij; row 2i+1: Im A_ij, Re A_ij) into shared memory.
+    static __device__ void load_circuit_digits(Smem &s, const double2 *As, int D)
+    {
+        const int D2 = 2 * D;
+        for (int i = threadIdx.x; i < D; i += blockDim.x) {
+            int fm = 0;
+            for (int j = 0; j < D; ++j) {
+                const double2 v = As[(size_t)i * D + j];
+                fm = max(fm, max(fexp(v.x), fexp(v.y)));
+            }
+            s.fA[2 * i] = s.fA[2 * i + 1] = fm;
+            s.sA[2 * i] = s.sA[2 * i + 1] = digit_scale(fm);
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < D2 * D2; e += blockDim.x) {
+            const int r = e / D2, c = e % D2;
+            const double2 v = As[(size_t)(r >> 1) * D + (c >> 1)];
+            const double x = (r & 1) ? ((c & 1) ? v.x : v.y) : ((c & 1) ? -v.y : v.x);
+            const uint64_t U = to_fixed(x, s.fA[r]);
+#pragma unroll
+            for (int sl = 0; sl < NDIG; ++sl)
+                s.Ad[((size_t)sl * D2 + r) * s.AS + c] = (uint16_t)digit_bits(U, sl);
+        }
+    }
+
+    static __device__ __forceinline__ uint32_t lda(const Smem &s, int sl, int row, int col, int D2)
+    {
+        return (row < D2 && col < D2) ? *(const uint32_t *)(s.Ad + ((size_t)sl * D2 + row) * s.AS + col)
+                                      : 0u;
+    }
+
+    static __device__ __forceinline__ void mma_bf16(float *c, const uint32_t *a, const uint32_t *b)
+    {
+        asm volatile(
+            "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+            "{%8,%9}, {%0,%1,%2,%3};\n"
+            : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+    }
+
+    // Rows row0 + i (i < N) of A x for the 32 pivots of this warp, whose reads
+    // sit in the warp's buffer (row c = 2j + {re, im}, column = lane).  MMA
+    // tile m16n8k16: M = output real rows, N = 8 pivots, K = input real rows.
+    // The products overwrite the buffer; each lane then emits its pivot's rows.
+    template <bool HASB, class Emit>
+    static __device__ __forceinline__ void matvec_tc(const Smem &s, int D, int row0, int N, unsigned nm,
+                                                     double2 pv, Emit emit)
+    {
+        const int lane = threadIdx.x & 31, grp = lane >> 2, tig = lane & 3;
+        const int D2 = 2 * D, r0 = 2 * row0, n2 = 2 * N, nks = (n2 + 15) >> 4;
+        double *wb = s.wb + (size_t)(threadIdx.x >> 5) * XS * WBS;
+        for (int c = n2; c < 16 * nks; ++c) wb[c * WBS + lane] = 0.0;
+        __syncwarp();
+#pragma unroll 1
+        for (int nt = 0; nt < 4; ++nt) {
+            const int p = nt * 8 + grp;
+            double xv[KS][2][2];
+            int fm = 0;
+#pragma unroll
+            for (int ks = 0; ks < KS; ++ks)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int c = 16 * ks + 8 * h + 2 * tig;
+                    xv[ks][h][0] = ks < nks ? wb[c * WBS + p] : 0.0;
+                    xv[ks][h][1] = ks < nks ? wb[(c + 1) * WBS + p] : 0.0;
+                    fm = max(fm, max(fexp(xv[ks][h][0]), fexp(xv[ks][h][1])));
+                }
+            fm = max(fm, __shfl_xor_sync(0xffffffffu, fm, 1));
+            fm = max(fm, __shfl_xor_sync(0xffffffffu, fm, 2));
+            uint32_t bq[NDIG][KS][2];
+#pragma unroll
+            for (int ks = 0; ks < KS; ++ks)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint64_t ur = to_fixed(xv[ks][h][0], fm), ui = to_fixed(xv[ks][h][1], fm);
+#pragma unroll
+                    for (int sl = 0; sl < NDIG; ++sl)
+                        bq[sl][ks][h] = digit_bits(ur, sl) | (digit_bits(ui, sl) << 16);
+                }
+            __syncwarp();   // every lane has read this N tile's reads
+            const double sx0 = digit_scale(__shfl_sync(0xffffffffu, fm, 8 * tig));
+            const double sx1 = digit_scale(__shfl_sync(0xffffffffu, fm, 8 * tig + 4));
+#pragma unroll 1
+            for (int mt = 0; mt < nks; ++mt) {
+                float acc[NDIG][4];
+#pragma unroll
+                for (int d = 0; d < NDIG; ++d)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[d][q] = 0.f;
+                const int row = r0 + 16 * mt + grp;
+#pragma unroll
+                for (int sa = 0; sa < NDIG; ++sa) {
+                    uint32_t af[KS][4];
+#pragma unroll
+                    for (int ks = 0; ks < KS; ++ks) {
+                        const int col = r0 + 16 * ks + 2 * tig;
+                        af[ks][0] = lda(s, sa, row, col, D2);
+                        af[ks][1] = lda(s, sa, row + 8, col, D2);
+                        af[ks][2] = lda(s, sa, row, col + 8, D2);
+                        af[ks][3] = lda(s, sa, row + 8, col + 8, D2);
+                    }
+#pragma unroll
+                    for (int u = 0; u + sa < NDIG; ++u)
+#pragma unroll
+                        for (int ks = 0; ks < KS; ++ks)
+                            if (ks < nks) mma_bf16(acc[sa + u], af[ks], bq[u][ks]);
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int r = 16 * mt + grp + 8 * (q >> 1), pc = nt * 8 + 2 * tig + (q & 1);
+                    if (r < n2) {
+                        long long Y = __float2int_rn(acc[0][q]);
+#pragma unroll
+                        for (int d = 1; d < NDIG - 1; ++d) Y = Y * 256 + __float2int_rn(acc[d][q]);
+                        Y += (long long)(__float2int_rn(acc[NDIG - 1][q]) >> 8);
+                        wb[r * WBS + pc] = __ll2double_rn(Y) * (s.sA[r0 + r] * ((q & 1) ? sx1 : sx0));
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        for (int i = 0; i < N; ++i) {
+            if (!((nm >> i) & 1u)) continue;
+            double2 v = make_double2(wb[(2 * i) * WBS + lane], wb[(2 * i + 1) * WBS + lane]);
+            if (HASB) v = cadd(v, cmul(s.bs[row0 + i], pv));
+            emit(i, v);
+        }
+    }
+
+    template <bool HASB, class Emit>
+    static __device__ __forceinline__ void matvec_any(const Smem &s, int D, int row0, int N, unsigned vm,
+                                                      unsigned nm, double2 pv, Emit emit)
+    {
+        if constexpr (TC) matvec_tc<HASB>(s, D, row0, N, nm, pv, emit);
+        else matvec<HASB>(s, D, row0, N, vm, nm, pv, emit);
     }
 
     // Columns row0 + j of A^H y for this thread's scaled output adjoints:
@@ -483,7 +732,7 @@ struct Walk {
         }
         const unsigned vm = __reduce_or_sync(0xffffffffu, g.vmask);
         const unsigned nm = __reduce_or_sync(0xffffffffu, g.nmask);
-        matvec<HASB>(s, D, 2 * K, N, vm, nm, FP, [&](int i, double2 acc) {
+        matvec_any<HASB>(s, D, 2 * K, N, vm, nm, FP, [&](int i, double2 acc) {
             if (!act || !((g.nmask >> i) & 1u)) return;
             int den;
             const int64_t addr = ap_write_addr(sh, g, e, K, i, s, &den);
@@ -519,7 +768,7 @@ struct Walk {
         }
         const unsigned vm = __reduce_or_sync(0xffffffffu, g.vmask);
         const unsigned nm = __reduce_or_sync(0xffffffffu, g.nmask);
-        matvec<true>(s, D, 0, N, vm, nm, FP, [&](int i, double2 acc) {
+        matvec_any<true>(s, D, 0, N, vm, nm, FP, [&](int i, double2 acc) {
             if (!act || !((g.nmask >> i) & 1u)) return;
             int den;
             const int64_t addr = dp_write_addr(sh, g, d, i, s, &den);
@@ -819,10 +1068,10 @@ struct Walk {
     // Vacuum-only problem (every cutoff is 1): p = c.
 };
 
-template <int TPB, int CH>
+template <int TPB, int CH, int KS>
 __global__ void __launch_bounds__(TPB) diag_forward_kernel(const __grid_constant__ DiagArgs a)
 {
-    Walk<TPB, CH>::forward(a);
+    Walk<TPB, CH, KS>::forward(a);
 }
 
 template <int TPB, int CH>
@@ -891,15 +1140,31 @@ struct Variant {
 template <int T, int C>
 Variant variant()
 {
-    return Variant{T, C, (const void *)diag_forward_kernel<T, C>, (const void *)diag_vjp_kernel<T, C>,
+    return Variant{T, C, (const void *)diag_forward_kernel<T, C, 0>, (const void *)diag_vjp_kernel<T, C>,
                    &Walk<T, C>::smem_bytes};
 }
 
 const Variant kVariants[] = {variant<128, 8>(), variant<128, 4>(), variant<64, 8>(),
                              variant<64, 4>(), variant<256, 8>()};
 
+// Tensor-core forward kernels, by KS = ceil(M / 4) (M <= 8).
+struct TcVariant {
+    int ks;
+    const void *fwd;
+    size_t (*smem)(int, int, bool);
+};
+
+template <int KS>
+TcVariant tc_variant()
+{
+    return TcVariant{KS, (const void *)diag_forward_kernel<128, 4, KS>, &Walk<128, 4, KS>::smem_bytes};
+}
+
+const TcVariant kTcVariants[] = {tc_variant<1>(), tc_variant<2>()};
+constexpr int kTcMaxModes = 8;
+
 std::mutex g_tune_mu;
-int g_tpb = 128, g_ch = 8, g_bps = 0;
+int g_tpb = 128, g_ch = 8, g_bps = 0, g_engine = FK_ENGINE_FP64;
 
 const Variant &current_variant(int *bps)
 {
@@ -910,7 +1175,37 @@ const Variant &current_variant(int *bps)
     return kVariants[0];
 }
 
+// Forward kernel, block size and shared memory for shape sh under the
+// current tuning and engine.
+void forward_kernel(const DiagShape &sh, const void **fn, int *tpb, size_t *smem, int *bps)
+{
+    const Variant &v = current_variant(bps);
+    int engine;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        engine = g_engine;
+    }
+    if (engine == FK_ENGINE_TENSOR && sh.M <= kTcMaxModes) {
+        const TcVariant &t = kTcVariants[(sh.M + 3) / 4 - 1];
+        *fn = t.fwd;
+        *tpb = 128;
+        *smem = t.smem(sh.M, sh.L, false);
+        return;
+    }
+    *fn = v.fwd;
+    *tpb = v.tpb;
+    *smem = v.smem(sh.M, sh.L, false);
+}
+
 }  // namespace
+
+int set_diag_engine(int engine)
+{
+    if (engine != FK_ENGINE_FP64 && engine != FK_ENGINE_TENSOR) return FK_EINVAL;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_engine = engine;
+    return FK_OK;
+}
 
 int set_diag_tuning(int tpb, int ch, int bps)
 {
@@ -933,14 +1228,21 @@ int diag_grid_size(const DiagShape &sh, bool vjp, int *grid)
     int sms = 0;
     int rc = device_sms(&sms);
     if (rc) return rc;
-    int bps = 0;
-    const Variant &v = current_variant(&bps);
-    const size_t smem = v.smem(sh.M, sh.L, vjp);
-    const void *fn = vjp ? v.vjp : v.fwd;
+    int bps = 0, tpb = 0;
+    size_t smem = 0;
+    const void *fn = nullptr;
+    if (vjp) {
+        const Variant &v = current_variant(&bps);
+        fn = v.vjp;
+        tpb = v.tpb;
+        smem = v.smem(sh.M, sh.L, true);
+    } else {
+        forward_kernel(sh, &fn, &tpb, &smem, &bps);
+    }
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return FK_ECUDA;
     int per = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, v.tpb, smem) != cudaSuccess) return FK_ECUDA;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, tpb, smem) != cudaSuccess) return FK_ECUDA;
     if (per < 1) return FK_EUNSUPPORTED;
     if (bps > 0 && bps < per) per = bps;
     *grid = per * sms;
@@ -989,9 +1291,11 @@ int launch_diag_forward(const DiagShape &sh, int batch, unsigned flags, const vo
     int rc = diag_grid_size(sh, false, &grid);
     if (rc) return rc;
     a.grid = grid;
-    int bps = 0;
-    const Variant &v = current_variant(&bps);
-    return launch_coop(v.fwd, grid, v.tpb, v.smem(sh.M, sh.L, false), &a, st);
+    int bps = 0, tpb = 0;
+    size_t smem = 0;
+    const void *fn = nullptr;
+    forward_kernel(sh, &fn, &tpb, &smem, &bps);
+    return launch_coop(fn, grid, tpb, smem, &a, st);
 }
 
 int launch_diag_vjp(const DiagShape &sh, int batch, unsigned flags, const void *A, const void *b,

@@ -32,7 +32,7 @@ EXPORTS = [
     "fk_conditional_workspace_size", "fock_conditional_dm", "fock_conditional_dm_batched",
     "fock_conditional_dm_vjp", "fock_conditional_dm_vjp_batched",
     "fk_circuit_triple", "fk_circuit_triple_batched", "fk_mlp_sizes", "fk_mlp_load", "fk_mlp_forward", "fk_mlp_backward", "fk_mlp_train_step",
-    "fk_herald_scores", "fk_diag_set_tuning",
+    "fk_herald_scores", "fk_diag_set_tuning", "fk_diag_set_engine",
 ]
 
 
@@ -79,6 +79,7 @@ def lib():
         L.fk_measure_fp64_fma_rate.argtypes = [P, Z, ctypes.POINTER(ctypes.c_double), P]
         L.fock_diag_probs_static.argtypes = [I, P, P, P, I, P, P, U, P, ctypes.POINTER(I)]
         L.fk_diag_set_tuning.argtypes = [I, I, I]
+        L.fk_diag_set_engine.argtypes = [I]
         L.fk_herald_scores.argtypes = [I, P, P, I, P, ctypes.c_double, P, P, P, P]
         L.fk_circuit_triple.argtypes = [I, P, ctypes.c_double, P, P, P, P, P, P]
         L.fk_circuit_triple_batched.argtypes = [I, I, P, ctypes.c_double, P, P, P, P, P, P, I]
@@ -362,3 +363,12 @@ def fock_conditional_dm_vjp_batched(A, b, c, cutoffs, mask, grad_rho, ws, flags=
 
 def fk_diag_set_tuning(tpb=0, ch=0, blocks_per_sm=0):
     _check(lib().fk_diag_set_tuning(int(tpb), int(ch), int(blocks_per_sm)), "fk_diag_set_tuning")
+
+
+FK_ENGINE_FP64, FK_ENGINE_TENSOR = 0, 1
+
+
+def fk_diag_set_engine(engine):
+    """Product engine of the all-detected forward walk (FK_ENGINE_FP64 or
+    FK_ENGINE_TENSOR: exact base-256 digit products on the bf16 tensor cores)."""
+    _check(lib().fk_diag_set_engine(int(engine)), "fk_diag_set_engine")
