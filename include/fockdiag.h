@@ -266,8 +266,12 @@ int fk_diag_set_tuning(int tpb, int ch, int blocks_per_sm);
  *     index sum <= 6 are accumulated exactly (integer partial sums below
  *     2^23 in fp32), recombined in int64 and scaled back with one rounding.
  *     The error is of the order of 2^-53 times the largest term of a sum,
- *     like FP64; values below 2^-997 count as zero.  Shapes with M > 8 use
- *     FP64.  The VJP always runs in FP64.
+ *     like FP64; values below 2^-997 count as zero.  The VJP runs the
+ *     adjoint products conj(A) Y the same way and forms each warp's
+ *     partial dL/dA = sum_t Y(t) X(t)^H from digits too, after moving each
+ *     pivot's power of two from its reads to its adjoints (products
+ *     unchanged), so each term is exact relative to the largest product of
+ *     its row.  Shapes with M > 8 use FP64.
  * Returns FK_EINVAL for another value.  Default FK_ENGINE_FP64.
  */
 #define FK_ENGINE_FP64 0

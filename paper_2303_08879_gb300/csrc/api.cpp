@@ -85,18 +85,19 @@ int diag_layout(const DiagShape &sh, int batch, bool vjp, DiagLayout *lay)
     lay->As = o; o = align_up(o + B * D * D * c16);
     lay->bs = o; o = align_up(o + B * D * c16);
     lay->F = o; o = align_up(o + B * (size_t)sh.circ_size * c16);
-    lay->grid_vjp = 0;
+    lay->grid_vjp = lay->slots_vjp = 0;
     if (vjp) {
-        int grid = 1;
+        int grid = 1, slots = 1;
         if (sh.M > 0) {
-            int rc = diag_grid_size(sh, true, &grid);
+            int rc = diag_grid_size(sh, true, &grid, &slots);
             if (rc) return rc;
         }
         lay->grid_vjp = grid;
+        lay->slots_vjp = slots;
         lay->Fbar = o; o = align_up(o + B * (size_t)sh.circ_size * c16);
         lay->scratch = o; o = align_up(o + B * (size_t)sh.n_ap * c16);
-        lay->partA = o; o = align_up(o + B * (size_t)grid * D * D * c16);
-        lay->partb = o; o = align_up(o + B * (size_t)grid * D * c16);
+        lay->partA = o; o = align_up(o + B * (size_t)slots * D * D * c16);
+        lay->partb = o; o = align_up(o + B * (size_t)slots * D * c16);
     } else {
         lay->Fbar = lay->scratch = lay->partA = lay->partb = o;
     }

@@ -30,7 +30,7 @@ int build_diag_shape(int M, const int *cutoffs, bool has_b, DiagShape *sh);
 // Workspace layout of the all-detected walk for `batch` circuits.
 struct DiagLayout {
     size_t ctl, As, bs, F, Fbar, scratch, partA, partb, total;
-    int grid_vjp;
+    int grid_vjp, slots_vjp;
 };
 int diag_layout(const DiagShape &sh, int batch, bool vjp, DiagLayout *lay);
 
@@ -95,7 +95,7 @@ int set_diag_tuning(int tpb, int ch, int blocks_per_sm);
 int set_diag_engine(int engine);
 
 // Launchers (walk_diag.cu).  All pointers are device pointers.
-int diag_grid_size(const DiagShape &sh, bool vjp, int *grid);
+int diag_grid_size(const DiagShape &sh, bool vjp, int *grid, int *slots = nullptr);
 int launch_diag_forward(const DiagShape &sh, int batch, unsigned flags, const void *A,
                         const void *b, const void *c, void *probs, void *ws,
                         const DiagLayout &lay, void *stream);

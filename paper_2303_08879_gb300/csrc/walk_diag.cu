@@ -39,6 +39,7 @@ struct DiagArgs {
     DiagShape sh;
     int B;
     int grid;
+    int slots;                    // partial-sum slots per circuit (grid x slots per block)
     unsigned flags;
     const double2 *A, *b, *c;     // caller layout, D_orig
     double2 *probs;
@@ -65,6 +66,9 @@ struct Smem {
     double *sA;       // tensor-core engine: [2D] row scales 2^(e_r - 1048)
     int *fA;          // tensor-core engine: [2D] row exponent fields e_r
     double *wb;       // tensor-core engine: per-warp [16 KS][WBS] reads in, products out
+    double *wy;       // tensor-core VJP: per-warp [16 KS][WBS] scaled output adjoints
+    int *wf;          // tensor-core VJP: [TPB] exponent field of each pivot's largest read
+    int *wg;          // tensor-core VJP: per-warp [32] row exponents of the partial dL/dA
     int AS;           // row stride of Ad (bf16 elements)
     int *idx;         // [M][TPB] box indices per pivot
     int *tiles;       // [M + 2] tile prefix sums of the current phase
@@ -119,23 +123,24 @@ struct Walk {
     static __host__ __device__ size_t smem_bytes(int M, int L, bool vjp)
     {
         const int D = 2 * M;
-        const bool tc = TC && !vjp;
         size_t n = 0;
         n += (size_t)(M + 1) * (L + 2) * sizeof(unsigned);
         n = (n + 15) & ~(size_t)15;
         n += 2 * TABN * sizeof(double);
-        if (tc) {
+        if (TC) {
             const int D2 = 2 * D;
+            const size_t buf = (size_t)(TPB / 32) * XS * WBS * sizeof(double);
             n += (size_t)D * sizeof(double2);
             n += (size_t)D2 * (sizeof(double) + sizeof(int));
             n = (n + 15) & ~(size_t)15;
-            n += (size_t)(TPB / 32) * XS * WBS * sizeof(double);
+            n += buf;
+            if (vjp) n += buf + (size_t)TPB * (sizeof(double2) + 2 * sizeof(int));
             n += (size_t)NDIG * D2 * digit_row_stride(D2) * sizeof(uint16_t);
         } else {
             n += 3 * (size_t)D * D * sizeof(double) + (size_t)D * sizeof(double2);
             n += 3 * (size_t)D * RS * sizeof(double);
+            if (vjp) n += 3 * (size_t)D * RS * sizeof(double) + RS * sizeof(double2);
         }
-        if (vjp) n += 3 * (size_t)D * RS * sizeof(double) + RS * sizeof(double2);
         n = (n + 15) & ~(size_t)15;
         n += (size_t)M * TPB * sizeof(int) + (M + 2) * sizeof(int);
         return n + 64;
@@ -153,33 +158,38 @@ struct Walk {
         p = (unsigned char *)(((uintptr_t)p + 15) & ~(uintptr_t)15);
         s.inv = (double *)p; p += TABN * sizeof(double);
         s.fact = (double *)p; p += TABN * sizeof(double);
+        s.A3 = s.R3 = s.Y3 = nullptr;
+        s.FP = nullptr;
         s.Ad = nullptr;
         s.sA = nullptr;
         s.fA = nullptr;
-        s.wb = nullptr;
+        s.wb = s.wy = nullptr;
+        s.wf = s.wg = nullptr;
         s.AS = 0;
-        if (TC && !vjp) {
+        if (TC) {
             const int D2 = 2 * D;
-            s.A3 = nullptr;
-            s.R3 = nullptr;
+            const size_t buf = (size_t)(TPB / 32) * XS * WBS;
             s.bs = (double2 *)p; p += (size_t)D * sizeof(double2);
             s.sA = (double *)p; p += (size_t)D2 * sizeof(double);
             s.fA = (int *)p; p += (size_t)D2 * sizeof(int);
             p = (unsigned char *)(((uintptr_t)p + 15) & ~(uintptr_t)15);
-            s.wb = (double *)p; p += (size_t)(TPB / 32) * XS * WBS * sizeof(double);
+            s.wb = (double *)p; p += buf * sizeof(double);
+            if (vjp) {
+                s.wy = (double *)p; p += buf * sizeof(double);
+                s.FP = (double2 *)p; p += (size_t)TPB * sizeof(double2);
+                s.wf = (int *)p; p += (size_t)TPB * sizeof(int);
+                s.wg = (int *)p; p += (size_t)TPB * sizeof(int);
+            }
             s.AS = digit_row_stride(D2);
             s.Ad = (uint16_t *)p; p += (size_t)NDIG * D2 * s.AS * sizeof(uint16_t);
         } else {
             s.A3 = (double *)p; p += 3 * (size_t)D * D * sizeof(double);
             s.bs = (double2 *)p; p += (size_t)D * sizeof(double2);
             s.R3 = (double *)p; p += 3 * (size_t)D * RS * sizeof(double);
-        }
-        if (vjp) {
-            s.Y3 = (double *)p; p += 3 * (size_t)D * RS * sizeof(double);
-            s.FP = (double2 *)p; p += RS * sizeof(double2);
-        } else {
-            s.Y3 = nullptr;
-            s.FP = nullptr;
+            if (vjp) {
+                s.Y3 = (double *)p; p += 3 * (size_t)D * RS * sizeof(double);
+                s.FP = (double2 *)p; p += RS * sizeof(double2);
+            }
         }
         p = (unsigned char *)(((uintptr_t)p + 15) & ~(uintptr_t)15);
         s.idx = (int *)p; p += (size_t)M * TPB * sizeof(int);
@@ -249,7 +259,7 @@ struct Walk {
     static __device__ __forceinline__ void store_read(Smem &s, int D, int j, int t, double2 x,
                                                       bool reverse)
     {
-        if (TC && !reverse) {
+        if (TC) {
             double *w = s.wb + (size_t)(t >> 5) * XS * WBS + (t & 31);
             w[(2 * j) * WBS] = x.x;
             w[(2 * j + 1) * WBS] = x.y;
@@ -263,6 +273,12 @@ struct Walk {
     // Three planes of a scaled output adjoint y: (Re y, Im y, Re y + Im y).
     static __device__ __forceinline__ void store_adj(Smem &s, int D, int i, int t, double2 y)
     {
+        if (TC) {
+            double *w = s.wy + (size_t)(t >> 5) * XS * WBS + (t & 31);
+            w[(2 * i) * WBS] = y.x;
+            w[(2 * i + 1) * WBS] = y.y;
+            return;
+        }
         s.Y3[(size_t)i * RS + t] = y.x;
         s.Y3[(size_t)(D + i) * RS + t] = y.y;
         s.Y3[(size_t)(2 * D + i) * RS + t] = y.x + y.y;
@@ -270,6 +286,10 @@ struct Walk {
 
     static __device__ __forceinline__ double2 load_adj(const Smem &s, int D, int i, int t)
     {
+        if (TC) {
+            const double *w = s.wy + (size_t)(t >> 5) * XS * WBS + (t & 31);
+            return make_double2(w[(2 * i) * WBS], w[(2 * i + 1) * WBS]);
+        }
         return make_double2(s.Y3[(size_t)i * RS + t], s.Y3[(size_t)(D + i) * RS + t]);
     }
 
@@ -405,18 +425,22 @@ struct Walk {
             : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
     }
 
-    // Rows row0 + i (i < N) of A x for the 32 pivots of this warp, whose reads
-    // sit in the warp's buffer (row c = 2j + {re, im}, column = lane).  MMA
-    // tile m16n8k16: M = output real rows, N = 8 pivots, K = input real rows.
-    // The products overwrite the buffer; each lane then emits its pivot's rows.
-    template <bool HASB, class Emit>
-    static __device__ __forceinline__ void matvec_tc(const Smem &s, int D, int row0, int N, unsigned nm,
-                                                     double2 pv, Emit emit)
+    // Products of the 32 pivots of this warp with the real form of A (CONJ:
+    // of conj(A)) restricted to rows and columns from row0 (complex index):
+    // out[r][p] = sum_c R[row0 + r][row0 + c] in[c][p] for r, c < 2N, in and
+    // out per-warp buffers (row = real index 2j + {re, im}, column = lane).
+    // MMA tile m16n8k16: M = output real rows, N = 8 pivots, K = input real
+    // rows.  out may alias in: an N tile is read before its products land.
+    template <bool CONJ>
+    static __device__ __forceinline__ void tc_products(const Smem &s, int D, int row0, int N, double *in,
+                                                       double *out)
     {
         const int lane = threadIdx.x & 31, grp = lane >> 2, tig = lane & 3;
         const int D2 = 2 * D, r0 = 2 * row0, n2 = 2 * N, nks = (n2 + 15) >> 4;
-        double *wb = s.wb + (size_t)(threadIdx.x >> 5) * XS * WBS;
-        for (int c = n2; c < 16 * nks; ++c) wb[c * WBS + lane] = 0.0;
+        // conj(A) in real form: the Im A entries change sign (high half of a
+        // fragment word in even rows, low half in odd rows; digits negate exactly)
+        const uint32_t cflip = CONJ ? ((grp & 1) ? 0x00008000u : 0x80000000u) : 0u;
+        for (int c = n2; c < 16 * nks; ++c) in[c * WBS + lane] = 0.0;
         __syncwarp();
 #pragma unroll 1
         for (int nt = 0; nt < 4; ++nt) {
@@ -428,8 +452,8 @@ struct Walk {
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int c = 16 * ks + 8 * h + 2 * tig;
-                    xv[ks][h][0] = ks < nks ? wb[c * WBS + p] : 0.0;
-                    xv[ks][h][1] = ks < nks ? wb[(c + 1) * WBS + p] : 0.0;
+                    xv[ks][h][0] = ks < nks ? in[c * WBS + p] : 0.0;
+                    xv[ks][h][1] = ks < nks ? in[(c + 1) * WBS + p] : 0.0;
                     fm = max(fm, max(fexp(xv[ks][h][0]), fexp(xv[ks][h][1])));
                 }
             fm = max(fm, __shfl_xor_sync(0xffffffffu, fm, 1));
@@ -444,7 +468,7 @@ struct Walk {
                     for (int sl = 0; sl < NDIG; ++sl)
                         bq[sl][ks][h] = digit_bits(ur, sl) | (digit_bits(ui, sl) << 16);
                 }
-            __syncwarp();   // every lane has read this N tile's reads
+            __syncwarp();   // every lane has read this N tile's inputs
             const double sx0 = digit_scale(__shfl_sync(0xffffffffu, fm, 8 * tig));
             const double sx1 = digit_scale(__shfl_sync(0xffffffffu, fm, 8 * tig + 4));
 #pragma unroll 1
@@ -461,10 +485,10 @@ struct Walk {
 #pragma unroll
                     for (int ks = 0; ks < KS; ++ks) {
                         const int col = r0 + 16 * ks + 2 * tig;
-                        af[ks][0] = lda(s, sa, row, col, D2);
-                        af[ks][1] = lda(s, sa, row + 8, col, D2);
-                        af[ks][2] = lda(s, sa, row, col + 8, D2);
-                        af[ks][3] = lda(s, sa, row + 8, col + 8, D2);
+                        af[ks][0] = lda(s, sa, row, col, D2) ^ cflip;
+                        af[ks][1] = lda(s, sa, row + 8, col, D2) ^ cflip;
+                        af[ks][2] = lda(s, sa, row, col + 8, D2) ^ cflip;
+                        af[ks][3] = lda(s, sa, row + 8, col + 8, D2) ^ cflip;
                     }
 #pragma unroll
                     for (int u = 0; u + sa < NDIG; ++u)
@@ -476,21 +500,155 @@ struct Walk {
                 for (int q = 0; q < 4; ++q) {
                     const int r = 16 * mt + grp + 8 * (q >> 1), pc = nt * 8 + 2 * tig + (q & 1);
                     if (r < n2) {
-                        long long Y = __float2int_rn(acc[0][q]);
-#pragma unroll
-                        for (int d = 1; d < NDIG - 1; ++d) Y = Y * 256 + __float2int_rn(acc[d][q]);
-                        Y += (long long)(__float2int_rn(acc[NDIG - 1][q]) >> 8);
-                        wb[r * WBS + pc] = __ll2double_rn(Y) * (s.sA[r0 + r] * ((q & 1) ? sx1 : sx0));
+                        const long long Y = combine_digits(acc, q);
+                        out[r * WBS + pc] = __ll2double_rn(Y) * (s.sA[r0 + r] * ((q & 1) ? sx1 : sx0));
                     }
                 }
             }
         }
         __syncwarp();
+    }
+
+    // Digit diagonals d = 0..6 of one accumulator element recombined:
+    // sum_d acc_d 256^(5 - d), the last diagonal shifted down (floor).
+    static __device__ __forceinline__ long long combine_digits(const float (&acc)[NDIG][4], int q)
+    {
+        long long Y = __float2int_rn(acc[0][q]);
+#pragma unroll
+        for (int d = 1; d < NDIG - 1; ++d) Y = Y * 256 + __float2int_rn(acc[d][q]);
+        return Y + (long long)(__float2int_rn(acc[NDIG - 1][q]) >> 8);
+    }
+
+    // Forward rows row0 + i (i < N) of A x for this warp's pivots (reads in
+    // the warp's buffer); each lane then emits its own pivot's rows.
+    template <bool HASB, class Emit>
+    static __device__ __forceinline__ void matvec_tc(const Smem &s, int D, int row0, int N, unsigned nm,
+                                                     double2 pv, Emit emit)
+    {
+        const int lane = threadIdx.x & 31;
+        double *wb = s.wb + (size_t)(threadIdx.x >> 5) * XS * WBS;
+        tc_products<false>(s, D, row0, N, wb, wb);
         for (int i = 0; i < N; ++i) {
             if (!((nm >> i) & 1u)) continue;
             double2 v = make_double2(wb[(2 * i) * WBS + lane], wb[(2 * i + 1) * WBS + lane]);
             if (HASB) v = cadd(v, cmul(s.bs[row0 + i], pv));
             emit(i, v);
+        }
+    }
+
+    // Biased fixed point of v relative to exponent field fm >= field(v)
+    // (no flush: the caller checks the scale).
+    static __device__ __forceinline__ uint64_t to_fixed_rel(double v, int fm)
+    {
+        const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
+        const int f = (hi >> 20) & 0x7ff;
+        long long X = 0;
+        if (f != 0) {
+            const unsigned long long m =
+                ((unsigned long long)((hi & 0xfffffu) | 0x100000u) << 32) | lo;
+            const int q = min(max(fm - f, 0), 63);
+            X = (long long)((((m << 2) >> q) + 1ull) >> 1);
+            if (hi >> 31) X = -X;
+        }
+        return (uint64_t)(X + 0x0080808080808080ll);
+    }
+
+    // Partial dL/dA of this warp's 32 pivots on the tensor cores:
+    //   P[w][j] = sum_t Y_w(t) conj(X_j(t)),  w, j < N (from row0),
+    // Y = scaled output adjoints (warp buffer wy), X = reads (warp buffer wb).
+    // Each pivot's reads are scaled by 2^(1022 - e_t) (e_t: largest exponent
+    // field of its reads) and its adjoints by the inverse, which leaves every
+    // product unchanged; the adjoints then share a power of two per row w
+    // over the 32 pivots, so each term is exact relative to the largest
+    // product of its row.  Real form: rows 2w -> Re P = sum (Yr Xr + Yi Xi),
+    // 2w+1 -> Im P = sum (Yi Xr - Yr Xi); K = (pivot, re/im) = 64.
+    // The result is added to the warp's own slot (single writer).
+    static __device__ void tc_partials(const DiagArgs &a, const Smem &s, int circ, int row0, int N)
+    {
+        const int lane = threadIdx.x & 31, grp = lane >> 2, tig = lane & 3, warp = threadIdx.x >> 5;
+        const int D = 2 * a.sh.M, n2 = 2 * N, nks = (n2 + 15) >> 4, nnt = (N + 7) >> 3;
+        const double *wx = s.wb + (size_t)warp * XS * WBS;
+        const double *wy = s.wy + (size_t)warp * XS * WBS;
+        const int *ef = s.wf + warp * 32;
+        const int *gy = s.wg + warp * 32;
+        const size_t slot = (size_t)blockIdx.x * (TPB / 32) + warp;
+        double *pA = (double *)(a.partA + ((size_t)circ * a.slots + slot) * D * D);
+#pragma unroll 1
+        for (int mt = 0; mt < nks; ++mt) {
+            float acc[NDIG][KS][4];
+#pragma unroll
+            for (int d = 0; d < NDIG; ++d)
+#pragma unroll
+                for (int nt = 0; nt < KS; ++nt)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[d][nt][q] = 0.f;
+            // this lane's A rows: m = 16 mt + grp (+8) -> w = 8 mt + grp / 2 (+4), rho = grp & 1
+            const int w0 = 8 * mt + (grp >> 1), rho = grp & 1;
+            const int g0 = w0 < N ? gy[w0] : 0, g1 = w0 + 4 < N ? gy[w0 + 4] : 0;
+#pragma unroll 1
+            for (int ks = 0; ks < 4; ++ks) {
+                const int t0 = 8 * ks + tig, t1 = t0 + 4;
+                const int e0 = ef[t0], e1 = ef[t1];
+                // A operand words: (rho = 0) (Yr, Yi), (rho = 1) (Yi, -Yr) of (w, t)
+                uint32_t aq[NDIG][4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int w = w0 + 4 * (k & 1), t = (k & 2) ? t1 : t0, e = (k & 2) ? e1 : e0;
+                    const int g = (k & 1) ? g1 : g0;
+                    double yr = 0.0, yi = 0.0;
+                    if (w < N && g != 0 && e != 0) {
+                        yr = wy[(2 * w) * WBS + t];
+                        yi = wy[(2 * w + 1) * WBS + t];
+                    }
+                    const int fm = g - e + 1022;
+                    const uint64_t ur = to_fixed_rel(rho ? yi : yr, fm);
+                    const uint64_t ui = to_fixed_rel(rho ? -yr : yi, fm);
+#pragma unroll
+                    for (int sl = 0; sl < NDIG; ++sl) aq[sl][k] = digit_bits(ur, sl) | (digit_bits(ui, sl) << 16);
+                }
+                // B operand words: (Xr, Xi) of (j = 8 nt + grp, t)
+                uint32_t bq[NDIG][KS][2];
+#pragma unroll
+                for (int nt = 0; nt < KS; ++nt)
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int j = 8 * nt + grp, t = h ? t1 : t0, e = h ? e1 : e0;
+                        double xr = 0.0, xi = 0.0;
+                        if (nt < nnt && j < N) {
+                            xr = wx[(2 * j) * WBS + t];
+                            xi = wx[(2 * j + 1) * WBS + t];
+                        }
+                        const uint64_t ur = to_fixed(xr, e), ui = to_fixed(xi, e);
+#pragma unroll
+                        for (int sl = 0; sl < NDIG; ++sl)
+                            bq[sl][nt][h] = digit_bits(ur, sl) | (digit_bits(ui, sl) << 16);
+                    }
+#pragma unroll
+                for (int sa = 0; sa < NDIG; ++sa)
+#pragma unroll
+                    for (int u = 0; u + sa < NDIG; ++u)
+#pragma unroll
+                        for (int nt = 0; nt < KS; ++nt)
+                            if (nt < nnt) mma_bf16(acc[sa + u][nt], aq[sa], bq[u][nt]);
+            }
+#pragma unroll
+            for (int nt = 0; nt < KS; ++nt) {
+                if (nt >= nnt) continue;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int w = w0 + 4 * (q >> 1), j = 8 * nt + 2 * tig + (q & 1);
+                    const int g = (q >> 1) ? g1 : g0;
+                    if (w < N && j < N && g >= 26) {
+                        float a7[NDIG][4];
+#pragma unroll
+                        for (int d = 0; d < NDIG; ++d) a7[d][0] = acc[d][nt][q];
+                        const long long Y = combine_digits(a7, 0);
+                        const double v = __ll2double_rn(Y) * digit_scale(g) * 0x1p-26;
+                        double *dst = pA + 2 * ((size_t)(row0 + w) * D + row0 + j) + rho;
+                        *dst += v;
+                    }
+                }
+            }
         }
     }
 
@@ -796,7 +954,7 @@ struct Walk {
         wm = s_m[0];
         jm = s_m[1];
         const int D = 2 * a.sh.M;
-        double2 *pA = a.partA + ((size_t)circ * a.grid + blockIdx.x) * D * D;
+        double2 *pA = a.partA + ((size_t)circ * a.slots + blockIdx.x) * D * D;
         for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
             const int w = e / N, j = e % N;
             if (!((wm >> w) & 1u) || !((jm >> j) & 1u)) continue;
@@ -814,7 +972,7 @@ struct Walk {
             dst = cadd(dst, make_double2(P - Q, P - T));
         }
         if (hasb) {
-            double2 *pb = a.partb + ((size_t)circ * a.grid + blockIdx.x) * D;
+            double2 *pb = a.partb + ((size_t)circ * a.slots + blockIdx.x) * D;
             for (int w = threadIdx.x; w < N; w += blockDim.x) {
                 if (!((wm >> w) & 1u)) continue;
                 double2 acc = make_double2(0, 0);
@@ -939,6 +1097,174 @@ struct Walk {
         reduce_partials(a, s, tl.circ, 0, N, true, nm, vm);
     }
 
+    // ------------------------------------------- reverse on the tensor cores
+    // Per warp: reads and scaled output adjoints land in the warp's buffers,
+    // the warp's partial dL/dA (and dL/db) is formed from them, then the read
+    // adjoints conj(A) Y overwrite the read buffer and each lane scatters its
+    // own pivot's.
+    static __device__ void tc_partb(const DiagArgs &a, const Smem &s, int circ, int row0, int N)
+    {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, D = 2 * a.sh.M;
+        const size_t slot = (size_t)blockIdx.x * (TPB / 32) + warp;
+        double2 *pb = a.partb + ((size_t)circ * a.slots + slot) * D;
+        const double *wy = s.wy + (size_t)warp * XS * WBS;
+        for (int w = lane; w < N; w += 32) {
+            double2 acc = make_double2(0, 0);
+            for (int tt = 0; tt < 32; ++tt)
+                acc = cfma_conj(s.FP[warp * 32 + tt], make_double2(wy[(2 * w) * WBS + tt], wy[(2 * w + 1) * WBS + tt]),
+                                acc);
+            pb[row0 + w] = cadd(pb[row0 + w], acc);
+        }
+    }
+
+    // Row exponents of the warp's partial dL/dA: for row w the largest
+    // exponent field of Y_w(t) 2^(e_t - 1022) over the warp's pivots (0: none).
+    static __device__ __forceinline__ void tc_row_exponents(Smem &s, int D, int N, int fx)
+    {
+        const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+        s.wf[t] = fx;
+        for (int w = 0; w < N; ++w) {
+            int gw = 0;
+            if (fx != 0) {
+                const double2 y = load_adj(s, D, w, t);
+                const int fy = max(fexp(y.x), fexp(y.y));
+                if (fy != 0) gw = max(fy + fx - 1022, 0);
+            }
+            gw = __reduce_max_sync(0xffffffffu, gw);
+            if (lane == 0) s.wg[warp * 32 + w] = gw;
+        }
+        __syncwarp();
+    }
+
+    template <bool HASB>
+    static __device__ void ap_reverse_tile_tc(const DiagArgs &a, Smem &s, const TileId &tl, int K, int lev)
+    {
+        const DiagShape &sh = a.sh;
+        const int t = threadIdx.x, lane = t & 31, D = 2 * sh.M, N = 2 * (sh.M - K);
+        load_circuit(a, s, tl.circ);
+        const double2 *F = a.F + (size_t)tl.circ * sh.circ_size;
+        double2 *Fb = a.Fbar + (size_t)tl.circ * sh.circ_size;
+        const unsigned r = tl.rank0 + t;
+        const bool act = r < tl.count;
+        Dig e;
+        ApGeom g{};
+        int fx = 0;
+        double2 FPv = make_double2(0, 0);
+        if (act) {
+            e = unrank(sh, s, K, 1, lev, r);
+            g = ap_geom(sh, e, K, s, HASB);
+            for (int j = 0; j < N; ++j) {
+                double2 v = make_double2(0, 0);
+                if ((g.vmask >> j) & 1u) v = __ldcg(F + ap_read_addr(sh, g, K, j, s));
+                fx = max(fx, max(fexp(v.x), fexp(v.y)));
+                store_read(s, D, j, t, v, true);
+            }
+            for (int i = 0; i < N; ++i) {
+                double2 v = make_double2(0, 0);
+                if ((g.nmask >> i) & 1u) {
+                    int den;
+                    const int64_t addr = ap_write_addr(sh, g, e, K, i, s, &den);
+                    v = rscale(__ldcg(Fb + addr), s.inv[den]);
+                }
+                store_adj(s, D, i, t, v);
+            }
+            if (HASB) FPv = __ldcg(F + sh.off_t1k[K] + g.t1k);
+        } else {
+            for (int j = 0; j < N; ++j) {
+                store_read(s, D, j, t, make_double2(0, 0), true);
+                store_adj(s, D, j, t, make_double2(0, 0));
+            }
+        }
+        s.FP[t] = FPv;
+        tc_row_exponents(s, D, N, fx);
+        tc_partials(a, s, tl.circ, 2 * K, N);
+        if (HASB) tc_partb(a, s, tl.circ, 2 * K, N);
+        __syncwarp();
+        double *wx = s.wb + (size_t)(t >> 5) * XS * WBS;
+        tc_products<true>(s, D, 2 * K, N, s.wy + (size_t)(t >> 5) * XS * WBS, wx);
+        if (act) {
+            for (int j = 0; j < N; ++j) {
+                if (!((g.vmask >> j) & 1u)) continue;
+                const double2 acc = make_double2(wx[(2 * j) * WBS + lane], wx[(2 * j + 1) * WBS + lane]);
+                if (j == 0) {
+                    const int64_t ia = box_index(sh, e, K, K, 1, -1, 0);
+                    a.scratch[(size_t)tl.circ * sh.n_ap + sh.off_ap[K] + ia] = acc;
+                } else {
+                    const int64_t addr = ap_read_addr(sh, g, K, j, s);
+                    Fb[addr] = cadd(__ldcg(Fb + addr), acc);
+                }
+            }
+            if (HASB) {
+                double2 fpb = make_double2(0, 0);
+                for (int i = 0; i < N; ++i)
+                    if ((g.nmask >> i) & 1u) fpb = cfma_conj(s.bs[2 * K + i], load_adj(s, D, i, t), fpb);
+                const int64_t addr = sh.off_t1k[K] + g.t1k;
+                Fb[addr] = cadd(__ldcg(Fb + addr), fpb);
+            }
+        }
+        __syncwarp();
+    }
+
+    static __device__ void dp_reverse_tile_tc(const DiagArgs &a, Smem &s, const TileId &tl, int lev)
+    {
+        const DiagShape &sh = a.sh;
+        const int t = threadIdx.x, lane = t & 31, D = 2 * sh.M, N = D;
+        load_circuit(a, s, tl.circ);
+        const double2 *F = a.F + (size_t)tl.circ * sh.circ_size;
+        double2 *Fb = a.Fbar + (size_t)tl.circ * sh.circ_size;
+        const unsigned r = tl.rank0 + t;
+        const bool act = r < tl.count;
+        Dig d;
+        DpGeom g{};
+        int fx = 0;
+        double2 FPv = make_double2(0, 0);
+        if (act) {
+            d = unrank(sh, s, 0, 1, lev, r);
+            g = dp_geom(sh, d, s);
+            for (int j = 0; j < N; ++j) {
+                double2 v = make_double2(0, 0);
+                if ((g.vmask >> j) & 1u) v = __ldcg(F + dp_read_addr(sh, g, j, s));
+                fx = max(fx, max(fexp(v.x), fexp(v.y)));
+                store_read(s, D, j, t, v, true);
+            }
+            for (int i = 0; i < N; ++i) {
+                double2 v = make_double2(0, 0);
+                if ((g.nmask >> i) & 1u) {
+                    int den;
+                    const int64_t addr = dp_write_addr(sh, g, d, i, s, &den);
+                    v = rscale(__ldcg(Fb + addr), s.inv[den]);
+                }
+                store_adj(s, D, i, t, v);
+            }
+            FPv = __ldcg(F + g.diag);
+        } else {
+            for (int j = 0; j < N; ++j) {
+                store_read(s, D, j, t, make_double2(0, 0), true);
+                store_adj(s, D, j, t, make_double2(0, 0));
+            }
+        }
+        s.FP[t] = FPv;
+        tc_row_exponents(s, D, N, fx);
+        tc_partials(a, s, tl.circ, 0, N);
+        tc_partb(a, s, tl.circ, 0, N);
+        __syncwarp();
+        double *wx = s.wb + (size_t)(t >> 5) * XS * WBS;
+        tc_products<true>(s, D, 0, N, s.wy + (size_t)(t >> 5) * XS * WBS, wx);
+        if (act) {
+            for (int j = 0; j < N; ++j) {
+                if (!((g.vmask >> j) & 1u)) continue;
+                const double2 acc = make_double2(wx[(2 * j) * WBS + lane], wx[(2 * j + 1) * WBS + lane]);
+                const int64_t addr = dp_read_addr(sh, g, j, s);
+                Fb[addr] = cadd(__ldcg(Fb + addr), acc);
+            }
+            double2 fpb = make_double2(0, 0);
+            for (int i = 0; i < N; ++i)
+                if ((g.nmask >> i) & 1u) fpb = cfma_conj(s.bs[i], load_adj(s, D, i, t), fpb);
+            Fb[g.diag] = cadd(__ldcg(Fb + g.diag), fpb);
+        }
+        __syncwarp();
+    }
+
     // ------------------------------------------------------ reverse DIAGSUM
     // Adjoint of every diagonal amplitude of level `lev`: upstream seed plus the
     // read contributions the AP(K) pivots with base d left in scratch.
@@ -1013,8 +1339,13 @@ struct Walk {
                 const int nt = phase_tiles(a, s, 0, lev);
                 for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
                     const TileId tl = decode_tile(a, s, 0, lev, tile);
-                    if (hb) ap_reverse_tile<true>(a, s, tl, tl.seg, lev);
-                    else ap_reverse_tile<false>(a, s, tl, tl.seg, lev);
+                    if constexpr (TC) {
+                        if (hb) ap_reverse_tile_tc<true>(a, s, tl, tl.seg, lev);
+                        else ap_reverse_tile_tc<false>(a, s, tl, tl.seg, lev);
+                    } else {
+                        if (hb) ap_reverse_tile<true>(a, s, tl, tl.seg, lev);
+                        else ap_reverse_tile<false>(a, s, tl, tl.seg, lev);
+                    }
                 }
                 if (!grid_sync(a.ctl, gridDim.x, a.timeout_ns)) return;
             }
@@ -1030,7 +1361,8 @@ struct Walk {
                 const int nt = phase_tiles(a, s, 1, lev);
                 for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
                     const TileId tl = decode_tile(a, s, 1, lev, tile);
-                    dp_reverse_tile(a, s, tl, lev);
+                    if constexpr (TC) dp_reverse_tile_tc(a, s, tl, lev);
+                    else dp_reverse_tile(a, s, tl, lev);
                 }
                 if (!grid_sync(a.ctl, gridDim.x, a.timeout_ns)) return;
             }
@@ -1047,8 +1379,8 @@ struct Walk {
             const int c = (int)(e / (D * D));
             const int w = (int)((e / D) % D), l = (int)(e % D);
             double2 x = make_double2(0, 0), y = make_double2(0, 0);
-            for (int blk = 0; blk < a.grid; ++blk) {
-                const double2 *pA = a.partA + ((size_t)c * a.grid + blk) * D * D;
+            for (int blk = 0; blk < a.slots; ++blk) {
+                const double2 *pA = a.partA + ((size_t)c * a.slots + blk) * D * D;
                 x = cadd(x, pA[(size_t)w * D + l]);
                 y = cadd(y, pA[(size_t)l * D + w]);
             }
@@ -1058,7 +1390,7 @@ struct Walk {
         for (int64_t e = gtid; e < (int64_t)a.B * D; e += gsz) {
             const int c = (int)(e / D), w = (int)(e % D);
             double2 x = make_double2(0, 0);
-            for (int blk = 0; blk < a.grid; ++blk) x = cadd(x, a.partb[((size_t)c * a.grid + blk) * D + w]);
+            for (int blk = 0; blk < a.slots; ++blk) x = cadd(x, a.partb[((size_t)c * a.slots + blk) * D + w]);
             const int ow = 2 * sh.mode_map[w / 2] + (w & 1);
             a.gb[(size_t)c * Do + ow] = x;
         }
@@ -1074,10 +1406,10 @@ __global__ void __launch_bounds__(TPB) diag_forward_kernel(const __grid_constant
     Walk<TPB, CH, KS>::forward(a);
 }
 
-template <int TPB, int CH>
+template <int TPB, int CH, int KS>
 __global__ void __launch_bounds__(TPB) diag_vjp_kernel(const __grid_constant__ DiagArgs a)
 {
-    Walk<TPB, CH>::vjp(a);
+    Walk<TPB, CH, KS>::vjp(a);
 }
 
 __global__ void copy_c_kernel(const double2 *c, double2 *probs, int B, int64_t stride)
@@ -1140,24 +1472,25 @@ struct Variant {
 template <int T, int C>
 Variant variant()
 {
-    return Variant{T, C, (const void *)diag_forward_kernel<T, C, 0>, (const void *)diag_vjp_kernel<T, C>,
+    return Variant{T, C, (const void *)diag_forward_kernel<T, C, 0>, (const void *)diag_vjp_kernel<T, C, 0>,
                    &Walk<T, C>::smem_bytes};
 }
 
 const Variant kVariants[] = {variant<128, 8>(), variant<128, 4>(), variant<64, 8>(),
                              variant<64, 4>(), variant<256, 8>()};
 
-// Tensor-core forward kernels, by KS = ceil(M / 4) (M <= 8).
+// Tensor-core kernels, by KS = ceil(M / 4) (M <= 8); 128 pivots per tile.
 struct TcVariant {
     int ks;
-    const void *fwd;
+    const void *fwd, *vjp;
     size_t (*smem)(int, int, bool);
 };
 
 template <int KS>
 TcVariant tc_variant()
 {
-    return TcVariant{KS, (const void *)diag_forward_kernel<128, 4, KS>, &Walk<128, 4, KS>::smem_bytes};
+    return TcVariant{KS, (const void *)diag_forward_kernel<128, 4, KS>, (const void *)diag_vjp_kernel<128, 4, KS>,
+                     &Walk<128, 4, KS>::smem_bytes};
 }
 
 const TcVariant kTcVariants[] = {tc_variant<1>(), tc_variant<2>()};
@@ -1175,9 +1508,10 @@ const Variant &current_variant(int *bps)
     return kVariants[0];
 }
 
-// Forward kernel, block size and shared memory for shape sh under the
-// current tuning and engine.
-void forward_kernel(const DiagShape &sh, const void **fn, int *tpb, size_t *smem, int *bps)
+// Kernel, block size, shared memory and partial-sum slots per block for
+// shape sh under the current tuning and engine (forward or VJP).
+void walk_kernel(const DiagShape &sh, bool vjp, const void **fn, int *tpb, size_t *smem, int *bps,
+                 int *slots_per_block)
 {
     const Variant &v = current_variant(bps);
     int engine;
@@ -1187,14 +1521,16 @@ void forward_kernel(const DiagShape &sh, const void **fn, int *tpb, size_t *smem
     }
     if (engine == FK_ENGINE_TENSOR && sh.M <= kTcMaxModes) {
         const TcVariant &t = kTcVariants[(sh.M + 3) / 4 - 1];
-        *fn = t.fwd;
+        *fn = vjp ? t.vjp : t.fwd;
         *tpb = 128;
-        *smem = t.smem(sh.M, sh.L, false);
+        *smem = t.smem(sh.M, sh.L, vjp);
+        *slots_per_block = 128 / 32;
         return;
     }
-    *fn = v.fwd;
+    *fn = vjp ? v.vjp : v.fwd;
     *tpb = v.tpb;
-    *smem = v.smem(sh.M, sh.L, false);
+    *smem = v.smem(sh.M, sh.L, vjp);
+    *slots_per_block = 1;
 }
 
 }  // namespace
@@ -1223,22 +1559,15 @@ int set_diag_tuning(int tpb, int ch, int bps)
     return FK_OK;
 }
 
-int diag_grid_size(const DiagShape &sh, bool vjp, int *grid)
+int diag_grid_size(const DiagShape &sh, bool vjp, int *grid, int *slots)
 {
     int sms = 0;
     int rc = device_sms(&sms);
     if (rc) return rc;
-    int bps = 0, tpb = 0;
+    int bps = 0, tpb = 0, spb = 1;
     size_t smem = 0;
     const void *fn = nullptr;
-    if (vjp) {
-        const Variant &v = current_variant(&bps);
-        fn = v.vjp;
-        tpb = v.tpb;
-        smem = v.smem(sh.M, sh.L, true);
-    } else {
-        forward_kernel(sh, &fn, &tpb, &smem, &bps);
-    }
+    walk_kernel(sh, vjp, &fn, &tpb, &smem, &bps, &spb);
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return FK_ECUDA;
     int per = 0;
@@ -1246,6 +1575,7 @@ int diag_grid_size(const DiagShape &sh, bool vjp, int *grid)
     if (per < 1) return FK_EUNSUPPORTED;
     if (bps > 0 && bps < per) per = bps;
     *grid = per * sms;
+    if (slots) *slots = per * sms * spb;
     return FK_OK;
 }
 
@@ -1291,10 +1621,10 @@ int launch_diag_forward(const DiagShape &sh, int batch, unsigned flags, const vo
     int rc = diag_grid_size(sh, false, &grid);
     if (rc) return rc;
     a.grid = grid;
-    int bps = 0, tpb = 0;
+    int bps = 0, tpb = 0, spb = 1;
     size_t smem = 0;
     const void *fn = nullptr;
-    forward_kernel(sh, &fn, &tpb, &smem, &bps);
+    walk_kernel(sh, false, &fn, &tpb, &smem, &bps, &spb);
     return launch_coop(fn, grid, tpb, smem, &a, st);
 }
 
@@ -1323,13 +1653,17 @@ int launch_diag_vjp(const DiagShape &sh, int batch, unsigned flags, const void *
     a.gb = (double2 *)gb;
     a.gc = (double2 *)gc;
     a.grid = lay.grid_vjp;
-    int bps = 0;
-    const Variant &v = current_variant(&bps);
-    int grid = 0;
-    int rc = diag_grid_size(sh, true, &grid);
+    a.slots = lay.slots_vjp;
+    int bps = 0, tpb = 0, spb = 1;
+    size_t smem = 0;
+    const void *fn = nullptr;
+    walk_kernel(sh, true, &fn, &tpb, &smem, &bps, &spb);
+    int grid = 0, slots = 0;
+    int rc = diag_grid_size(sh, true, &grid, &slots);
     if (rc) return rc;
-    if (grid != lay.grid_vjp) return FK_EWORKSPACE;   // tuning changed since the layout was sized
-    return launch_coop(v.vjp, lay.grid_vjp, v.tpb, v.smem(sh.M, sh.L, true), &a, st);
+    // tuning or engine changed since the layout was sized
+    if (grid != lay.grid_vjp || slots != lay.slots_vjp) return FK_EWORKSPACE;
+    return launch_coop(fn, lay.grid_vjp, tpb, smem, &a, st);
 }
 
 int launch_wait_selftest(void *ws, unsigned long long timeout_ns, void *stream)

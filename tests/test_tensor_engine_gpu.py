@@ -162,17 +162,71 @@ def oracle_vjp(A, b, c, cut, gbar_probs):
     return ograd.vjp(G, gfull, c)
 
 
-@pytest.mark.parametrize("cut,withb", [((4, 3), True), ((3, 3, 3), False), ((2, 2, 2, 2), True)])
-def test_vjp_after_tensor_forward(fd, cut, withb):
+VJP_CASES = [((4, 3), True), ((3, 3, 3), False), ((3, 4, 2), True), ((2, 1, 3), True),
+             ((5,), True), ((2, 2, 2, 2), False), ((4, 4), False), ((2, 2, 2, 2), True),
+             ((4, 4, 4, 3), True), ((3, 3, 3, 3), False)]
+
+
+@pytest.mark.parametrize("cut,withb", VJP_CASES)
+def test_tensor_vjp_matches_oracle_gradient(fd, cut, withb):
+    """Forward and VJP both on the tensor engine (b != 0: DP tiles and dL/db)."""
     rng = np.random.default_rng(100 + sum(cut))
     A, b = inputs.random_symmetric(2 * len(cut), rng, with_b=withb)
     c = 0.8 - 0.1j
     gbar = rng.normal(size=cut) + 1j * rng.normal(size=cut)
     rA, rb, rc = oracle_vjp(A, b, c, cut, gbar)
+    for flags in ((0, fd.FK_FLAG_B_ZERO) if not withb else (0,)):
+        _, (Ad, bd, cd, ws) = gpu_probs(fd, A, b, c, cut, flags)
+        gA, gb, gc = fd.fock_diag_probs_vjp_batched(Ad, bd, cd, cut, cuda(gbar[None]), ws, flags=flags)
+        fd.check_workspace(ws)
+        assert_grad_close(gA[0].cpu().numpy(), rA, "grad_A")
+        if withb:
+            assert_grad_close(gb[0].cpu().numpy(), rb, "grad_b")
+        else:
+            assert np.max(np.abs(gb[0].cpu().numpy())) < 1e-12 * max(1, np.max(np.abs(rA)))
+        assert abs(gc[0].item() - rc) <= VJP_RTOL * max(abs(rc), 1e-300)
+
+
+def test_tensor_vjp_scaled_adjoints(fd):
+    """Upstream gradients spanning 1e-150..1e150 across outputs: the partial
+    dL/dA rows take their power of two from the largest product."""
+    rng = np.random.default_rng(8)
+    cut = (4, 3, 4)
+    A, b = inputs.random_symmetric(6, rng, with_b=True)
+    c = 0.7 + 0.2j
+    gbar = (rng.normal(size=cut) + 1j * rng.normal(size=cut)) * 10.0 ** rng.uniform(-150, 150, size=cut)
+    rA, rb, rc = oracle_vjp(A, b, c, cut, gbar)
     _, (Ad, bd, cd, ws) = gpu_probs(fd, A, b, c, cut)
     gA, gb, gc = fd.fock_diag_probs_vjp_batched(Ad, bd, cd, cut, cuda(gbar[None]), ws)
     fd.check_workspace(ws)
     assert_grad_close(gA[0].cpu().numpy(), rA, "grad_A")
-    if withb:
-        assert_grad_close(gb[0].cpu().numpy(), rb, "grad_b")
-    assert abs(gc[0].item() - rc) <= VJP_RTOL * max(abs(rc), 1e-300)
+    assert_grad_close(gb[0].cpu().numpy(), rb, "grad_b")
+
+
+def test_tensor_vjp_gbs_m8_c6_batch16_matches_fp64_engine(fd):
+    """Full-size benchmark workload: forward + VJP on the tensor engine against
+    the FP64 engine for every circuit (1e-10 of each gradient's largest entry)."""
+    circs = inputs.workload("gbs_m8_c6_batch16")
+    cut = circs[0].cutoffs
+    trip = [fd.fk_gaussian_to_triple(c.V, c.mean) for c in circs]
+    A = np.stack([t[0] for t in trip]); b = np.stack([t[1] for t in trip])
+    c = np.array([t[2] for t in trip])
+    w = np.random.default_rng(1000).normal(size=(16,) + cut).astype(np.complex128)
+
+    def run():
+        _, (Ad, bd, cd, ws) = gpu_probs(fd, A, b, c, cut, flags=fd.FK_FLAG_B_ZERO)
+        g = fd.fock_diag_probs_vjp_batched(Ad, bd, cd, cut, cuda(w), ws, flags=fd.FK_FLAG_B_ZERO)
+        fd.check_workspace(ws)
+        return [x.cpu().numpy() for x in g]
+
+    gA, gb, gc = run()
+    try:
+        fd.fk_diag_set_engine(fd.FK_ENGINE_FP64)
+        rA, rb, rc = run()
+    finally:
+        fd.fk_diag_set_engine(fd.FK_ENGINE_TENSOR)
+    for i in range(16):
+        scale = np.max(np.abs(rA[i]))
+        assert np.max(np.abs(gA[i] - rA[i])) <= 1e-10 * scale, i
+        assert np.allclose(gA[i], gA[i].T, rtol=0, atol=1e-14 * scale)
+    assert np.max(np.abs(gc - rc)) <= 1e-10 * np.max(np.abs(rc))
