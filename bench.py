@@ -38,14 +38,23 @@ UNIT = "amplitudes/s"
 NCIRC = 16
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant
-# kernel (diag_vjp_kernel) per launch of this 16-circuit workload.  Captured
-# with ncu on a 2-circuit launch (9.990 GB read + 1.553 GB written) and scaled
-# by 8: circuits share no data, so traffic grows in proportion to them.  Valid
-# only for the kernel source it was measured on (sha256 prefix of
-# csrc/walk_diag.cu) and tile shape (pivots per tile / rows per chunk /
-# blocks-per-SM cap); reported as null once either differs.
-TRAFFIC = {"kernel_sha": "bbee46fa125744b9", "tuning": None,
-           "bytes_per_launch": 8 * (9.990473e9 + 1.552535e9)}
+# kernel (diag_vjp_kernel) per launch of this 16-circuit workload, captured
+# with ncu on a 2-circuit launch and scaled by 8: circuits share no data, so
+# traffic grows in proportion to them.  Valid only for the kernel source it
+# was measured on (sha256 prefix of csrc/walk_diag.cu) and the engine / tile
+# shape; reported as null once either differs.
+TRAFFIC = {"kernel_sha": None, "tuning": None, "bytes_per_launch": None}
+
+FALLBACK_HBM_GBS = 6800.0
+
+
+def measured_hbm_gbs():
+    """HBM copy bandwidth of this GPU model from MEASURED_PEAKS.json."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, burst copy)"
+    except (OSError, ValueError, KeyError):
+        return FALLBACK_HBM_GBS, "fallback (6.8 TB/s, one earlier GB300 measurement)"
 
 
 def kernel_sha():
@@ -244,17 +253,18 @@ def run_gpu(args):
     flags = fd.FK_FLAG_B_ZERO
     probs = torch.empty((NCIRC,) + cut, dtype=torch.complex128, device=dev)
     gA, gb, gc = torch.empty_like(A), torch.empty_like(b), torch.empty_like(c)
-    tuning = None
+    from paper_2303_08879_gb300 import autotune
+    best, times = (autotune.TENSOR, 128, 4, 0), None
     if args.tuning:
-        best = tuple(int(v) for v in args.tuning.split("/"))
-        fd.fk_diag_set_tuning(*best)
-        tuning = {"tile_pivots": best[0], "chunk_rows": best[1], "blocks_per_sm_cap": best[2],
-                  "ms_per_candidate": None}
+        parts = args.tuning.split("/")
+        if len(parts) == 3:
+            parts = [autotune.FP64] + parts
+        best = (parts[0],) + tuple(int(v) for v in parts[1:])
     elif not args.no_autotune:
-        from paper_2303_08879_gb300 import autotune
         best, times = autotune.tune_diag(A, b, c, cut, w, flags=flags)
-        tuning = {"tile_pivots": best[0], "chunk_rows": best[1], "blocks_per_sm_cap": best[2],
-                  "ms_per_candidate": times}
+    autotune.apply(best)
+    tuning = {"engine": best[0], "tile_pivots": best[1], "chunk_rows": best[2],
+              "blocks_per_sm_cap": best[3], "ms_per_candidate": times}
     ws = fd.workspace(fd.fk_workspace_size(M, cut, NCIRC, fd.FK_OP_DIAG_VJP, flags), dev)
     stream = torch.cuda.current_stream()
     ev = lambda: torch.cuda.Event(enable_timing=True)
@@ -326,12 +336,36 @@ def run_gpu(args):
         flops_fwd = NCIRC * algorithmic_flops(cut)
         flops_vjp = 2 * flops_fwd
         peak, peaks = measure_fp64_peak(torch)
-        achieved = flops_vjp / (vjp_ms * 1e-3) / 1e12
+        fp64_eq = flops_vjp / (vjp_ms * 1e-3) / 1e12
         sha = kernel_sha()
-        shape = None if tuning is None else [tuning["tile_pivots"], tuning["chunk_rows"],
-                                             tuning["blocks_per_sm_cap"]]
+        shape = list(best)
         traffic = (TRAFFIC["bytes_per_launch"]
                    if TRAFFIC["kernel_sha"] == sha and TRAFFIC["tuning"] == shape else None)
+        stored = fd.fk_describe_diag_schedule(M, cut, flags)["stored"]
+        nout = int(np.prod(cut))
+        bytes_fwd = NCIRC * (32 * stored + 16 * nout)
+        bytes_vjp = NCIRC * (48 * stored + 16 * nout)
+        if best[0] == autotune.TENSOR:
+            hbm, hbm_src = measured_hbm_gbs()
+            gbs = bytes_vjp / (vjp_ms * 1e-3) / 1e9
+            roof = {"bound": "hbm", "kernel": "diag_vjp_kernel", "achieved": gbs, "peak": hbm,
+                    "unit": "GB/s", "frac": gbs / hbm, "traffic": traffic,
+                    "algorithmic_bytes_per_launch": bytes_vjp,
+                    "peak_source": hbm_src,
+                    "forward": {"achieved": bytes_fwd / (fwd_ms * 1e-3) / 1e9,
+                                "frac": bytes_fwd / (fwd_ms * 1e-3) / 1e9 / hbm,
+                                "algorithmic_bytes_per_launch": bytes_fwd},
+                    "fp64_equivalent": {"achieved_tflops": fp64_eq, "fp64_peak_tflops": peak,
+                                        "ratio": fp64_eq / peak, "peaks_measured": peaks,
+                                        "forward_tflops": flops_fwd / (fwd_ms * 1e-3) / 1e12}}
+        else:
+            roof = {"bound": "alu", "kernel": "diag_vjp_kernel", "achieved": fp64_eq,
+                    "peak": peak, "unit": "TFLOP/s", "frac": fp64_eq / peak,
+                    "traffic": traffic,
+                    "peak_source": "measured live: max of FP64 FMA-chain probe and cuBLAS DGEMM",
+                    "peaks_measured": peaks, "peak_nominal": 1.25,
+                    "forward": {"achieved": flops_fwd / (fwd_ms * 1e-3) / 1e12,
+                                "frac": flops_fwd / (fwd_ms * 1e-3) / 1e12 / peak}}
         out = {
             "metric": METRIC, "value": amps / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -342,13 +376,7 @@ def run_gpu(args):
             "e2e": {"value": amps / (e2e_ms * 1e-3), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": 2 * args.steps,
-            "roofline": {"bound": "alu", "kernel": "diag_vjp_kernel", "achieved": achieved,
-                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                         "traffic": traffic,
-                         "peak_source": "measured live: max of FP64 FMA-chain probe and cuBLAS DGEMM",
-                         "peaks_measured": peaks, "peak_nominal": 1.25,
-                         "forward": {"achieved": flops_fwd / (fwd_ms * 1e-3) / 1e12,
-                                     "frac": flops_fwd / (fwd_ms * 1e-3) / 1e12 / peak}},
+            "roofline": roof,
             "clocks": clocks,
             "autotune": tuning,
         }
@@ -374,7 +402,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tuning", default=None,
-                    help="fixed tile shape 'pivots/rows/cap' instead of the autotuner")
+                    help="fixed engine and tile shape 'tensor|fp64/pivots/rows/cap' instead of "
+                         "the autotuner ('pivots/rows/cap' = fp64)")
     ap.add_argument("--circuits", type=int, default=NCIRC,
                     help="circuits per GPU (default 16; smaller only for profiler captures)")
     args = ap.parse_args()

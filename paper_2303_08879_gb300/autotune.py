@@ -1,10 +1,12 @@
-"""Autotuner for the tile shape of the all-detected walk.
+"""Autotuner for the product engine and tile shape of the all-detected walk.
 
-For one workload (shape of the batch, b = 0 or not) it times every compiled
-tile shape (pivots per tile x output rows per register chunk) and a few caps
-on resident blocks per SM, forward + VJP, with CUDA events, and sets the
-fastest with ``fk_diag_set_tuning``.  Results are cached in a JSON file keyed
-by (modes, cutoffs, batch, flags, device name) so later runs reuse them.
+For one workload (shape of the batch, b = 0 or not) it times the tensor-core
+engine and every compiled FP64 tile shape (pivots per tile x output rows per
+register chunk) with a few caps on resident blocks per SM, forward + VJP,
+with CUDA events, and sets the fastest with ``fk_diag_set_engine`` and
+``fk_diag_set_tuning``.  Both engines meet the same accuracy bar.  Results
+are cached in a JSON file keyed by (modes, cutoffs, batch, flags, device
+name) so later runs reuse them.
 """
 from __future__ import annotations
 
@@ -15,8 +17,28 @@ import torch
 
 from . import fockdiag as fd
 
-CANDIDATES = [(128, 8, 0), (128, 4, 0), (64, 8, 0), (64, 4, 0), (256, 8, 0),
-              (128, 8, 2), (128, 4, 3), (64, 8, 4)]
+# (engine, pivots per tile, rows per chunk, blocks-per-SM cap); the tensor
+# engine has one tile shape (128 pivots) and ignores the chunk size.
+TENSOR, FP64 = "tensor", "fp64"
+CANDIDATES = [(TENSOR, 128, 4, 0),
+              (FP64, 128, 8, 0), (FP64, 128, 4, 0), (FP64, 64, 8, 0), (FP64, 64, 4, 0), (FP64, 256, 8, 0),
+              (FP64, 128, 8, 2), (FP64, 128, 4, 3), (FP64, 64, 8, 4)]
+
+
+def apply(cand):
+    """Set engine and tile shape of a candidate."""
+    engine, tpb, ch, cap = cand
+    fd.fk_diag_set_engine(fd.FK_ENGINE_TENSOR if engine == TENSOR else fd.FK_ENGINE_FP64)
+    fd.fk_diag_set_tuning(tpb, ch, cap)
+
+
+def _name(cand):
+    return "%s/%d/%d/%d" % cand
+
+
+def _parse(name):
+    e, t, c, b = name.split("/")
+    return (e, int(t), int(c), int(b))
 
 
 def _key(cutoffs, batch, flags):
@@ -36,13 +58,13 @@ def _load(path):
 
 def tune_diag(A, b, c, cutoffs, grad_probs, flags=0, steps=2, cache_path=None,
               candidates=CANDIDATES):
-    """Pick and set the fastest tile shape for this batch; returns
+    """Pick and set the fastest engine and tile shape for this batch; returns
     (best candidate, {candidate: ms per forward + VJP})."""
     cache = _load(cache_path)
     key = _key(cutoffs, A.shape[0], flags)
     if key in cache:
-        best = tuple(cache[key]["best"])
-        fd.fk_diag_set_tuning(*best)
+        best = _parse(cache[key]["best"])
+        apply(best)
         return best, cache[key]["ms"]
     M = len(cutoffs)
     B = A.shape[0]
@@ -51,7 +73,7 @@ def tune_diag(A, b, c, cutoffs, grad_probs, flags=0, steps=2, cache_path=None,
     gA, gb, gc = torch.empty_like(A), torch.empty_like(b), torch.empty_like(c)
     for cand in candidates:
         try:
-            fd.fk_diag_set_tuning(*cand)
+            apply(cand)
             ws = fd.workspace(fd.fk_workspace_size(M, cutoffs, B, fd.FK_OP_DIAG_VJP, flags), A.device)
         except fd.FockError:
             continue
@@ -67,13 +89,13 @@ def tune_diag(A, b, c, cutoffs, grad_probs, flags=0, steps=2, cache_path=None,
         e1.record()
         torch.cuda.synchronize()
         fd.check_workspace(ws, where="autotune")
-        times["%d/%d/%d" % cand] = e0.elapsed_time(e1) / steps
+        times[_name(cand)] = e0.elapsed_time(e1) / steps
         del ws
     best_s = min(times, key=times.get)
-    best = tuple(int(v) for v in best_s.split("/"))
-    fd.fk_diag_set_tuning(*best)
+    best = _parse(best_s)
+    apply(best)
     if cache_path:
-        cache[key] = {"best": list(best), "ms": times}
+        cache[key] = {"best": best_s, "ms": times}
         tmp = cache_path + ".tmp"
         with open(tmp, "w") as f:
             json.dump(cache, f, indent=1)
