@@ -384,6 +384,25 @@ struct Walk {
         return __float_as_uint(d) >> 16;                                      // exact in bf16
     }
 
+    // The seven digits of a pair (lo, hi) of biased fixed points as packed
+    // bf16 words: word s = digit s of lo in bits 0-15, of hi in bits 16-31.
+    // Byte k of U is moved into the mantissa of 2^23 (one byte permute), the
+    // float subtraction of 2^23 + 128 gives the digit exactly, and its top
+    // half is its bf16 encoding.
+    static __device__ __forceinline__ void digit_words(uint64_t lo, uint64_t hi, uint32_t (&w)[NDIG])
+    {
+        const uint32_t l0 = (uint32_t)lo, l1 = (uint32_t)(lo >> 32);
+        const uint32_t h0 = (uint32_t)hi, h1 = (uint32_t)(hi >> 32);
+#pragma unroll
+        for (int sl = 0; sl < NDIG; ++sl) {
+            const int k = NDIG - 1 - sl;
+            const uint32_t sel = 0x7650u | (uint32_t)(k & 3);
+            const float a = __uint_as_float(__byte_perm(k >= 4 ? l1 : l0, 0x4B000000u, sel)) - 8388736.0f;
+            const float b = __uint_as_float(__byte_perm(k >= 4 ? h1 : h0, 0x4B000000u, sel)) - 8388736.0f;
+            w[sl] = __byte_perm(__float_as_uint(a), __float_as_uint(b), 0x7632);
+        }
+    }
+
     // Digit slices of the real form R of A_s (row 2i: Re, col 2j -> Re A_ij,
     // col 2j+1 -> -Im A_ij; row 2i+1: Im A_ij, Re A_ij) into shared memory.
     static __device__ void load_circuit_digits(Smem &s, const double2 *As, int D)
@@ -463,10 +482,10 @@ struct Walk {
             for (int ks = 0; ks < KS; ++ks)
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const uint64_t ur = to_fixed(xv[ks][h][0], fm), ui = to_fixed(xv[ks][h][1], fm);
+                    uint32_t wd[NDIG];
+                    digit_words(to_fixed(xv[ks][h][0], fm), to_fixed(xv[ks][h][1], fm), wd);
 #pragma unroll
-                    for (int sl = 0; sl < NDIG; ++sl)
-                        bq[sl][ks][h] = digit_bits(ur, sl) | (digit_bits(ui, sl) << 16);
+                    for (int sl = 0; sl < NDIG; ++sl) bq[sl][ks][h] = wd[sl];
                 }
             __syncwarp();   // every lane has read this N tile's inputs
             const double sx0 = digit_scale(__shfl_sync(0xffffffffu, fm, 8 * tig));
@@ -560,93 +579,90 @@ struct Walk {
     // field of its reads) and its adjoints by the inverse, which leaves every
     // product unchanged; the adjoints then share a power of two per row w
     // over the 32 pivots, so each term is exact relative to the largest
-    // product of its row.  Real form: rows 2w -> Re P = sum (Yr Xr + Yi Xi),
-    // 2w+1 -> Im P = sum (Yi Xr - Yr Xi); K = (pivot, re/im) = 64.
+    // product of its row.  Real form with K = (pivot t, re/im) = 64:
+    //   A[w][(t,0)] = Yr, A[w][(t,1)] = Yi;  B[(t,0)][2j] = Xr, B[(t,1)][2j] = Xi,
+    //   B[(t,0)][2j+1] = -Xi, B[(t,1)][2j+1] = Xr,
+    // so column 2j of A B is Re P[w][j] and column 2j+1 is Im P[w][j].
     // The result is added to the warp's own slot (single writer).
     static __device__ void tc_partials(const DiagArgs &a, const Smem &s, int circ, int row0, int N)
     {
+        constexpr int NT = 2 * KS;   // N tiles over the 2N real columns (N <= 8 KS)
         const int lane = threadIdx.x & 31, grp = lane >> 2, tig = lane & 3, warp = threadIdx.x >> 5;
-        const int D = 2 * a.sh.M, n2 = 2 * N, nks = (n2 + 15) >> 4, nnt = (N + 7) >> 3;
+        const int D = 2 * a.sh.M, nnt = (2 * N + 7) >> 3;
         const double *wx = s.wb + (size_t)warp * XS * WBS;
         const double *wy = s.wy + (size_t)warp * XS * WBS;
         const int *ef = s.wf + warp * 32;
         const int *gy = s.wg + warp * 32;
         const size_t slot = (size_t)blockIdx.x * (TPB / 32) + warp;
         double *pA = (double *)(a.partA + ((size_t)circ * a.slots + slot) * D * D);
+        float acc[NDIG][NT][4];
+#pragma unroll
+        for (int d = 0; d < NDIG; ++d)
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[d][nt][q] = 0.f;
+        // A rows of this lane: w0 = grp, w1 = grp + 8
+        const int g0 = grp < N ? gy[grp] : 0, g1 = grp + 8 < N ? gy[grp + 8] : 0;
 #pragma unroll 1
-        for (int mt = 0; mt < nks; ++mt) {
-            float acc[NDIG][KS][4];
+        for (int ks = 0; ks < 4; ++ks) {
+            const int t0 = 8 * ks + tig, t1 = t0 + 4;
+            const int e0 = ef[t0], e1 = ef[t1];
+            uint32_t aq[NDIG][4];
 #pragma unroll
-            for (int d = 0; d < NDIG; ++d)
-#pragma unroll
-                for (int nt = 0; nt < KS; ++nt)
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) acc[d][nt][q] = 0.f;
-            // this lane's A rows: m = 16 mt + grp (+8) -> w = 8 mt + grp / 2 (+4), rho = grp & 1
-            const int w0 = 8 * mt + (grp >> 1), rho = grp & 1;
-            const int g0 = w0 < N ? gy[w0] : 0, g1 = w0 + 4 < N ? gy[w0 + 4] : 0;
-#pragma unroll 1
-            for (int ks = 0; ks < 4; ++ks) {
-                const int t0 = 8 * ks + tig, t1 = t0 + 4;
-                const int e0 = ef[t0], e1 = ef[t1];
-                // A operand words: (rho = 0) (Yr, Yi), (rho = 1) (Yi, -Yr) of (w, t)
-                uint32_t aq[NDIG][4];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const int w = w0 + 4 * (k & 1), t = (k & 2) ? t1 : t0, e = (k & 2) ? e1 : e0;
-                    const int g = (k & 1) ? g1 : g0;
-                    double yr = 0.0, yi = 0.0;
-                    if (w < N && g != 0 && e != 0) {
-                        yr = wy[(2 * w) * WBS + t];
-                        yi = wy[(2 * w + 1) * WBS + t];
-                    }
-                    const int fm = g - e + 1022;
-                    const uint64_t ur = to_fixed_rel(rho ? yi : yr, fm);
-                    const uint64_t ui = to_fixed_rel(rho ? -yr : yi, fm);
-#pragma unroll
-                    for (int sl = 0; sl < NDIG; ++sl) aq[sl][k] = digit_bits(ur, sl) | (digit_bits(ui, sl) << 16);
+            for (int k = 0; k < 4; ++k) {
+                const int w = grp + 8 * (k & 1), t = (k & 2) ? t1 : t0, e = (k & 2) ? e1 : e0;
+                const int g = (k & 1) ? g1 : g0;
+                double yr = 0.0, yi = 0.0;
+                if (w < N && g != 0 && e != 0) {
+                    yr = wy[(2 * w) * WBS + t];
+                    yi = wy[(2 * w + 1) * WBS + t];
                 }
-                // B operand words: (Xr, Xi) of (j = 8 nt + grp, t)
-                uint32_t bq[NDIG][KS][2];
+                const int fm = g - e + 1022;
+                uint32_t wd[NDIG];
+                digit_words(to_fixed_rel(yr, fm), to_fixed_rel(yi, fm), wd);
 #pragma unroll
-                for (int nt = 0; nt < KS; ++nt)
+                for (int sl = 0; sl < NDIG; ++sl) aq[sl][k] = wd[sl];
+            }
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int j = 8 * nt + grp, t = h ? t1 : t0, e = h ? e1 : e0;
-                        double xr = 0.0, xi = 0.0;
-                        if (nt < nnt && j < N) {
-                            xr = wx[(2 * j) * WBS + t];
-                            xi = wx[(2 * j + 1) * WBS + t];
-                        }
-                        const uint64_t ur = to_fixed(xr, e), ui = to_fixed(xi, e);
+            for (int nt = 0; nt < NT; ++nt) {
+                if (nt >= nnt) continue;
+                const int n = 8 * nt + grp, j = n >> 1, im = n & 1;
+                uint32_t bq[NDIG][2];
 #pragma unroll
-                        for (int sl = 0; sl < NDIG; ++sl)
-                            bq[sl][nt][h] = digit_bits(ur, sl) | (digit_bits(ui, sl) << 16);
+                for (int h = 0; h < 2; ++h) {
+                    const int t = h ? t1 : t0, e = h ? e1 : e0;
+                    double xr = 0.0, xi = 0.0;
+                    if (j < N) {
+                        xr = wx[(2 * j) * WBS + t];
+                        xi = wx[(2 * j + 1) * WBS + t];
                     }
+                    uint32_t wd[NDIG];
+                    digit_words(to_fixed(im ? -xi : xr, e), to_fixed(im ? xr : xi, e), wd);
+#pragma unroll
+                    for (int sl = 0; sl < NDIG; ++sl) bq[sl][h] = wd[sl];
+                }
 #pragma unroll
                 for (int sa = 0; sa < NDIG; ++sa)
 #pragma unroll
-                    for (int u = 0; u + sa < NDIG; ++u)
-#pragma unroll
-                        for (int nt = 0; nt < KS; ++nt)
-                            if (nt < nnt) mma_bf16(acc[sa + u][nt], aq[sa], bq[u][nt]);
+                    for (int u = 0; u + sa < NDIG; ++u) mma_bf16(acc[sa + u][nt], aq[sa], bq[u]);
             }
+        }
 #pragma unroll
-            for (int nt = 0; nt < KS; ++nt) {
-                if (nt >= nnt) continue;
+        for (int nt = 0; nt < NT; ++nt) {
+            if (nt >= nnt) continue;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int w = w0 + 4 * (q >> 1), j = 8 * nt + 2 * tig + (q & 1);
-                    const int g = (q >> 1) ? g1 : g0;
-                    if (w < N && j < N && g >= 26) {
-                        float a7[NDIG][4];
+            for (int q = 0; q < 4; ++q) {
+                const int w = grp + 8 * (q >> 1), n = 8 * nt + 2 * tig + (q & 1), j = n >> 1;
+                const int g = (q >> 1) ? g1 : g0;
+                if (w < N && j < N && g >= 26) {
+                    float a7[NDIG][4];
 #pragma unroll
-                        for (int d = 0; d < NDIG; ++d) a7[d][0] = acc[d][nt][q];
-                        const long long Y = combine_digits(a7, 0);
-                        const double v = __ll2double_rn(Y) * digit_scale(g) * 0x1p-26;
-                        double *dst = pA + 2 * ((size_t)(row0 + w) * D + row0 + j) + rho;
-                        *dst += v;
-                    }
+                    for (int d = 0; d < NDIG; ++d) a7[d][0] = acc[d][nt][q];
+                    const long long Y = combine_digits(a7, 0);
+                    const double v = __ll2double_rn(Y) * digit_scale(g) * 0x1p-26;
+                    double *dst = pA + 2 * ((size_t)(row0 + w) * D + row0 + j) + (n & 1);
+                    *dst += v;
                 }
             }
         }
