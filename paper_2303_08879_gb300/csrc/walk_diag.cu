@@ -712,9 +712,12 @@ struct Walk {
         }
     }
 
-    // Tile bookkeeping for one phase: segment k (anchor K for AP, 0 for DP and
-    // DIAG) x circuit, ceil(count / TPB) tiles each; tiles[k] = prefix over k.
-    // kind: 0 = AP, 1 = DP, 2 = DIAG.
+    // Tiles of a phase are numbered circuit-major: circuit c, then segment k
+    // (anchor K for AP; one segment for DP and DIAG), then ceil(count / TPB)
+    // tiles; tiles[k] = prefix over k within one circuit, tiles[nseg] = tiles
+    // per circuit.  Blocks take tiles round robin, so at any moment the grid
+    // works on one or two circuits and the reads that pivots of different
+    // anchors share stay in L2.  kind: 0 = AP, 1 = DP, 2 = DIAG.
     static __device__ int phase_tiles(const DiagArgs &a, Smem &s, int kind, int lev)
     {
         const DiagShape &sh = a.sh;
@@ -728,31 +731,30 @@ struct Walk {
                 if (kind == 0) cnt = level_count(sh, s, k, 1, lev);
                 else if (kind == 1) cnt = level_count(sh, s, 0, 1, lev);
                 else cnt = level_count(sh, s, 0, 0, lev);
-                acc += a.B * (int)((cnt + TPB - 1) / TPB);
+                acc += (int)((cnt + TPB - 1) / TPB);
             }
             s.tiles[nseg] = acc;
         }
         __syncthreads();
-        return s.tiles[(kind == 0) ? sh.M : 1];
+        return a.B * s.tiles[(kind == 0) ? sh.M : 1];
     }
-
 
     static __device__ TileId decode_tile(const DiagArgs &a, const Smem &s, int kind, int lev, int tile)
     {
         const DiagShape &sh = a.sh;
         TileId t;
         const int nseg = (kind == 0) ? sh.M : 1;
+        const int Tc = s.tiles[nseg];
+        t.circ = tile / Tc;
+        const int r = tile - t.circ * Tc;
         int k = 0;
-        while (k + 1 < nseg && tile >= s.tiles[k + 1]) ++k;
+        while (k + 1 < nseg && r >= s.tiles[k + 1]) ++k;
         t.seg = k;
         unsigned cnt;
         if (kind == 0) cnt = level_count(sh, s, k, 1, lev);
         else if (kind == 1) cnt = level_count(sh, s, 0, 1, lev);
         else cnt = level_count(sh, s, 0, 0, lev);
-        const int per = (int)((cnt + TPB - 1) / TPB);
-        const int rem = tile - s.tiles[k];
-        t.circ = rem / per;
-        t.rank0 = (unsigned)(rem % per) * TPB;
+        t.rank0 = (unsigned)(r - s.tiles[k]) * TPB;
         t.count = cnt;
         return t;
     }
