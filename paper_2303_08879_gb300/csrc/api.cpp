@@ -44,7 +44,11 @@ int build_diag_shape(int M, const int *cutoffs, bool has_b, DiagShape *sh)
         sh->stride[i] = st;
         st *= sh->C[i];
     }
-    // amplitude boxes, concatenated: DIAG, T2(K), P1010/P1001(K,m), T1K/T1B(j)
+    // amplitude boxes, concatenated: DIAG, T2(K), P1010/P1001(K,m), T1K/T1B(j).
+    // P1010(K,m) and P1001(K,m) share their index space and are interleaved
+    // (element i of P1010 at off + 2i, of P1001 at off + 2i + 1): a pivot
+    // reads and writes both at the same index, so each 32-byte sector it
+    // touches holds two of its own values.
     int64_t off = nd;
     for (int K = 0; K < k; ++K) {
         sh->off_t2[K] = off;
@@ -54,9 +58,8 @@ int build_diag_shape(int M, const int *cutoffs, bool has_b, DiagShape *sh)
         for (int m = K + 1; m < k; ++m) {
             const int64_t n = box_size(*sh, K, K, 1, m, 1);
             sh->off_1010[K][m] = off;
-            off += n;
-            sh->off_1001[K][m] = off;
-            off += n;
+            sh->off_1001[K][m] = off + 1;
+            off += 2 * n;
         }
     if (has_b) {
         for (int j = 0; j < k; ++j) {

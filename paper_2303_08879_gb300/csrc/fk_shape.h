@@ -56,8 +56,8 @@ struct DiagShape {
     int64_t off_t2[FK_MAXM];
     int64_t off_t1k[FK_MAXM];
     int64_t off_t1b[FK_MAXM];
-    int64_t off_1010[FK_MAXM][FK_MAXM];
-    int64_t off_1001[FK_MAXM][FK_MAXM];
+    int64_t off_1010[FK_MAXM][FK_MAXM];   // P1010(K,m) element i at off_1010 + 2 i
+    int64_t off_1001[FK_MAXM][FK_MAXM];   // P1001(K,m) element i at off_1001 + 2 i (interleaved)
     int64_t off_ap[FK_MAXM];  // AP(K) pivot boxes inside the VJP scratch array
     int64_t n_ap;             // sum_K |AP(K)|
     int64_t stride[FK_MAXM];  // DIAG strides S_j = prod_{i>j} C_i

@@ -315,10 +315,10 @@ __device__ PGeom ap_geom(const DiagShape &ds, const Dig &e, int K, const CSmem &
         const int j = 2 * (m - K);
         const int64_t ip = box_index(ds, e, K, K, 1, m, 1);
         const int em = e(m);
-        g.yr[j] = ds.off_1001[K][m] + ip - ds.stride[m];
-        g.yr[j + 1] = ds.off_1010[K][m] + ip - ds.stride[m];
-        g.yw[j] = ds.off_1010[K][m] + ip;
-        g.yw[j + 1] = ds.off_1001[K][m] + ip;
+        g.yr[j] = ds.off_1001[K][m] + 2 * (ip - ds.stride[m]);   // P1010/P1001 interleaved
+        g.yr[j + 1] = ds.off_1010[K][m] + 2 * (ip - ds.stride[m]);
+        g.yw[j] = ds.off_1010[K][m] + 2 * ip;
+        g.yw[j + 1] = ds.off_1001[K][m] + 2 * ip;
         g.den[j] = g.den[j + 1] = em + 1;
         if (em >= 1) g.vmask |= 3u << j;
         if (em <= ds.C[m] - 2) g.nmask |= 3u << j;

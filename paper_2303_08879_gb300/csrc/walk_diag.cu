@@ -788,7 +788,7 @@ struct Walk {
         if (j == 1) return sh.off_t2[K] + g.t2 - sh.stride[K];
         const int m = K + j / 2;
         const int64_t ip = s.idx[m * TPB + threadIdx.x];
-        return ((j & 1) ? sh.off_1010[K][m] : sh.off_1001[K][m]) + ip - sh.stride[m];
+        return ((j & 1) ? sh.off_1010[K][m] : sh.off_1001[K][m]) + 2 * (ip - sh.stride[m]);
     }
 
     // Flat address of AP write row i and its scale index P_w + 1.
@@ -801,7 +801,7 @@ struct Walk {
         const int m = K + i / 2;
         *den = e(m) + 1;
         const int64_t ip = s.idx[m * TPB + threadIdx.x];
-        return ((i & 1) ? sh.off_1001[K][m] : sh.off_1010[K][m]) + ip;
+        return ((i & 1) ? sh.off_1001[K][m] : sh.off_1010[K][m]) + 2 * ip;
     }
 
 
