@@ -39,11 +39,14 @@ NCIRC = 16
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant
 # kernel (diag_vjp_kernel) per launch of this 16-circuit workload, captured
-# with ncu on a 2-circuit launch and scaled by 8: circuits share no data, so
-# traffic grows in proportion to them.  Valid only for the kernel source it
+# with ncu on a 2-circuit launch (7.735 GB read + 1.196 GB written) and
+# scaled by 8: circuits share no data, so traffic grows in proportion to them
+# (measured per circuit: 5.5 / 6.0 / 6.2 GB at 1 / 2 / 4 circuits, so the
+# scaled figure is a slight underestimate).  Valid only for the kernel source it
 # was measured on (sha256 prefix of csrc/walk_diag.cu) and the engine / tile
 # shape; reported as null once either differs.
-TRAFFIC = {"kernel_sha": None, "tuning": None, "bytes_per_launch": None}
+TRAFFIC = {"kernel_sha": "784a2210dc977cc7", "tuning": ["tensor", 128, 4, 0],
+           "bytes_per_launch": 8 * (7734632448 + 1195694336)}
 
 FALLBACK_HBM_GBS = 6800.0
 
@@ -218,6 +221,88 @@ def measure_fp64_peak(torch):
     return max(fma, best), {"fma_probe": fma, "dgemm": best}
 
 
+def measured_bf16_tflops():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured (MEASURED_PEAKS.json bf16_tflops, burst)"
+    except (OSError, ValueError, KeyError):
+        return 1900.0, "fallback (1.9 PFLOP/s, one earlier GB300 measurement)"
+
+
+def secondary_rows(torch, fd, inputs, dev, reps=5):
+    """The other hot-path rows on their own workloads, CUDA-event timed after
+    warm-up (reported beside the headline; not part of ``value``)."""
+    rows = {}
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    # Algorithm 2 forward + VJP: 64 conditional circuits, per-circuit cutoffs, b != 0
+    mask = (1, 1, 0)
+    circs = inputs.workload("cond_m3_batch64")
+    cuts = [cc.cutoffs for cc in circs]
+    trip = [fd.fk_gaussian_to_triple(cc.V, cc.mean) for cc in circs]
+    A = torch.from_numpy(np.stack([t[0] for t in trip])).to(dev)
+    b = torch.from_numpy(np.stack([t[1] for t in trip])).to(dev)
+    c = torch.from_numpy(np.array([t[2] for t in trip], np.complex128)).to(dev)
+    rho, offs, ws = fd.fock_conditional_dm_batched(A, b, c, cuts, mask)
+    g = torch.randn(rho.shape, dtype=torch.float64, device=dev).to(torch.complex128)
+    out = tuple(torch.empty_like(x) for x in (A, b, c))
+    for _ in range(3):
+        fd.fock_conditional_dm_batched(A, b, c, cuts, mask, rho=rho, ws=ws)
+        fd.fock_conditional_dm_vjp_batched(A, b, c, cuts, mask, g, ws, out=out)
+    torch.cuda.synchronize()
+    t0, t1, t2 = ev(), ev(), ev()
+    fwd = vjp = 0.0
+    for _ in range(reps):
+        t0.record()
+        fd.fock_conditional_dm_batched(A, b, c, cuts, mask, rho=rho, ws=ws)
+        t1.record()
+        fd.fock_conditional_dm_vjp_batched(A, b, c, cuts, mask, g, ws, out=out)
+        t2.record()
+        torch.cuda.synchronize()
+        fwd += t0.elapsed_time(t1); vjp += t1.elapsed_time(t2)
+    fd.check_workspace(ws, where="conditional rows")
+    fwd /= reps; vjp /= reps
+    n_out = int(offs[-1])
+    rows["conditional_walk"] = {
+        "workload": "cond_m3_batch64: 64 circuits, modes 0,1 detected (C 10..20), mode 2 "
+                    "undetected (C 20..30), b != 0",
+        "forward_ms": fwd, "vjp_ms": vjp, "outputs": n_out,
+        "outputs_per_s": n_out / ((fwd + vjp) * 1e-3), "engine": "fp64"}
+    del rho, ws, g
+    # BF16 MLP training step (15-256-256-256-2, forward + backward + Adam): the
+    # training batch (2048) and a large batch (65536) for the GEMM roofline
+    from paper_2303_08879_gb300.mlp import MLP, init_params, IN, HIDDEN, OUT
+    macs = IN * HIDDEN + 2 * HIDDEN * HIDDEN + HIDDEN * OUT
+    peak, src = measured_bf16_tflops()
+    res = {}
+    for batch in (2048, 65536):
+        mlp = MLP(init_params(0), batch, dev)
+        gen = torch.Generator(device=dev); gen.manual_seed(0)
+        X = torch.rand((batch, IN), device=dev, generator=gen) * 2 - 1
+        Y = torch.rand((batch, OUT), device=dev, generator=gen)
+        for _ in range(5):
+            mlp.train_step(X, Y)
+        torch.cuda.synchronize()
+        steps = 20
+        e0, e1 = ev(), ev()
+        e0.record()
+        for _ in range(steps):
+            mlp.train_step(X, Y)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        tf = 3 * 2 * batch * macs / (ms * 1e-3) / 1e12   # forward + two backward GEMMs per layer
+        res[batch] = (ms, tf)
+        del mlp
+    ms, tf = res[65536]
+    rows["mlp_train_step"] = {
+        "workload": "BF16 MLP 15-256-256-256-2, forward + backward + Adam",
+        "train_batch_2048_ms": res[2048][0], "batch_65536_ms": ms,
+        "samples_per_s": 65536 / (ms * 1e-3),
+        "roofline": {"bound": "tensor", "batch": 65536, "achieved": tf, "peak": peak,
+                     "unit": "TFLOP/s", "frac": tf / peak, "peak_source": src}}
+    return rows
+
+
 def run_gpu(args):
     if not args.no_cpu_baseline and int(os.environ.get("WORLD_SIZE", "1")) == 1:
         import oracle                  # compile the oracle before any CUDA work
@@ -380,6 +465,8 @@ def run_gpu(args):
             "clocks": clocks,
             "autotune": tuning,
         }
+        if world == 1 and not args.no_rows:
+            out["rows"] = secondary_rows(torch, fd, inputs, dev)
         if world == 1 and not args.no_cpu_baseline:
             n, dt, scut = oracle_sample(20.0)
             out["cpu_baseline"] = {
@@ -401,6 +488,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-rows", action="store_true",
+                    help="skip the secondary rows (conditional walk, MLP step)")
     ap.add_argument("--tuning", default=None,
                     help="fixed engine and tile shape 'tensor|fp64/pivots/rows/cap' instead of "
                          "the autotuner ('pivots/rows/cap' = fp64)")
