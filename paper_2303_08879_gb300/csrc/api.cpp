@@ -70,6 +70,27 @@ int build_diag_shape(int M, const int *cutoffs, bool has_b, DiagShape *sh)
         }
     }
     sh->circ_size = off;
+    // level-major layout (walk_diag.cu)
+    int64_t lo = nd;
+    for (int K = 0; K < k; ++K) {
+        int64_t f = sh->C[K] - 1;
+        for (int i = K + 1; i < k; ++i) f *= sh->C[i];
+        sh->fam[K] = f;
+    }
+    for (int K = 0; K < k; ++K) {
+        sh->lm_t2[K] = lo;
+        lo += sh->fam[K];
+    }
+    for (int K = 0; K < k; ++K) {
+        sh->lm_p[K] = lo;
+        lo += 2 * (int64_t)(k - 1 - K) * sh->fam[K];
+    }
+    if (has_b)
+        for (int j = 0; j < k; ++j) {
+            sh->lm_t1[j] = lo;
+            lo += 2 * sh->fam[0];
+        }
+    sh->circ_alloc = lo;
     int64_t ap = 0;
     for (int K = 0; K < k; ++K) {
         sh->off_ap[K] = ap;
@@ -87,7 +108,7 @@ int diag_layout(const DiagShape &sh, int batch, bool vjp, DiagLayout *lay)
     lay->ctl = o; o = align_up(o + sizeof(Control));
     lay->As = o; o = align_up(o + B * D * D * c16);
     lay->bs = o; o = align_up(o + B * D * c16);
-    lay->F = o; o = align_up(o + B * (size_t)sh.circ_size * c16);
+    lay->F = o; o = align_up(o + B * (size_t)sh.circ_alloc * c16);
     lay->grid_vjp = lay->slots_vjp = 0;
     if (vjp) {
         int grid = 1, slots = 1;
@@ -97,7 +118,7 @@ int diag_layout(const DiagShape &sh, int batch, bool vjp, DiagLayout *lay)
         }
         lay->grid_vjp = grid;
         lay->slots_vjp = slots;
-        lay->Fbar = o; o = align_up(o + B * (size_t)sh.circ_size * c16);
+        lay->Fbar = o; o = align_up(o + B * (size_t)sh.circ_alloc * c16);
         lay->scratch = o; o = align_up(o + B * (size_t)sh.n_ap * c16);
         lay->partA = o; o = align_up(o + B * (size_t)slots * D * D * c16);
         lay->partb = o; o = align_up(o + B * (size_t)slots * D * c16);

@@ -14,8 +14,18 @@
 //   T1B(j)        d + 1_{2j+1}        d_j in [0, C_j-2]; T1B(0): d_0 <= C_0-3
 //
 // T1K/T1B (offset_1) are needed only when b != 0 (their weight is odd,
-// eq. recrel_noB).  Each box is a dense row-major array over its digits
-// (mode M-1 fastest); the boxes of one circuit are concatenated.
+// eq. recrel_noB).  Two layouts of the boxes exist:
+//  * mixed radix (off_* fields, used by the conditional walk): each box is
+//    a dense row-major array over its digits (mode M-1 fastest);
+//  * level-major (lm_* fields, used by the all-detected walk): the vectors of
+//    "family K" -- digits over modes K..M-1, e_K <= C_K-2 -- are ordered by
+//    digit sum, then lexicographically (mode K slowest).  DIAG uses the
+//    family of all modes without the restriction; T2(K) and every
+//    P1010/P1001(K,m) pair use family K; the T1K/T1B(j) pairs use family 0.
+//    A box whose own digit ranges are narrower leaves those entries unused.
+//    Within a level, a vector's position is its rank, computed from
+//    prefix sums of the level counts; a pivot's writes sit at its own rank
+//    and consecutive pivots touch consecutive entries.
 //
 // Pivots (Algorithm 1):
 //   AP(K) off-diagonal pivot e + 1_{2K}, modes < K zero, e_K in [0, C_K-2]
@@ -60,6 +70,12 @@ struct DiagShape {
     int64_t off_1001[FK_MAXM][FK_MAXM];   // P1001(K,m) element i at off_1001 + 2 i (interleaved)
     int64_t off_ap[FK_MAXM];  // AP(K) pivot boxes inside the VJP scratch array
     int64_t n_ap;             // sum_K |AP(K)|
+    int64_t fam[FK_MAXM];     // |family K| = (C_K - 1) prod_{i>K} C_i
+    int64_t lm_t2[FK_MAXM];   // level-major T2(K)
+    int64_t lm_p[FK_MAXM];    // level-major P pairs of anchor K: pair (K,m) at lm_p[K] + 2 (m-K-1) fam[K],
+                              // P1010 at even, P1001 at odd positions
+    int64_t lm_t1[FK_MAXM];   // level-major T1 pair of mode j (b != 0): T1B at even, T1K at odd
+    int64_t circ_alloc;       // level-major amplitudes allocated per circuit (>= circ_size)
     int64_t stride[FK_MAXM];  // DIAG strides S_j = prod_{i>j} C_i
 };
 

@@ -129,6 +129,21 @@ struct LevelTab {
     }
 };
 
+// The same counts kept as prefix sums over t: S[i][t] = sum_{u <= t} W[i][u]
+// (one table serves counts, level offsets and lexicographic ranks).
+struct PrefixTab {
+    const unsigned *S;
+    int Wn;
+    __device__ __forceinline__ unsigned pre(int i, int t) const
+    {
+        return t < 0 ? 0u : S[i * Wn + (t < Wn ? t : Wn - 1)];
+    }
+    __device__ __forceinline__ unsigned at(int i, int t) const
+    {
+        return (t < 0 || t >= Wn) ? 0u : pre(i, t) - pre(i, t - 1);
+    }
+};
+
 // Block-cooperative construction of the table for cutoffs C[0..M-1].
 __device__ __forceinline__ void build_level_table(unsigned *W, int Wn, const int *C, int M)
 {
@@ -144,10 +159,24 @@ __device__ __forceinline__ void build_level_table(unsigned *W, int Wn, const int
     }
 }
 
+// Block-cooperative prefix form: W, then each row summed in place.
+__device__ __forceinline__ void build_prefix_table(unsigned *S, int Wn, const int *C, int M)
+{
+    build_level_table(S, Wn, C, M);
+    for (int i = threadIdx.x; i <= M; i += blockDim.x) {
+        unsigned acc = 0;
+        for (int t = 0; t < Wn; ++t) {
+            acc += S[i * Wn + t];
+            S[i * Wn + t] = acc;
+        }
+    }
+    __syncthreads();
+}
+
 // Number of digit vectors over modes k0..M-1 with digit k0 in [0, C_k0 - dk0)
 // and the others in [0, C_i), summing to s.
-__device__ __forceinline__ unsigned level_count(const int *C, const LevelTab &W, int k0, int dk0,
-                                                int s)
+template <class Tab>
+__device__ __forceinline__ unsigned level_count(const int *C, const Tab &W, int k0, int dk0, int s)
 {
     unsigned n = 0;
     for (int v = 0; v < C[k0] - dk0; ++v) n += W.at(k0 + 1, s - v);
@@ -155,8 +184,9 @@ __device__ __forceinline__ unsigned level_count(const int *C, const LevelTab &W,
 }
 
 // The rank-th such vector in lexicographic order (mode k0 slowest).
-__device__ __forceinline__ Dig unrank(const int *C, int M, const LevelTab &W, int k0, int dk0,
-                                      int s, unsigned rank)
+template <class Tab>
+__device__ __forceinline__ Dig unrank(const int *C, int M, const Tab &W, int k0, int dk0, int s,
+                                      unsigned rank)
 {
     Dig d;
     int rem = s;

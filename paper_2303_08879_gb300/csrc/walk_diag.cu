@@ -53,7 +53,10 @@ struct DiagArgs {
 
 // ------------------------------------------------------------ shared memory
 struct Smem {
-    unsigned *W;      // [(M+1)][L+2]: ways digits i..M-1 (extents C) sum to t
+    unsigned *S;      // [(M+1)][L+2]: S[i][t] = number of digit vectors over modes
+                      // i..M-1 (extents C) with digit sum <= t
+    int64_t *cum0;    // [M] offset of the current phase's level in family K
+    int64_t *cum1;    // [M] offset of the level below
     int Wn;           // row length
     double *inv;      // 1/v
     double *fact;     // v!
@@ -82,19 +85,26 @@ struct TileId {
 };
 
 // AP(K) pivot with base e: read column j / write row i addresses and masks.
+// (level-major addresses inside the circuit's amplitude array, see fk_shape.h)
 struct ApGeom {
-    int64_t diag;    // DIAG index of e
-    int64_t t2;      // T2(K) index of e
-    int64_t t1k;     // T1K(K) index of e (pivot value)
-    unsigned vmask;  // valid reads
-    unsigned nmask;  // needed writes
+    int64_t r;        // rank of the pivot e in family K at its level s
+    int64_t rd;       // DIAG[e]            (level s)
+    int64_t rt2;      // T2(K)[e - 1_K]     (level s - 1; valid if e_K >= 1)
+    int64_t wt2;      // T2(K)[e]
+    int64_t wdiag;    // DIAG[e + 1_K]      (level s + 1)
+    int64_t pout;     // caller's probability index of e + 1_K (row-major over modes)
+    int64_t lk0, lkm; // family-K offsets of levels s and s - 1
+    int64_t fp;       // T1K(K)[e] (pivot value, b != 0)
+    unsigned vmask;   // valid reads
+    unsigned nmask;   // needed writes
 };
 
 // DP pivot d (b != 0): read column j = 2q -> T1B(q)[d-1_q], 2q+1 -> T1K(q)[d-1_q];
 // write row i = 2q -> T1K(q)[d], 2q+1 -> T1B(q)[d].
 struct DpGeom {
-    int64_t diag;
-    int64_t t1b0;    // T1B(0) index of d
+    int64_t r;        // rank of d in family 0 at its level s
+    int64_t rdiag;    // DIAG[d] (the pivot value)
+    int64_t l00, l0m; // family-0 offsets of levels s and s - 1
     unsigned vmask, nmask;
 };
 
@@ -126,6 +136,7 @@ struct Walk {
         size_t n = 0;
         n += (size_t)(M + 1) * (L + 2) * sizeof(unsigned);
         n = (n + 15) & ~(size_t)15;
+        n += 2 * (size_t)M * sizeof(int64_t);
         n += 2 * TABN * sizeof(double);
         if (TC) {
             const int D2 = 2 * D;
@@ -152,10 +163,12 @@ struct Walk {
         Smem s;
         const int M = sh.M, D = 2 * M;
         unsigned char *p = smem_raw;
-        s.W = (unsigned *)p;
+        s.S = (unsigned *)p;
         s.Wn = sh.L + 2;
         p += (size_t)(M + 1) * s.Wn * sizeof(unsigned);
         p = (unsigned char *)(((uintptr_t)p + 15) & ~(uintptr_t)15);
+        s.cum0 = (int64_t *)p; p += (size_t)M * sizeof(int64_t);
+        s.cum1 = (int64_t *)p; p += (size_t)M * sizeof(int64_t);
         s.inv = (double *)p; p += TABN * sizeof(double);
         s.fact = (double *)p; p += TABN * sizeof(double);
         s.A3 = s.R3 = s.Y3 = nullptr;
@@ -203,10 +216,48 @@ struct Walk {
     static __device__ void build_tables(const DiagShape &sh, Smem &s)
     {
         build_scalar_tables(s.inv, s.fact);
-        build_level_table(s.W, s.Wn, sh.C, sh.M);
+        build_prefix_table(s.S, s.Wn, sh.C, sh.M);
     }
 
-    static __device__ __forceinline__ LevelTab ltab(const Smem &s) { return LevelTab{s.W, s.Wn}; }
+    // Level-major ranks.  For a family over modes k0..M-1 (suffix extents C),
+    // the rank of x among the vectors of its digit sum in lexicographic order
+    // is sum_i Pf(i, t_i, x_i) with t_i the digit sum of x_i..x_{M-1} and
+    //   Pf(i, t, x) = sum_{v < x} W[i+1][t - v] = S[i+1][t] - S[i+1][t - x].
+    // A restriction x_k0 <= C_k0 - 2 never changes the rank of an admitted x.
+    static __device__ __forceinline__ unsigned Sv(const Smem &s, int i, int t)
+    {
+        return t < 0 ? 0u : s.S[i * s.Wn + (t < s.Wn ? t : s.Wn - 1)];
+    }
+
+    static __device__ __forceinline__ int64_t Pf(const Smem &s, int i, int t, int x)
+    {
+        return (int64_t)(Sv(s, i + 1, t) - Sv(s, i + 1, t - x));
+    }
+
+    // Offset of level `lev` in the DIAG family (all modes, all digits).
+    static __device__ __forceinline__ int64_t cum_full(const Smem &s, int lev)
+    {
+        return (int64_t)Sv(s, 0, lev - 1);
+    }
+
+    // Offset of level `lev` in family K: sum over the levels below of the
+    // family's counts Pf(K, l, C_K - 1).  Thread 0 fills s.cum0 / s.cum1 for
+    // the level of each phase and the one below.
+    static __device__ void phase_offsets(const DiagShape &sh, Smem &s, int lev)
+    {
+        for (int K = 0; K < sh.M; ++K) {
+            int64_t c0 = 0, c1 = 0;
+            for (int l = 0; l < lev; ++l) {
+                const int64_t n = Pf(s, K, l, sh.C[K] - 1);
+                c0 += n;
+                if (l + 1 < lev) c1 += n;
+            }
+            s.cum0[K] = c0;
+            s.cum1[K] = c1;
+        }
+    }
+
+    static __device__ __forceinline__ PrefixTab ltab(const Smem &s) { return PrefixTab{s.S, s.Wn}; }
 
     static __device__ __forceinline__ unsigned level_count(const DiagShape &sh, const Smem &sm, int k0,
                                                     int dk0, int s)
@@ -723,6 +774,7 @@ struct Walk {
         const DiagShape &sh = a.sh;
         __syncthreads();
         if (threadIdx.x == 0) {
+            phase_offsets(sh, s, lev);
             int acc = 0;
             const int nseg = (kind == 0) ? sh.M : 1;
             for (int k = 0; k < nseg; ++k) {
@@ -761,60 +813,91 @@ struct Walk {
 
     // ------------------------------------------------------- per-pivot geometry
 
+    // AP(K) pivot e of level `lev` with rank r in family K: addresses of its
+    // reads and writes; the ranks of e - 1_m (m > K) go to s.idx[m][thread].
     static __device__ __forceinline__ ApGeom ap_geom(const DiagShape &sh, const Dig &e, int K, Smem &s,
-                                              bool hasb)
+                                                     int lev, int64_t r)
     {
         ApGeom g;
         const int eK = e(K);
-        g.diag = diag_index(sh, e, K);
-        g.t2 = box_index(sh, e, K, K, 2, -1, 0);
-        g.t1k = hasb ? box_index(sh, e, 0, 0, 1, K > 0 ? K : -1, 1) : 0;
+        g.r = r;
+        g.rd = cum_full(s, lev) + r;
+        g.lk0 = s.cum0[K];
+        g.lkm = s.cum1[K];
+        g.wt2 = sh.lm_t2[K] + g.lk0 + r;
+        g.fp = sh.has_b ? sh.lm_t1[K] + 2 * (s.cum0[0] + r) + 1 : 0;
+        int64_t pout = sh.stride[K];
+        for (int i = K; i < sh.M; ++i) pout += (int64_t)e(i) * sh.stride[i];
+        g.pout = pout;
+        int t = lev;
+        int64_t cum = Pf(s, K, t, eK);
+        g.rt2 = eK >= 1 ? sh.lm_t2[K] + g.lkm + Pf(s, K, t - 1, eK - 1) + (r - cum) : 0;
+        g.wdiag = cum_full(s, lev + 1) + Pf(s, K, lev + 1, eK + 1) + (r - cum);
+        int64_t pre = Pf(s, K, t - 1, eK);
+        t -= eK;
         g.vmask = 1u | (eK >= 1 ? 2u : 0u);
         g.nmask = 2u | (eK <= sh.C[K] - 3 ? 1u : 0u);
         for (int m = K + 1; m < sh.M; ++m) {
-            s.idx[m * TPB + threadIdx.x] = (int)box_index(sh, e, K, K, 1, m, 1);
             const int em = e(m);
+            cum += Pf(s, m, t, em);
+            s.idx[m * TPB + threadIdx.x] = em >= 1 ? (int)(pre + Pf(s, m, t - 1, em - 1) + (r - cum)) : 0;
+            pre += Pf(s, m, t - 1, em);
+            t -= em;
             if (em >= 1) g.vmask |= 3u << (2 * (m - K));
             if (em <= sh.C[m] - 2) g.nmask |= 3u << (2 * (m - K));
         }
         return g;
     }
 
-    // Flat address (within the circuit's amplitude array) of AP read column j.
+    // P1010/P1001(K,m) pair base (interleaved: P1010 even, P1001 odd).
+    static __device__ __forceinline__ int64_t pair_base(const DiagShape &sh, int K, int m)
+    {
+        return sh.lm_p[K] + 2 * (int64_t)(m - K - 1) * sh.fam[K];
+    }
+
+    // Address (within the circuit's amplitude array) of AP read column j.
     static __device__ __forceinline__ int64_t ap_read_addr(const DiagShape &sh, const ApGeom &g, int K,
                                                     int j, const Smem &s)
     {
-        if (j == 0) return g.diag;
-        if (j == 1) return sh.off_t2[K] + g.t2 - sh.stride[K];
+        if (j == 0) return g.rd;
+        if (j == 1) return g.rt2;
         const int m = K + j / 2;
-        const int64_t ip = s.idx[m * TPB + threadIdx.x];
-        return ((j & 1) ? sh.off_1010[K][m] : sh.off_1001[K][m]) + 2 * (ip - sh.stride[m]);
+        const int64_t rk = s.idx[m * TPB + threadIdx.x];
+        return pair_base(sh, K, m) + 2 * (g.lkm + rk) + ((j & 1) ? 0 : 1);
     }
 
-    // Flat address of AP write row i and its scale index P_w + 1.
+    // Address of AP write row i and its scale index P_w + 1.
     static __device__ __forceinline__ int64_t ap_write_addr(const DiagShape &sh, const ApGeom &g,
                                                      const Dig &e, int K, int i, const Smem &s,
                                                      int *den)
     {
-        if (i == 0) { *den = e(K) + 2; return sh.off_t2[K] + g.t2; }
-        if (i == 1) { *den = e(K) + 1; return g.diag + sh.stride[K]; }
+        if (i == 0) { *den = e(K) + 2; return g.wt2; }
+        if (i == 1) { *den = e(K) + 1; return g.wdiag; }
         const int m = K + i / 2;
         *den = e(m) + 1;
-        const int64_t ip = s.idx[m * TPB + threadIdx.x];
-        return ((i & 1) ? sh.off_1001[K][m] : sh.off_1010[K][m]) + 2 * ip;
+        return pair_base(sh, K, m) + 2 * (g.lk0 + g.r) + (i & 1);
     }
 
-
-    static __device__ __forceinline__ DpGeom dp_geom(const DiagShape &sh, const Dig &d, Smem &s)
+    // DP pivot d of level `lev` with rank r in family 0; ranks of d - 1_q go
+    // to s.idx[q][thread].
+    static __device__ __forceinline__ DpGeom dp_geom(const DiagShape &sh, const Dig &d, Smem &s, int lev,
+                                                     int64_t r)
     {
         DpGeom g;
-        g.diag = diag_index(sh, d, 0);
-        g.t1b0 = box_index(sh, d, 0, 0, 2, -1, 0);
+        g.r = r;
+        g.rdiag = cum_full(s, lev) + r;
+        g.l00 = s.cum0[0];
+        g.l0m = s.cum1[0];
         g.vmask = 0;
         g.nmask = 0;
+        int t = lev;
+        int64_t cum = 0, pre = 0;
         for (int q = 0; q < sh.M; ++q) {
-            s.idx[q * TPB + threadIdx.x] = (int)box_index(sh, d, 0, 0, 1, q > 0 ? q : -1, 1);
             const int dq = d(q);
+            cum += Pf(s, q, t, dq);
+            s.idx[q * TPB + threadIdx.x] = dq >= 1 ? (int)(pre + Pf(s, q, t - 1, dq - 1) + (r - cum)) : 0;
+            pre += Pf(s, q, t - 1, dq);
+            t -= dq;
             if (dq >= 1) g.vmask |= 3u << (2 * q);
             if (q == 0) {
                 g.nmask |= 1u;
@@ -826,13 +909,12 @@ struct Walk {
         return g;
     }
 
+    // T1 pair of mode q (interleaved: T1B even, T1K odd).
     static __device__ __forceinline__ int64_t dp_read_addr(const DiagShape &sh, const DpGeom &g, int j,
                                                     const Smem &s)
     {
         const int q = j / 2;
-        if (j & 1) return sh.off_t1k[q] + s.idx[q * TPB + threadIdx.x] - sh.stride[q];
-        const int64_t ib = (q == 0) ? g.t1b0 : (int64_t)s.idx[q * TPB + threadIdx.x];
-        return sh.off_t1b[q] + ib - sh.stride[q];
+        return sh.lm_t1[q] + 2 * (g.l0m + s.idx[q * TPB + threadIdx.x]) + (j & 1);
     }
 
     static __device__ __forceinline__ int64_t dp_write_addr(const DiagShape &sh, const DpGeom &g,
@@ -840,9 +922,7 @@ struct Walk {
     {
         const int q = i / 2;
         *den = d(q) + 1;
-        if ((i & 1) == 0) return sh.off_t1k[q] + s.idx[q * TPB + threadIdx.x];
-        const int64_t ib = (q == 0) ? g.t1b0 : (int64_t)s.idx[q * TPB + threadIdx.x];
-        return sh.off_t1b[q] + ib;
+        return sh.lm_t1[q] + 2 * (g.l00 + g.r) + ((i & 1) ? 0 : 1);
     }
 
     // ---------------------------------------------------------------- prologue
@@ -873,7 +953,7 @@ struct Walk {
         if (seed) {
             for (int64_t c = gtid; c < a.B; c += gsz) {
                 const double2 v = a.c[c];
-                a.F[(size_t)c * sh.circ_size] = v;
+                a.F[(size_t)c * sh.circ_alloc] = v;
                 a.probs[(size_t)c * sh.n_diag] = v;
             }
         }
@@ -886,7 +966,7 @@ struct Walk {
         const DiagShape &sh = a.sh;
         const int t = threadIdx.x, D = 2 * sh.M, N = 2 * (sh.M - K);
         load_circuit(a, s, tl.circ);
-        double2 *F = a.F + (size_t)tl.circ * sh.circ_size;
+        double2 *F = a.F + (size_t)tl.circ * sh.circ_alloc;
         const unsigned r = tl.rank0 + t;
         const bool act = r < tl.count;
         Dig e;
@@ -895,13 +975,13 @@ struct Walk {
         double fe = 1.0;
         if (act) {
             e = unrank(sh, s, K, 1, lev, r);
-            g = ap_geom(sh, e, K, s, HASB);
+            g = ap_geom(sh, e, K, s, lev, (int64_t)r);
             for (int j = 0; j < N; ++j) {
                 double2 v = make_double2(0, 0);
                 if ((g.vmask >> j) & 1u) v = __ldcg(F + ap_read_addr(sh, g, K, j, s));
                 store_read(s, D, j, t, v, false);
             }
-            if (HASB) FP = __ldcg(F + sh.off_t1k[K] + g.t1k);
+            if (HASB) FP = __ldcg(F + g.fp);
             for (int i = K; i < sh.M; ++i) fe *= s.fact[e(i)];
         } else {
             for (int j = 0; j < N; ++j) store_read(s, D, j, t, make_double2(0, 0), false);
@@ -914,7 +994,7 @@ struct Walk {
             const int64_t addr = ap_write_addr(sh, g, e, K, i, s, &den);
             const double2 v = rscale(acc, s.inv[den]);
             F[addr] = v;
-            if (i == 1) a.probs[(size_t)tl.circ * sh.n_diag + addr] = rscale(v, fe * (double)(e(K) + 1));
+            if (i == 1) a.probs[(size_t)tl.circ * sh.n_diag + g.pout] = rscale(v, fe * (double)(e(K) + 1));
         });
     }
 
@@ -924,7 +1004,7 @@ struct Walk {
         const DiagShape &sh = a.sh;
         const int t = threadIdx.x, D = 2 * sh.M, N = D;
         load_circuit(a, s, tl.circ);
-        double2 *F = a.F + (size_t)tl.circ * sh.circ_size;
+        double2 *F = a.F + (size_t)tl.circ * sh.circ_alloc;
         const unsigned r = tl.rank0 + t;
         const bool act = r < tl.count;
         Dig d;
@@ -932,13 +1012,13 @@ struct Walk {
         double2 FP = make_double2(0, 0);
         if (act) {
             d = unrank(sh, s, 0, 1, lev, r);
-            g = dp_geom(sh, d, s);
+            g = dp_geom(sh, d, s, lev, (int64_t)r);
             for (int j = 0; j < N; ++j) {
                 double2 v = make_double2(0, 0);
                 if ((g.vmask >> j) & 1u) v = __ldcg(F + dp_read_addr(sh, g, j, s));
                 store_read(s, D, j, t, v, false);
             }
-            FP = __ldcg(F + g.diag);
+            FP = __ldcg(F + g.rdiag);
         } else {
             for (int j = 0; j < N; ++j) store_read(s, D, j, t, make_double2(0, 0), false);
         }
@@ -1008,15 +1088,15 @@ struct Walk {
         const DiagShape &sh = a.sh;
         const int t = threadIdx.x, D = 2 * sh.M, N = 2 * (sh.M - K);
         load_circuit(a, s, tl.circ);
-        const double2 *F = a.F + (size_t)tl.circ * sh.circ_size;
-        double2 *Fb = a.Fbar + (size_t)tl.circ * sh.circ_size;
+        const double2 *F = a.F + (size_t)tl.circ * sh.circ_alloc;
+        double2 *Fb = a.Fbar + (size_t)tl.circ * sh.circ_alloc;
         const unsigned r = tl.rank0 + t;
         const bool act = r < tl.count;
         Dig e;
         ApGeom g{};
         if (act) {
             e = unrank(sh, s, K, 1, lev, r);
-            g = ap_geom(sh, e, K, s, HASB);
+            g = ap_geom(sh, e, K, s, lev, (int64_t)r);
             for (int j = 0; j < N; ++j) {
                 double2 v = make_double2(0, 0);
                 if ((g.vmask >> j) & 1u) v = __ldcg(F + ap_read_addr(sh, g, K, j, s));
@@ -1031,7 +1111,7 @@ struct Walk {
                 }
                 store_adj(s, D, i, t, v);
             }
-            s.FP[t] = HASB ? __ldcg(F + sh.off_t1k[K] + g.t1k) : make_double2(0, 0);
+            s.FP[t] = HASB ? __ldcg(F + g.fp) : make_double2(0, 0);
         } else {
             for (int j = 0; j < N; ++j) {
                 store_read(s, D, j, t, make_double2(0, 0), true);
@@ -1045,7 +1125,7 @@ struct Walk {
         matvec_adj(s, D, 2 * K, N, vm, nm, [&](int j, double2 acc) {
             if (!act || !((g.vmask >> j) & 1u)) return;
             if (j == 0) {
-                const int64_t ia = box_index(sh, e, K, K, 1, -1, 0);
+                const int64_t ia = g.lk0 + g.r;
                 a.scratch[(size_t)tl.circ * sh.n_ap + sh.off_ap[K] + ia] = acc;
             } else {
                 const int64_t addr = ap_read_addr(sh, g, K, j, s);
@@ -1056,7 +1136,7 @@ struct Walk {
             double2 fpb = make_double2(0, 0);
             for (int i = 0; i < N; ++i)
                 if ((g.nmask >> i) & 1u) fpb = cfma_conj(s.bs[2 * K + i], load_adj(s, D, i, t), fpb);
-            const int64_t addr = sh.off_t1k[K] + g.t1k;
+            const int64_t addr = g.fp;
             Fb[addr] = cadd(__ldcg(Fb + addr), fpb);
         }
         reduce_partials(a, s, tl.circ, K, N, HASB, nm, vm);
@@ -1068,15 +1148,15 @@ struct Walk {
         const DiagShape &sh = a.sh;
         const int t = threadIdx.x, D = 2 * sh.M, N = D;
         load_circuit(a, s, tl.circ);
-        const double2 *F = a.F + (size_t)tl.circ * sh.circ_size;
-        double2 *Fb = a.Fbar + (size_t)tl.circ * sh.circ_size;
+        const double2 *F = a.F + (size_t)tl.circ * sh.circ_alloc;
+        double2 *Fb = a.Fbar + (size_t)tl.circ * sh.circ_alloc;
         const unsigned r = tl.rank0 + t;
         const bool act = r < tl.count;
         Dig d;
         DpGeom g{};
         if (act) {
             d = unrank(sh, s, 0, 1, lev, r);
-            g = dp_geom(sh, d, s);
+            g = dp_geom(sh, d, s, lev, (int64_t)r);
             for (int j = 0; j < N; ++j) {
                 double2 v = make_double2(0, 0);
                 if ((g.vmask >> j) & 1u) v = __ldcg(F + dp_read_addr(sh, g, j, s));
@@ -1091,7 +1171,7 @@ struct Walk {
                 }
                 store_adj(s, D, i, t, v);
             }
-            s.FP[t] = __ldcg(F + g.diag);
+            s.FP[t] = __ldcg(F + g.rdiag);
         } else {
             for (int j = 0; j < N; ++j) {
                 store_read(s, D, j, t, make_double2(0, 0), true);
@@ -1110,7 +1190,7 @@ struct Walk {
             double2 fpb = make_double2(0, 0);
             for (int i = 0; i < N; ++i)
                 if ((g.nmask >> i) & 1u) fpb = cfma_conj(s.bs[i], load_adj(s, D, i, t), fpb);
-            Fb[g.diag] = cadd(__ldcg(Fb + g.diag), fpb);
+            Fb[g.rdiag] = cadd(__ldcg(Fb + g.rdiag), fpb);
         }
         reduce_partials(a, s, tl.circ, 0, N, true, nm, vm);
     }
@@ -1160,8 +1240,8 @@ struct Walk {
         const DiagShape &sh = a.sh;
         const int t = threadIdx.x, lane = t & 31, D = 2 * sh.M, N = 2 * (sh.M - K);
         load_circuit(a, s, tl.circ);
-        const double2 *F = a.F + (size_t)tl.circ * sh.circ_size;
-        double2 *Fb = a.Fbar + (size_t)tl.circ * sh.circ_size;
+        const double2 *F = a.F + (size_t)tl.circ * sh.circ_alloc;
+        double2 *Fb = a.Fbar + (size_t)tl.circ * sh.circ_alloc;
         const unsigned r = tl.rank0 + t;
         const bool act = r < tl.count;
         Dig e;
@@ -1170,7 +1250,7 @@ struct Walk {
         double2 FPv = make_double2(0, 0);
         if (act) {
             e = unrank(sh, s, K, 1, lev, r);
-            g = ap_geom(sh, e, K, s, HASB);
+            g = ap_geom(sh, e, K, s, lev, (int64_t)r);
             for (int j = 0; j < N; ++j) {
                 double2 v = make_double2(0, 0);
                 if ((g.vmask >> j) & 1u) v = __ldcg(F + ap_read_addr(sh, g, K, j, s));
@@ -1186,7 +1266,7 @@ struct Walk {
                 }
                 store_adj(s, D, i, t, v);
             }
-            if (HASB) FPv = __ldcg(F + sh.off_t1k[K] + g.t1k);
+            if (HASB) FPv = __ldcg(F + g.fp);
         } else {
             for (int j = 0; j < N; ++j) {
                 store_read(s, D, j, t, make_double2(0, 0), true);
@@ -1205,7 +1285,7 @@ struct Walk {
                 if (!((g.vmask >> j) & 1u)) continue;
                 const double2 acc = make_double2(wx[(2 * j) * WBS + lane], wx[(2 * j + 1) * WBS + lane]);
                 if (j == 0) {
-                    const int64_t ia = box_index(sh, e, K, K, 1, -1, 0);
+                    const int64_t ia = g.lk0 + g.r;
                     a.scratch[(size_t)tl.circ * sh.n_ap + sh.off_ap[K] + ia] = acc;
                 } else {
                     const int64_t addr = ap_read_addr(sh, g, K, j, s);
@@ -1216,7 +1296,7 @@ struct Walk {
                 double2 fpb = make_double2(0, 0);
                 for (int i = 0; i < N; ++i)
                     if ((g.nmask >> i) & 1u) fpb = cfma_conj(s.bs[2 * K + i], load_adj(s, D, i, t), fpb);
-                const int64_t addr = sh.off_t1k[K] + g.t1k;
+                const int64_t addr = g.fp;
                 Fb[addr] = cadd(__ldcg(Fb + addr), fpb);
             }
         }
@@ -1228,8 +1308,8 @@ struct Walk {
         const DiagShape &sh = a.sh;
         const int t = threadIdx.x, lane = t & 31, D = 2 * sh.M, N = D;
         load_circuit(a, s, tl.circ);
-        const double2 *F = a.F + (size_t)tl.circ * sh.circ_size;
-        double2 *Fb = a.Fbar + (size_t)tl.circ * sh.circ_size;
+        const double2 *F = a.F + (size_t)tl.circ * sh.circ_alloc;
+        double2 *Fb = a.Fbar + (size_t)tl.circ * sh.circ_alloc;
         const unsigned r = tl.rank0 + t;
         const bool act = r < tl.count;
         Dig d;
@@ -1238,7 +1318,7 @@ struct Walk {
         double2 FPv = make_double2(0, 0);
         if (act) {
             d = unrank(sh, s, 0, 1, lev, r);
-            g = dp_geom(sh, d, s);
+            g = dp_geom(sh, d, s, lev, (int64_t)r);
             for (int j = 0; j < N; ++j) {
                 double2 v = make_double2(0, 0);
                 if ((g.vmask >> j) & 1u) v = __ldcg(F + dp_read_addr(sh, g, j, s));
@@ -1254,7 +1334,7 @@ struct Walk {
                 }
                 store_adj(s, D, i, t, v);
             }
-            FPv = __ldcg(F + g.diag);
+            FPv = __ldcg(F + g.rdiag);
         } else {
             for (int j = 0; j < N; ++j) {
                 store_read(s, D, j, t, make_double2(0, 0), true);
@@ -1278,7 +1358,7 @@ struct Walk {
             double2 fpb = make_double2(0, 0);
             for (int i = 0; i < N; ++i)
                 if ((g.nmask >> i) & 1u) fpb = cfma_conj(s.bs[i], load_adj(s, D, i, t), fpb);
-            Fb[g.diag] = cadd(__ldcg(Fb + g.diag), fpb);
+            Fb[g.rdiag] = cadd(__ldcg(Fb + g.rdiag), fpb);
         }
         __syncwarp();
     }
@@ -1292,7 +1372,7 @@ struct Walk {
         const unsigned r = tl.rank0 + threadIdx.x;
         if (r >= tl.count) return;
         const Dig d = unrank(sh, s, 0, 0, lev, r);
-        const int64_t idx = diag_index(sh, d, 0);
+        const int64_t idx = diag_index(sh, d, 0);   // caller's row-major index
         double f = 1.0;
         int fnz = sh.M;
         for (int i = 0; i < sh.M; ++i) {
@@ -1304,8 +1384,8 @@ struct Walk {
         const double2 *sc = a.scratch + (size_t)tl.circ * sh.n_ap;
         const int kmax = fnz < sh.M ? fnz : sh.M - 1;
         for (int K = 0; K <= kmax; ++K)
-            if (d(K) <= sh.C[K] - 2) acc = cadd(acc, __ldcg(sc + sh.off_ap[K] + box_index(sh, d, K, K, 1, -1, 0)));
-        a.Fbar[(size_t)tl.circ * sh.circ_size + idx] = acc;
+            if (d(K) <= sh.C[K] - 2) acc = cadd(acc, __ldcg(sc + sh.off_ap[K] + s.cum0[K] + r));
+        a.Fbar[(size_t)tl.circ * sh.circ_alloc + cum_full(s, lev) + r] = acc;
     }
 
     // ------------------------------------------------------------------ kernels
@@ -1412,7 +1492,7 @@ struct Walk {
             const int ow = 2 * sh.mode_map[w / 2] + (w & 1);
             a.gb[(size_t)c * Do + ow] = x;
         }
-        for (int64_t c = gtid; c < a.B; c += gsz) a.gc[c] = a.Fbar[(size_t)c * sh.circ_size];
+        for (int64_t c = gtid; c < a.B; c += gsz) a.gc[c] = a.Fbar[(size_t)c * sh.circ_alloc];
     }
 
     // Vacuum-only problem (every cutoff is 1): p = c.
