@@ -242,6 +242,40 @@ int fock_diag_probs_static(int batch, const fk_c128 *d_A, const fk_c128 *d_b, co
                            void *stream, int *host_status);
 
 /*
+ * Global photon-number cutoff (Sec. 2.3, eq. global_boundary_conditions, with
+ * Algorithm 1 changed as Sec. 3.1.3 describes: the level loop runs to n_max,
+ * the per-mode cutoff tests drop out): the probabilities of every detection
+ * pattern n with n_1 + ... + n_M < n_max.  Storage and work grow like
+ * binomial(n_max + M, M) (App. B.1) instead of n_max^M.
+ *
+ * Outputs (and upstream gradients) are packed level-major: by total photon
+ * number, then lexicographically with mode 0 slowest; fk_global_size gives
+ * the count per circuit (binomial(n_max - 1 + M, M)) and
+ * fk_global_pattern_index the position of a pattern (-1 if n_1 + ... + n_M
+ * >= n_max or a count is negative).  The batched forward / VJP take
+ * A [B][2M][2M], b [B][2M], c [B] (device) like fock_diag_probs_batched;
+ * probs and grad_probs are [B][count]; flags, workspace, stream and errors as
+ * for fock_diag_probs_batched / fock_diag_probs_vjp_batched (workspace from
+ * fk_global_workspace_size with op FK_OP_DIAG or FK_OP_DIAG_VJP).  n_max in
+ * [1, FK_MAX_CUTOFF], M <= 12.
+ */
+int fk_global_size(int M, int n_max, int64_t *count);
+int fk_global_pattern_index(int M, int n_max, const int *host_pattern, int64_t *index);
+int fk_global_workspace_size(int batch, int M, int n_max, int op, unsigned flags, size_t *bytes);
+int fock_diag_probs_global_batched(int batch, const fk_c128 *d_A, const fk_c128 *d_b,
+                                   const fk_c128 *d_c, int M, int n_max, fk_c128 *d_probs,
+                                   unsigned flags, void *d_ws, size_t ws_bytes, void *stream);
+int fock_diag_probs_global_vjp_batched(int batch, const fk_c128 *d_A, const fk_c128 *d_b,
+                                       const fk_c128 *d_c, int M, int n_max,
+                                       const fk_c128 *d_grad_probs, fk_c128 *d_grad_A,
+                                       fk_c128 *d_grad_b, fk_c128 *d_grad_c, unsigned flags,
+                                       void *d_ws, size_t ws_bytes, void *stream);
+/* Storage of the global-cutoff walk: out[0] = amplitudes allocated per
+ * circuit, out[1] = pivots applied (App. B.1 count), out[2] = outputs per
+ * circuit.  out_len >= 3. */
+int fk_describe_global_schedule(int M, int n_max, unsigned flags, int64_t *out, int out_len);
+
+/*
  * Tile shape of the all-detected walk kernels, process-wide (the paper has
  * no counterpart: the autotuner in paper_2303_08879_gb300/autotune.py times
  * the shapes on the caller's workload and sets the fastest).  tpb = pivots

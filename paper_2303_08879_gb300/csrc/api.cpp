@@ -276,6 +276,97 @@ static int gaussian_to_triple(int M, const double *V, const double *mean, fk_c12
 
 static bool aligned(const void *p) { return ((uintptr_t)p % kAlign) == 0; }
 
+
+// ------------------------------------------------------------ global cutoff
+// With a global cutoff the per-mode cutoffs are n_max (never binding below
+// digit sum n_max) and the walk stops after level L = n_max - 2 of pivots:
+// its DIAG writes at level L + 1 = n_max - 1 complete every pattern with
+// fewer than n_max photons.  The level-major families are cut after digit
+// sum L + 1, so storage grows like binomial(n_max + M, M) instead of n_max^M.
+int build_global_shape(int M, int n_max, bool has_b, DiagShape *sh)
+{
+    if (M < 1 || n_max < 1 || !sh) return FK_EINVAL;
+    if (n_max > FK_MAX_CUTOFF) return FK_EUNSUPPORTED;
+    std::memset(sh, 0, sizeof(*sh));
+    sh->M_orig = M;
+    sh->D_orig = 2 * M;
+    sh->global = 1;
+    sh->has_b = has_b ? 1 : 0;
+    if (n_max == 1) {               // vacuum only
+        sh->M = 0;
+        sh->n_diag = 1;
+        sh->circ_size = sh->circ_alloc = 1;
+        return FK_OK;
+    }
+    if (M > FK_MAXM) return FK_EUNSUPPORTED;
+    sh->M = M;
+    for (int j = 0; j < M; ++j) {
+        sh->C[j] = n_max;
+        sh->mode_map[j] = j;
+    }
+    const int L = n_max - 1;        // pivot levels 0..L-1, stored digit sums 0..L
+    if (L > FK_MAX_LEVELS) return FK_EUNSUPPORTED;
+    sh->L = L;
+    auto total = [&](const std::vector<int64_t> &h) {
+        int64_t n = 0;
+        for (int t = 0; t <= L; ++t) n += h[t];
+        return n;
+    };
+    std::vector<int> full(M, n_max);
+    const int64_t nd = total(level_hist(full, L));
+    if (nd >= (int64_t(1) << 31)) return FK_EUNSUPPORTED;
+    sh->n_diag = nd;
+    int64_t lo = nd;
+    for (int K = 0; K < M; ++K) sh->fam[K] = total(level_hist(extents(*sh, K, K, 1, -1, 0), L));
+    for (int K = 0; K < M; ++K) {
+        sh->lm_t2[K] = lo;
+        lo += sh->fam[K];
+    }
+    for (int K = 0; K < M; ++K) {
+        sh->lm_p[K] = lo;
+        lo += 2 * (int64_t)(M - 1 - K) * sh->fam[K];
+    }
+    if (has_b)
+        for (int j = 0; j < M; ++j) {
+            sh->lm_t1[j] = lo;
+            lo += 2 * sh->fam[0];
+        }
+    sh->circ_size = sh->circ_alloc = lo;
+    int64_t ap = 0;
+    for (int K = 0; K < M; ++K) {
+        sh->off_ap[K] = ap;
+        ap += sh->fam[K];
+    }
+    sh->n_ap = ap;
+    return FK_OK;
+}
+
+// Position of a pattern in the level-major output (digit sum, then
+// lexicographic with mode 0 slowest); -1 if its photon number is >= n_max.
+static int64_t global_index(int M, int n_max, const int *n)
+{
+    int s = 0;
+    for (int j = 0; j < M; ++j) {
+        if (n[j] < 0) return -1;
+        s += n[j];
+    }
+    if (s >= n_max) return -1;
+    // W[i][t]: vectors over modes i..M-1 (digits < n_max) with digit sum t
+    std::vector<std::vector<int64_t>> W(M + 1, std::vector<int64_t>(n_max, 0));
+    W[M][0] = 1;
+    for (int i = M - 1; i >= 0; --i)
+        for (int t = 0; t < n_max; ++t)
+            for (int v = 0; v <= t && v < n_max; ++v) W[i][t] += W[i + 1][t - v];
+    int64_t idx = 0;
+    for (int t = 0; t < s; ++t) idx += W[0][t];
+    int rem = s;
+    for (int i = 0; i < M; ++i) {
+        for (int v = 0; v < n[i]; ++v) idx += W[i + 1][rem - v];
+        rem -= n[i];
+    }
+    return idx;
+}
+
 }  // namespace fk
 
 using namespace fk;
@@ -538,6 +629,94 @@ int fk_describe_diag_schedule(int M, const int *cutoffs, unsigned flags, int64_t
     out[1] = pivots;
     out[2] = L + 1;
     for (int i = 0; i < (int)rows.size() && 3 + i < out_len; ++i) out[3 + i] = rows[i];
+    return FK_OK;
+}
+
+
+int fk_global_size(int M, int n_max, int64_t *count)
+{
+    if (!count) return FK_EINVAL;
+    DiagShape sh;
+    int rc = build_global_shape(M, n_max, false, &sh);
+    if (rc) return rc;
+    *count = sh.n_diag;
+    return FK_OK;
+}
+
+int fk_global_pattern_index(int M, int n_max, const int *pattern, int64_t *index)
+{
+    if (M < 1 || n_max < 1 || !pattern || !index) return FK_EINVAL;
+    *index = global_index(M, n_max, pattern);
+    return FK_OK;
+}
+
+int fk_global_workspace_size(int batch, int M, int n_max, int op, unsigned flags, size_t *bytes)
+{
+    if (!bytes || batch < 1 || (op != FK_OP_DIAG && op != FK_OP_DIAG_VJP)) return FK_EINVAL;
+    DiagShape sh;
+    int rc = build_global_shape(M, n_max, !(flags & FK_FLAG_B_ZERO), &sh);
+    if (rc) return rc;
+    DiagLayout lay;
+    rc = diag_layout(sh, batch, op == FK_OP_DIAG_VJP, &lay);
+    if (rc) return rc;
+    *bytes = lay.total;
+    return FK_OK;
+}
+
+int fock_diag_probs_global_batched(int batch, const fk_c128 *A, const fk_c128 *b, const fk_c128 *c,
+                                   int M, int n_max, fk_c128 *probs, unsigned flags, void *ws,
+                                   size_t ws_bytes, void *stream)
+{
+    if (batch < 1 || !A || !b || !c || !probs || !ws) return FK_EINVAL;
+    DiagShape sh;
+    int rc = build_global_shape(M, n_max, !(flags & FK_FLAG_B_ZERO), &sh);
+    if (rc) return rc;
+    DiagLayout lay;
+    rc = diag_layout(sh, batch, false, &lay);
+    if (rc) return rc;
+    if (ws_bytes < lay.total || !aligned(ws)) return FK_EWORKSPACE;
+    return launch_diag_forward(sh, batch, flags, A, b, c, probs, ws, lay, stream);
+}
+
+int fock_diag_probs_global_vjp_batched(int batch, const fk_c128 *A, const fk_c128 *b,
+                                       const fk_c128 *c, int M, int n_max, const fk_c128 *gprobs,
+                                       fk_c128 *gA, fk_c128 *gb, fk_c128 *gc, unsigned flags,
+                                       void *ws, size_t ws_bytes, void *stream)
+{
+    if (batch < 1 || !A || !b || !c || !gprobs || !gA || !gb || !gc || !ws) return FK_EINVAL;
+    DiagShape sh;
+    int rc = build_global_shape(M, n_max, !(flags & FK_FLAG_B_ZERO), &sh);
+    if (rc) return rc;
+    DiagLayout lay;
+    rc = diag_layout(sh, batch, true, &lay);
+    if (rc) return rc;
+    if (ws_bytes < lay.total || !aligned(ws)) return FK_EWORKSPACE;
+    if (flags & FK_FLAG_RECOMPUTE) {
+        void *tmp = (char *)ws + lay.Fbar;
+        rc = launch_diag_forward(sh, batch, flags, A, b, c, tmp, ws, lay, stream);
+        if (rc) return rc;
+    }
+    return launch_diag_vjp(sh, batch, flags, A, b, c, gprobs, gA, gb, gc, ws, lay, stream);
+}
+
+int fk_describe_global_schedule(int M, int n_max, unsigned flags, int64_t *out, int out_len)
+{
+    if (!out || out_len < 3) return FK_EINVAL;
+    DiagShape sh;
+    int rc = build_global_shape(M, n_max, !(flags & FK_FLAG_B_ZERO), &sh);
+    if (rc) return rc;
+    int64_t pivots = 0;
+    for (int K = 0; K < sh.M; ++K) {
+        const auto h = level_hist(extents(sh, K, K, 1, -1, 0), sh.L);
+        for (int s = 0; s < sh.L; ++s) pivots += h[s];
+    }
+    if (sh.has_b && sh.M > 0) {
+        const auto h = level_hist(extents(sh, 0, 0, 1, -1, 0), sh.L);
+        for (int s = 0; s < sh.L; ++s) pivots += h[s];
+    }
+    out[0] = sh.circ_alloc;
+    out[1] = pivots;
+    out[2] = sh.n_diag;
     return FK_OK;
 }
 

@@ -26,6 +26,9 @@ inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 // Build the storage geometry of the all-detected walk (modes with C_j = 1
 // dropped).  Returns 0 or an fk_status.
 int build_diag_shape(int M, const int *cutoffs, bool has_b, DiagShape *sh);
+// Global photon cutoff n_max (Sec. 2.3, applied to Algorithm 1 as Sec. 3.1.3
+// describes): every pattern with n_1 + ... + n_M < n_max, no per-mode cutoff.
+int build_global_shape(int M, int n_max, bool has_b, DiagShape *sh);
 
 // Workspace layout of the all-detected walk for `batch` circuits.
 struct DiagLayout {

@@ -59,6 +59,8 @@ struct DiagShape {
     int D_orig;               // 2 * M_orig
     int L;                    // levels: pivots have digit sums s = 0..L-1
     int has_b;                // storage for offset_1 types present
+    int global;               // global photon cutoff (C_j = n_max, levels < n_max - 1): the
+                              // families hold only digit sums <= L, outputs are level-major
     int C[FK_MAXM];           // cutoffs of the kept modes
     int mode_map[FK_MAXM];    // kept mode -> caller's mode
     int64_t n_diag;           // prod C_j

@@ -994,7 +994,7 @@ struct Walk {
             const int64_t addr = ap_write_addr(sh, g, e, K, i, s, &den);
             const double2 v = rscale(acc, s.inv[den]);
             F[addr] = v;
-            if (i == 1) a.probs[(size_t)tl.circ * sh.n_diag + g.pout] = rscale(v, fe * (double)(e(K) + 1));
+            if (i == 1) a.probs[(size_t)tl.circ * sh.n_diag + (sh.global ? g.wdiag : g.pout)] = rscale(v, fe * (double)(e(K) + 1));
         });
     }
 
@@ -1380,9 +1380,12 @@ struct Walk {
             f *= s.fact[v];
             if (v > 0 && fnz == sh.M) fnz = i;
         }
-        double2 acc = rscale(a.gprobs[(size_t)tl.circ * sh.n_diag + idx], f);
+        // upstream gradient: caller's row-major index, or level-major (global cutoff)
+        double2 acc = rscale(a.gprobs[(size_t)tl.circ * sh.n_diag + (sh.global ? cum_full(s, lev) + r : idx)], f);
         const double2 *sc = a.scratch + (size_t)tl.circ * sh.n_ap;
-        const int kmax = fnz < sh.M ? fnz : sh.M - 1;
+        // AP pivots exist on levels < L only (with a global cutoff a DIAG value of
+        // level L can have digits below C_K - 1 that no pivot above it reads)
+        const int kmax = lev < sh.L ? (fnz < sh.M ? fnz : sh.M - 1) : -1;
         for (int K = 0; K <= kmax; ++K)
             if (d(K) <= sh.C[K] - 2) acc = cadd(acc, __ldcg(sc + sh.off_ap[K] + s.cum0[K] + r));
         a.Fbar[(size_t)tl.circ * sh.circ_alloc + cum_full(s, lev) + r] = acc;

@@ -33,6 +33,9 @@ EXPORTS = [
     "fock_conditional_dm_vjp", "fock_conditional_dm_vjp_batched",
     "fk_circuit_triple", "fk_circuit_triple_batched", "fk_mlp_sizes", "fk_mlp_load", "fk_mlp_forward", "fk_mlp_backward", "fk_mlp_train_step",
     "fk_herald_scores", "fk_diag_set_tuning", "fk_diag_set_engine",
+    "fk_global_size", "fk_global_pattern_index", "fk_global_workspace_size",
+    "fock_diag_probs_global_batched", "fock_diag_probs_global_vjp_batched",
+    "fk_describe_global_schedule",
 ]
 
 
@@ -78,6 +81,12 @@ def lib():
         L.fk_describe_diag_schedule.argtypes = [I, P, U, P, I]
         L.fk_measure_fp64_fma_rate.argtypes = [P, Z, ctypes.POINTER(ctypes.c_double), P]
         L.fock_diag_probs_static.argtypes = [I, P, P, P, I, P, P, U, P, ctypes.POINTER(I)]
+        L.fk_global_size.argtypes = [I, I, ctypes.POINTER(ctypes.c_int64)]
+        L.fk_global_pattern_index.argtypes = [I, I, P, ctypes.POINTER(ctypes.c_int64)]
+        L.fk_global_workspace_size.argtypes = [I, I, I, I, U, ctypes.POINTER(Z)]
+        L.fock_diag_probs_global_batched.argtypes = [I, P, P, P, I, I, P, U, P, Z, P]
+        L.fock_diag_probs_global_vjp_batched.argtypes = [I, P, P, P, I, I, P, P, P, P, U, P, Z, P]
+        L.fk_describe_global_schedule.argtypes = [I, I, U, P, I]
         L.fk_diag_set_tuning.argtypes = [I, I, I]
         L.fk_diag_set_engine.argtypes = [I]
         L.fk_herald_scores.argtypes = [I, P, P, I, P, ctypes.c_double, P, P, P, P]
@@ -256,6 +265,78 @@ def fock_diag_probs_vjp_batched(A, b, c, cutoffs, grad_probs, ws, flags=0, strea
                                            _ptr(grad_probs), _ptr(gA), _ptr(gb), _ptr(gc), flags,
                                            _ptr(ws), ws.numel(), _stream(stream))
     _check(st, "fock_diag_probs_vjp_batched")
+    return gA, gb, gc
+
+
+# ------------------------------------------------------ global photon cutoff
+def fk_global_size(M, n_max):
+    """Patterns with n_1 + ... + n_M < n_max (outputs per circuit)."""
+    n = ctypes.c_int64(0)
+    _check(lib().fk_global_size(int(M), int(n_max), ctypes.byref(n)), "fk_global_size")
+    return int(n.value)
+
+
+def fk_global_pattern_index(M, n_max, pattern):
+    """Position of a pattern in the level-major output (-1 if outside)."""
+    arr = (ctypes.c_int * M)(*[int(v) for v in pattern])
+    n = ctypes.c_int64(0)
+    _check(lib().fk_global_pattern_index(int(M), int(n_max), arr, ctypes.byref(n)),
+           "fk_global_pattern_index")
+    return int(n.value)
+
+
+def fk_global_workspace_size(M, n_max, batch=1, op=FK_OP_DIAG_VJP, flags=0):
+    n = ctypes.c_size_t(0)
+    _check(lib().fk_global_workspace_size(int(batch), int(M), int(n_max), int(op), int(flags),
+                                          ctypes.byref(n)), "fk_global_workspace_size")
+    return int(n.value)
+
+
+def fk_describe_global_schedule(M, n_max, flags=0):
+    out = np.zeros(3, np.int64)
+    _check(lib().fk_describe_global_schedule(int(M), int(n_max), int(flags), out.ctypes.data, 3),
+           "fk_describe_global_schedule")
+    return {"allocated": int(out[0]), "pivots": int(out[1]), "outputs": int(out[2])}
+
+
+def fock_diag_probs_global_batched(A, b, c, n_max, probs=None, flags=0, ws=None, stream=None,
+                                   for_vjp=True):
+    """p(n) for every pattern with fewer than n_max photons (global cutoff),
+    packed level-major [B, fk_global_size(M, n_max)].  Returns (probs, ws)."""
+    for n, t in (("A", A), ("b", b), ("c", c)):
+        _need_cuda_c128(n, t)
+    B, M = A.shape[0], A.shape[1] // 2
+    if A.shape != (B, 2 * M, 2 * M) or b.shape != (B, 2 * M) or c.shape != (B,):
+        raise ValueError("shapes must be A[B,2M,2M], b[B,2M], c[B]")
+    if probs is None:
+        probs = torch.empty((B, fk_global_size(M, n_max)), dtype=torch.complex128, device=A.device)
+    _need_cuda_c128("probs", probs)
+    need = fk_global_workspace_size(M, n_max, B, FK_OP_DIAG_VJP if for_vjp else FK_OP_DIAG, flags)
+    if ws is None:
+        ws = workspace(need, A.device)
+    st = lib().fock_diag_probs_global_batched(B, _ptr(A), _ptr(b), _ptr(c), M, int(n_max),
+                                              _ptr(probs), flags, _ptr(ws), ws.numel(),
+                                              _stream(stream))
+    _check(st, "fock_diag_probs_global_batched")
+    return probs, ws
+
+
+def fock_diag_probs_global_vjp_batched(A, b, c, n_max, grad_probs, ws, flags=0, stream=None,
+                                       out=None):
+    for n, t in (("A", A), ("b", b), ("c", c), ("grad_probs", grad_probs)):
+        _need_cuda_c128(n, t)
+    B, M = A.shape[0], A.shape[1] // 2
+    if out is None:
+        gA = torch.empty_like(A); gb = torch.empty_like(b); gc = torch.empty_like(c)
+    else:
+        gA, gb, gc = out
+    if ws is None:
+        ws = workspace(fk_global_workspace_size(M, n_max, B, FK_OP_DIAG_VJP, flags), A.device)
+        flags |= FK_FLAG_RECOMPUTE
+    st = lib().fock_diag_probs_global_vjp_batched(B, _ptr(A), _ptr(b), _ptr(c), M, int(n_max),
+                                                  _ptr(grad_probs), _ptr(gA), _ptr(gb), _ptr(gc),
+                                                  flags, _ptr(ws), ws.numel(), _stream(stream))
+    _check(st, "fock_diag_probs_global_vjp_batched")
     return gA, gb, gc
 
 
