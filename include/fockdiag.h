@@ -242,6 +242,30 @@ int fock_diag_probs_static(int batch, const fk_c128 *d_A, const fk_c128 *d_b, co
                            void *stream, int *host_status);
 
 /*
+ * Early stop on the probability sum (Sec. 2.3, last paragraph): after the
+ * pivots of each level (photon number) are applied, a circuit stops once its
+ * probabilities with at most that many photons sum to >= 1 - eps; the
+ * probabilities of higher photon numbers are returned as 0.  Decisions are
+ * per circuit and deterministic (the sums are kept in 2^-56 fixed point).
+ * d_levels [B] (device, or NULL) receives the number of photon numbers
+ * completed per circuit (0 .. levels-1 are exact).  eps in [0, 1]; eps = 0
+ * runs the full walk.  The VJP differentiates the stopped walk (its zero
+ * outputs are constants) and needs the workspace of the stopped forward with
+ * the same eps (or FK_FLAG_RECOMPUTE).  Shapes, workspace (fk_workspace_size
+ * with FK_OP_DIAG / FK_OP_DIAG_VJP), flags, stream and errors as for
+ * fock_diag_probs_batched / fock_diag_probs_vjp_batched.
+ */
+int fock_diag_probs_stop_batched(int batch, const fk_c128 *d_A, const fk_c128 *d_b,
+                                 const fk_c128 *d_c, int M, const int *host_cutoffs, double eps,
+                                 fk_c128 *d_probs, int *d_levels, unsigned flags, void *d_ws,
+                                 size_t ws_bytes, void *stream);
+int fock_diag_probs_stop_vjp_batched(int batch, const fk_c128 *d_A, const fk_c128 *d_b,
+                                     const fk_c128 *d_c, int M, const int *host_cutoffs,
+                                     double eps, const fk_c128 *d_grad_probs, fk_c128 *d_grad_A,
+                                     fk_c128 *d_grad_b, fk_c128 *d_grad_c, unsigned flags,
+                                     void *d_ws, size_t ws_bytes, void *stream);
+
+/*
  * Global photon-number cutoff (Sec. 2.3, eq. global_boundary_conditions, with
  * Algorithm 1 changed as Sec. 3.1.3 describes: the level loop runs to n_max,
  * the per-mode cutoff tests drop out): the probabilities of every detection

@@ -106,6 +106,8 @@ int diag_layout(const DiagShape &sh, int batch, bool vjp, DiagLayout *lay)
     const size_t c16 = 16;
     size_t o = 0;
     lay->ctl = o; o = align_up(o + sizeof(Control));
+    // per circuit and photon number: fixed-point sums of the probabilities (early stop)
+    lay->lvl = o; o = align_up(o + B * (size_t)(sh.L + 2) * sizeof(unsigned long long));
     lay->As = o; o = align_up(o + B * D * D * c16);
     lay->bs = o; o = align_up(o + B * D * c16);
     lay->F = o; o = align_up(o + B * (size_t)sh.circ_alloc * c16);
@@ -718,6 +720,46 @@ int fk_describe_global_schedule(int M, int n_max, unsigned flags, int64_t *out, 
     out[1] = pivots;
     out[2] = sh.n_diag;
     return FK_OK;
+}
+
+
+int fock_diag_probs_stop_batched(int batch, const fk_c128 *A, const fk_c128 *b, const fk_c128 *c,
+                                 int M, const int *cutoffs, double eps, fk_c128 *probs, int *levels,
+                                 unsigned flags, void *ws, size_t ws_bytes, void *stream)
+{
+    if (batch < 1 || !A || !b || !c || !probs || !ws || !(eps >= 0.0 && eps <= 1.0)) return FK_EINVAL;
+    DiagShape sh;
+    int rc = build_diag_shape(M, cutoffs, !(flags & FK_FLAG_B_ZERO), &sh);
+    if (rc) return rc;
+    DiagLayout lay;
+    rc = diag_layout(sh, batch, false, &lay);
+    if (rc) return rc;
+    if (ws_bytes < lay.total || !aligned(ws)) return FK_EWORKSPACE;
+    const EarlyStop es{eps, levels};
+    return launch_diag_forward(sh, batch, flags, A, b, c, probs, ws, lay, stream, &es);
+}
+
+int fock_diag_probs_stop_vjp_batched(int batch, const fk_c128 *A, const fk_c128 *b,
+                                     const fk_c128 *c, int M, const int *cutoffs, double eps,
+                                     const fk_c128 *gprobs, fk_c128 *gA, fk_c128 *gb, fk_c128 *gc,
+                                     unsigned flags, void *ws, size_t ws_bytes, void *stream)
+{
+    if (batch < 1 || !A || !b || !c || !gprobs || !gA || !gb || !gc || !ws || !(eps >= 0.0 && eps <= 1.0))
+        return FK_EINVAL;
+    DiagShape sh;
+    int rc = build_diag_shape(M, cutoffs, !(flags & FK_FLAG_B_ZERO), &sh);
+    if (rc) return rc;
+    DiagLayout lay;
+    rc = diag_layout(sh, batch, true, &lay);
+    if (rc) return rc;
+    if (ws_bytes < lay.total || !aligned(ws)) return FK_EWORKSPACE;
+    const EarlyStop es{eps, nullptr};
+    if (flags & FK_FLAG_RECOMPUTE) {
+        void *tmp = (char *)ws + lay.Fbar;
+        rc = launch_diag_forward(sh, batch, flags, A, b, c, tmp, ws, lay, stream, &es);
+        if (rc) return rc;
+    }
+    return launch_diag_vjp(sh, batch, flags, A, b, c, gprobs, gA, gb, gc, ws, lay, stream, &es);
 }
 
 }  // extern "C"

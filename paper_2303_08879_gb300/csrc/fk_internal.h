@@ -32,7 +32,7 @@ int build_global_shape(int M, int n_max, bool has_b, DiagShape *sh);
 
 // Workspace layout of the all-detected walk for `batch` circuits.
 struct DiagLayout {
-    size_t ctl, As, bs, F, Fbar, scratch, partA, partb, total;
+    size_t ctl, lvl, As, bs, F, Fbar, scratch, partA, partb, total;
     int grid_vjp, slots_vjp;
 };
 int diag_layout(const DiagShape &sh, int batch, bool vjp, DiagLayout *lay);
@@ -99,12 +99,19 @@ int set_diag_engine(int engine);
 
 // Launchers (walk_diag.cu).  All pointers are device pointers.
 int diag_grid_size(const DiagShape &sh, bool vjp, int *grid, int *slots = nullptr);
+// Early stop on the probability sum (Sec. 2.3): the pivots of a circuit stop
+// once its probabilities with at most `level` photons sum to >= 1 - eps.
+struct EarlyStop {
+    double eps;
+    int *levels;    // [B] device: photon numbers completed per circuit, or null
+};
 int launch_diag_forward(const DiagShape &sh, int batch, unsigned flags, const void *A,
                         const void *b, const void *c, void *probs, void *ws,
-                        const DiagLayout &lay, void *stream);
+                        const DiagLayout &lay, void *stream, const EarlyStop *es = nullptr);
 int launch_diag_vjp(const DiagShape &sh, int batch, unsigned flags, const void *A,
                     const void *b, const void *c, const void *gprobs, void *gA, void *gb,
-                    void *gc, void *ws, const DiagLayout &lay, void *stream);
+                    void *gc, void *ws, const DiagLayout &lay, void *stream,
+                    const EarlyStop *es = nullptr);
 int launch_wait_selftest(void *ws, unsigned long long timeout_ns, void *stream);
 int read_status(const void *ws, void *stream, int *status);
 

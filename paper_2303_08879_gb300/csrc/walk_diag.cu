@@ -49,6 +49,12 @@ struct DiagArgs {
     double2 *Fbar, *scratch, *partA, *partb;
     double2 *gA, *gb, *gc;
     unsigned long long timeout_ns;
+    // early stop on the probability sum (Sec. 2.3): lvl[c][n] = fixed-point
+    // (2^56) sum of the probabilities with n photons written so far
+    int early;
+    unsigned long long thr;       // (1 - eps) 2^56
+    unsigned long long *lvl;      // [B][L + 2]
+    int *levels;                  // [B] photon numbers completed (device, optional)
 };
 
 // ------------------------------------------------------------ shared memory
@@ -763,6 +769,42 @@ struct Walk {
         }
     }
 
+    // ------------------------------------------------------------ early stop
+    // A pivot tile of level `lev` runs while the probabilities with at most
+    // `lev` photons sum to less than 1 - eps.  The per-photon-number sums are
+    // final once the level below has passed its barrier, and fixed point
+    // keeps them independent of the order of the additions, so every block
+    // takes the same decision.
+    static __device__ __forceinline__ unsigned long long fixed_prob(double p)
+    {
+        return p > 0.0 ? (unsigned long long)(p * 0x1p56) : 0ull;
+    }
+
+    static __device__ __forceinline__ bool pivots_run(const DiagArgs &a, int circ, int lev)
+    {
+        if (!a.early) return lev < a.sh.L;
+        if (lev >= a.sh.L) return false;
+        const unsigned long long *l = a.lvl + (size_t)circ * (a.sh.L + 2);
+        unsigned long long cum = 0;
+        for (int n = 0; n <= lev; ++n) cum += __ldcg(l + n);
+        return cum < a.thr;
+    }
+
+    // Block-wide sum of v added to lvl[circ][n] (thread 0).
+    static __device__ void add_level_prob(const DiagArgs &a, int circ, int n, double v)
+    {
+        __shared__ double s_part[32];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_part[w];
+            atomicAdd(a.lvl + (size_t)circ * (a.sh.L + 2) + n, fixed_prob(t));
+        }
+        __syncthreads();
+    }
+
     // Tiles of a phase are numbered circuit-major: circuit c, then segment k
     // (anchor K for AP; one segment for DP and DIAG), then ceil(count / TPB)
     // tiles; tiles[k] = prefix over k within one circuit, tiles[nseg] = tiles
@@ -953,6 +995,7 @@ struct Walk {
         if (seed) {
             for (int64_t c = gtid; c < a.B; c += gsz) {
                 const double2 v = a.c[c];
+                if (a.early) a.lvl[(size_t)c * (sh.L + 2)] = fixed_prob(v.x);
                 a.F[(size_t)c * sh.circ_alloc] = v;
                 a.probs[(size_t)c * sh.n_diag] = v;
             }
@@ -960,7 +1003,7 @@ struct Walk {
     }
 
     // ------------------------------------------------------------- forward AP
-    template <bool HASB>
+    template <bool HASB, bool EARLY>
     static __device__ void ap_forward_tile(const DiagArgs &a, Smem &s, const TileId &tl, int K, int lev)
     {
         const DiagShape &sh = a.sh;
@@ -972,7 +1015,7 @@ struct Walk {
         Dig e;
         ApGeom g{};
         double2 FP = make_double2(0, 0);
-        double fe = 1.0;
+        double fe = 1.0, psum = 0.0;
         if (act) {
             e = unrank(sh, s, K, 1, lev, r);
             g = ap_geom(sh, e, K, s, lev, (int64_t)r);
@@ -994,8 +1037,13 @@ struct Walk {
             const int64_t addr = ap_write_addr(sh, g, e, K, i, s, &den);
             const double2 v = rscale(acc, s.inv[den]);
             F[addr] = v;
-            if (i == 1) a.probs[(size_t)tl.circ * sh.n_diag + (sh.global ? g.wdiag : g.pout)] = rscale(v, fe * (double)(e(K) + 1));
+            if (i == 1) {
+                const double2 p = rscale(v, fe * (double)(e(K) + 1));
+                a.probs[(size_t)tl.circ * sh.n_diag + (sh.global ? g.wdiag : g.pout)] = p;
+                if (EARLY) psum += p.x;
+            }
         });
+        if (EARLY) add_level_prob(a, tl.circ, lev + 1, psum);
     }
 
     // ------------------------------------------------------------- forward DP
@@ -1383,9 +1431,10 @@ struct Walk {
         // upstream gradient: caller's row-major index, or level-major (global cutoff)
         double2 acc = rscale(a.gprobs[(size_t)tl.circ * sh.n_diag + (sh.global ? cum_full(s, lev) + r : idx)], f);
         const double2 *sc = a.scratch + (size_t)tl.circ * sh.n_ap;
-        // AP pivots exist on levels < L only (with a global cutoff a DIAG value of
-        // level L can have digits below C_K - 1 that no pivot above it reads)
-        const int kmax = lev < sh.L ? (fnz < sh.M ? fnz : sh.M - 1) : -1;
+        // scratch exists where the AP pivots of this level ran: levels < L (with a
+        // global cutoff a DIAG value of level L can have digits below C_K - 1
+        // that no pivot reads) and, with an early stop, below the stop
+        const int kmax = pivots_run(a, tl.circ, lev) ? (fnz < sh.M ? fnz : sh.M - 1) : -1;
         for (int K = 0; K <= kmax; ++K)
             if (d(K) <= sh.C[K] - 2) acc = cadd(acc, __ldcg(sc + sh.off_ap[K] + s.cum0[K] + r));
         a.Fbar[(size_t)tl.circ * sh.circ_alloc + cum_full(s, lev) + r] = acc;
@@ -1409,6 +1458,7 @@ struct Walk {
                 const int nt = phase_tiles(a, s, 1, lev);
                 for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
                     const TileId tl = decode_tile(a, s, 1, lev, tile);
+                    if (!pivots_run(a, tl.circ, lev)) continue;
                     dp_forward_tile(a, s, tl, lev);
                 }
                 if (!grid_sync(a.ctl, gridDim.x, a.timeout_ns)) return;
@@ -1416,10 +1466,24 @@ struct Walk {
             const int nt = phase_tiles(a, s, 0, lev);
             for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
                 const TileId tl = decode_tile(a, s, 0, lev, tile);
-                if (hb) ap_forward_tile<true>(a, s, tl, tl.seg, lev);
-                else ap_forward_tile<false>(a, s, tl, tl.seg, lev);
+                if (!pivots_run(a, tl.circ, lev)) continue;
+                if (a.early) {
+                    if (hb) ap_forward_tile<true, true>(a, s, tl, tl.seg, lev);
+                    else ap_forward_tile<false, true>(a, s, tl, tl.seg, lev);
+                } else {
+                    if (hb) ap_forward_tile<true, false>(a, s, tl, tl.seg, lev);
+                    else ap_forward_tile<false, false>(a, s, tl, tl.seg, lev);
+                }
             }
-            if (lev + 1 < sh.L && !grid_sync(a.ctl, gridDim.x, a.timeout_ns)) return;
+            if ((lev + 1 < sh.L || a.early) && !grid_sync(a.ctl, gridDim.x, a.timeout_ns)) return;
+        }
+        if (a.early && a.levels != nullptr && blockIdx.x == 0) {
+            // photon numbers completed: 0 .. (first level whose pivots did not run)
+            for (int c = threadIdx.x; c < a.B; c += blockDim.x) {
+                int n = 0;
+                while (n < sh.L && pivots_run(a, c, n)) ++n;
+                a.levels[c] = n + 1;
+            }
         }
     }
 
@@ -1440,6 +1504,7 @@ struct Walk {
                 const int nt = phase_tiles(a, s, 0, lev);
                 for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
                     const TileId tl = decode_tile(a, s, 0, lev, tile);
+                    if (!pivots_run(a, tl.circ, lev)) continue;
                     if constexpr (TC) {
                         if (hb) ap_reverse_tile_tc<true>(a, s, tl, tl.seg, lev);
                         else ap_reverse_tile_tc<false>(a, s, tl, tl.seg, lev);
@@ -1454,6 +1519,8 @@ struct Walk {
                 const int nt = phase_tiles(a, s, 2, lev);
                 for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
                     const TileId tl = decode_tile(a, s, 2, lev, tile);
+                    // the DIAG values with lev photons exist once the pivots of level lev-1 ran
+                    if (lev > 0 && !pivots_run(a, tl.circ, lev - 1)) continue;
                     diag_reverse_tile(a, s, tl, lev);
                 }
                 if (!grid_sync(a.ctl, gridDim.x, a.timeout_ns)) return;
@@ -1462,6 +1529,7 @@ struct Walk {
                 const int nt = phase_tiles(a, s, 1, lev);
                 for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
                     const TileId tl = decode_tile(a, s, 1, lev, tile);
+                    if (!pivots_run(a, tl.circ, lev)) continue;
                     if constexpr (TC) dp_reverse_tile_tc(a, s, tl, lev);
                     else dp_reverse_tile(a, s, tl, lev);
                 }
@@ -1526,6 +1594,12 @@ __global__ void vacuum_vjp_kernel(const double2 *gprobs, double2 *gA, double2 *g
     if (i < B * Do * Do) gA[i] = make_double2(0, 0);
     if (i < B * Do) gb[i] = make_double2(0, 0);
     if (i < B) gc[i] = gprobs[i];
+}
+
+__global__ void fill_int_kernel(int *p, int n, int v)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
 }
 
 __global__ void wait_selftest_kernel(Control *ctl, unsigned long long timeout_ns)
@@ -1702,22 +1776,39 @@ static DiagArgs make_args(const DiagShape &sh, int batch, unsigned flags, const 
     a.As = (double2 *)(w + lay.As);
     a.bs = (double2 *)(w + lay.bs);
     a.F = (double2 *)(w + lay.F);
+    a.lvl = (unsigned long long *)(w + lay.lvl);
     a.timeout_ns = kBarrierTimeoutNs;
     return a;
 }
 
+static unsigned long long stop_threshold(double eps)
+{
+    return (unsigned long long)((1.0 - eps) * 0x1p56);
+}
+
 int launch_diag_forward(const DiagShape &sh, int batch, unsigned flags, const void *A,
                         const void *b, const void *c, void *probs, void *ws,
-                        const DiagLayout &lay, void *stream)
+                        const DiagLayout &lay, void *stream, const EarlyStop *es)
 {
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemsetAsync((char *)ws + lay.ctl, 0, sizeof(Control), st) != cudaSuccess) return FK_ECUDA;
     if (sh.M == 0) {
         copy_c_kernel<<<(batch + 127) / 128, 128, 0, st>>>((const double2 *)c, (double2 *)probs, batch, 1);
+        if (es && es->levels)
+            fill_int_kernel<<<(batch + 127) / 128, 128, 0, st>>>(es->levels, batch, 1);
         return cudaGetLastError() == cudaSuccess ? FK_OK : FK_ECUDA;
     }
     DiagArgs a = make_args(sh, batch, flags, A, b, c, ws, lay);
     a.probs = (double2 *)probs;
+    if (es) {
+        // unstarted photon numbers stay zero; the per-level sums start from zero
+        if (cudaMemsetAsync(probs, 0, (size_t)batch * sh.n_diag * 16, st) != cudaSuccess) return FK_ECUDA;
+        if (cudaMemsetAsync((char *)ws + lay.lvl, 0, (size_t)batch * (sh.L + 2) * 8, st) != cudaSuccess)
+            return FK_ECUDA;
+        a.early = 1;
+        a.thr = stop_threshold(es->eps);
+        a.levels = es->levels;
+    }
     int grid = 0;
     int rc = diag_grid_size(sh, false, &grid);
     if (rc) return rc;
@@ -1731,7 +1822,7 @@ int launch_diag_forward(const DiagShape &sh, int batch, unsigned flags, const vo
 
 int launch_diag_vjp(const DiagShape &sh, int batch, unsigned flags, const void *A, const void *b,
                     const void *c, const void *gprobs, void *gA, void *gb, void *gc, void *ws,
-                    const DiagLayout &lay, void *stream)
+                    const DiagLayout &lay, void *stream, const EarlyStop *es)
 {
     cudaStream_t st = (cudaStream_t)stream;
     if (sh.M == 0) {
@@ -1755,6 +1846,10 @@ int launch_diag_vjp(const DiagShape &sh, int batch, unsigned flags, const void *
     a.gc = (double2 *)gc;
     a.grid = lay.grid_vjp;
     a.slots = lay.slots_vjp;
+    if (es) {
+        a.early = 1;
+        a.thr = stop_threshold(es->eps);
+    }
     int bps = 0, tpb = 0, spb = 1;
     size_t smem = 0;
     const void *fn = nullptr;

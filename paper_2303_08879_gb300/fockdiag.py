@@ -35,7 +35,7 @@ EXPORTS = [
     "fk_herald_scores", "fk_diag_set_tuning", "fk_diag_set_engine",
     "fk_global_size", "fk_global_pattern_index", "fk_global_workspace_size",
     "fock_diag_probs_global_batched", "fock_diag_probs_global_vjp_batched",
-    "fk_describe_global_schedule",
+    "fk_describe_global_schedule", "fock_diag_probs_stop_batched", "fock_diag_probs_stop_vjp_batched",
 ]
 
 
@@ -87,6 +87,9 @@ def lib():
         L.fock_diag_probs_global_batched.argtypes = [I, P, P, P, I, I, P, U, P, Z, P]
         L.fock_diag_probs_global_vjp_batched.argtypes = [I, P, P, P, I, I, P, P, P, P, U, P, Z, P]
         L.fk_describe_global_schedule.argtypes = [I, I, U, P, I]
+        Dbl = ctypes.c_double
+        L.fock_diag_probs_stop_batched.argtypes = [I, P, P, P, I, P, Dbl, P, P, U, P, Z, P]
+        L.fock_diag_probs_stop_vjp_batched.argtypes = [I, P, P, P, I, P, Dbl, P, P, P, P, U, P, Z, P]
         L.fk_diag_set_tuning.argtypes = [I, I, I]
         L.fk_diag_set_engine.argtypes = [I]
         L.fk_herald_scores.argtypes = [I, P, P, I, P, ctypes.c_double, P, P, P, P]
@@ -265,6 +268,46 @@ def fock_diag_probs_vjp_batched(A, b, c, cutoffs, grad_probs, ws, flags=0, strea
                                            _ptr(grad_probs), _ptr(gA), _ptr(gb), _ptr(gc), flags,
                                            _ptr(ws), ws.numel(), _stream(stream))
     _check(st, "fock_diag_probs_vjp_batched")
+    return gA, gb, gc
+
+
+# ------------------------------------------------------------- early stop
+def fock_diag_probs_stop_batched(A, b, c, cutoffs, eps, probs=None, flags=0, ws=None, stream=None):
+    """Algorithm 1 with the probability-sum stop of Sec. 2.3: per circuit, the
+    pivots stop once the probabilities with at most n photons sum to >= 1 - eps.
+    Returns (probs [B, *cutoffs] with zeros above the stop, levels [B] = photon
+    numbers completed, ws)."""
+    for n, t in (("A", A), ("b", b), ("c", c)):
+        _need_cuda_c128(n, t)
+    B, M = A.shape[0], len(cutoffs)
+    if A.shape != (B, 2 * M, 2 * M) or b.shape != (B, 2 * M) or c.shape != (B,):
+        raise ValueError("shapes must be A[B,2M,2M], b[B,2M], c[B]")
+    if probs is None:
+        probs = torch.empty((B,) + tuple(int(x) for x in cutoffs), dtype=torch.complex128,
+                            device=A.device)
+    levels = torch.zeros(B, dtype=torch.int32, device=A.device)
+    if ws is None:
+        ws = workspace(fk_workspace_size(M, cutoffs, B, FK_OP_DIAG_VJP, flags), A.device)
+    st = lib().fock_diag_probs_stop_batched(B, _ptr(A), _ptr(b), _ptr(c), M, _cut(cutoffs),
+                                            float(eps), _ptr(probs), _ptr(levels), flags,
+                                            _ptr(ws), ws.numel(), _stream(stream))
+    _check(st, "fock_diag_probs_stop_batched")
+    return probs, levels, ws
+
+
+def fock_diag_probs_stop_vjp_batched(A, b, c, cutoffs, eps, grad_probs, ws, flags=0, stream=None):
+    for n, t in (("A", A), ("b", b), ("c", c), ("grad_probs", grad_probs)):
+        _need_cuda_c128(n, t)
+    B, M = A.shape[0], len(cutoffs)
+    gA = torch.empty_like(A); gb = torch.empty_like(b); gc = torch.empty_like(c)
+    if ws is None:
+        ws = workspace(fk_workspace_size(M, cutoffs, B, FK_OP_DIAG_VJP, flags), A.device)
+        flags |= FK_FLAG_RECOMPUTE
+    st = lib().fock_diag_probs_stop_vjp_batched(B, _ptr(A), _ptr(b), _ptr(c), M, _cut(cutoffs),
+                                                float(eps), _ptr(grad_probs), _ptr(gA), _ptr(gb),
+                                                _ptr(gc), flags, _ptr(ws), ws.numel(),
+                                                _stream(stream))
+    _check(st, "fock_diag_probs_stop_vjp_batched")
     return gA, gb, gc
 
 
