@@ -242,6 +242,39 @@ int fock_diag_probs_static(int batch, const fk_c128 *d_A, const fk_c128 *d_b, co
                            void *stream, int *host_status);
 
 /*
+ * State-vector walk (Sec. 2.2, "State vector simulations") of a pure
+ * Gaussian state: psi_k for every k < cutoffs over M modes from the pure
+ * triple (A_psi [M][M], b_psi [M], psi_0) by eq. recrel, pivots in order of
+ * weight, each amplitude from its canonical parent (first nonzero index).
+ * fk_gaussian_to_pure_triple builds the triple on the host from a pure
+ * state's quadrature covariance V [2M][2M] and mean [2M] (hbar = 1, as
+ * fk_gaussian_to_triple); it returns FK_EINVAL for a mixed state.  psi_0 is
+ * taken real and positive (the global phase is free).
+ *
+ * fock_pure_amplitudes_batched: A [B][M][M] (symmetrised internally), b [B][M],
+ * c [B], psi [B][prod C] row-major (mode 0 slowest), all device pointers.
+ * FK_FLAG_B_ZERO promises b = 0: odd weights are zero and skipped (Sec. 2.4).
+ * fock_pure_amplitudes_vjp_batched: grad_psi [B][prod C] -> grad_A (symmetric),
+ * grad_b, grad_c in the PyTorch convention, all weights included; needs the
+ * forward's workspace or FK_FLAG_RECOMPUTE.  Workspace from
+ * fk_pure_workspace_size (op FK_OP_DIAG / FK_OP_DIAG_VJP), M <= 16,
+ * prod C < 2^31, C_j <= FK_MAX_CUTOFF.  Errors as for the density-matrix walk.
+ */
+int fk_gaussian_to_pure_triple(int M, const double *host_V, const double *host_mean,
+                               fk_c128 *host_A, fk_c128 *host_b, fk_c128 *host_c);
+int fk_pure_workspace_size(int batch, int M, const int *host_cutoffs, int op, unsigned flags,
+                           size_t *bytes);
+int fock_pure_amplitudes_batched(int batch, const fk_c128 *d_A, const fk_c128 *d_b,
+                                 const fk_c128 *d_c, int M, const int *host_cutoffs,
+                                 fk_c128 *d_psi, unsigned flags, void *d_ws, size_t ws_bytes,
+                                 void *stream);
+int fock_pure_amplitudes_vjp_batched(int batch, const fk_c128 *d_A, const fk_c128 *d_b,
+                                     const fk_c128 *d_c, int M, const int *host_cutoffs,
+                                     const fk_c128 *d_grad_psi, fk_c128 *d_grad_A,
+                                     fk_c128 *d_grad_b, fk_c128 *d_grad_c, unsigned flags,
+                                     void *d_ws, size_t ws_bytes, void *stream);
+
+/*
  * Early stop on the probability sum (Sec. 2.3, last paragraph): after the
  * pivots of each level (photon number) are applied, a circuit stops once its
  * probabilities with at most that many photons sum to >= 1 - eps; the

@@ -48,3 +48,15 @@ def gaussian_to_triple(V, mean):
     # lattice index 2j <- a^dag_j (block index M + j), 2j+1 <- a_j (block index j)
     perm = [v for j in range(M) for v in (M + j, j)]
     return A[np.ix_(perm, perm)], b[perm], complex(c)
+
+
+def pure_triple(V, mean):
+    """(A_psi, b_psi, psi_0) of a pure Gaussian state.  Its density triple has
+    no coupling between ket and bra indices (A_rho = A_psi (+) conj(A_psi),
+    Sec. 2.1); with the pair order above the ket index m of <m|rho|n> is the
+    even lattice index, so A_psi and b_psi are the even-even block and even
+    entries, and psi_0 = sqrt(rho_0) (Sec. 2.2, global phase dropped)."""
+    A, b, c = gaussian_to_triple(V, mean)
+    if np.max(np.abs(A[0::2, 1::2])) > 1e-9 * max(1.0, np.max(np.abs(A))):
+        raise ValueError("state is not pure")
+    return A[0::2, 0::2].copy(), b[0::2].copy(), complex(np.sqrt(c.real))

@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfockdiag.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cpp", "circuit.cpp", "walk_diag.cu", "walk_cond.cu", "mlp.cu", "herald.cu", "probe.cu", "static_ws.cu"]
+SOURCES = ["api.cpp", "circuit.cpp", "walk_diag.cu", "walk_cond.cu", "mlp.cu", "herald.cu", "probe.cu", "static_ws.cu",
+           "walk_pure.cu"]
 
 
 def nvcc() -> str:

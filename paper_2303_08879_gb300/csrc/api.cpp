@@ -1,6 +1,7 @@
 // api.cpp -- host side of the C ABI declared in include/fockdiag.h:
 // argument checking, storage geometry, workspace layout, the Gaussian ->
 // Bargmann triple map, and dispatch to the CUDA launchers.
+#include <algorithm>
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -760,6 +761,40 @@ int fock_diag_probs_stop_vjp_batched(int batch, const fk_c128 *A, const fk_c128 
         if (rc) return rc;
     }
     return launch_diag_vjp(sh, batch, flags, A, b, c, gprobs, gA, gb, gc, ws, lay, stream, &es);
+}
+
+
+int fk_gaussian_to_pure_triple(int M, const double *V, const double *mean, fk_c128 *A, fk_c128 *b,
+                               fk_c128 *c)
+{
+    if (M < 1 || M > 64 || !V || !mean || !A || !b || !c) return FK_EINVAL;
+    const int D = 2 * M;
+    std::vector<fk_c128> Ar((size_t)D * D), br(D);
+    fk_c128 cr;
+    int rc;
+    try {
+        rc = gaussian_to_triple(M, V, mean, Ar.data(), br.data(), &cr);
+    } catch (...) {
+        return FK_ENOMEM;
+    }
+    if (rc) return rc;
+    // a pure state's density triple has no ket-bra coupling: A_rho = A_psi (+) conj(A_psi)
+    double amax = 0.0, cross = 0.0;
+    for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) {
+            const fk_c128 v = Ar[(size_t)i * D + j];
+            const double m = std::hypot(v.re, v.im);
+            amax = std::max(amax, m);
+            if ((i & 1) != (j & 1)) cross = std::max(cross, m);
+        }
+    if (cross > 1e-9 * std::max(amax, 1.0) || !(cr.re > 0.0)) return FK_EINVAL;
+    for (int i = 0; i < M; ++i) {
+        for (int j = 0; j < M; ++j) A[(size_t)i * M + j] = Ar[(size_t)(2 * i) * D + 2 * j];
+        b[i] = br[2 * i];
+    }
+    c->re = std::sqrt(cr.re);   // psi_0 = sqrt(rho_0) up to a global phase (Sec. 2.2)
+    c->im = 0.0;
+    return FK_OK;
 }
 
 }  // extern "C"

@@ -36,6 +36,8 @@ EXPORTS = [
     "fk_global_size", "fk_global_pattern_index", "fk_global_workspace_size",
     "fock_diag_probs_global_batched", "fock_diag_probs_global_vjp_batched",
     "fk_describe_global_schedule", "fock_diag_probs_stop_batched", "fock_diag_probs_stop_vjp_batched",
+    "fk_gaussian_to_pure_triple", "fk_pure_workspace_size", "fock_pure_amplitudes_batched",
+    "fock_pure_amplitudes_vjp_batched",
 ]
 
 
@@ -90,6 +92,10 @@ def lib():
         Dbl = ctypes.c_double
         L.fock_diag_probs_stop_batched.argtypes = [I, P, P, P, I, P, Dbl, P, P, U, P, Z, P]
         L.fock_diag_probs_stop_vjp_batched.argtypes = [I, P, P, P, I, P, Dbl, P, P, P, P, U, P, Z, P]
+        L.fk_gaussian_to_pure_triple.argtypes = [I, P, P, P, P, P]
+        L.fk_pure_workspace_size.argtypes = [I, I, P, I, U, ctypes.POINTER(Z)]
+        L.fock_pure_amplitudes_batched.argtypes = [I, P, P, P, I, P, P, U, P, Z, P]
+        L.fock_pure_amplitudes_vjp_batched.argtypes = [I, P, P, P, I, P, P, P, P, P, U, P, Z, P]
         L.fk_diag_set_tuning.argtypes = [I, I, I]
         L.fk_diag_set_engine.argtypes = [I]
         L.fk_herald_scores.argtypes = [I, P, P, I, P, ctypes.c_double, P, P, P, P]
@@ -268,6 +274,59 @@ def fock_diag_probs_vjp_batched(A, b, c, cutoffs, grad_probs, ws, flags=0, strea
                                            _ptr(grad_probs), _ptr(gA), _ptr(gb), _ptr(gc), flags,
                                            _ptr(ws), ws.numel(), _stream(stream))
     _check(st, "fock_diag_probs_vjp_batched")
+    return gA, gb, gc
+
+
+# ------------------------------------------------------- pure state vector
+def fk_gaussian_to_pure_triple(V, mean):
+    """(A_psi [M, M], b_psi [M], psi_0) of a pure Gaussian state (host)."""
+    V = np.ascontiguousarray(np.asarray(V, dtype=np.float64))
+    mean = np.ascontiguousarray(np.asarray(mean, dtype=np.float64))
+    M = V.shape[0] // 2
+    A = np.zeros((M, M), np.complex128); b = np.zeros(M, np.complex128); c = np.zeros(1, np.complex128)
+    st = lib().fk_gaussian_to_pure_triple(M, V.ctypes.data, mean.ctypes.data, A.ctypes.data,
+                                          b.ctypes.data, c.ctypes.data)
+    _check(st, "fk_gaussian_to_pure_triple")
+    return A, b, complex(c[0])
+
+
+def fk_pure_workspace_size(cutoffs, batch=1, op=FK_OP_DIAG_VJP, flags=0):
+    n = ctypes.c_size_t(0)
+    _check(lib().fk_pure_workspace_size(int(batch), len(cutoffs), _cut(cutoffs), int(op), int(flags),
+                                        ctypes.byref(n)), "fk_pure_workspace_size")
+    return int(n.value)
+
+
+def fock_pure_amplitudes_batched(A, b, c, cutoffs, psi=None, flags=0, ws=None, stream=None):
+    """State vectors psi [B, *cutoffs] of pure states (A [B, M, M], b [B, M],
+    c [B]).  Returns (psi, ws); ws keeps the walk for a following VJP."""
+    for n, t in (("A", A), ("b", b), ("c", c)):
+        _need_cuda_c128(n, t)
+    B, M = A.shape[0], len(cutoffs)
+    if A.shape != (B, M, M) or b.shape != (B, M) or c.shape != (B,):
+        raise ValueError("shapes must be A[B,M,M], b[B,M], c[B]")
+    if psi is None:
+        psi = torch.empty((B,) + tuple(int(x) for x in cutoffs), dtype=torch.complex128, device=A.device)
+    if ws is None:
+        ws = workspace(fk_pure_workspace_size(cutoffs, B, FK_OP_DIAG_VJP, flags), A.device)
+    st = lib().fock_pure_amplitudes_batched(B, _ptr(A), _ptr(b), _ptr(c), M, _cut(cutoffs), _ptr(psi),
+                                            flags, _ptr(ws), ws.numel(), _stream(stream))
+    _check(st, "fock_pure_amplitudes_batched")
+    return psi, ws
+
+
+def fock_pure_amplitudes_vjp_batched(A, b, c, cutoffs, grad_psi, ws, flags=0, stream=None):
+    for n, t in (("A", A), ("b", b), ("c", c), ("grad_psi", grad_psi)):
+        _need_cuda_c128(n, t)
+    B, M = A.shape[0], len(cutoffs)
+    gA = torch.empty_like(A); gb = torch.empty_like(b); gc = torch.empty_like(c)
+    if ws is None:
+        ws = workspace(fk_pure_workspace_size(cutoffs, B, FK_OP_DIAG_VJP, flags), A.device)
+        flags |= FK_FLAG_RECOMPUTE
+    st = lib().fock_pure_amplitudes_vjp_batched(B, _ptr(A), _ptr(b), _ptr(c), M, _cut(cutoffs),
+                                                _ptr(grad_psi), _ptr(gA), _ptr(gb), _ptr(gc), flags,
+                                                _ptr(ws), ws.numel(), _stream(stream))
+    _check(st, "fock_pure_amplitudes_vjp_batched")
     return gA, gb, gc
 
 

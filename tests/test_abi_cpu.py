@@ -116,3 +116,20 @@ def test_workspace_size_monotone_in_batch_and_b(fd):
     s2 = fd.fk_workspace_size(3, (4, 5, 3), 4, fd.FK_OP_DIAG, 0)
     s0 = fd.fk_workspace_size(3, (4, 5, 3), 1, fd.FK_OP_DIAG, fd.FK_FLAG_B_ZERO)
     assert s2 > s1 > s0
+
+
+def test_pure_triple_matches_oracle(fd):
+    """fk_gaussian_to_pure_triple (host C++) against the oracle's pure triple;
+    mixed states are refused."""
+    from oracle import triple as otriple
+    from paper_2303_08879_gb300 import inputs
+    rng = np.random.default_rng(12)
+    for M in (1, 2, 4):
+        circ = inputs.make_circuit(M, rng, r_range=(0.1, 1.0), eta_range=(1.0, 1.0), alpha_var=0.5,
+                                   cutoffs=(2,) * M)
+        A, b, c = fd.fk_gaussian_to_pure_triple(circ.V, circ.mean)
+        Ao, bo, co = otriple.pure_triple(circ.V, circ.mean)
+        assert np.max(np.abs(A - Ao)) < 1e-13 and np.max(np.abs(b - bo)) < 1e-13 and abs(c - co) < 1e-14
+    lossy = inputs.make_circuit(2, rng, r_range=(0.4, 0.5), eta_range=(0.5, 0.6), cutoffs=(2, 2))
+    with pytest.raises(fd.FockError):
+        fd.fk_gaussian_to_pure_triple(lossy.V, lossy.mean)

@@ -334,3 +334,40 @@ def test_vjp_closed_form_matches_finite_differences():
         d_re = (L(A, b + e) - L(A, b - e)) / (2 * h)
         d_im = (L(A, b + 1j * e) - L(A, b - 1j * e)) / (2 * h)
         assert abs(complex(d_re, d_im) - gb[m]) < 1e-7
+
+
+# ------------------------------------------------------------- pure states
+def test_pure_state_vector_squares_to_density_diagonal():
+    # |psi_n|^2 from the M-mode recurrence on the pure triple equals the
+    # diagonal of the density matrix from the 2M-mode recurrence (Sec. 2.2)
+    rng = inputs.rng_for(98, 1)
+    circ = inputs.make_circuit(3, rng, r_range=(0.2, 0.9), eta_range=(1.0, 1.0), alpha_var=0.4,
+                               cutoffs=(4, 3, 4))
+    Ap, bp, cp = triple.pure_triple(circ.V, circ.mean)
+    psi = oracle.full_lattice(Ap, bp, cp, (4, 3, 4))
+    A, b, c = triple.gaussian_to_triple(circ.V, circ.mean)
+    P = oracle.full_dm_probs(A, b, c, (4, 3, 4))
+    assert np.max(np.abs(np.abs(psi) ** 2 - P.real)) < 1e-14
+    with pytest.raises(ValueError):
+        lossy = inputs.make_circuit(2, rng, r_range=(0.5, 0.6), eta_range=(0.5, 0.6), cutoffs=(2, 2))
+        triple.pure_triple(lossy.V, lossy.mean)
+
+
+def test_pure_coherent_and_squeezed_closed_forms():
+    # coherent: psi_n = e^{-|a|^2/2} a^n / sqrt(n!)
+    al = 0.6 + 0.3j
+    Ap, bp, cp = triple.pure_triple(np.eye(2) / 2, math.sqrt(2) * np.array([al.real, al.imag]))
+    psi = oracle.full_lattice(Ap, bp, cp, (10,))
+    for n in range(10):
+        ex = math.exp(-abs(al) ** 2 / 2) * al ** n / math.sqrt(math.factorial(n))
+        assert abs(psi[n] - ex) < 1e-15
+    # x-squeezed vacuum: psi_2k = (-tanh r / 2)^k sqrt((2k)!) / (k! sqrt(cosh r)), odd = 0
+    r = 0.7
+    V = np.diag([math.exp(-2 * r), math.exp(2 * r)]) / 2
+    Ap, bp, cp = triple.pure_triple(V, np.zeros(2))
+    psi = oracle.full_lattice(Ap, bp, cp, (12,))
+    for n in range(12):
+        k = n // 2
+        ex = ((-math.tanh(r) / 2) ** k * math.sqrt(math.factorial(n)) / math.factorial(k)
+              / math.sqrt(math.cosh(r))) if n % 2 == 0 else 0.0
+        assert abs(psi[n] - ex) < 1e-15
