@@ -39,14 +39,13 @@ NCIRC = 16
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant
 # kernel (diag_vjp_kernel) per launch of this 16-circuit workload, captured
-# with ncu on a 2-circuit launch (7.735 GB read + 1.196 GB written) and
-# scaled by 8: circuits share no data, so traffic grows in proportion to them
-# (measured per circuit: 5.5 / 6.0 / 6.2 GB at 1 / 2 / 4 circuits, so the
-# scaled figure is a slight underestimate).  Valid only for the kernel source it
-# was measured on (sha256 prefix of csrc/walk_diag.cu) and the engine / tile
-# shape; reported as null once either differs.
-TRAFFIC = {"kernel_sha": "784a2210dc977cc7", "tuning": ["tensor", 128, 4, 0],
-           "bytes_per_launch": 8 * (7734632448 + 1195694336)}
+# with ncu on a 2-circuit launch (2.427 GB read + 0.857 GB written) and
+# scaled by 8: circuits share no data, so traffic grows in proportion to
+# them.  Valid only for the kernel source it was measured on (sha256 prefix
+# of csrc/walk_diag.cu) and the engine / tile shape; reported as null once
+# either differs.
+TRAFFIC = {"kernel_sha": "7a6bf87dd61945b0", "tuning": ["tensor", 128, 4, 0],
+           "bytes_per_launch": 8 * (2426514432 + 857377280)}
 
 FALLBACK_HBM_GBS = 6800.0
 
