@@ -50,8 +50,14 @@ StateLayout state_layout()
 // Workspace per batch: activations (bf16) and pre-activations (fp32) of the
 // three hidden layers, the padded input, the output, and backward buffers.
 struct WsLayout {
-    size_t x, z1, a1, z2, a2, z3, a3, y, g3, g2, g1, gy, gp, loss, total;
+    size_t x, z1, a1, z2, a2, z3, a3, y, g3, g2, g1, gy, gp, loss, wpart, bpart, total;
 };
+
+// The weight gradients contract over the batch: from 1024 samples on their
+// K range is split over ksplit(B) slices written to a scratch array and summed
+// in a fixed order (the output tiles alone give 4-16 CTAs).
+constexpr int kBiasRows = 4096;   // batch rows per block of the bias-gradient sums
+int ksplit(int B) { return B >= 1024 ? (B / 512 < 32 ? B / 512 : 32) : 1; }
 
 WsLayout ws_layout(int B)
 {
@@ -72,6 +78,8 @@ WsLayout ws_layout(int B)
     w.g1 = o; o = al(o + b * H * 2);
     w.gp = o; o = al(o + NPARAM * 4);
     w.loss = o; o = al(o + 64);
+    w.wpart = o; o = al(o + (size_t)ksplit(B) * H * H * 4);
+    w.bpart = o; o = al(o + (size_t)((B + kBiasRows - 1) / kBiasRows) * H * 4);
     w.total = o;
     return w;
 }
@@ -96,6 +104,8 @@ struct GemmArgs {
     float *wgrad;               // EPI_WGRAD destination [M][ldw]
     int ldo;                    // leading dimension of the outputs
     int nvalid;                 // columns actually stored (<= N)
+    int ksplit;                 // EPI_WGRAD: K slices (blockIdx.z), partials to wpart
+    float *wpart;               // [ksplit][M][ldo]
 };
 
 __device__ __forceinline__ float silu(float z) { return z / (1.0f + expf(-z)); }
@@ -131,16 +141,22 @@ __global__ void __launch_bounds__(128) gemm_kernel(GemmArgs g)
 #pragma unroll
             for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
     const __nv_bfloat16 zero = __float2bfloat16(0.f);
-    for (int k0 = 0; k0 < g.K; k0 += BK) {
+    // K slice of this block (split-K for the weight gradients)
+    const int kper = ((g.K + g.ksplit - 1) / g.ksplit + BK - 1) / BK * BK;
+    const int kbeg = blockIdx.z * kper, kend = min(g.K, kbeg + kper);
+    // operands stored k-major (transposed) are filled with m (n) fastest so a
+    // warp reads consecutive addresses
+    const bool at = g.sak > g.sam, bt = g.sbk > g.sbn;
+    for (int k0 = kbeg; k0 < kend; k0 += BK) {
         for (int e = tid; e < BM * BK; e += blockDim.x) {
-            const int r = e / BK, kk = e % BK;
+            const int r = at ? e % BM : e / BK, kk = at ? e / BM : e % BK;
             const int m = m0 + r, k = k0 + kk;
-            As[r][kk] = (m < g.M && k < g.K) ? g.A[m * g.sam + k * g.sak] : zero;
+            As[r][kk] = (m < g.M && k < kend) ? g.A[(int64_t)m * g.sam + (int64_t)k * g.sak] : zero;
         }
         for (int e = tid; e < BN * BK; e += blockDim.x) {
-            const int r = e / BK, kk = e % BK;
+            const int r = bt ? e % BN : e / BK, kk = bt ? e / BN : e % BK;
             const int n = n0 + r, k = k0 + kk;
-            Bs[r][kk] = (n < g.N && k < g.K) ? g.B[n * g.sbn + k * g.sbk] : zero;
+            Bs[r][kk] = (n < g.N && k < kend) ? g.B[(int64_t)n * g.sbn + (int64_t)k * g.sbk] : zero;
         }
         __syncthreads();
 #pragma unroll
@@ -188,16 +204,33 @@ __global__ void __launch_bounds__(128) gemm_kernel(GemmArgs g)
                 }
                 case EPI_OUT: g.z[o] = v + g.bias[n]; break;
                 case EPI_BACK_HIDDEN: g.act[o] = __float2bfloat16(v * dsilu(g.zprev[o])); break;
-                case EPI_WGRAD: g.wgrad[o] = v; break;
+                case EPI_WGRAD:
+                    if (g.ksplit > 1) g.wpart[(int64_t)blockIdx.z * g.M * g.ldo + o] = v;
+                    else g.wgrad[o] = v;
+                    break;
                 default: break;
                 }
             }
 }
 
-int gemm(const GemmArgs &g, cudaStream_t st)
+__global__ void sum_slices(const float *part, int slices, int64_t n, float *out)
 {
-    dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM);
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float s = 0.f;
+    for (int z = 0; z < slices; ++z) s += part[(int64_t)z * n + i];
+    out[i] = s;
+}
+
+int gemm(GemmArgs g, cudaStream_t st)
+{
+    if (g.ksplit < 1 || g.epi != EPI_WGRAD) g.ksplit = 1;
+    dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, g.ksplit);
     gemm_kernel<<<grid, 128, 0, st>>>(g);
+    if (g.ksplit > 1) {
+        const int64_t n = (int64_t)g.M * g.ldo;
+        sum_slices<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g.wpart, g.ksplit, n, g.wgrad);
+    }
     return cudaGetLastError() == cudaSuccess ? FK_OK : FK_ECUDA;
 }
 
@@ -262,14 +295,31 @@ __global__ void pack_grad(const float *gy, __nv_bfloat16 *out, int B)
     out[(int64_t)b * OUTP + j] = __float2bfloat16(gy[i]);
 }
 
-// bias gradients: column sums of a [B][ld] bf16 gradient (first n columns)
-__global__ void bias_grad(const __nv_bfloat16 *g, int B, int ld, int n, float *out)
+// bias gradients: column sums of a [B][ld] bf16 gradient (first n columns).
+// Block (x: 32 columns, y: kBiasRows rows), 32 x 8 threads; the 8 row
+// strands are summed in a fixed order, then the row blocks (second kernel).
+__global__ void bias_grad_part(const __nv_bfloat16 *g, int B, int ld, int n, float *part)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
+    __shared__ float red[8][33];
+    const int j = blockIdx.x * 32 + threadIdx.x;
+    const int b0 = blockIdx.y * kBiasRows, b1 = min(B, b0 + kBiasRows);
     float s = 0.f;
-    for (int b = 0; b < B; ++b) s += __bfloat162float(g[(int64_t)b * ld + j]);
-    out[j] = s;
+    if (j < n)
+        for (int b = b0 + threadIdx.y; b < b1; b += 8) s += __bfloat162float(g[(int64_t)b * ld + j]);
+    red[threadIdx.y][threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.y == 0 && j < n) {
+        float t = 0.f;
+        for (int y = 0; y < 8; ++y) t += red[y][threadIdx.x];
+        part[(int64_t)blockIdx.y * n + j] = t;
+    }
+}
+
+void bias_grad(const __nv_bfloat16 *g, int B, int ld, int n, float *part, float *out, cudaStream_t st)
+{
+    const int rb = (B + kBiasRows - 1) / kBiasRows;
+    bias_grad_part<<<dim3((n + 31) / 32, rb), dim3(32, 8), 0, st>>>(g, B, ld, n, part);
+    sum_slices<<<(n + 255) / 256, 256, 0, st>>>(part, rb, n, out);
 }
 
 __global__ void adam_kernel(float *w, float *m, float *v, const float *g, int64_t n, float lr,
@@ -289,7 +339,7 @@ struct Ptrs {
     float *master, *m, *v;
     __nv_bfloat16 *w1, *w2, *w3, *w4;
     __nv_bfloat16 *x, *a1, *a2, *a3, *gy, *g3, *g2, *g1;
-    float *z1, *z2, *z3, *y, *gp, *loss;
+    float *z1, *z2, *z3, *y, *gp, *loss, *wpart, *bpart;
 };
 
 Ptrs ptrs(void *state, void *ws, int B)
@@ -319,6 +369,8 @@ Ptrs ptrs(void *state, void *ws, int B)
     p.g1 = (__nv_bfloat16 *)(W + w.g1);
     p.gp = (float *)(W + w.gp);
     p.loss = (float *)(W + w.loss);
+    p.wpart = (float *)(W + w.wpart);
+    p.bpart = (float *)(W + w.bpart);
     return p;
 }
 
@@ -356,8 +408,9 @@ int backward(const Ptrs &p, int B, cudaStream_t st)
     g.A = p.gy; g.sam = 1; g.sak = OUTP;          // A(m=j, k=b) = gy[b][j]
     g.B = p.a3; g.sbn = 1; g.sbk = H;             // B(n, k=b) = a3[b][n]
     g.epi = EPI_WGRAD; g.wgrad = p.gp + OW4; g.ldo = H; g.nvalid = H;
+    g.ksplit = ksplit(B); g.wpart = p.wpart;
     if ((rc = gemm(g, st))) return rc;
-    bias_grad<<<1, 32, 0, st>>>(p.gy, B, OUTP, OUT, p.gp + OB4);
+    bias_grad(p.gy, B, OUTP, OUT, p.bpart, p.gp + OB4, st);
     // dL/dz3 = (gy W4) * silu'(z3)
     g = GemmArgs{};
     g.M = B; g.N = H; g.K = OUTP;
@@ -381,8 +434,9 @@ int backward(const Ptrs &p, int B, cudaStream_t st)
         g.epi = EPI_WGRAD; g.wgrad = p.gp + ow[l];
         g.ldo = (l == 2) ? IN : Kin[l];
         g.nvalid = (l == 2) ? IN : Kin[l];
+        g.ksplit = ksplit(B); g.wpart = p.wpart;
         if ((rc = gemm(g, st))) return rc;
-        bias_grad<<<(H + 127) / 128, 128, 0, st>>>(gin[l], B, H, H, p.gp + ob[l]);
+        bias_grad(gin[l], B, H, H, p.bpart, p.gp + ob[l], st);
         if (gout[l]) {
             g = GemmArgs{};
             g.M = B; g.N = H; g.K = H;

@@ -26,7 +26,7 @@ def _blocks(v):
     return out
 
 
-@pytest.mark.parametrize("B", [1, 37, 256, 1000])
+@pytest.mark.parametrize("B", [1, 37, 256, 1000, 20000])   # 20000: split-K weight gradients
 def test_forward_backward_match_reference(mlpmod, B):
     rng = np.random.default_rng(B)
     p = mlpmod.init_params(B)
