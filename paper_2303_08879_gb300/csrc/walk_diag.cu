@@ -34,6 +34,7 @@ namespace fk {
 namespace {
 
 constexpr int TABN = kTabN;
+constexpr unsigned long long kMagicBits = 0x4B400000ull;   // bit pattern of the fp32 1.5 * 2^23
 
 struct DiagArgs {
     DiagShape sh;
@@ -71,14 +72,13 @@ struct Smem {
     double *R3;       // [3][D][RS] reads per pivot (three planes, see store_read)
     double *Y3;       // [3][D][RS] scaled output adjoints per pivot (VJP)
     double2 *FP;      // [RS] pivot values (VJP, b != 0)
-    uint16_t *Ad;     // tensor-core engine: [7][2D][AS] bf16 digit slices of the real form of A
-    double *sA;       // tensor-core engine: [2D] row scales 2^(e_r - 1048)
+    uint4 *Af;        // tensor-core engine: [KS][KS][7][32] fp16 digit fragments of the real
+                      // form of A (m16n8k16 A-operand order, one 16-byte word per lane)
     int *fA;          // tensor-core engine: [2D] row exponent fields e_r
     double *wb;       // tensor-core engine: per-warp [16 KS][WBS] reads in, products out
     double *wy;       // tensor-core VJP: per-warp [16 KS][WBS] scaled output adjoints
     int *wf;          // tensor-core VJP: [TPB] exponent field of each pivot's largest read
     int *wg;          // tensor-core VJP: per-warp [32] row exponents of the partial dL/dA
-    int AS;           // row stride of Ad (bf16 elements)
     int *idx;         // [M][TPB] box indices per pivot
     int *tiles;       // [M + 2] tile prefix sums of the current phase
     int loaded_circ;
@@ -114,16 +114,6 @@ struct DpGeom {
     unsigned vmask, nmask;
 };
 
-// Row stride (bf16 elements) of a digit slice of the 2D x 2D real form of A:
-// at least 2D, and a word stride of 4 mod 8 so the eight rows one fragment
-// load touches fall in distinct banks.
-__host__ __device__ inline int digit_row_stride(int D2)
-{
-    int w = D2 / 2;
-    w += (12 - w % 8) % 8;
-    return 2 * w;
-}
-
 // The walk for one tile shape: TPB pivots per tile (= threads per block) and
 // either CH output rows per FP64 register chunk (KS = 0) or, for KS > 0, the
 // tensor-core digit engine with up to 16 KS real rows (M <= 4 KS); the
@@ -148,11 +138,11 @@ struct Walk {
             const int D2 = 2 * D;
             const size_t buf = (size_t)(TPB / 32) * XS * WBS * sizeof(double);
             n += (size_t)D * sizeof(double2);
-            n += (size_t)D2 * (sizeof(double) + sizeof(int));
+            n += (size_t)D2 * sizeof(int);
             n = (n + 15) & ~(size_t)15;
             n += buf;
             if (vjp) n += buf + (size_t)TPB * (sizeof(double2) + 2 * sizeof(int));
-            n += (size_t)NDIG * D2 * digit_row_stride(D2) * sizeof(uint16_t);
+            n += (size_t)KS * KS * NDIG * 32 * sizeof(uint4);
         } else {
             n += 3 * (size_t)D * D * sizeof(double) + (size_t)D * sizeof(double2);
             n += 3 * (size_t)D * RS * sizeof(double);
@@ -179,17 +169,14 @@ struct Walk {
         s.fact = (double *)p; p += TABN * sizeof(double);
         s.A3 = s.R3 = s.Y3 = nullptr;
         s.FP = nullptr;
-        s.Ad = nullptr;
-        s.sA = nullptr;
+        s.Af = nullptr;
         s.fA = nullptr;
         s.wb = s.wy = nullptr;
         s.wf = s.wg = nullptr;
-        s.AS = 0;
         if (TC) {
             const int D2 = 2 * D;
             const size_t buf = (size_t)(TPB / 32) * XS * WBS;
             s.bs = (double2 *)p; p += (size_t)D * sizeof(double2);
-            s.sA = (double *)p; p += (size_t)D2 * sizeof(double);
             s.fA = (int *)p; p += (size_t)D2 * sizeof(int);
             p = (unsigned char *)(((uintptr_t)p + 15) & ~(uintptr_t)15);
             s.wb = (double *)p; p += buf * sizeof(double);
@@ -199,8 +186,8 @@ struct Walk {
                 s.wf = (int *)p; p += (size_t)TPB * sizeof(int);
                 s.wg = (int *)p; p += (size_t)TPB * sizeof(int);
             }
-            s.AS = digit_row_stride(D2);
-            s.Ad = (uint16_t *)p; p += (size_t)NDIG * D2 * s.AS * sizeof(uint16_t);
+            p = (unsigned char *)(((uintptr_t)p + 15) & ~(uintptr_t)15);
+            s.Af = (uint4 *)p; p += (size_t)KS * KS * NDIG * 32 * sizeof(uint4);
         } else {
             s.A3 = (double *)p; p += 3 * (size_t)D * D * sizeof(double);
             s.bs = (double2 *)p; p += (size_t)D * sizeof(double2);
@@ -293,7 +280,7 @@ struct Walk {
         __syncthreads();
         const int D = 2 * a.sh.M, DD = D * D;
         const double2 *As = a.As + (size_t)circ * DD;
-        if (TC && s.Ad != nullptr) {
+        if (TC && s.Af != nullptr) {
             load_circuit_digits(s, As, D);
             for (int e = threadIdx.x; e < D; e += blockDim.x) s.bs[e] = a.bs[(size_t)circ * D + e];
             __syncthreads();
@@ -393,29 +380,40 @@ struct Walk {
     }
 
     // ------------------------------------------------- tensor-core engine
-    // A real product sum_c R[r][c] x[c] is computed exactly on the bf16 tensor
+    // A real product sum_c R[r][c] x[c] is computed exactly on the fp16 tensor
     // cores (an Ozaki-type split): each value is turned into a 56-bit fixed
     // point integer relative to a power of two shared along the contraction
     // (per row r of R, per pivot for x), written as seven balanced base-256
-    // digits in [-128, 127] (exact in bf16), and the digit products are summed
+    // digits in [-128, 127] (exact in fp16), and the digit products are summed
     // in fp32 per digit diagonal d = s + u <= 6.  Every partial sum is an
-    // integer below 2^23 (|digit product| <= 2^14, at most 7 x 2D terms), so
-    // fp32 holds it exactly; the diagonals are recombined in int64 and scaled
-    // back in one rounding.  Dropped diagonals and the fixed-point cut leave a
-    // relative error near 2^-53 of the largest term, like FP64.
+    // integer below 2^22 in magnitude (|digit product| <= 2^14, at most 7 x 32
+    // terms), so fp32 holds it exactly; the diagonals are recombined in int64
+    // and scaled back by an exponent shift.  Dropped diagonals and the
+    // fixed-point cut leave a relative error near 2^-53 of the largest term,
+    // like FP64.
 
     static __device__ __forceinline__ int fexp(double v) { return (__double2hiint(v) >> 20) & 0x7ff; }
 
-    // 2^(f - 1048) (the scale of a value whose largest exponent field is f), 0
-    // for f < 26 (values below 2^-997 are flushed to zero).
-    static __device__ __forceinline__ double digit_scale(int f)
+    // 2^e as a double for e in [-1022, 1023].
+    static __device__ __forceinline__ double pow2(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
+
+    // v 2^k for v = 0 or an integer-valued double: the exponent field moves by
+    // k while the result stays normal (exact, no floating-point instruction);
+    // otherwise two power-of-two factors, the first exact, so a subnormal or
+    // infinite result is rounded once.
+    static __device__ __forceinline__ double scale2(double v, int k)
     {
-        return f >= 26 ? __longlong_as_double((long long)(f - 25) << 52) : 0.0;
+        const long long bits = __double_as_longlong(v);
+        const int f = (int)((bits >> 52) & 0x7ff);
+        if (f != 0 && f + k >= 1 && f + k <= 2046) return __longlong_as_double(bits + ((long long)k << 52));
+        k = max(k, -2044);   // |v| < 2^64: anything smaller is zero after rounding anyway
+        const int k1 = k / 2;
+        return v * pow2(k1) * pow2(k - k1);
     }
 
     // Biased fixed point U = round(v * 2^(1076 - fmax)) + 0x0080808080808080:
     // |round(...)| < 2^54, so 0 < U < 2^56 and byte k of U minus 128 is the
-    // k-th balanced base-256 digit.
+    // k-th balanced base-256 digit.  fmax < 26 (values below 2^-997) gives 0.
     static __device__ __forceinline__ uint64_t to_fixed(double v, int fmax)
     {
         const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
@@ -431,71 +429,73 @@ struct Walk {
         return (uint64_t)(X + 0x0080808080808080ll);
     }
 
-    // bf16 bits of digit s (0 = most significant) of a biased fixed point U.
-    static __device__ __forceinline__ uint32_t digit_bits(uint64_t U, int sl)
-    {
-        const int k = NDIG - 1 - sl;
-        const uint32_t w = (k >= 4) ? (uint32_t)(U >> 32) : (uint32_t)U;
-        const uint32_t byte = (w >> (8 * (k & 3))) & 0xffu;
-        const float d = __uint_as_float(0x4B000000u | byte) - 8388736.0f;   // byte - 128, exact
-        return __float_as_uint(d) >> 16;                                      // exact in bf16
-    }
-
     // The seven digits of a pair (lo, hi) of biased fixed points as packed
-    // bf16 words: word s = digit s of lo in bits 0-15, of hi in bits 16-31.
-    // Byte k of U is moved into the mantissa of 2^23 (one byte permute), the
-    // float subtraction of 2^23 + 128 gives the digit exactly, and its top
-    // half is its bf16 encoding.
+    // fp16 words: word s = digit s (0 = most significant) of lo in bits 0-15,
+    // of hi in bits 16-31.  Bytes k of lo and hi are first interleaved, then
+    // one byte permute places each as the low mantissa byte of an fp16 with
+    // exponent field 25 (the value 1024 + byte), and one packed fp16
+    // subtraction of 1152 leaves byte - 128, the balanced digit, exactly.
     static __device__ __forceinline__ void digit_words(uint64_t lo, uint64_t hi, uint32_t (&w)[NDIG])
     {
         const uint32_t l0 = (uint32_t)lo, l1 = (uint32_t)(lo >> 32);
         const uint32_t h0 = (uint32_t)hi, h1 = (uint32_t)(hi >> 32);
+        // t[k >> 1]: byte k of lo at byte 2 (k & 1), of hi at byte 2 (k & 1) + 1
+        const uint32_t t[4] = {__byte_perm(l0, h0, 0x5140), __byte_perm(l0, h0, 0x7362),
+                               __byte_perm(l1, h1, 0x5140), __byte_perm(l1, h1, 0x7362)};
 #pragma unroll
         for (int sl = 0; sl < NDIG; ++sl) {
             const int k = NDIG - 1 - sl;
-            const uint32_t sel = 0x7650u | (uint32_t)(k & 3);
-            const float a = __uint_as_float(__byte_perm(k >= 4 ? l1 : l0, 0x4B000000u, sel)) - 8388736.0f;
-            const float b = __uint_as_float(__byte_perm(k >= 4 ? h1 : h0, 0x4B000000u, sel)) - 8388736.0f;
-            w[sl] = __byte_perm(__float_as_uint(a), __float_as_uint(b), 0x7632);
+            const uint32_t v = __byte_perm(t[k >> 1], 0x64646464u, (k & 1) ? 0x4342 : 0x4140);
+            uint32_t d;
+            asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(d) : "r"(v), "r"(0x64806480u));
+            w[sl] = d;
         }
     }
 
-    // Digit slices of the real form R of A_s (row 2i: Re, col 2j -> Re A_ij,
-    // col 2j+1 -> -Im A_ij; row 2i+1: Im A_ij, Re A_ij) into shared memory.
+    // Digit fragments of the real form R of A_s (row 2i: Re A_ij at column 2j,
+    // -Im A_ij at 2j+1; row 2i+1: Im A_ij, Re A_ij), padded with zeros to
+    // 16 KS x 16 KS, into shared memory in the register order of the A operand
+    // of mma m16n8k16: tile (mt, ks), digit s, lane (grp, tig) holds rows
+    // 16 mt + grp (+8) and columns 16 ks + 2 tig (+1, +8, +9).  Row r is fixed
+    // point relative to the largest exponent field of its row of A.
     static __device__ void load_circuit_digits(Smem &s, const double2 *As, int D)
     {
         const int D2 = 2 * D;
-        for (int i = threadIdx.x; i < D; i += blockDim.x) {
-            int fm = 0;
-            for (int j = 0; j < D; ++j) {
-                const double2 v = As[(size_t)i * D + j];
-                fm = max(fm, max(fexp(v.x), fexp(v.y)));
-            }
-            s.fA[2 * i] = s.fA[2 * i + 1] = fm;
-            s.sA[2 * i] = s.sA[2 * i + 1] = digit_scale(fm);
+        constexpr int P = 16 * (KS > 0 ? KS : 1);
+        for (int r = threadIdx.x; r < D2; r += blockDim.x) s.fA[r] = 0;
+        __syncthreads();
+        for (int e = threadIdx.x; e < D * D; e += blockDim.x) {
+            const double2 v = As[e];
+            const int f = max(fexp(v.x), fexp(v.y));
+            if (f != 0) atomicMax(&s.fA[2 * (e / D)], f);
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < D2 * D2; e += blockDim.x) {
-            const int r = e / D2, c = e % D2;
-            const double2 v = As[(size_t)(r >> 1) * D + (c >> 1)];
-            const double x = (r & 1) ? ((c & 1) ? v.x : v.y) : ((c & 1) ? -v.y : v.x);
-            const uint64_t U = to_fixed(x, s.fA[r]);
+        for (int i = threadIdx.x; i < D; i += blockDim.x) s.fA[2 * i + 1] = s.fA[2 * i];
+        __syncthreads();
+        uint32_t *Af = (uint32_t *)s.Af;
+        for (int e = threadIdx.x; e < P * P / 2; e += blockDim.x) {
+            const int r = e / (P / 2), c = 2 * (e % (P / 2));
+            uint32_t wd[NDIG];
+            if (r < D2 && c < D2) {
+                const double2 v = As[(size_t)(r >> 1) * D + (c >> 1)];
+                const double x0 = (r & 1) ? v.y : v.x, x1 = (r & 1) ? v.x : -v.y;
+                digit_words(to_fixed(x0, s.fA[r]), to_fixed(x1, s.fA[r]), wd);
+            } else {
 #pragma unroll
-            for (int sl = 0; sl < NDIG; ++sl)
-                s.Ad[((size_t)sl * D2 + r) * s.AS + c] = (uint16_t)digit_bits(U, sl);
+                for (int sl = 0; sl < NDIG; ++sl) wd[sl] = 0u;
+            }
+            const int rr = r & 15, cc = c & 15;
+            const int lane = (rr & 7) * 4 + ((cc & 7) >> 1), k = (rr >> 3) | ((cc >> 3) << 1);
+            const int tile = (r >> 4) * KS + (c >> 4);
+#pragma unroll
+            for (int sl = 0; sl < NDIG; ++sl) Af[(((tile * NDIG + sl) * 32 + lane) << 2) + k] = wd[sl];
         }
     }
 
-    static __device__ __forceinline__ uint32_t lda(const Smem &s, int sl, int row, int col, int D2)
-    {
-        return (row < D2 && col < D2) ? *(const uint32_t *)(s.Ad + ((size_t)sl * D2 + row) * s.AS + col)
-                                      : 0u;
-    }
-
-    static __device__ __forceinline__ void mma_bf16(float *c, const uint32_t *a, const uint32_t *b)
+    static __device__ __forceinline__ void mma_f16(float *c, const uint32_t *a, const uint32_t *b)
     {
         asm volatile(
-            "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+            "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
             "{%8,%9}, {%0,%1,%2,%3};\n"
             : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
             : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
@@ -503,21 +503,23 @@ struct Walk {
 
     // Products of the 32 pivots of this warp with the real form of A (CONJ:
     // of conj(A)) restricted to rows and columns from row0 (complex index):
-    // out[r][p] = sum_c R[row0 + r][row0 + c] in[c][p] for r, c < 2N, in and
-    // out per-warp buffers (row = real index 2j + {re, im}, column = lane).
-    // MMA tile m16n8k16: M = output real rows, N = 8 pivots, K = input real
-    // rows.  out may alias in: an N tile is read before its products land.
+    // out[r][p] = sum_c R[2 row0 + r][2 row0 + c] in[c][p] for r, c < 2N, in
+    // and out per-warp buffers (row = real index 2j + {re, im} relative to
+    // row0, column = lane).  The MMA tiles are the aligned 16 x 16 tiles of R
+    // that the rows [2 row0, 2 row0 + 2N) meet; inputs outside that range
+    // enter as zeros.  MMA tile m16n8k16: M = output real rows, N = 8 pivots,
+    // K = input real rows.  out may alias in: an N tile is read before its
+    // products land.
     template <bool CONJ>
     static __device__ __forceinline__ void tc_products(const Smem &s, int D, int row0, int N, double *in,
                                                        double *out)
     {
         const int lane = threadIdx.x & 31, grp = lane >> 2, tig = lane & 3;
-        const int D2 = 2 * D, r0 = 2 * row0, n2 = 2 * N, nks = (n2 + 15) >> 4;
+        const int r0 = 2 * row0, n2 = 2 * N, t0 = r0 >> 4, t1 = (r0 + n2 + 15) >> 4;
         // conj(A) in real form: the Im A entries change sign (high half of a
         // fragment word in even rows, low half in odd rows; digits negate exactly)
         const uint32_t cflip = CONJ ? ((grp & 1) ? 0x00008000u : 0x80000000u) : 0u;
-        for (int c = n2; c < 16 * nks; ++c) in[c * WBS + lane] = 0.0;
-        __syncwarp();
+        const uint4 *Af = s.Af + lane;
 #pragma unroll 1
         for (int nt = 0; nt < 4; ++nt) {
             const int p = nt * 8 + grp;
@@ -527,9 +529,10 @@ struct Walk {
             for (int ks = 0; ks < KS; ++ks)
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const int c = 16 * ks + 8 * h + 2 * tig;
-                    xv[ks][h][0] = ks < nks ? in[c * WBS + p] : 0.0;
-                    xv[ks][h][1] = ks < nks ? in[(c + 1) * WBS + p] : 0.0;
+                    const int c = 16 * ks + 8 * h + 2 * tig - r0;
+                    const bool ok = ks >= t0 && ks < t1 && c >= 0 && c < n2;
+                    xv[ks][h][0] = ok ? in[c * WBS + p] : 0.0;
+                    xv[ks][h][1] = ok ? in[(c + 1) * WBS + p] : 0.0;
                     fm = max(fm, max(fexp(xv[ks][h][0]), fexp(xv[ks][h][1])));
                 }
             fm = max(fm, __shfl_xor_sync(0xffffffffu, fm, 1));
@@ -545,39 +548,40 @@ struct Walk {
                     for (int sl = 0; sl < NDIG; ++sl) bq[sl][ks][h] = wd[sl];
                 }
             __syncwarp();   // every lane has read this N tile's inputs
-            const double sx0 = digit_scale(__shfl_sync(0xffffffffu, fm, 8 * tig));
-            const double sx1 = digit_scale(__shfl_sync(0xffffffffu, fm, 8 * tig + 4));
+            // exponent fields of the two pivots whose products this lane combines
+            const int fx0 = __shfl_sync(0xffffffffu, fm, 8 * tig) - 2096;
+            const int fx1 = __shfl_sync(0xffffffffu, fm, 8 * tig + 4) - 2096;
 #pragma unroll 1
-            for (int mt = 0; mt < nks; ++mt) {
+            for (int mt = t0; mt < t1; ++mt) {
                 float acc[NDIG][4];
 #pragma unroll
                 for (int d = 0; d < NDIG; ++d)
 #pragma unroll
                     for (int q = 0; q < 4; ++q) acc[d][q] = 0.f;
-                const int row = r0 + 16 * mt + grp;
 #pragma unroll
                 for (int sa = 0; sa < NDIG; ++sa) {
                     uint32_t af[KS][4];
 #pragma unroll
                     for (int ks = 0; ks < KS; ++ks) {
-                        const int col = r0 + 16 * ks + 2 * tig;
-                        af[ks][0] = lda(s, sa, row, col, D2) ^ cflip;
-                        af[ks][1] = lda(s, sa, row + 8, col, D2) ^ cflip;
-                        af[ks][2] = lda(s, sa, row, col + 8, D2) ^ cflip;
-                        af[ks][3] = lda(s, sa, row + 8, col + 8, D2) ^ cflip;
+                        const uint4 f = Af[((mt * KS + ks) * NDIG + sa) * 32];
+                        af[ks][0] = f.x ^ cflip;
+                        af[ks][1] = f.y ^ cflip;
+                        af[ks][2] = f.z ^ cflip;
+                        af[ks][3] = f.w ^ cflip;
                     }
 #pragma unroll
                     for (int u = 0; u + sa < NDIG; ++u)
 #pragma unroll
                         for (int ks = 0; ks < KS; ++ks)
-                            if (ks < nks) mma_bf16(acc[sa + u], af[ks], bq[u][ks]);
+                            if (ks >= t0 && ks < t1) mma_f16(acc[sa + u], af[ks], bq[u][ks]);
                 }
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const int r = 16 * mt + grp + 8 * (q >> 1), pc = nt * 8 + 2 * tig + (q & 1);
-                    if (r < n2) {
+                    const int ra = 16 * mt + grp + 8 * (q >> 1), r = ra - r0;
+                    const int pc = nt * 8 + 2 * tig + (q & 1);
+                    if (r >= 0 && r < n2) {
                         const long long Y = combine_digits(acc, q);
-                        out[r * WBS + pc] = __ll2double_rn(Y) * (s.sA[r0 + r] * ((q & 1) ? sx1 : sx0));
+                        out[r * WBS + pc] = scale2(__ll2double_rn(Y), s.fA[ra] + ((q & 1) ? fx1 : fx0));
                     }
                 }
             }
@@ -586,8 +590,30 @@ struct Walk {
     }
 
     // Digit diagonals d = 0..6 of one accumulator element recombined:
-    // sum_d acc_d 256^(5 - d), the last diagonal shifted down (floor).
+    // sum_d acc_d 256^(5 - d), the last diagonal shifted down (floor).  For
+    // |acc_d| < 2^22 the fp32 sum acc_d + 1.5 * 2^23 is exact and its bit
+    // pattern is 0x4B400000 + acc_d, so the integers come from one add each;
+    // the constant those offsets contribute is removed at the end (modulo
+    // 2^64, where the true sum fits).
+    static __host__ __device__ constexpr unsigned long long combine_bias()
+    {
+        unsigned long long y = kMagicBits;
+        for (int d = 1; d < NDIG - 1; ++d) y = (y << 8) + kMagicBits;
+        return y + (kMagicBits >> 8);
+    }
+
     static __device__ __forceinline__ long long combine_digits(const float (&acc)[NDIG][4], int q)
+    {
+        unsigned long long Y = __float_as_uint(acc[0][q] + 12582912.0f);
+#pragma unroll
+        for (int d = 1; d < NDIG - 1; ++d) Y = (Y << 8) + __float_as_uint(acc[d][q] + 12582912.0f);
+        Y += __float_as_uint(acc[NDIG - 1][q] + 12582912.0f) >> 8;
+        constexpr unsigned long long bias = combine_bias();
+        return (long long)(Y - bias);
+    }
+
+    // The same for partial sums below 2^23 in magnitude (conversions to int).
+    static __device__ __forceinline__ long long combine_digits_wide(const float (&acc)[NDIG][4], int q)
     {
         long long Y = __float2int_rn(acc[0][q]);
 #pragma unroll
@@ -702,7 +728,7 @@ struct Walk {
 #pragma unroll
                 for (int sa = 0; sa < NDIG; ++sa)
 #pragma unroll
-                    for (int u = 0; u + sa < NDIG; ++u) mma_bf16(acc[sa + u][nt], aq[sa], bq[u]);
+                    for (int u = 0; u + sa < NDIG; ++u) mma_f16(acc[sa + u][nt], aq[sa], bq[u]);
             }
         }
 #pragma unroll
@@ -716,8 +742,8 @@ struct Walk {
                     float a7[NDIG][4];
 #pragma unroll
                     for (int d = 0; d < NDIG; ++d) a7[d][0] = acc[d][nt][q];
-                    const long long Y = combine_digits(a7, 0);
-                    const double v = __ll2double_rn(Y) * digit_scale(g) * 0x1p-26;
+                    const long long Y = combine_digits_wide(a7, 0);
+                    const double v = scale2(__ll2double_rn(Y), g - 1074);
                     double *dst = pA + 2 * ((size_t)(row0 + w) * D + row0 + j) + (n & 1);
                     *dst += v;
                 }
@@ -1176,8 +1202,9 @@ struct Walk {
                 const int64_t ia = g.lk0 + g.r;
                 a.scratch[(size_t)tl.circ * sh.n_ap + sh.off_ap[K] + ia] = acc;
             } else {
-                const int64_t addr = ap_read_addr(sh, g, K, j, s);
-                Fb[addr] = cadd(__ldcg(Fb + addr), acc);
+                // T2 and P1010/P1001 values have this pivot as their only
+                // reader, so their adjoint is this one term
+                Fb[ap_read_addr(sh, g, K, j, s)] = acc;
             }
         });
         if (HASB && act) {
@@ -1336,8 +1363,7 @@ struct Walk {
                     const int64_t ia = g.lk0 + g.r;
                     a.scratch[(size_t)tl.circ * sh.n_ap + sh.off_ap[K] + ia] = acc;
                 } else {
-                    const int64_t addr = ap_read_addr(sh, g, K, j, s);
-                    Fb[addr] = cadd(__ldcg(Fb + addr), acc);
+                    Fb[ap_read_addr(sh, g, K, j, s)] = acc;   // the value's only reader
                 }
             }
             if (HASB) {
