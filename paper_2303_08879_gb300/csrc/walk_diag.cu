@@ -298,6 +298,26 @@ struct Walk {
         s.loaded_circ = circ;
     }
 
+    // Per-pivot gather of N values: load(j) gives value j, put(j, v) stores
+    // it.  With the tensor engine the loop is unrolled to its largest length
+    // so that every load is in flight before the first store (one memory
+    // latency per gather instead of one per value).
+    template <class Load, class Put>
+    static __device__ __forceinline__ void gather(int N, Load load, Put put)
+    {
+        if constexpr (TC) {
+            constexpr int NM = 8 * (KS > 0 ? KS : 1);
+            double2 v[NM];
+#pragma unroll
+            for (int j = 0; j < NM; ++j) v[j] = j < N ? load(j) : make_double2(0, 0);
+#pragma unroll
+            for (int j = 0; j < NM; ++j)
+                if (j < N) put(j, v[j]);
+        } else {
+            for (int j = 0; j < N; ++j) put(j, load(j));
+        }
+    }
+
     // Three planes of a read x: forward (Re x, Im x, Re x + Im x); reverse
     // (Re x, Re x - Im x, Re x + Im x).
     static __device__ __forceinline__ void store_read(Smem &s, int D, int j, int t, double2 x,
@@ -558,22 +578,17 @@ struct Walk {
                 for (int d = 0; d < NDIG; ++d)
 #pragma unroll
                     for (int q = 0; q < 4; ++q) acc[d][q] = 0.f;
+                // consecutive MMAs go to different digit diagonals
 #pragma unroll
-                for (int sa = 0; sa < NDIG; ++sa) {
-                    uint32_t af[KS][4];
+                for (int ks = 0; ks < KS; ++ks) {
+                    if (ks < t0 || ks >= t1) continue;
 #pragma unroll
-                    for (int ks = 0; ks < KS; ++ks) {
+                    for (int sa = 0; sa < NDIG; ++sa) {
                         const uint4 f = Af[((mt * KS + ks) * NDIG + sa) * 32];
-                        af[ks][0] = f.x ^ cflip;
-                        af[ks][1] = f.y ^ cflip;
-                        af[ks][2] = f.z ^ cflip;
-                        af[ks][3] = f.w ^ cflip;
+                        const uint32_t af[4] = {f.x ^ cflip, f.y ^ cflip, f.z ^ cflip, f.w ^ cflip};
+#pragma unroll
+                        for (int u = 0; u + sa < NDIG; ++u) mma_f16(acc[sa + u], af, bq[u][ks]);
                     }
-#pragma unroll
-                    for (int u = 0; u + sa < NDIG; ++u)
-#pragma unroll
-                        for (int ks = 0; ks < KS; ++ks)
-                            if (ks >= t0 && ks < t1) mma_f16(acc[sa + u], af[ks], bq[u][ks]);
                 }
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
@@ -1045,11 +1060,12 @@ struct Walk {
         if (act) {
             e = unrank(sh, s, K, 1, lev, r);
             g = ap_geom(sh, e, K, s, lev, (int64_t)r);
-            for (int j = 0; j < N; ++j) {
-                double2 v = make_double2(0, 0);
-                if ((g.vmask >> j) & 1u) v = __ldcg(F + ap_read_addr(sh, g, K, j, s));
-                store_read(s, D, j, t, v, false);
-            }
+            gather(
+                N,
+                [&](int j) {
+                    return ((g.vmask >> j) & 1u) ? __ldcg(F + ap_read_addr(sh, g, K, j, s)) : make_double2(0, 0);
+                },
+                [&](int j, double2 v) { store_read(s, D, j, t, v, false); });
             if (HASB) FP = __ldcg(F + g.fp);
             for (int i = K; i < sh.M; ++i) fe *= s.fact[e(i)];
         } else {
@@ -1087,11 +1103,12 @@ struct Walk {
         if (act) {
             d = unrank(sh, s, 0, 1, lev, r);
             g = dp_geom(sh, d, s, lev, (int64_t)r);
-            for (int j = 0; j < N; ++j) {
-                double2 v = make_double2(0, 0);
-                if ((g.vmask >> j) & 1u) v = __ldcg(F + dp_read_addr(sh, g, j, s));
-                store_read(s, D, j, t, v, false);
-            }
+            gather(
+                N,
+                [&](int j) {
+                    return ((g.vmask >> j) & 1u) ? __ldcg(F + dp_read_addr(sh, g, j, s)) : make_double2(0, 0);
+                },
+                [&](int j, double2 v) { store_read(s, D, j, t, v, false); });
             FP = __ldcg(F + g.rdiag);
         } else {
             for (int j = 0; j < N; ++j) store_read(s, D, j, t, make_double2(0, 0), false);
@@ -1326,21 +1343,24 @@ struct Walk {
         if (act) {
             e = unrank(sh, s, K, 1, lev, r);
             g = ap_geom(sh, e, K, s, lev, (int64_t)r);
-            for (int j = 0; j < N; ++j) {
-                double2 v = make_double2(0, 0);
-                if ((g.vmask >> j) & 1u) v = __ldcg(F + ap_read_addr(sh, g, K, j, s));
-                fx = max(fx, max(fexp(v.x), fexp(v.y)));
-                store_read(s, D, j, t, v, true);
-            }
-            for (int i = 0; i < N; ++i) {
-                double2 v = make_double2(0, 0);
-                if ((g.nmask >> i) & 1u) {
+            gather(
+                N,
+                [&](int j) {
+                    return ((g.vmask >> j) & 1u) ? __ldcg(F + ap_read_addr(sh, g, K, j, s)) : make_double2(0, 0);
+                },
+                [&](int j, double2 v) {
+                    fx = max(fx, max(fexp(v.x), fexp(v.y)));
+                    store_read(s, D, j, t, v, true);
+                });
+            gather(
+                N,
+                [&](int i) {
+                    if (!((g.nmask >> i) & 1u)) return make_double2(0, 0);
                     int den;
                     const int64_t addr = ap_write_addr(sh, g, e, K, i, s, &den);
-                    v = rscale(__ldcg(Fb + addr), s.inv[den]);
-                }
-                store_adj(s, D, i, t, v);
-            }
+                    return rscale(__ldcg(Fb + addr), s.inv[den]);
+                },
+                [&](int i, double2 v) { store_adj(s, D, i, t, v); });
             if (HASB) FPv = __ldcg(F + g.fp);
         } else {
             for (int j = 0; j < N; ++j) {
@@ -1393,21 +1413,24 @@ struct Walk {
         if (act) {
             d = unrank(sh, s, 0, 1, lev, r);
             g = dp_geom(sh, d, s, lev, (int64_t)r);
-            for (int j = 0; j < N; ++j) {
-                double2 v = make_double2(0, 0);
-                if ((g.vmask >> j) & 1u) v = __ldcg(F + dp_read_addr(sh, g, j, s));
-                fx = max(fx, max(fexp(v.x), fexp(v.y)));
-                store_read(s, D, j, t, v, true);
-            }
-            for (int i = 0; i < N; ++i) {
-                double2 v = make_double2(0, 0);
-                if ((g.nmask >> i) & 1u) {
+            gather(
+                N,
+                [&](int j) {
+                    return ((g.vmask >> j) & 1u) ? __ldcg(F + dp_read_addr(sh, g, j, s)) : make_double2(0, 0);
+                },
+                [&](int j, double2 v) {
+                    fx = max(fx, max(fexp(v.x), fexp(v.y)));
+                    store_read(s, D, j, t, v, true);
+                });
+            gather(
+                N,
+                [&](int i) {
+                    if (!((g.nmask >> i) & 1u)) return make_double2(0, 0);
                     int den;
                     const int64_t addr = dp_write_addr(sh, g, d, i, s, &den);
-                    v = rscale(__ldcg(Fb + addr), s.inv[den]);
-                }
-                store_adj(s, D, i, t, v);
-            }
+                    return rscale(__ldcg(Fb + addr), s.inv[den]);
+                },
+                [&](int i, double2 v) { store_adj(s, D, i, t, v); });
             FPv = __ldcg(F + g.rdiag);
         } else {
             for (int j = 0; j < N; ++j) {
