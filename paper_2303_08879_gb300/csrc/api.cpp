@@ -111,6 +111,7 @@ int diag_layout(const DiagShape &sh, int batch, bool vjp, DiagLayout *lay)
     lay->lvl = o; o = align_up(o + B * (size_t)(sh.L + 2) * sizeof(unsigned long long));
     lay->As = o; o = align_up(o + B * D * D * c16);
     lay->bs = o; o = align_up(o + B * D * c16);
+    lay->dig = o; o = align_up(o + B * diag_digit_bytes(sh.M));
     lay->F = o; o = align_up(o + B * (size_t)sh.circ_alloc * c16);
     lay->grid_vjp = lay->slots_vjp = 0;
     if (vjp) {

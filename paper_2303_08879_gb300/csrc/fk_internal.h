@@ -30,9 +30,16 @@ int build_diag_shape(int M, const int *cutoffs, bool has_b, DiagShape *sh);
 // describes): every pattern with n_1 + ... + n_M < n_max, no per-mode cutoff.
 int build_global_shape(int M, int n_max, bool has_b, DiagShape *sh);
 
+// Per-circuit digit fragments of A for the tensor-core engine (M <= 8): the
+// 2D row exponent fields (padded to 256 bytes), then the fp16 digit fragments
+// of the real form of A (up to 2 x 2 tiles x 7 digits x 32 lanes x 16 bytes).
+constexpr size_t kDigFragBytes = 2 * 2 * 7 * 32 * 16;
+constexpr size_t kDigBytes = 256 + kDigFragBytes;
+inline size_t diag_digit_bytes(int M) { return M <= 8 ? kDigBytes : 0; }
+
 // Workspace layout of the all-detected walk for `batch` circuits.
 struct DiagLayout {
-    size_t ctl, lvl, As, bs, F, Fbar, scratch, partA, partb, total;
+    size_t ctl, lvl, As, bs, dig, F, Fbar, scratch, partA, partb, total;
     int grid_vjp, slots_vjp;
 };
 int diag_layout(const DiagShape &sh, int batch, bool vjp, DiagLayout *lay);

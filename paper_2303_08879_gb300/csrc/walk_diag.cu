@@ -46,6 +46,7 @@ struct DiagArgs {
     double2 *probs;
     Control *ctl;
     double2 *As, *bs, *F;
+    unsigned char *dig;           // tensor engine: per-circuit digit fragments of A (kDigBytes each)
     const double2 *gprobs;
     double2 *Fbar, *scratch, *partA, *partb;
     double2 *gA, *gb, *gc;
@@ -281,7 +282,11 @@ struct Walk {
         const int D = 2 * a.sh.M, DD = D * D;
         const double2 *As = a.As + (size_t)circ * DD;
         if (TC && s.Af != nullptr) {
-            load_circuit_digits(s, As, D);
+            // digit fragments prepared once per launch by build_digits
+            const unsigned char *src = a.dig + (size_t)circ * kDigBytes;
+            const uint4 *gf = (const uint4 *)(src + 256);
+            for (int e = threadIdx.x; e < KS * KS * NDIG * 32; e += blockDim.x) s.Af[e] = __ldcg(gf + e);
+            for (int r = threadIdx.x; r < 2 * D; r += blockDim.x) s.fA[r] = __ldcg((const int *)src + r);
             for (int e = threadIdx.x; e < D; e += blockDim.x) s.bs[e] = a.bs[(size_t)circ * D + e];
             __syncthreads();
             s.loaded_circ = circ;
@@ -425,7 +430,8 @@ struct Walk {
     {
         const long long bits = __double_as_longlong(v);
         const int f = (int)((bits >> 52) & 0x7ff);
-        if (f != 0 && f + k >= 1 && f + k <= 2046) return __longlong_as_double(bits + ((long long)k << 52));
+        if (f == 0) return v;   // zero
+        if (f + k >= 1 && f + k <= 2046) return __longlong_as_double(bits + ((long long)k << 52));
         k = max(k, -2044);   // |v| < 2^64: anything smaller is zero after rounding anyway
         const int k1 = k / 2;
         return v * pow2(k1) * pow2(k - k1);
@@ -472,44 +478,63 @@ struct Walk {
         }
     }
 
-    // Digit fragments of the real form R of A_s (row 2i: Re A_ij at column 2j,
-    // -Im A_ij at 2j+1; row 2i+1: Im A_ij, Re A_ij), padded with zeros to
-    // 16 KS x 16 KS, into shared memory in the register order of the A operand
-    // of mma m16n8k16: tile (mt, ks), digit s, lane (grp, tig) holds rows
-    // 16 mt + grp (+8) and columns 16 ks + 2 tig (+1, +8, +9).  Row r is fixed
-    // point relative to the largest exponent field of its row of A.
-    static __device__ void load_circuit_digits(Smem &s, const double2 *As, int D)
+    // Entry (w, l) of A_s = (A + A^T)/2 restricted to the kept modes, from the
+    // caller's A (the same arithmetic as the prologue's copy).
+    static __device__ __forceinline__ double2 as_entry(const DiagArgs &a, int c, int w, int l)
     {
-        const int D2 = 2 * D;
+        const DiagShape &sh = a.sh;
+        const int Do = sh.D_orig;
+        const int ow = 2 * sh.mode_map[w / 2] + (w & 1), ol = 2 * sh.mode_map[l / 2] + (l & 1);
+        const double2 x = a.A[(size_t)c * Do * Do + (size_t)ow * Do + ol];
+        const double2 y = a.A[(size_t)c * Do * Do + (size_t)ol * Do + ow];
+        return make_double2(0.5 * (x.x + y.x), 0.5 * (x.y + y.y));
+    }
+
+    // Digit fragments of the real form R of every circuit's A_s (row 2i: Re
+    // A_ij at column 2j, -Im A_ij at 2j+1; row 2i+1: Im A_ij, Re A_ij), padded
+    // with zeros to 16 KS x 16 KS, in the register order of the A operand of
+    // mma m16n8k16: tile (mt, ks), digit s, lane (grp, tig) holds rows
+    // 16 mt + grp (+8) and columns 16 ks + 2 tig (+1, +8, +9).  Row r is fixed
+    // point relative to the largest exponent field of its row of A.  One block
+    // per circuit writes them to the workspace (row exponent fields first).
+    static __device__ void build_digits(const DiagArgs &a, Smem &s)
+    {
+        const int D = 2 * a.sh.M, D2 = 2 * D;
         constexpr int P = 16 * (KS > 0 ? KS : 1);
-        for (int r = threadIdx.x; r < D2; r += blockDim.x) s.fA[r] = 0;
-        __syncthreads();
-        for (int e = threadIdx.x; e < D * D; e += blockDim.x) {
-            const double2 v = As[e];
-            const int f = max(fexp(v.x), fexp(v.y));
-            if (f != 0) atomicMax(&s.fA[2 * (e / D)], f);
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < D; i += blockDim.x) s.fA[2 * i + 1] = s.fA[2 * i];
-        __syncthreads();
-        uint32_t *Af = (uint32_t *)s.Af;
-        for (int e = threadIdx.x; e < P * P / 2; e += blockDim.x) {
-            const int r = e / (P / 2), c = 2 * (e % (P / 2));
-            uint32_t wd[NDIG];
-            if (r < D2 && c < D2) {
-                const double2 v = As[(size_t)(r >> 1) * D + (c >> 1)];
-                const double x0 = (r & 1) ? v.y : v.x, x1 = (r & 1) ? v.x : -v.y;
-                digit_words(to_fixed(x0, s.fA[r]), to_fixed(x1, s.fA[r]), wd);
-            } else {
-#pragma unroll
-                for (int sl = 0; sl < NDIG; ++sl) wd[sl] = 0u;
+        for (int circ = blockIdx.x; circ < a.B; circ += gridDim.x) {
+            int *gA = (int *)(a.dig + (size_t)circ * kDigBytes);
+            uint32_t *Af = (uint32_t *)(a.dig + (size_t)circ * kDigBytes + 256);
+            __syncthreads();
+            for (int r = threadIdx.x; r < D2; r += blockDim.x) s.fA[r] = 0;
+            __syncthreads();
+            for (int e = threadIdx.x; e < D * D; e += blockDim.x) {
+                const double2 v = as_entry(a, circ, e / D, e % D);
+                const int f = max(fexp(v.x), fexp(v.y));
+                if (f != 0) atomicMax(&s.fA[2 * (e / D)], f);
             }
-            const int rr = r & 15, cc = c & 15;
-            const int lane = (rr & 7) * 4 + ((cc & 7) >> 1), k = (rr >> 3) | ((cc >> 3) << 1);
-            const int tile = (r >> 4) * KS + (c >> 4);
+            __syncthreads();
+            for (int i = threadIdx.x; i < D; i += blockDim.x) s.fA[2 * i + 1] = s.fA[2 * i];
+            __syncthreads();
+            for (int r = threadIdx.x; r < D2; r += blockDim.x) gA[r] = s.fA[r];
+            for (int e = threadIdx.x; e < P * P / 2; e += blockDim.x) {
+                const int r = e / (P / 2), c = 2 * (e % (P / 2));
+                uint32_t wd[NDIG];
+                if (r < D2 && c < D2) {
+                    const double2 v = as_entry(a, circ, r >> 1, c >> 1);
+                    const double x0 = (r & 1) ? v.y : v.x, x1 = (r & 1) ? v.x : -v.y;
+                    digit_words(to_fixed(x0, s.fA[r]), to_fixed(x1, s.fA[r]), wd);
+                } else {
 #pragma unroll
-            for (int sl = 0; sl < NDIG; ++sl) Af[(((tile * NDIG + sl) * 32 + lane) << 2) + k] = wd[sl];
+                    for (int sl = 0; sl < NDIG; ++sl) wd[sl] = 0u;
+                }
+                const int rr = r & 15, cc = c & 15;
+                const int lane = (rr & 7) * 4 + ((cc & 7) >> 1), k = (rr >> 3) | ((cc >> 3) << 1);
+                const int tile = (r >> 4) * KS + (c >> 4);
+#pragma unroll
+                for (int sl = 0; sl < NDIG; ++sl) Af[(((tile * NDIG + sl) * 32 + lane) << 2) + k] = wd[sl];
+            }
         }
+        __syncthreads();
     }
 
     static __device__ __forceinline__ void mma_f16(float *c, const uint32_t *a, const uint32_t *b)
@@ -1010,7 +1035,7 @@ struct Walk {
 
     // ---------------------------------------------------------------- prologue
     // A_s = (A + A^T)/2 restricted to kept modes, b restricted, vacuum seeds.
-    static __device__ void prologue(const DiagArgs &a, bool seed)
+    static __device__ void prologue(const DiagArgs &a, Smem &s, bool seed)
     {
         const DiagShape &sh = a.sh;
         const int D = 2 * sh.M, Do = sh.D_orig;
@@ -1033,6 +1058,7 @@ struct Walk {
             if (v.x != 0.0 || v.y != 0.0) nz = 1;
         }
         if (__syncthreads_or(nz) && threadIdx.x == 0) atomicOr(&a.ctl->has_b, 1);
+        if constexpr (TC) build_digits(a, s);
         if (seed) {
             for (int64_t c = gtid; c < a.B; c += gsz) {
                 const double2 v = a.c[c];
@@ -1495,7 +1521,7 @@ struct Walk {
         const DiagShape &sh = a.sh;
         Smem s = carve_smem(sh, false);
         build_tables(sh, s);
-        prologue(a, true);
+        prologue(a, s, true);
         if (!grid_sync(a.ctl, gridDim.x, a.timeout_ns)) return;
         const int hb = *(volatile int *)&a.ctl->has_b;
         if (hb && !sh.has_b) {
@@ -1541,7 +1567,7 @@ struct Walk {
         const DiagShape &sh = a.sh;
         Smem s = carve_smem(sh, true);
         build_tables(sh, s);
-        prologue(a, false);
+        prologue(a, s, false);
         if (!grid_sync(a.ctl, gridDim.x, a.timeout_ns)) return;
         const int hb = *(volatile int *)&a.ctl->has_b;
         if (hb && !sh.has_b) {
@@ -1824,6 +1850,7 @@ static DiagArgs make_args(const DiagShape &sh, int batch, unsigned flags, const 
     a.ctl = (Control *)(w + lay.ctl);
     a.As = (double2 *)(w + lay.As);
     a.bs = (double2 *)(w + lay.bs);
+    a.dig = (unsigned char *)(w + lay.dig);
     a.F = (double2 *)(w + lay.F);
     a.lvl = (unsigned long long *)(w + lay.lvl);
     a.timeout_ns = kBarrierTimeoutNs;
