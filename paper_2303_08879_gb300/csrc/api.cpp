@@ -112,6 +112,7 @@ int diag_layout(const DiagShape &sh, int batch, bool vjp, DiagLayout *lay)
     lay->As = o; o = align_up(o + B * D * D * c16);
     lay->bs = o; o = align_up(o + B * D * c16);
     lay->dig = o; o = align_up(o + B * diag_digit_bytes(sh.M));
+    lay->geo = o; o = align_up(o + diag_geo_bytes(sh));
     lay->F = o; o = align_up(o + B * (size_t)sh.circ_alloc * c16);
     lay->grid_vjp = lay->slots_vjp = 0;
     if (vjp) {

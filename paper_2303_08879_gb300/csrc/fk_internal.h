@@ -37,9 +37,19 @@ constexpr size_t kDigFragBytes = 2 * 2 * 7 * 32 * 16;
 constexpr size_t kDigBytes = 256 + kDigFragBytes;
 inline size_t diag_digit_bytes(int M) { return M <= 8 ? kDigBytes : 0; }
 
+// Geometry of every AP(K) pivot (M <= 8), shared by all circuits of a launch:
+// 12 ints per pivot, indexed like the VJP scratch (off_ap[K] + level offset
+// + rank): the digits (two words), the ranks of e - 1_m for m = K+1..K+7,
+// the T2 read offset and the DIAG write offset relative to their levels.
+constexpr int kGeoInts = 12;
+inline size_t diag_geo_bytes(const DiagShape &sh)
+{
+    return sh.M >= 1 && sh.M <= 8 ? (size_t)sh.n_ap * kGeoInts * sizeof(int) : 0;
+}
+
 // Workspace layout of the all-detected walk for `batch` circuits.
 struct DiagLayout {
-    size_t ctl, lvl, As, bs, dig, F, Fbar, scratch, partA, partb, total;
+    size_t ctl, lvl, As, bs, dig, geo, F, Fbar, scratch, partA, partb, total;
     int grid_vjp, slots_vjp;
 };
 int diag_layout(const DiagShape &sh, int batch, bool vjp, DiagLayout *lay);

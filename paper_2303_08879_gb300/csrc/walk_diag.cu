@@ -47,6 +47,7 @@ struct DiagArgs {
     Control *ctl;
     double2 *As, *bs, *F;
     unsigned char *dig;           // tensor engine: per-circuit digit fragments of A (kDigBytes each)
+    int *geo;                     // AP pivot geometry shared by the circuits (M <= 8), or null
     const double2 *gprobs;
     double2 *Fbar, *scratch, *partA, *partb;
     double2 *gA, *gb, *gc;
@@ -921,6 +922,74 @@ struct Walk {
 
     // ------------------------------------------------------- per-pivot geometry
 
+    // The circuit-independent part of an AP(K) pivot's geometry (pivot e of
+    // level `lev`, rank r in family K): the ranks of e - 1_m (m > K) within
+    // their level, the offset of T2(K)[e - 1_K] within level lev - 1 of family
+    // K and of DIAG[e + 1_K] within level lev + 1 of the DIAG family.
+    struct ApRel {
+        int idx[7];       // idx[m - K - 1] for m = K+1..M-1 (M <= 8)
+        int rt2, wdiag;
+    };
+
+    static __device__ __forceinline__ ApRel ap_rel(const DiagShape &sh, const Dig &e, int K, const Smem &s,
+                                                   int lev, int64_t r)
+    {
+        ApRel q;
+        const int eK = e(K);
+        int t = lev;
+        int64_t cum = Pf(s, K, t, eK);
+        q.rt2 = eK >= 1 ? (int)(Pf(s, K, t - 1, eK - 1) + (r - cum)) : 0;
+        q.wdiag = (int)(Pf(s, K, lev + 1, eK + 1) + (r - cum));
+        int64_t pre = Pf(s, K, t - 1, eK);
+        t -= eK;
+#pragma unroll
+        for (int i = 0; i < 7; ++i) {
+            const int m = K + 1 + i;
+            q.idx[i] = 0;
+            if (m >= sh.M) continue;
+            const int em = e(m);
+            cum += Pf(s, m, t, em);
+            q.idx[i] = em >= 1 ? (int)(pre + Pf(s, m, t - 1, em - 1) + (r - cum)) : 0;
+            pre += Pf(s, m, t - 1, em);
+            t -= em;
+        }
+        return q;
+    }
+
+    // AP(K) pivot e of level `lev` with rank r in family K (M <= 8):
+    // addresses of its reads and writes from its relative geometry; the ranks
+    // of e - 1_m (m > K) go to s.idx[m][thread].  ap_geom below is the same
+    // computation for any M.
+    static __device__ __forceinline__ ApGeom ap_assemble(const DiagShape &sh, const Dig &e, int K, Smem &s,
+                                                         int lev, int64_t r, const ApRel &q)
+    {
+        ApGeom g;
+        const int eK = e(K);
+        g.r = r;
+        g.rd = cum_full(s, lev) + r;
+        g.lk0 = s.cum0[K];
+        g.lkm = s.cum1[K];
+        g.wt2 = sh.lm_t2[K] + g.lk0 + r;
+        g.fp = sh.has_b ? sh.lm_t1[K] + 2 * (s.cum0[0] + r) + 1 : 0;
+        int64_t pout = sh.stride[K];
+        for (int i = K; i < sh.M; ++i) pout += (int64_t)e(i) * sh.stride[i];
+        g.pout = pout;
+        g.rt2 = eK >= 1 ? sh.lm_t2[K] + g.lkm + q.rt2 : 0;
+        g.wdiag = cum_full(s, lev + 1) + q.wdiag;
+        g.vmask = 1u | (eK >= 1 ? 2u : 0u);
+        g.nmask = 2u | (eK <= sh.C[K] - 3 ? 1u : 0u);
+#pragma unroll
+        for (int i = 0; i < 7; ++i) {
+            const int m = K + 1 + i;
+            if (m >= sh.M) continue;
+            const int em = e(m);
+            s.idx[m * TPB + threadIdx.x] = q.idx[i];
+            if (em >= 1) g.vmask |= 3u << (2 * (m - K));
+            if (em <= sh.C[m] - 2) g.nmask |= 3u << (2 * (m - K));
+        }
+        return g;
+    }
+
     // AP(K) pivot e of level `lev` with rank r in family K: addresses of its
     // reads and writes; the ranks of e - 1_m (m > K) go to s.idx[m][thread].
     static __device__ __forceinline__ ApGeom ap_geom(const DiagShape &sh, const Dig &e, int K, Smem &s,
@@ -955,6 +1024,53 @@ struct Walk {
             if (em <= sh.C[m] - 2) g.nmask |= 3u << (2 * (m - K));
         }
         return g;
+    }
+
+    // Pivot e and its geometry: from the launch's shared table when there is
+    // one (same values as computing them), else computed.
+    static __device__ __forceinline__ ApGeom ap_pivot(const DiagArgs &a, Smem &s, int K, int lev, unsigned r,
+                                                      Dig &e)
+    {
+        const DiagShape &sh = a.sh;
+        if (a.geo == nullptr) {
+            e = unrank(sh, s, K, 1, lev, r);
+            return ap_geom(sh, e, K, s, lev, (int64_t)r);
+        }
+        const int4 *rec = (const int4 *)(a.geo + (size_t)(sh.off_ap[K] + s.cum0[K] + r) * kGeoInts);
+        const int4 w0 = __ldcg(rec), w1 = __ldcg(rec + 1), w2 = __ldcg(rec + 2);
+        e.lo = (uint64_t)(unsigned)w0.x | ((uint64_t)(unsigned)w0.y << 32);
+        e.hi = 0;
+        ApRel q;
+        q.idx[0] = w0.z; q.idx[1] = w0.w;
+        q.idx[2] = w1.x; q.idx[3] = w1.y; q.idx[4] = w1.z; q.idx[5] = w1.w;
+        q.idx[6] = w2.x;
+        q.rt2 = w2.y;
+        q.wdiag = w2.z;
+        return ap_assemble(sh, e, K, s, lev, (int64_t)r, q);
+    }
+
+    // The table: every AP pivot of the pivot levels (one grid-stride pass per
+    // (K, level); every thread keeps the level offsets).
+    static __device__ void build_geometry(const DiagArgs &a, const Smem &s)
+    {
+        const DiagShape &sh = a.sh;
+        const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+        for (int K = 0; K < sh.M; ++K) {
+            int64_t off = sh.off_ap[K];
+            for (int lev = 0; lev < sh.L; ++lev) {
+                const int64_t cnt = Pf(s, K, lev, sh.C[K] - 1);
+                for (int64_t r = gtid; r < cnt; r += gsz) {
+                    const Dig e = unrank(sh, s, K, 1, lev, (unsigned)r);
+                    const ApRel q = ap_rel(sh, e, K, s, lev, r);
+                    int4 *rec = (int4 *)(a.geo + (size_t)(off + r) * kGeoInts);
+                    rec[0] = make_int4((int)(unsigned)e.lo, (int)(unsigned)(e.lo >> 32), q.idx[0], q.idx[1]);
+                    rec[1] = make_int4(q.idx[2], q.idx[3], q.idx[4], q.idx[5]);
+                    rec[2] = make_int4(q.idx[6], q.rt2, q.wdiag, 0);
+                }
+                off += cnt;
+            }
+        }
     }
 
     // P1010/P1001(K,m) pair base (interleaved: P1010 even, P1001 odd).
@@ -1059,6 +1175,7 @@ struct Walk {
         }
         if (__syncthreads_or(nz) && threadIdx.x == 0) atomicOr(&a.ctl->has_b, 1);
         if constexpr (TC) build_digits(a, s);
+        if (a.geo != nullptr) build_geometry(a, s);
         if (seed) {
             for (int64_t c = gtid; c < a.B; c += gsz) {
                 const double2 v = a.c[c];
@@ -1084,8 +1201,7 @@ struct Walk {
         double2 FP = make_double2(0, 0);
         double fe = 1.0, psum = 0.0;
         if (act) {
-            e = unrank(sh, s, K, 1, lev, r);
-            g = ap_geom(sh, e, K, s, lev, (int64_t)r);
+            g = ap_pivot(a, s, K, lev, r, e);
             gather(
                 N,
                 [&](int j) {
@@ -1212,8 +1328,7 @@ struct Walk {
         Dig e;
         ApGeom g{};
         if (act) {
-            e = unrank(sh, s, K, 1, lev, r);
-            g = ap_geom(sh, e, K, s, lev, (int64_t)r);
+            g = ap_pivot(a, s, K, lev, r, e);
             for (int j = 0; j < N; ++j) {
                 double2 v = make_double2(0, 0);
                 if ((g.vmask >> j) & 1u) v = __ldcg(F + ap_read_addr(sh, g, K, j, s));
@@ -1367,8 +1482,7 @@ struct Walk {
         int fx = 0;
         double2 FPv = make_double2(0, 0);
         if (act) {
-            e = unrank(sh, s, K, 1, lev, r);
-            g = ap_geom(sh, e, K, s, lev, (int64_t)r);
+            g = ap_pivot(a, s, K, lev, r, e);
             gather(
                 N,
                 [&](int j) {
@@ -1851,6 +1965,7 @@ static DiagArgs make_args(const DiagShape &sh, int batch, unsigned flags, const 
     a.As = (double2 *)(w + lay.As);
     a.bs = (double2 *)(w + lay.bs);
     a.dig = (unsigned char *)(w + lay.dig);
+    a.geo = lay.geo != lay.F ? (int *)(w + lay.geo) : nullptr;
     a.F = (double2 *)(w + lay.F);
     a.lvl = (unsigned long long *)(w + lay.lvl);
     a.timeout_ns = kBarrierTimeoutNs;
