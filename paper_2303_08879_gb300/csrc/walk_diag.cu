@@ -786,7 +786,11 @@ struct Walk {
                     const long long Y = combine_digits_wide(a7, 0);
                     const double v = scale2(__ll2double_rn(Y), g - 1074);
                     double *dst = pA + 2 * ((size_t)(row0 + w) * D + row0 + j) + (n & 1);
-                    *dst += v;
+                    // reduction without return: the warp does not wait for the
+                    // old value.  The slot has one warp as its only writer and
+                    // its updates are ordered by the warp's barriers between
+                    // tiles, so the sum order is fixed.
+                    atomicAdd(dst, v);
                 }
             }
         }
@@ -1444,7 +1448,8 @@ struct Walk {
             for (int tt = 0; tt < 32; ++tt)
                 acc = cfma_conj(s.FP[warp * 32 + tt], make_double2(wy[(2 * w) * WBS + tt], wy[(2 * w + 1) * WBS + tt]),
                                 acc);
-            pb[row0 + w] = cadd(pb[row0 + w], acc);
+            atomicAdd(&pb[row0 + w].x, acc.x);   // one writer, ordered as above
+            atomicAdd(&pb[row0 + w].y, acc.y);
         }
     }
 
