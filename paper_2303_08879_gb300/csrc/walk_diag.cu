@@ -66,6 +66,7 @@ struct Smem {
                       // i..M-1 (extents C) with digit sum <= t
     int64_t *cum0;    // [M] offset of the current phase's level in family K
     int64_t *cum1;    // [M] offset of the level below
+    int64_t *cum2;    // [M] offset of the level above
     int Wn;           // row length
     double *inv;      // 1/v
     double *fact;     // v!
@@ -134,7 +135,8 @@ struct Walk {
         size_t n = 0;
         n += (size_t)(M + 1) * (L + 2) * sizeof(unsigned);
         n = (n + 15) & ~(size_t)15;
-        n += 2 * (size_t)M * sizeof(int64_t);
+        n += 3 * (size_t)M * sizeof(int64_t);
+        n = (n + 15) & ~(size_t)15;
         n += 2 * TABN * sizeof(double);
         if (TC) {
             const int D2 = 2 * D;
@@ -167,6 +169,8 @@ struct Walk {
         p = (unsigned char *)(((uintptr_t)p + 15) & ~(uintptr_t)15);
         s.cum0 = (int64_t *)p; p += (size_t)M * sizeof(int64_t);
         s.cum1 = (int64_t *)p; p += (size_t)M * sizeof(int64_t);
+        s.cum2 = (int64_t *)p; p += (size_t)M * sizeof(int64_t);
+        p = (unsigned char *)(((uintptr_t)p + 15) & ~(uintptr_t)15);   // double2 tables follow
         s.inv = (double *)p; p += TABN * sizeof(double);
         s.fact = (double *)p; p += TABN * sizeof(double);
         s.A3 = s.R3 = s.Y3 = nullptr;
@@ -236,8 +240,8 @@ struct Walk {
     }
 
     // Offset of level `lev` in family K: sum over the levels below of the
-    // family's counts Pf(K, l, C_K - 1).  Thread 0 fills s.cum0 / s.cum1 for
-    // the level of each phase and the one below.
+    // family's counts Pf(K, l, C_K - 1).  Thread 0 fills s.cum0 / s.cum1 /
+    // s.cum2 for the level of each phase, the one below and the one above.
     static __device__ void phase_offsets(const DiagShape &sh, Smem &s, int lev)
     {
         for (int K = 0; K < sh.M; ++K) {
@@ -249,6 +253,7 @@ struct Walk {
             }
             s.cum0[K] = c0;
             s.cum1[K] = c1;
+            s.cum2[K] = c0 + Pf(s, K, lev, sh.C[K] - 1);
         }
     }
 
@@ -1318,6 +1323,46 @@ struct Walk {
         __syncthreads();
     }
 
+    // Adjoint of the DIAG value x = e + 1_K (level lev + 1) written by the
+    // AP(K) pivot e of level lev: the upstream seed of p_x (times the
+    // factorials f_x = prod_i x_i!), the read adjoints that the AP(k) pivots
+    // with base x (k <= K, the first nonzero mode of x) left in scratch when
+    // level lev + 1 ran, and, with b != 0, what the DP pivots of level lev + 1
+    // added in Fbar.  x has this pivot as its only writer, so its adjoint is
+    // complete here and is formed by its one reader instead of in a pass over
+    // the DIAG values.
+    template <bool HASB>
+    static __device__ __forceinline__ double2 diag_adjoint(const DiagArgs &a, const Smem &s, int circ, int K,
+                                                           int lev, const ApGeom &g, const Dig &e)
+    {
+        const DiagShape &sh = a.sh;
+        double fe = 1.0;
+        for (int i = K; i < sh.M; ++i) fe *= s.fact[e(i)];
+        const int xK = e(K) + 1;
+        double2 acc = rscale(a.gprobs[(size_t)circ * sh.n_diag + (sh.global ? g.wdiag : g.pout)],
+                             fe * (double)xK);
+        if (pivots_run(a, circ, lev + 1)) {
+            const double2 *sc = a.scratch + (size_t)circ * sh.n_ap;
+            const int64_t rx = g.wdiag - cum_full(s, lev + 1);
+            for (int k = 0; k <= K; ++k)
+                if (k < K || xK <= sh.C[K] - 2) acc = cadd(acc, __ldcg(sc + sh.off_ap[k] + s.cum2[k] + rx));
+        }
+        if (HASB) acc = cadd(acc, __ldcg(a.Fbar + (size_t)circ * sh.circ_alloc + g.wdiag));
+        return acc;
+    }
+
+    // Adjoint of the vacuum (dL/dc): its seed, the read adjoints of the AP(k)
+    // pivots of level 0 and, with b != 0, the DP contribution in Fbar.
+    static __device__ double2 vacuum_adjoint(const DiagArgs &a, int circ, bool hb)
+    {
+        const DiagShape &sh = a.sh;
+        double2 acc = a.gprobs[(size_t)circ * sh.n_diag];
+        if (pivots_run(a, circ, 0))
+            for (int k = 0; k < sh.M; ++k) acc = cadd(acc, __ldcg(a.scratch + (size_t)circ * sh.n_ap + sh.off_ap[k]));
+        if (hb) acc = cadd(acc, __ldcg(a.Fbar + (size_t)circ * sh.circ_alloc));
+        return acc;
+    }
+
     // --------------------------------------------------------- reverse AP
     template <bool HASB>
     static __device__ void ap_reverse_tile(const DiagArgs &a, Smem &s, const TileId &tl, int K, int lev)
@@ -1343,7 +1388,8 @@ struct Walk {
                 if ((g.nmask >> i) & 1u) {
                     int den;
                     const int64_t addr = ap_write_addr(sh, g, e, K, i, s, &den);
-                    v = rscale(__ldcg(Fb + addr), s.inv[den]);
+                    const double2 y = i == 1 ? diag_adjoint<HASB>(a, s, tl.circ, K, lev, g, e) : __ldcg(Fb + addr);
+                    v = rscale(y, s.inv[den]);
                 }
                 store_adj(s, D, i, t, v);
             }
@@ -1503,7 +1549,8 @@ struct Walk {
                     if (!((g.nmask >> i) & 1u)) return make_double2(0, 0);
                     int den;
                     const int64_t addr = ap_write_addr(sh, g, e, K, i, s, &den);
-                    return rscale(__ldcg(Fb + addr), s.inv[den]);
+                    const double2 y = i == 1 ? diag_adjoint<HASB>(a, s, tl.circ, K, lev, g, e) : __ldcg(Fb + addr);
+                    return rscale(y, s.inv[den]);
                 },
                 [&](int i, double2 v) { store_adj(s, D, i, t, v); });
             if (HASB) FPv = __ldcg(F + g.fp);
@@ -1605,35 +1652,6 @@ struct Walk {
         __syncwarp();
     }
 
-    // ------------------------------------------------------ reverse DIAGSUM
-    // Adjoint of every diagonal amplitude of level `lev`: upstream seed plus the
-    // read contributions the AP(K) pivots with base d left in scratch.
-    static __device__ void diag_reverse_tile(const DiagArgs &a, Smem &s, const TileId &tl, int lev)
-    {
-        const DiagShape &sh = a.sh;
-        const unsigned r = tl.rank0 + threadIdx.x;
-        if (r >= tl.count) return;
-        const Dig d = unrank(sh, s, 0, 0, lev, r);
-        const int64_t idx = diag_index(sh, d, 0);   // caller's row-major index
-        double f = 1.0;
-        int fnz = sh.M;
-        for (int i = 0; i < sh.M; ++i) {
-            const int v = d(i);
-            f *= s.fact[v];
-            if (v > 0 && fnz == sh.M) fnz = i;
-        }
-        // upstream gradient: caller's row-major index, or level-major (global cutoff)
-        double2 acc = rscale(a.gprobs[(size_t)tl.circ * sh.n_diag + (sh.global ? cum_full(s, lev) + r : idx)], f);
-        const double2 *sc = a.scratch + (size_t)tl.circ * sh.n_ap;
-        // scratch exists where the AP pivots of this level ran: levels < L (with a
-        // global cutoff a DIAG value of level L can have digits below C_K - 1
-        // that no pivot reads) and, with an early stop, below the stop
-        const int kmax = pivots_run(a, tl.circ, lev) ? (fnz < sh.M ? fnz : sh.M - 1) : -1;
-        for (int K = 0; K <= kmax; ++K)
-            if (d(K) <= sh.C[K] - 2) acc = cadd(acc, __ldcg(sc + sh.off_ap[K] + s.cum0[K] + r));
-        a.Fbar[(size_t)tl.circ * sh.circ_alloc + cum_full(s, lev) + r] = acc;
-    }
-
     // ------------------------------------------------------------------ kernels
     static __device__ void forward(const DiagArgs &a)
     {
@@ -1709,16 +1727,6 @@ struct Walk {
                 }
                 if (!grid_sync(a.ctl, gridDim.x, a.timeout_ns)) return;
             }
-            {
-                const int nt = phase_tiles(a, s, 2, lev);
-                for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
-                    const TileId tl = decode_tile(a, s, 2, lev, tile);
-                    // the DIAG values with lev photons exist once the pivots of level lev-1 ran
-                    if (lev > 0 && !pivots_run(a, tl.circ, lev - 1)) continue;
-                    diag_reverse_tile(a, s, tl, lev);
-                }
-                if (!grid_sync(a.ctl, gridDim.x, a.timeout_ns)) return;
-            }
             if (hb && lev < sh.L) {
                 const int nt = phase_tiles(a, s, 1, lev);
                 for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
@@ -1757,7 +1765,7 @@ struct Walk {
             const int ow = 2 * sh.mode_map[w / 2] + (w & 1);
             a.gb[(size_t)c * Do + ow] = x;
         }
-        for (int64_t c = gtid; c < a.B; c += gsz) a.gc[c] = a.Fbar[(size_t)c * sh.circ_alloc];
+        for (int64_t c = gtid; c < a.B; c += gsz) a.gc[c] = vacuum_adjoint(a, (int)c, hb != 0);
     }
 
     // Vacuum-only problem (every cutoff is 1): p = c.
