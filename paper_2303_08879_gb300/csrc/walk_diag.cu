@@ -1374,6 +1374,7 @@ struct Walk {
         double2 *Fb = a.Fbar + (size_t)tl.circ * sh.circ_alloc;
         const unsigned r = tl.rank0 + t;
         const bool act = r < tl.count;
+        const bool up = pivots_run(a, tl.circ, lev + 1);   // level lev + 1 ran in reverse
         Dig e;
         ApGeom g{};
         if (act) {
@@ -1388,7 +1389,10 @@ struct Walk {
                 if ((g.nmask >> i) & 1u) {
                     int den;
                     const int64_t addr = ap_write_addr(sh, g, e, K, i, s, &den);
-                    const double2 y = i == 1 ? diag_adjoint<HASB>(a, s, tl.circ, K, lev, g, e) : __ldcg(Fb + addr);
+                    // T2 and P values of a level whose pivots did not run have no
+                    // reader: their adjoint is zero (Fbar is not cleared for b = 0)
+                    const double2 y = i == 1 ? diag_adjoint<HASB>(a, s, tl.circ, K, lev, g, e)
+                                      : up ? __ldcg(Fb + addr) : make_double2(0, 0);
                     v = rscale(y, s.inv[den]);
                 }
                 store_adj(s, D, i, t, v);
@@ -1528,6 +1532,7 @@ struct Walk {
         double2 *Fb = a.Fbar + (size_t)tl.circ * sh.circ_alloc;
         const unsigned r = tl.rank0 + t;
         const bool act = r < tl.count;
+        const bool up = pivots_run(a, tl.circ, lev + 1);   // level lev + 1 ran in reverse
         Dig e;
         ApGeom g{};
         int fx = 0;
@@ -1549,7 +1554,10 @@ struct Walk {
                     if (!((g.nmask >> i) & 1u)) return make_double2(0, 0);
                     int den;
                     const int64_t addr = ap_write_addr(sh, g, e, K, i, s, &den);
-                    const double2 y = i == 1 ? diag_adjoint<HASB>(a, s, tl.circ, K, lev, g, e) : __ldcg(Fb + addr);
+                    // T2 and P values of a level whose pivots did not run have no
+                    // reader: their adjoint is zero (Fbar is not cleared for b = 0)
+                    const double2 y = i == 1 ? diag_adjoint<HASB>(a, s, tl.circ, K, lev, g, e)
+                                      : up ? __ldcg(Fb + addr) : make_double2(0, 0);
                     return rscale(y, s.inv[den]);
                 },
                 [&](int i, double2 v) { store_adj(s, D, i, t, v); });
@@ -2037,7 +2045,9 @@ int launch_diag_vjp(const DiagShape &sh, int batch, unsigned flags, const void *
     }
     char *w = (char *)ws;
     if (cudaMemsetAsync(w + lay.ctl, 0, sizeof(Control), st) != cudaSuccess) return FK_ECUDA;
-    if (cudaMemsetAsync(w + lay.Fbar, 0, lay.scratch - lay.Fbar, st) != cudaSuccess) return FK_ECUDA;
+    // With b = 0 every adjoint the walk reads is stored before it is read (or
+    // read as zero), so Fbar needs clearing only for the b != 0 sums.
+    if (sh.has_b && cudaMemsetAsync(w + lay.Fbar, 0, lay.scratch - lay.Fbar, st) != cudaSuccess) return FK_ECUDA;
     if (cudaMemsetAsync(w + lay.partA, 0, lay.total - lay.partA, st) != cudaSuccess) return FK_ECUDA;
     DiagArgs a = make_args(sh, batch, flags, A, b, c, ws, lay);
     a.gprobs = (const double2 *)gprobs;
