@@ -49,7 +49,7 @@ inline size_t diag_geo_bytes(const DiagShape &sh)
 
 // Workspace layout of the all-detected walk for `batch` circuits.
 struct DiagLayout {
-    size_t ctl, lvl, As, bs, dig, geo, F, Fbar, scratch, partA, partb, total;
+    size_t ctl, lvl, ctr, As, bs, dig, geo, F, Fbar, scratch, partA, partb, total;
     int grid_vjp, slots_vjp;
 };
 int diag_layout(const DiagShape &sh, int batch, bool vjp, DiagLayout *lay);

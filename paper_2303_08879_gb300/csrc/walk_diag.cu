@@ -48,6 +48,7 @@ struct DiagArgs {
     double2 *As, *bs, *F;
     unsigned char *dig;           // tensor engine: per-circuit digit fragments of A (kDigBytes each)
     int *geo;                     // AP pivot geometry shared by the circuits (M <= 8), or null
+    int *ctr;                     // [2 (L + 1)] next-tile counters: DP phase of level l at 2l, AP at 2l + 1
     const double2 *gprobs;
     double2 *Fbar, *scratch, *partA, *partb;
     double2 *gA, *gb, *gc;
@@ -881,6 +882,26 @@ struct Walk {
         __syncthreads();
     }
 
+    // fn(tile) over the tiles [0, nt) of a phase: block b first takes tile b,
+    // then the next free tile of the phase's counter (requested while the
+    // current tile runs), so blocks that drew light tiles take more of them
+    // and a phase ends at most about one tile after its mean.
+    template <class Fn>
+    static __device__ void run_tiles(int *ctr, int nt, Fn fn)
+    {
+        __shared__ int s_next[2];
+        int tile = blockIdx.x, k = 0;
+        while (tile < nt) {
+            int nxt = 0;
+            if (threadIdx.x == 0) nxt = atomicAdd(ctr, 1);
+            fn(tile);
+            if (threadIdx.x == 0) s_next[k & 1] = (int)gridDim.x + nxt;
+            __syncthreads();
+            tile = s_next[k & 1];
+            ++k;
+        }
+    }
+
     // Tiles of a phase are numbered circuit-major: circuit c, then segment k
     // (anchor K for AP; one segment for DP and DIAG), then ceil(count / TPB)
     // tiles; tiles[k] = prefix over k within one circuit, tiles[nseg] = tiles
@@ -1183,6 +1204,7 @@ struct Walk {
             if (v.x != 0.0 || v.y != 0.0) nz = 1;
         }
         if (__syncthreads_or(nz) && threadIdx.x == 0) atomicOr(&a.ctl->has_b, 1);
+        for (int64_t e = gtid; e < 2 * (int64_t)(sh.L + 1); e += gsz) a.ctr[e] = 0;
         if constexpr (TC) build_digits(a, s);
         if (a.geo != nullptr) build_geometry(a, s);
         if (seed) {
@@ -1676,17 +1698,17 @@ struct Walk {
         for (int lev = 0; lev < sh.L; ++lev) {
             if (hb) {
                 const int nt = phase_tiles(a, s, 1, lev);
-                for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+                run_tiles(a.ctr + 2 * lev, nt, [&](int tile) {
                     const TileId tl = decode_tile(a, s, 1, lev, tile);
-                    if (!pivots_run(a, tl.circ, lev)) continue;
+                    if (!pivots_run(a, tl.circ, lev)) return;
                     dp_forward_tile(a, s, tl, lev);
-                }
+                });
                 if (!grid_sync(a.ctl, gridDim.x, a.timeout_ns)) return;
             }
             const int nt = phase_tiles(a, s, 0, lev);
-            for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+            run_tiles(a.ctr + 2 * lev + 1, nt, [&](int tile) {
                 const TileId tl = decode_tile(a, s, 0, lev, tile);
-                if (!pivots_run(a, tl.circ, lev)) continue;
+                if (!pivots_run(a, tl.circ, lev)) return;
                 if (a.early) {
                     if (hb) ap_forward_tile<true, true>(a, s, tl, tl.seg, lev);
                     else ap_forward_tile<false, true>(a, s, tl, tl.seg, lev);
@@ -1694,7 +1716,7 @@ struct Walk {
                     if (hb) ap_forward_tile<true, false>(a, s, tl, tl.seg, lev);
                     else ap_forward_tile<false, false>(a, s, tl, tl.seg, lev);
                 }
-            }
+            });
             if ((lev + 1 < sh.L || a.early) && !grid_sync(a.ctl, gridDim.x, a.timeout_ns)) return;
         }
         if (a.early && a.levels != nullptr && blockIdx.x == 0) {
@@ -1722,9 +1744,9 @@ struct Walk {
         for (int lev = sh.L; lev >= 0; --lev) {
             if (lev < sh.L) {
                 const int nt = phase_tiles(a, s, 0, lev);
-                for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+                run_tiles(a.ctr + 2 * lev + 1, nt, [&](int tile) {
                     const TileId tl = decode_tile(a, s, 0, lev, tile);
-                    if (!pivots_run(a, tl.circ, lev)) continue;
+                    if (!pivots_run(a, tl.circ, lev)) return;
                     if constexpr (TC) {
                         if (hb) ap_reverse_tile_tc<true>(a, s, tl, tl.seg, lev);
                         else ap_reverse_tile_tc<false>(a, s, tl, tl.seg, lev);
@@ -1732,17 +1754,17 @@ struct Walk {
                         if (hb) ap_reverse_tile<true>(a, s, tl, tl.seg, lev);
                         else ap_reverse_tile<false>(a, s, tl, tl.seg, lev);
                     }
-                }
+                });
                 if (!grid_sync(a.ctl, gridDim.x, a.timeout_ns)) return;
             }
             if (hb && lev < sh.L) {
                 const int nt = phase_tiles(a, s, 1, lev);
-                for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+                run_tiles(a.ctr + 2 * lev, nt, [&](int tile) {
                     const TileId tl = decode_tile(a, s, 1, lev, tile);
-                    if (!pivots_run(a, tl.circ, lev)) continue;
+                    if (!pivots_run(a, tl.circ, lev)) return;
                     if constexpr (TC) dp_reverse_tile_tc(a, s, tl, lev);
                     else dp_reverse_tile(a, s, tl, lev);
-                }
+                });
                 if (!grid_sync(a.ctl, gridDim.x, a.timeout_ns)) return;
             }
         }
@@ -1986,6 +2008,7 @@ static DiagArgs make_args(const DiagShape &sh, int batch, unsigned flags, const 
     a.As = (double2 *)(w + lay.As);
     a.bs = (double2 *)(w + lay.bs);
     a.dig = (unsigned char *)(w + lay.dig);
+    a.ctr = (int *)(w + lay.ctr);
     a.geo = lay.geo != lay.F ? (int *)(w + lay.geo) : nullptr;
     a.F = (double2 *)(w + lay.F);
     a.lvl = (unsigned long long *)(w + lay.lvl);
