@@ -130,7 +130,11 @@ struct Walk {
     static constexpr int WBS = 34;       // column stride (doubles) of a per-warp buffer
     static constexpr int NDIG = 7;       // base-256 digits per value (Sec. 2.1 accuracy)
 
-    static __host__ __device__ size_t smem_bytes(int M, int L, bool vjp)
+    // The tensor-engine forward keeps its read ranks in registers (from the
+    // geometry table) and needs the per-thread index array only for DP tiles.
+    static __host__ __device__ bool needs_idx(bool vjp, bool has_b) { return !TC || vjp || has_b; }
+
+    static __host__ __device__ size_t smem_bytes(int M, int L, bool vjp, bool has_b)
     {
         const int D = 2 * M;
         size_t n = 0;
@@ -154,7 +158,8 @@ struct Walk {
             if (vjp) n += 3 * (size_t)D * RS * sizeof(double) + RS * sizeof(double2);
         }
         n = (n + 15) & ~(size_t)15;
-        n += (size_t)M * TPB * sizeof(int) + (M + 2) * sizeof(int);
+        if (needs_idx(vjp, has_b)) n += (size_t)M * TPB * sizeof(int);
+        n += (M + 2) * sizeof(int);
         return n + 64;
     }
 
@@ -205,7 +210,11 @@ struct Walk {
             }
         }
         p = (unsigned char *)(((uintptr_t)p + 15) & ~(uintptr_t)15);
-        s.idx = (int *)p; p += (size_t)M * TPB * sizeof(int);
+        s.idx = nullptr;
+        if (needs_idx(vjp, sh.has_b)) {
+            s.idx = (int *)p;
+            p += (size_t)M * TPB * sizeof(int);
+        }
         s.tiles = (int *)p;
         s.loaded_circ = -1;
         return s;
@@ -990,6 +999,7 @@ struct Walk {
     // addresses of its reads and writes from its relative geometry; the ranks
     // of e - 1_m (m > K) go to s.idx[m][thread].  ap_geom below is the same
     // computation for any M.
+    template <bool STORE_IDX = true>
     static __device__ __forceinline__ ApGeom ap_assemble(const DiagShape &sh, const Dig &e, int K, Smem &s,
                                                          int lev, int64_t r, const ApRel &q)
     {
@@ -1013,7 +1023,7 @@ struct Walk {
             const int m = K + 1 + i;
             if (m >= sh.M) continue;
             const int em = e(m);
-            s.idx[m * TPB + threadIdx.x] = q.idx[i];
+            if (STORE_IDX) s.idx[m * TPB + threadIdx.x] = q.idx[i];
             if (em >= 1) g.vmask |= 3u << (2 * (m - K));
             if (em <= sh.C[m] - 2) g.nmask |= 3u << (2 * (m - K));
         }
@@ -1079,6 +1089,28 @@ struct Walk {
         return ap_assemble(sh, e, K, s, lev, (int64_t)r, q);
     }
 
+    // The same from the table (M <= 8), the ranks of the reads left in q.
+    static __device__ __forceinline__ ApGeom ap_pivot_regs(const DiagArgs &a, Smem &s, int K, int lev,
+                                                           unsigned r, Dig &e, ApRel &q)
+    {
+        const DiagShape &sh = a.sh;
+        if (a.geo == nullptr) {
+            e = unrank(sh, s, K, 1, lev, r);
+            q = ap_rel(sh, e, K, s, lev, (int64_t)r);
+            return ap_assemble<false>(sh, e, K, s, lev, (int64_t)r, q);
+        }
+        const int4 *rec = (const int4 *)(a.geo + (size_t)(sh.off_ap[K] + s.cum0[K] + r) * kGeoInts);
+        const int4 w0 = __ldcg(rec), w1 = __ldcg(rec + 1), w2 = __ldcg(rec + 2);
+        e.lo = (uint64_t)(unsigned)w0.x | ((uint64_t)(unsigned)w0.y << 32);
+        e.hi = 0;
+        q.idx[0] = w0.z; q.idx[1] = w0.w;
+        q.idx[2] = w1.x; q.idx[3] = w1.y; q.idx[4] = w1.z; q.idx[5] = w1.w;
+        q.idx[6] = w2.x;
+        q.rt2 = w2.y;
+        q.wdiag = w2.z;
+        return ap_assemble<false>(sh, e, K, s, lev, (int64_t)r, q);
+    }
+
     // The table: every AP pivot of the pivot levels (one grid-stride pass per
     // (K, level); every thread keeps the level offsets).
     static __device__ void build_geometry(const DiagArgs &a, const Smem &s)
@@ -1118,6 +1150,17 @@ struct Walk {
         const int m = K + j / 2;
         const int64_t rk = s.idx[m * TPB + threadIdx.x];
         return pair_base(sh, K, m) + 2 * (g.lkm + rk) + ((j & 1) ? 0 : 1);
+    }
+
+    // The same with the ranks of e - 1_m in registers (q.idx[m - K - 1]); j is
+    // a compile-time index in the unrolled gather.
+    static __device__ __forceinline__ int64_t ap_read_addr_q(const DiagShape &sh, const ApGeom &g, int K,
+                                                             int j, const ApRel &q)
+    {
+        if (j == 0) return g.rd;
+        if (j == 1) return g.rt2;
+        const int m = K + j / 2;
+        return pair_base(sh, K, m) + 2 * (g.lkm + q.idx[j / 2 - 1]) + ((j & 1) ? 0 : 1);
     }
 
     // Address of AP write row i and its scale index P_w + 1.
@@ -1232,13 +1275,26 @@ struct Walk {
         double2 FP = make_double2(0, 0);
         double fe = 1.0, psum = 0.0;
         if (act) {
-            g = ap_pivot(a, s, K, lev, r, e);
-            gather(
-                N,
-                [&](int j) {
-                    return ((g.vmask >> j) & 1u) ? __ldcg(F + ap_read_addr(sh, g, K, j, s)) : make_double2(0, 0);
-                },
-                [&](int j, double2 v) { store_read(s, D, j, t, v, false); });
+            if constexpr (TC) {
+                ApRel q;
+                g = ap_pivot_regs(a, s, K, lev, r, e, q);
+                gather(
+                    N,
+                    [&](int j) {
+                        return ((g.vmask >> j) & 1u) ? __ldcg(F + ap_read_addr_q(sh, g, K, j, q))
+                                                     : make_double2(0, 0);
+                    },
+                    [&](int j, double2 v) { store_read(s, D, j, t, v, false); });
+            } else {
+                g = ap_pivot(a, s, K, lev, r, e);
+                gather(
+                    N,
+                    [&](int j) {
+                        return ((g.vmask >> j) & 1u) ? __ldcg(F + ap_read_addr(sh, g, K, j, s))
+                                                     : make_double2(0, 0);
+                    },
+                    [&](int j, double2 v) { store_read(s, D, j, t, v, false); });
+            }
             if (HASB) FP = __ldcg(F + g.fp);
             for (int i = K; i < sh.M; ++i) fe *= s.fact[e(i)];
         } else {
@@ -1802,7 +1858,7 @@ struct Walk {
 };
 
 template <int TPB, int CH, int KS>
-__global__ void __launch_bounds__(TPB) diag_forward_kernel(const __grid_constant__ DiagArgs a)
+__global__ void __launch_bounds__(TPB, (KS > 0 ? 4 : 1)) diag_forward_kernel(const __grid_constant__ DiagArgs a)
 {
     Walk<TPB, CH, KS>::forward(a);
 }
@@ -1873,7 +1929,7 @@ int device_sms(int *sms)
 struct Variant {
     int tpb, ch;
     const void *fwd, *vjp;
-    size_t (*smem)(int, int, bool);
+    size_t (*smem)(int, int, bool, bool);
 };
 
 template <int T, int C>
@@ -1890,7 +1946,7 @@ const Variant kVariants[] = {variant<128, 8>(), variant<128, 4>(), variant<64, 8
 struct TcVariant {
     int ks;
     const void *fwd, *vjp;
-    size_t (*smem)(int, int, bool);
+    size_t (*smem)(int, int, bool, bool);
 };
 
 template <int KS>
@@ -1930,13 +1986,13 @@ void walk_kernel(const DiagShape &sh, bool vjp, const void **fn, int *tpb, size_
         const TcVariant &t = kTcVariants[(sh.M + 3) / 4 - 1];
         *fn = vjp ? t.vjp : t.fwd;
         *tpb = 128;
-        *smem = t.smem(sh.M, sh.L, vjp);
+        *smem = t.smem(sh.M, sh.L, vjp, sh.has_b != 0);
         *slots_per_block = 128 / 32;
         return;
     }
     *fn = vjp ? v.vjp : v.fwd;
     *tpb = v.tpb;
-    *smem = v.smem(sh.M, sh.L, vjp);
+    *smem = v.smem(sh.M, sh.L, vjp, sh.has_b != 0);
     *slots_per_block = 1;
 }
 
