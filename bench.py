@@ -459,7 +459,8 @@ def run_gpu(args):
             "kernel_ms": {"diag_forward_kernel": fwd_ms, "diag_vjp_kernel": vjp_ms},
             "e2e": {"value": amps / (e2e_ms * 1e-3), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": 2 * args.steps,
+            # forward: one launch; VJP: the reverse walk plus (tensor engine) the partial pass
+            "gpu_launches": (3 if tuning["engine"] == "tensor" else 2) * args.steps,
             "roofline": roof,
             "clocks": clocks,
             "autotune": tuning,

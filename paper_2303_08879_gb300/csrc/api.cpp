@@ -109,8 +109,9 @@ int diag_layout(const DiagShape &sh, int batch, bool vjp, DiagLayout *lay)
     lay->ctl = o; o = align_up(o + sizeof(Control));
     // per circuit and photon number: fixed-point sums of the probabilities (early stop)
     lay->lvl = o; o = align_up(o + B * (size_t)(sh.L + 2) * sizeof(unsigned long long));
-    // tile counters of the phases (two per level), cleared by the kernels
-    lay->ctr = o; o = align_up(o + 2 * (size_t)(sh.L + 1) * sizeof(int));
+    // tile counters of the phases (two per level for the walk, two more for
+    // the tensor engine's partial pass), cleared by the kernels
+    lay->ctr = o; o = align_up(o + 4 * (size_t)(sh.L + 1) * sizeof(int));
     lay->As = o; o = align_up(o + B * D * D * c16);
     lay->bs = o; o = align_up(o + B * D * c16);
     lay->dig = o; o = align_up(o + B * diag_digit_bytes(sh.M));

@@ -48,7 +48,8 @@ struct DiagArgs {
     double2 *As, *bs, *F;
     unsigned char *dig;           // tensor engine: per-circuit digit fragments of A (kDigBytes each)
     int *geo;                     // AP pivot geometry shared by the circuits (M <= 8), or null
-    int *ctr;                     // [2 (L + 1)] next-tile counters: DP phase of level l at 2l, AP at 2l + 1
+    int *ctr;                     // [4 (L + 1)] next-tile counters: DP phase of level l at 2l, AP at
+                                  // 2l + 1; the tensor engine's partial pass at 2 (L + 1) + the same
     const double2 *gprobs;
     double2 *Fbar, *scratch, *partA, *partb;
     double2 *gA, *gb, *gc;
@@ -118,6 +119,9 @@ struct DpGeom {
     unsigned vmask, nmask;
 };
 
+// Shared-memory layouts of the walk kernels (see Walk::smem_plan).
+constexpr int kFwd = 0, kVjp = 1, kPart = 2;
+
 // The walk for one tile shape: TPB pivots per tile (= threads per block) and
 // either CH output rows per FP64 register chunk (KS = 0) or, for KS > 0, the
 // tensor-core digit engine with up to 16 KS real rows (M <= 4 KS); the
@@ -130,92 +134,89 @@ struct Walk {
     static constexpr int WBS = 34;       // column stride (doubles) of a per-warp buffer
     static constexpr int NDIG = 7;       // base-256 digits per value (Sec. 2.1 accuracy)
 
-    // The tensor-engine forward keeps its read ranks in registers (from the
-    // geometry table) and needs the per-thread index array only for DP tiles.
-    static __host__ __device__ bool needs_idx(bool vjp, bool has_b) { return !TC || vjp || has_b; }
+    // Shared-memory plan, one for sizing (host) and carving (device) so the two
+    // cannot disagree.  Modes: kFwd the forward walk; kVjp the reverse walk
+    // (FP64 engine: with the partial dL/dA; tensor engine: products only, in
+    // place in the adjoint buffer); kPart the tensor engine's partial dL/dA
+    // pass.  Absent regions have offset kNone.
+    static constexpr size_t kNone = ~(size_t)0;
+    struct SmemPlan {
+        size_t S, cum, inv, bs, fA, wb, wy, FP, wf, wg, Af, A3, R3, Y3, idx, tiles, bytes;
+    };
 
-    static __host__ __device__ size_t smem_bytes(int M, int L, bool vjp, bool has_b)
+    static __host__ __device__ SmemPlan smem_plan(int M, int L, int mode, bool has_b)
     {
-        const int D = 2 * M;
+        SmemPlan q;
+        q.bs = q.fA = q.wb = q.wy = q.FP = q.wf = q.wg = q.Af = q.A3 = q.R3 = q.Y3 = q.idx = kNone;
+        const int D = 2 * M, D2 = 2 * D;
         size_t n = 0;
-        n += (size_t)(M + 1) * (L + 2) * sizeof(unsigned);
-        n = (n + 15) & ~(size_t)15;
-        n += 3 * (size_t)M * sizeof(int64_t);
-        n = (n + 15) & ~(size_t)15;
-        n += 2 * TABN * sizeof(double);
+        const auto al = [&n]() { n = (n + 15) & ~(size_t)15; };
+        q.S = n; n += (size_t)(M + 1) * (L + 2) * sizeof(unsigned); al();
+        q.cum = n; n += 3 * (size_t)M * sizeof(int64_t); al();
+        q.inv = n; n += 2 * TABN * sizeof(double); al();
         if (TC) {
-            const int D2 = 2 * D;
             const size_t buf = (size_t)(TPB / 32) * XS * WBS * sizeof(double);
-            n += (size_t)D * sizeof(double2);
-            n += (size_t)D2 * sizeof(int);
-            n = (n + 15) & ~(size_t)15;
-            n += buf;
-            if (vjp) n += buf + (size_t)TPB * (sizeof(double2) + 2 * sizeof(int));
-            n += (size_t)KS * KS * NDIG * 32 * sizeof(uint4);
+            if (mode != kPart) {
+                q.bs = n; n += (size_t)D * sizeof(double2);
+                q.fA = n; n += (size_t)D2 * sizeof(int); al();
+                q.Af = n; n += (size_t)KS * KS * NDIG * 32 * sizeof(uint4); al();
+            }
+            if (mode != kVjp) { q.wb = n; n += buf; al(); }
+            if (mode != kFwd) { q.wy = n; n += buf; al(); }
+            if (mode == kPart) {
+                if (has_b) { q.FP = n; n += (size_t)TPB * sizeof(double2); }
+                q.wf = n; n += (size_t)TPB * sizeof(int);
+                q.wg = n; n += (size_t)TPB * sizeof(int); al();
+            }
+            // the forward and the partial pass keep AP read ranks in registers
+            if (mode == kVjp || has_b) { q.idx = n; n += (size_t)M * TPB * sizeof(int); al(); }
         } else {
-            n += 3 * (size_t)D * D * sizeof(double) + (size_t)D * sizeof(double2);
-            n += 3 * (size_t)D * RS * sizeof(double);
-            if (vjp) n += 3 * (size_t)D * RS * sizeof(double) + RS * sizeof(double2);
+            q.A3 = n; n += 3 * (size_t)D * D * sizeof(double); al();
+            q.bs = n; n += (size_t)D * sizeof(double2); al();
+            q.R3 = n; n += 3 * (size_t)D * RS * sizeof(double); al();
+            if (mode == kVjp) {
+                q.Y3 = n; n += 3 * (size_t)D * RS * sizeof(double); al();
+                q.FP = n; n += RS * sizeof(double2); al();
+            }
+            q.idx = n; n += (size_t)M * TPB * sizeof(int); al();
         }
-        n = (n + 15) & ~(size_t)15;
-        if (needs_idx(vjp, has_b)) n += (size_t)M * TPB * sizeof(int);
-        n += (M + 2) * sizeof(int);
-        return n + 64;
+        q.tiles = n; n += (M + 2) * sizeof(int);
+        q.bytes = n + 64;
+        return q;
     }
 
-    static __device__ Smem carve_smem(const DiagShape &sh, bool vjp)
+    static __host__ __device__ size_t smem_bytes(int M, int L, int mode, bool has_b)
+    {
+        return smem_plan(M, L, mode, has_b).bytes;
+    }
+
+    static __device__ Smem carve_smem(const DiagShape &sh, int mode)
     {
         extern __shared__ __align__(16) unsigned char smem_raw[];
+        const SmemPlan q = smem_plan(sh.M, sh.L, mode, sh.has_b != 0);
+        const auto at = [&](size_t o) { return o == kNone ? nullptr : (void *)(smem_raw + o); };
+        const int M = sh.M;
         Smem s;
-        const int M = sh.M, D = 2 * M;
-        unsigned char *p = smem_raw;
-        s.S = (unsigned *)p;
+        s.S = (unsigned *)at(q.S);
         s.Wn = sh.L + 2;
-        p += (size_t)(M + 1) * s.Wn * sizeof(unsigned);
-        p = (unsigned char *)(((uintptr_t)p + 15) & ~(uintptr_t)15);
-        s.cum0 = (int64_t *)p; p += (size_t)M * sizeof(int64_t);
-        s.cum1 = (int64_t *)p; p += (size_t)M * sizeof(int64_t);
-        s.cum2 = (int64_t *)p; p += (size_t)M * sizeof(int64_t);
-        p = (unsigned char *)(((uintptr_t)p + 15) & ~(uintptr_t)15);   // double2 tables follow
-        s.inv = (double *)p; p += TABN * sizeof(double);
-        s.fact = (double *)p; p += TABN * sizeof(double);
-        s.A3 = s.R3 = s.Y3 = nullptr;
-        s.FP = nullptr;
-        s.Af = nullptr;
-        s.fA = nullptr;
-        s.wb = s.wy = nullptr;
-        s.wf = s.wg = nullptr;
-        if (TC) {
-            const int D2 = 2 * D;
-            const size_t buf = (size_t)(TPB / 32) * XS * WBS;
-            s.bs = (double2 *)p; p += (size_t)D * sizeof(double2);
-            s.fA = (int *)p; p += (size_t)D2 * sizeof(int);
-            p = (unsigned char *)(((uintptr_t)p + 15) & ~(uintptr_t)15);
-            s.wb = (double *)p; p += buf * sizeof(double);
-            if (vjp) {
-                s.wy = (double *)p; p += buf * sizeof(double);
-                s.FP = (double2 *)p; p += (size_t)TPB * sizeof(double2);
-                s.wf = (int *)p; p += (size_t)TPB * sizeof(int);
-                s.wg = (int *)p; p += (size_t)TPB * sizeof(int);
-            }
-            p = (unsigned char *)(((uintptr_t)p + 15) & ~(uintptr_t)15);
-            s.Af = (uint4 *)p; p += (size_t)KS * KS * NDIG * 32 * sizeof(uint4);
-        } else {
-            s.A3 = (double *)p; p += 3 * (size_t)D * D * sizeof(double);
-            s.bs = (double2 *)p; p += (size_t)D * sizeof(double2);
-            s.R3 = (double *)p; p += 3 * (size_t)D * RS * sizeof(double);
-            if (vjp) {
-                s.Y3 = (double *)p; p += 3 * (size_t)D * RS * sizeof(double);
-                s.FP = (double2 *)p; p += RS * sizeof(double2);
-            }
-        }
-        p = (unsigned char *)(((uintptr_t)p + 15) & ~(uintptr_t)15);
-        s.idx = nullptr;
-        if (needs_idx(vjp, sh.has_b)) {
-            s.idx = (int *)p;
-            p += (size_t)M * TPB * sizeof(int);
-        }
-        s.tiles = (int *)p;
+        s.cum0 = (int64_t *)at(q.cum);
+        s.cum1 = s.cum0 + M;
+        s.cum2 = s.cum0 + 2 * M;
+        s.inv = (double *)at(q.inv);
+        s.fact = s.inv + TABN;
+        s.bs = (double2 *)at(q.bs);
+        s.fA = (int *)at(q.fA);
+        s.Af = (uint4 *)at(q.Af);
+        s.wb = (double *)at(q.wb);
+        s.wy = (double *)at(q.wy);
+        s.FP = (double2 *)at(q.FP);
+        s.wf = (int *)at(q.wf);
+        s.wg = (int *)at(q.wg);
+        s.A3 = (double *)at(q.A3);
+        s.R3 = (double *)at(q.R3);
+        s.Y3 = (double *)at(q.Y3);
+        s.idx = (int *)at(q.idx);
+        s.tiles = (int *)at(q.tiles);
         s.loaded_circ = -1;
         return s;
     }
@@ -1247,7 +1248,7 @@ struct Walk {
             if (v.x != 0.0 || v.y != 0.0) nz = 1;
         }
         if (__syncthreads_or(nz) && threadIdx.x == 0) atomicOr(&a.ctl->has_b, 1);
-        for (int64_t e = gtid; e < 2 * (int64_t)(sh.L + 1); e += gsz) a.ctr[e] = 0;
+        for (int64_t e = gtid; e < 4 * (int64_t)(sh.L + 1); e += gsz) a.ctr[e] = 0;
         if constexpr (TC) build_digits(a, s);
         if (a.geo != nullptr) build_geometry(a, s);
         if (seed) {
@@ -1600,27 +1601,138 @@ struct Walk {
         __syncwarp();
     }
 
+    // Reverse step of an AP(K) tile on the tensor engine (the walk): scaled
+    // output adjoints into the warp's buffer (the DIAG one formed here and kept
+    // in Fbar for the partial pass), the read adjoints conj(A) Y in place, then
+    // each lane scatters its pivot's.
     template <bool HASB>
     static __device__ void ap_reverse_tile_tc(const DiagArgs &a, Smem &s, const TileId &tl, int K, int lev)
     {
         const DiagShape &sh = a.sh;
         const int t = threadIdx.x, lane = t & 31, D = 2 * sh.M, N = 2 * (sh.M - K);
         load_circuit(a, s, tl.circ);
-        const double2 *F = a.F + (size_t)tl.circ * sh.circ_alloc;
         double2 *Fb = a.Fbar + (size_t)tl.circ * sh.circ_alloc;
         const unsigned r = tl.rank0 + t;
         const bool act = r < tl.count;
         const bool up = pivots_run(a, tl.circ, lev + 1);   // level lev + 1 ran in reverse
         Dig e;
         ApGeom g{};
-        int fx = 0;
-        double2 FPv = make_double2(0, 0);
         if (act) {
             g = ap_pivot(a, s, K, lev, r, e);
             gather(
                 N,
+                [&](int i) {
+                    if (!((g.nmask >> i) & 1u)) return make_double2(0, 0);
+                    int den;
+                    const int64_t addr = ap_write_addr(sh, g, e, K, i, s, &den);
+                    double2 y;
+                    if (i == 1) {
+                        y = diag_adjoint<HASB>(a, s, tl.circ, K, lev, g, e);
+                        Fb[addr] = y;   // complete: the partial pass reads it back
+                    } else {
+                        // T2 and P values of a level whose pivots did not run have no
+                        // reader: their adjoint is zero (Fbar is not cleared for b = 0)
+                        y = up ? __ldcg(Fb + addr) : make_double2(0, 0);
+                    }
+                    return rscale(y, s.inv[den]);
+                },
+                [&](int i, double2 v) { store_adj(s, D, i, t, v); });
+        } else {
+            for (int j = 0; j < N; ++j) store_adj(s, D, j, t, make_double2(0, 0));
+        }
+        double2 fpb = make_double2(0, 0);
+        if (HASB && act)
+            for (int i = 0; i < N; ++i)
+                if ((g.nmask >> i) & 1u) fpb = cfma_conj(s.bs[2 * K + i], load_adj(s, D, i, t), fpb);
+        __syncwarp();
+        double *wy = s.wy + (size_t)(t >> 5) * XS * WBS;
+        tc_products<true>(s, D, 2 * K, N, wy, wy);
+        if (act) {
+            for (int j = 0; j < N; ++j) {
+                if (!((g.vmask >> j) & 1u)) continue;
+                const double2 acc = make_double2(wy[(2 * j) * WBS + lane], wy[(2 * j + 1) * WBS + lane]);
+                if (j == 0) {
+                    const int64_t ia = g.lk0 + g.r;
+                    a.scratch[(size_t)tl.circ * sh.n_ap + sh.off_ap[K] + ia] = acc;
+                } else {
+                    Fb[ap_read_addr(sh, g, K, j, s)] = acc;   // the value's only reader
+                }
+            }
+            if (HASB) Fb[g.fp] = cadd(__ldcg(Fb + g.fp), fpb);
+        }
+        __syncwarp();
+    }
+
+    static __device__ void dp_reverse_tile_tc(const DiagArgs &a, Smem &s, const TileId &tl, int lev)
+    {
+        const DiagShape &sh = a.sh;
+        const int t = threadIdx.x, lane = t & 31, D = 2 * sh.M, N = D;
+        load_circuit(a, s, tl.circ);
+        double2 *Fb = a.Fbar + (size_t)tl.circ * sh.circ_alloc;
+        const unsigned r = tl.rank0 + t;
+        const bool act = r < tl.count;
+        Dig d;
+        DpGeom g{};
+        if (act) {
+            d = unrank(sh, s, 0, 1, lev, r);
+            g = dp_geom(sh, d, s, lev, (int64_t)r);
+            gather(
+                N,
+                [&](int i) {
+                    if (!((g.nmask >> i) & 1u)) return make_double2(0, 0);
+                    int den;
+                    const int64_t addr = dp_write_addr(sh, g, d, i, s, &den);
+                    return rscale(__ldcg(Fb + addr), s.inv[den]);
+                },
+                [&](int i, double2 v) { store_adj(s, D, i, t, v); });
+        } else {
+            for (int j = 0; j < N; ++j) store_adj(s, D, j, t, make_double2(0, 0));
+        }
+        double2 fpb = make_double2(0, 0);
+        if (act)
+            for (int i = 0; i < N; ++i)
+                if ((g.nmask >> i) & 1u) fpb = cfma_conj(s.bs[i], load_adj(s, D, i, t), fpb);
+        __syncwarp();
+        double *wy = s.wy + (size_t)(t >> 5) * XS * WBS;
+        tc_products<true>(s, D, 0, N, wy, wy);
+        if (act) {
+            for (int j = 0; j < N; ++j) {
+                if (!((g.vmask >> j) & 1u)) continue;
+                const double2 acc = make_double2(wy[(2 * j) * WBS + lane], wy[(2 * j + 1) * WBS + lane]);
+                const int64_t addr = dp_read_addr(sh, g, j, s);
+                Fb[addr] = cadd(__ldcg(Fb + addr), acc);
+            }
+            Fb[g.rdiag] = cadd(__ldcg(Fb + g.rdiag), fpb);
+        }
+        __syncwarp();
+    }
+
+    // ------------------------------------------ partial dL/dA, dL/db (tensor)
+    // After the reverse walk every adjoint is final, so the partial sums
+    // sum_t Y_w(t) conj(X_j(t)) (and the dL/db terms) of all pivots are formed
+    // in one pass without level barriers: reads X and scaled output adjoints Y
+    // are gathered again (the DIAG adjoint from where the walk left it).
+    template <bool HASB>
+    static __device__ void ap_partial_tile(const DiagArgs &a, Smem &s, const TileId &tl, int K, int lev)
+    {
+        const DiagShape &sh = a.sh;
+        const int t = threadIdx.x, D = 2 * sh.M, N = 2 * (sh.M - K);
+        const double2 *F = a.F + (size_t)tl.circ * sh.circ_alloc;
+        const double2 *Fb = a.Fbar + (size_t)tl.circ * sh.circ_alloc;
+        const unsigned r = tl.rank0 + t;
+        const bool act = r < tl.count;
+        const bool up = pivots_run(a, tl.circ, lev + 1);
+        int fx = 0;
+        double2 FPv = make_double2(0, 0);
+        if (act) {
+            Dig e;
+            ApRel q;
+            const ApGeom g = ap_pivot_regs(a, s, K, lev, r, e, q);
+            gather(
+                N,
                 [&](int j) {
-                    return ((g.vmask >> j) & 1u) ? __ldcg(F + ap_read_addr(sh, g, K, j, s)) : make_double2(0, 0);
+                    return ((g.vmask >> j) & 1u) ? __ldcg(F + ap_read_addr_q(sh, g, K, j, q))
+                                                 : make_double2(0, 0);
                 },
                 [&](int j, double2 v) {
                     fx = max(fx, max(fexp(v.x), fexp(v.y)));
@@ -1632,10 +1744,7 @@ struct Walk {
                     if (!((g.nmask >> i) & 1u)) return make_double2(0, 0);
                     int den;
                     const int64_t addr = ap_write_addr(sh, g, e, K, i, s, &den);
-                    // T2 and P values of a level whose pivots did not run have no
-                    // reader: their adjoint is zero (Fbar is not cleared for b = 0)
-                    const double2 y = i == 1 ? diag_adjoint<HASB>(a, s, tl.circ, K, lev, g, e)
-                                      : up ? __ldcg(Fb + addr) : make_double2(0, 0);
+                    const double2 y = (i == 1 || up) ? __ldcg(Fb + addr) : make_double2(0, 0);
                     return rscale(y, s.inv[den]);
                 },
                 [&](int i, double2 v) { store_adj(s, D, i, t, v); });
@@ -1646,51 +1755,26 @@ struct Walk {
                 store_adj(s, D, j, t, make_double2(0, 0));
             }
         }
-        s.FP[t] = FPv;
+        if (HASB) s.FP[t] = FPv;
         tc_row_exponents(s, D, N, fx);
         tc_partials(a, s, tl.circ, 2 * K, N);
         if (HASB) tc_partb(a, s, tl.circ, 2 * K, N);
         __syncwarp();
-        double *wx = s.wb + (size_t)(t >> 5) * XS * WBS;
-        tc_products<true>(s, D, 2 * K, N, s.wy + (size_t)(t >> 5) * XS * WBS, wx);
-        if (act) {
-            for (int j = 0; j < N; ++j) {
-                if (!((g.vmask >> j) & 1u)) continue;
-                const double2 acc = make_double2(wx[(2 * j) * WBS + lane], wx[(2 * j + 1) * WBS + lane]);
-                if (j == 0) {
-                    const int64_t ia = g.lk0 + g.r;
-                    a.scratch[(size_t)tl.circ * sh.n_ap + sh.off_ap[K] + ia] = acc;
-                } else {
-                    Fb[ap_read_addr(sh, g, K, j, s)] = acc;   // the value's only reader
-                }
-            }
-            if (HASB) {
-                double2 fpb = make_double2(0, 0);
-                for (int i = 0; i < N; ++i)
-                    if ((g.nmask >> i) & 1u) fpb = cfma_conj(s.bs[2 * K + i], load_adj(s, D, i, t), fpb);
-                const int64_t addr = g.fp;
-                Fb[addr] = cadd(__ldcg(Fb + addr), fpb);
-            }
-        }
-        __syncwarp();
     }
 
-    static __device__ void dp_reverse_tile_tc(const DiagArgs &a, Smem &s, const TileId &tl, int lev)
+    static __device__ void dp_partial_tile(const DiagArgs &a, Smem &s, const TileId &tl, int lev)
     {
         const DiagShape &sh = a.sh;
-        const int t = threadIdx.x, lane = t & 31, D = 2 * sh.M, N = D;
-        load_circuit(a, s, tl.circ);
+        const int t = threadIdx.x, D = 2 * sh.M, N = D;
         const double2 *F = a.F + (size_t)tl.circ * sh.circ_alloc;
-        double2 *Fb = a.Fbar + (size_t)tl.circ * sh.circ_alloc;
+        const double2 *Fb = a.Fbar + (size_t)tl.circ * sh.circ_alloc;
         const unsigned r = tl.rank0 + t;
         const bool act = r < tl.count;
-        Dig d;
-        DpGeom g{};
         int fx = 0;
         double2 FPv = make_double2(0, 0);
         if (act) {
-            d = unrank(sh, s, 0, 1, lev, r);
-            g = dp_geom(sh, d, s, lev, (int64_t)r);
+            const Dig d = unrank(sh, s, 0, 1, lev, r);
+            const DpGeom g = dp_geom(sh, d, s, lev, (int64_t)r);
             gather(
                 N,
                 [&](int j) {
@@ -1721,28 +1805,13 @@ struct Walk {
         tc_partials(a, s, tl.circ, 0, N);
         tc_partb(a, s, tl.circ, 0, N);
         __syncwarp();
-        double *wx = s.wb + (size_t)(t >> 5) * XS * WBS;
-        tc_products<true>(s, D, 0, N, s.wy + (size_t)(t >> 5) * XS * WBS, wx);
-        if (act) {
-            for (int j = 0; j < N; ++j) {
-                if (!((g.vmask >> j) & 1u)) continue;
-                const double2 acc = make_double2(wx[(2 * j) * WBS + lane], wx[(2 * j + 1) * WBS + lane]);
-                const int64_t addr = dp_read_addr(sh, g, j, s);
-                Fb[addr] = cadd(__ldcg(Fb + addr), acc);
-            }
-            double2 fpb = make_double2(0, 0);
-            for (int i = 0; i < N; ++i)
-                if ((g.nmask >> i) & 1u) fpb = cfma_conj(s.bs[i], load_adj(s, D, i, t), fpb);
-            Fb[g.rdiag] = cadd(__ldcg(Fb + g.rdiag), fpb);
-        }
-        __syncwarp();
     }
 
     // ------------------------------------------------------------------ kernels
     static __device__ void forward(const DiagArgs &a)
     {
         const DiagShape &sh = a.sh;
-        Smem s = carve_smem(sh, false);
+        Smem s = carve_smem(sh, kFwd);
         build_tables(sh, s);
         prologue(a, s, true);
         if (!grid_sync(a.ctl, gridDim.x, a.timeout_ns)) return;
@@ -1788,7 +1857,7 @@ struct Walk {
     static __device__ void vjp(const DiagArgs &a)
     {
         const DiagShape &sh = a.sh;
-        Smem s = carve_smem(sh, true);
+        Smem s = carve_smem(sh, kVjp);
         build_tables(sh, s);
         prologue(a, s, false);
         if (!grid_sync(a.ctl, gridDim.x, a.timeout_ns)) return;
@@ -1824,8 +1893,47 @@ struct Walk {
                 if (!grid_sync(a.ctl, gridDim.x, a.timeout_ns)) return;
             }
         }
-        // Final reduction of the per-block partials (fixed order -> deterministic),
-        // symmetrisation dL/dA <- (dL/dA + dL/dA^T)/2, scatter to the caller's modes.
+        if constexpr (!TC) finish_vjp(a, hb);   // the tensor engine's partial pass finishes
+    }
+
+    // Partial dL/dA and dL/db of every pivot (tensor engine, after the walk):
+    // no level barriers, one counter per (level, kind) from the second half of
+    // the counter array; then the final reduction.
+    static __device__ void vjp_partials(const DiagArgs &a)
+    {
+        const DiagShape &sh = a.sh;
+        if (ld_status(a.ctl) != 0) return;   // the walk failed
+        Smem s = carve_smem(sh, kPart);
+        build_tables(sh, s);
+        __syncthreads();
+        const int hb = *(volatile int *)&a.ctl->has_b;
+        int *ctr = a.ctr + 2 * (sh.L + 1);
+        for (int lev = 0; lev < sh.L; ++lev) {
+            const int nt = phase_tiles(a, s, 0, lev);
+            run_tiles(ctr + 2 * lev + 1, nt, [&](int tile) {
+                const TileId tl = decode_tile(a, s, 0, lev, tile);
+                if (!pivots_run(a, tl.circ, lev)) return;
+                if (hb) ap_partial_tile<true>(a, s, tl, tl.seg, lev);
+                else ap_partial_tile<false>(a, s, tl, tl.seg, lev);
+            });
+            if (hb) {
+                const int nd = phase_tiles(a, s, 1, lev);
+                run_tiles(ctr + 2 * lev, nd, [&](int tile) {
+                    const TileId tl = decode_tile(a, s, 1, lev, tile);
+                    if (!pivots_run(a, tl.circ, lev)) return;
+                    dp_partial_tile(a, s, tl, lev);
+                });
+            }
+        }
+        finish_vjp(a, hb);
+    }
+
+    // Final reduction of the partial slots (fixed order -> deterministic),
+    // symmetrisation dL/dA <- (dL/dA + dL/dA^T)/2, scatter to the caller's
+    // modes, and dL/dc.
+    static __device__ void finish_vjp(const DiagArgs &a, int hb)
+    {
+        const DiagShape &sh = a.sh;
         const int D = 2 * sh.M, Do = sh.D_orig;
         const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
         const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
@@ -1864,9 +1972,15 @@ __global__ void __launch_bounds__(TPB, (KS > 0 ? 4 : 1)) diag_forward_kernel(con
 }
 
 template <int TPB, int CH, int KS>
-__global__ void __launch_bounds__(TPB) diag_vjp_kernel(const __grid_constant__ DiagArgs a)
+__global__ void __launch_bounds__(TPB, (KS > 0 ? 4 : 1)) diag_vjp_kernel(const __grid_constant__ DiagArgs a)
 {
     Walk<TPB, CH, KS>::vjp(a);
+}
+
+template <int TPB, int CH, int KS>
+__global__ void __launch_bounds__(TPB, (KS > 0 ? 3 : 1)) diag_vjp_partials_kernel(const __grid_constant__ DiagArgs a)
+{
+    if constexpr (KS > 0) Walk<TPB, CH, KS>::vjp_partials(a);
 }
 
 __global__ void copy_c_kernel(const double2 *c, double2 *probs, int B, int64_t stride)
@@ -1929,7 +2043,7 @@ int device_sms(int *sms)
 struct Variant {
     int tpb, ch;
     const void *fwd, *vjp;
-    size_t (*smem)(int, int, bool, bool);
+    size_t (*smem)(int, int, int, bool);
 };
 
 template <int T, int C>
@@ -1943,17 +2057,18 @@ const Variant kVariants[] = {variant<128, 8>(), variant<128, 4>(), variant<64, 8
                              variant<64, 4>(), variant<256, 8>()};
 
 // Tensor-core kernels, by KS = ceil(M / 4) (M <= 8); 128 pivots per tile.
+// The VJP is two launches: the reverse walk, then the partial pass.
 struct TcVariant {
     int ks;
-    const void *fwd, *vjp;
-    size_t (*smem)(int, int, bool, bool);
+    const void *fwd, *vjp, *part;
+    size_t (*smem)(int, int, int, bool);
 };
 
 template <int KS>
 TcVariant tc_variant()
 {
     return TcVariant{KS, (const void *)diag_forward_kernel<128, 4, KS>, (const void *)diag_vjp_kernel<128, 4, KS>,
-                     &Walk<128, 4, KS>::smem_bytes};
+                     (const void *)diag_vjp_partials_kernel<128, 4, KS>, &Walk<128, 4, KS>::smem_bytes};
 }
 
 const TcVariant kTcVariants[] = {tc_variant<1>(), tc_variant<2>()};
@@ -1972,9 +2087,12 @@ const Variant &current_variant(int *bps)
 }
 
 // Kernel, block size, shared memory and partial-sum slots per block for
-// shape sh under the current tuning and engine (forward or VJP).
+// shape sh under the current tuning and engine: the forward (vjp false) or
+// the VJP launch that owns the partial-sum slots (vjp true: the FP64
+// engine's reverse walk, the tensor engine's partial pass).  tc_walk: the
+// tensor engine's reverse walk instead.
 void walk_kernel(const DiagShape &sh, bool vjp, const void **fn, int *tpb, size_t *smem, int *bps,
-                 int *slots_per_block)
+                 int *slots_per_block, bool tc_walk = false)
 {
     const Variant &v = current_variant(bps);
     int engine;
@@ -1984,16 +2102,23 @@ void walk_kernel(const DiagShape &sh, bool vjp, const void **fn, int *tpb, size_
     }
     if (engine == FK_ENGINE_TENSOR && sh.M <= kTcMaxModes) {
         const TcVariant &t = kTcVariants[(sh.M + 3) / 4 - 1];
-        *fn = vjp ? t.vjp : t.fwd;
+        const int mode = tc_walk ? kVjp : (vjp ? kPart : kFwd);
+        *fn = tc_walk ? t.vjp : (vjp ? t.part : t.fwd);
         *tpb = 128;
-        *smem = t.smem(sh.M, sh.L, vjp, sh.has_b != 0);
+        *smem = t.smem(sh.M, sh.L, mode, sh.has_b != 0);
         *slots_per_block = 128 / 32;
         return;
     }
     *fn = vjp ? v.vjp : v.fwd;
     *tpb = v.tpb;
-    *smem = v.smem(sh.M, sh.L, vjp, sh.has_b != 0);
+    *smem = v.smem(sh.M, sh.L, vjp ? kVjp : kFwd, sh.has_b != 0);
     *slots_per_block = 1;
+}
+
+bool tc_engine_for(const DiagShape &sh)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    return g_engine == FK_ENGINE_TENSOR && sh.M <= kTcMaxModes;
 }
 
 }  // namespace
@@ -2152,6 +2277,22 @@ int launch_diag_vjp(const DiagShape &sh, int batch, unsigned flags, const void *
     if (rc) return rc;
     // tuning or engine changed since the layout was sized
     if (grid != lay.grid_vjp || slots != lay.slots_vjp) return FK_EWORKSPACE;
+    if (tc_engine_for(sh)) {
+        // the reverse walk (its own grid), then the partial pass that owns the slots
+        const void *wfn = nullptr;
+        int wtpb = 0, wbps = 0, wspb = 1;
+        size_t wsmem = 0;
+        walk_kernel(sh, true, &wfn, &wtpb, &wsmem, &wbps, &wspb, true);
+        if (cudaFuncSetAttribute(wfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem) != cudaSuccess)
+            return FK_ECUDA;
+        int per = 0, sms = 0;
+        if ((rc = device_sms(&sms)) != 0) return rc;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, wfn, wtpb, wsmem) != cudaSuccess) return FK_ECUDA;
+        if (per < 1) return FK_EUNSUPPORTED;
+        DiagArgs w = a;
+        w.grid = per * sms;
+        if ((rc = launch_coop(wfn, w.grid, wtpb, wsmem, &w, st)) != 0) return rc;
+    }
     return launch_coop(fn, lay.grid_vjp, tpb, smem, &a, st);
 }
 
