@@ -37,15 +37,16 @@ METRIC = "Fock diag amplitudes/s (c128); fwd+VJP circuits/s vs plain, rel err<=1
 UNIT = "amplitudes/s"
 NCIRC = 16
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant
-# kernel (diag_vjp_kernel) per launch of this 16-circuit workload, captured
-# with ncu on a 2-circuit launch (2.427 GB read + 0.857 GB written) and
-# scaled by 8: circuits share no data, so traffic grows in proportion to
-# them.  Valid only for the kernel source it was measured on (sha256 prefix
-# of csrc/walk_diag.cu) and the engine / tile shape; reported as null once
-# either differs.
-TRAFFIC = {"kernel_sha": "5b95a492c2b965bb", "tuning": ["tensor", 128, 4, 0],
-           "bytes_per_launch": 8 * (1851789568 + 890358528)}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of
+# each walk kernel on this 16-circuit workload, captured with ncu on a
+# 2-circuit launch and scaled by 8: circuits share no data, so traffic grows
+# in proportion to them.  Valid only for the kernel source it was measured on
+# (sha256 prefix of csrc/walk_diag.cu) and the engine / tile shape; reported
+# as null once either differs.
+TRAFFIC = {"kernel_sha": "3435c7c4cb1b2b2b", "tuning": ["tensor", 128, 4, 0],
+           "bytes_per_launch": {"diag_forward_kernel": 8 * (495086592 + 854074624),
+                                "diag_vjp_kernel": 8 * (704236288 + 806338560),
+                                "diag_vjp_partials_kernel": 8 * (1734099712 + 140261120)}}
 
 FALLBACK_HBM_GBS = 6800.0
 
@@ -353,12 +354,16 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
     ev = lambda: torch.cuda.Event(enable_timing=True)
 
+    split = best[0] == autotune.TENSOR   # the VJP is two launches: reverse walk, partial pass
+
     def step(tk=None):
         if tk is not None:
             tk[0].record(stream)
         fd.fock_diag_probs_batched(A, b, c, cut, probs=probs, flags=flags, ws=ws)
         if tk is not None:
             tk[1].record(stream)
+            if split:
+                fd.fk_diag_set_vjp_split_event(tk[3])   # recorded between the two launches
         fd.fock_diag_probs_vjp_batched(A, b, c, cut, w, ws, flags=flags, out=(gA, gb, gc))
         if tk is not None:
             tk[2].record(stream)
@@ -369,7 +374,9 @@ def run_gpu(args):
     barrier(); torch.cuda.synchronize()
     sampler = ClockSampler(local)
     sampler.start()
-    marks = [[ev(), ev(), ev()] for _ in range(args.steps)]
+    marks = [[ev(), ev(), ev(), ev()] for _ in range(args.steps)]
+    for m in marks:
+        m[3].record(stream)   # creates the event the library records between the VJP launches
     t0, t1 = ev(), ev()
     t0.record(stream)
     for i in range(args.steps):
@@ -380,8 +387,16 @@ def run_gpu(args):
     barrier()
     fd.check_workspace(ws, where="timed steps")
     ms = t0.elapsed_time(t1) / args.steps
+    fd.fk_diag_set_vjp_split_event(None)
     fwd_ms = statistics.mean(m[0].elapsed_time(m[1]) for m in marks)
     vjp_ms = statistics.mean(m[1].elapsed_time(m[2]) for m in marks)
+    if split:
+        walk_ms = statistics.mean(m[1].elapsed_time(m[3]) for m in marks)
+        part_ms = statistics.mean(m[3].elapsed_time(m[2]) for m in marks)
+        kernel_ms = {"diag_forward_kernel": fwd_ms, "diag_vjp_kernel": walk_ms,
+                     "diag_vjp_partials_kernel": part_ms}
+    else:
+        kernel_ms = {"diag_forward_kernel": fwd_ms, "diag_vjp_kernel": vjp_ms}
     if world > 1:
         t = torch.tensor([ms], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -424,18 +439,30 @@ def run_gpu(args):
         sha = kernel_sha()
         shape = list(best)
         traffic = (TRAFFIC["bytes_per_launch"]
-                   if TRAFFIC["kernel_sha"] == sha and TRAFFIC["tuning"] == shape else None)
+                   if TRAFFIC["kernel_sha"] == sha and TRAFFIC["tuning"] == shape else {})
         stored = fd.fk_describe_diag_schedule(M, cut, flags)["stored"]
         nout = int(np.prod(cut))
         bytes_fwd = NCIRC * (32 * stored + 16 * nout)
         bytes_vjp = NCIRC * (48 * stored + 16 * nout)
         if best[0] == autotune.TENSOR:
             hbm, hbm_src = measured_hbm_gbs()
-            gbs = bytes_vjp / (vjp_ms * 1e-3) / 1e9
-            roof = {"bound": "hbm", "kernel": "diag_vjp_kernel", "achieved": gbs, "peak": hbm,
-                    "unit": "GB/s", "frac": gbs / hbm, "traffic": traffic,
-                    "algorithmic_bytes_per_launch": bytes_vjp,
+            # algorithmic bytes per launch: forward 32 B per walk amplitude (value read and
+            # written) + 16 B per output; reverse walk 32 B per walk amplitude (adjoint read
+            # and written) + 16 B per upstream gradient; partial pass 32 B per walk amplitude
+            # (value and adjoint read)
+            alg = {"diag_forward_kernel": bytes_fwd,
+                   "diag_vjp_kernel": NCIRC * (32 * stored + 16 * nout),
+                   "diag_vjp_partials_kernel": NCIRC * 32 * stored}
+            per = {k: {"ms": kernel_ms[k], "achieved": alg[k] / (kernel_ms[k] * 1e-3) / 1e9,
+                       "frac": alg[k] / (kernel_ms[k] * 1e-3) / 1e9 / hbm,
+                       "algorithmic_bytes_per_launch": alg[k], "traffic": traffic.get(k)}
+                   for k in kernel_ms}
+            top = max(kernel_ms, key=kernel_ms.get)   # the dominant kernel
+            roof = {"bound": "hbm", "kernel": top, "achieved": per[top]["achieved"], "peak": hbm,
+                    "unit": "GB/s", "frac": per[top]["frac"], "traffic": per[top]["traffic"],
+                    "algorithmic_bytes_per_launch": alg[top],
                     "peak_source": hbm_src,
+                    "kernels": per,
                     "forward": {"achieved": bytes_fwd / (fwd_ms * 1e-3) / 1e9,
                                 "frac": bytes_fwd / (fwd_ms * 1e-3) / 1e9 / hbm,
                                 "algorithmic_bytes_per_launch": bytes_fwd},
@@ -445,7 +472,7 @@ def run_gpu(args):
         else:
             roof = {"bound": "alu", "kernel": "diag_vjp_kernel", "achieved": fp64_eq,
                     "peak": peak, "unit": "TFLOP/s", "frac": fp64_eq / peak,
-                    "traffic": traffic,
+                    "traffic": traffic.get("diag_vjp_kernel"),
                     "peak_source": "measured live: max of FP64 FMA-chain probe and cuBLAS DGEMM",
                     "peaks_measured": peaks, "peak_nominal": 1.25,
                     "forward": {"achieved": flops_fwd / (fwd_ms * 1e-3) / 1e12,
@@ -456,7 +483,7 @@ def run_gpu(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
             "data": "synthetic", "config": config_block(),
             "circuits_per_s": world * NCIRC / (ms * 1e-3),
-            "kernel_ms": {"diag_forward_kernel": fwd_ms, "diag_vjp_kernel": vjp_ms},
+            "kernel_ms": kernel_ms, "vjp_ms": vjp_ms,
             "e2e": {"value": amps / (e2e_ms * 1e-3), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             # forward: one launch; VJP: the reverse walk plus (tensor engine) the partial pass

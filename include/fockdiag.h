@@ -353,7 +353,7 @@ int fk_diag_set_tuning(int tpb, int ch, int blocks_per_sm);
  *   FK_ENGINE_TENSOR: the same sums on the bf16 tensor cores: every value is
  *     cut to a 56-bit fixed-point integer relative to a power of two shared
  *     by a row of A or by one pivot's reads, split into seven balanced
- *     base-256 digits (exact in bf16), and the digit products with digit
+ *     base-256 digits (exact in fp16), and the digit products with digit
  *     index sum <= 6 are accumulated exactly (integer partial sums below
  *     2^23 in fp32), recombined in int64 and scaled back with one rounding.
  *     The error is of the order of 2^-53 times the largest term of a sum,
@@ -362,12 +362,24 @@ int fk_diag_set_tuning(int tpb, int ch, int blocks_per_sm);
  *     partial dL/dA = sum_t Y(t) X(t)^H from digits too, after moving each
  *     pivot's power of two from its reads to its adjoints (products
  *     unchanged), so each term is exact relative to the largest product of
- *     its row.  Shapes with M > 8 use FP64.
+ *     its row.  With this engine the VJP is two launches on the stream:
+ *     the reverse walk, then the pass that forms the partial sums.  Shapes
+ *     with M > 8 use FP64.
  * Returns FK_EINVAL for another value.  Default FK_ENGINE_FP64.
  */
 #define FK_ENGINE_FP64 0
 #define FK_ENGINE_TENSOR 1
 int fk_diag_set_engine(int engine);
+
+/*
+ * Measurement hook (no counterpart in the paper): when `event` is a CUDA
+ * event (cudaEvent_t passed as a pointer), every following tensor-engine
+ * all-detected VJP records it on its stream between its two launches, so a
+ * caller can time the reverse walk and the partial-sum pass apart.  NULL
+ * switches the hook off (the default).  The caller keeps the event alive
+ * while the hook is set.  Process-wide; returns FK_OK.
+ */
+int fk_diag_set_vjp_split_event(void *event);
 
 /*
  * Reads the device-side status word of a workspace after the calls queued

@@ -584,6 +584,11 @@ int fk_diag_set_engine(int engine)
     return set_diag_engine(engine);
 }
 
+int fk_diag_set_vjp_split_event(void *event)
+{
+    return set_vjp_split_event(event);
+}
+
 int fk_workspace_status(const void *ws, void *stream, int *status)
 {
     if (!ws || !status) return FK_EINVAL;

@@ -113,6 +113,7 @@ int launch_cond_vjp(const CondPlan &plan, unsigned flags, const void *A, const v
 int set_diag_tuning(int tpb, int ch, int blocks_per_sm);
 // Product engine of the all-detected forward walk (FK_ENGINE_*).  Process-wide.
 int set_diag_engine(int engine);
+int set_vjp_split_event(void *event);
 
 // Launchers (walk_diag.cu).  All pointers are device pointers.
 int diag_grid_size(const DiagShape &sh, bool vjp, int *grid, int *slots = nullptr);

@@ -2123,6 +2123,18 @@ bool tc_engine_for(const DiagShape &sh)
 
 }  // namespace
 
+namespace {
+std::mutex g_split_mu;
+void *g_split_event = nullptr;   // cudaEvent_t recorded between the two VJP launches
+}  // namespace
+
+int set_vjp_split_event(void *event)
+{
+    std::lock_guard<std::mutex> lk(g_split_mu);
+    g_split_event = event;
+    return FK_OK;
+}
+
 int set_diag_engine(int engine)
 {
     if (engine != FK_ENGINE_FP64 && engine != FK_ENGINE_TENSOR) return FK_EINVAL;
@@ -2292,6 +2304,12 @@ int launch_diag_vjp(const DiagShape &sh, int batch, unsigned flags, const void *
         DiagArgs w = a;
         w.grid = per * sms;
         if ((rc = launch_coop(wfn, w.grid, wtpb, wsmem, &w, st)) != 0) return rc;
+        void *ev = nullptr;
+        {
+            std::lock_guard<std::mutex> lk(g_split_mu);
+            ev = g_split_event;
+        }
+        if (ev && cudaEventRecord((cudaEvent_t)ev, st) != cudaSuccess) return FK_ECUDA;
     }
     return launch_coop(fn, lay.grid_vjp, tpb, smem, &a, st);
 }

@@ -32,7 +32,7 @@ EXPORTS = [
     "fk_conditional_workspace_size", "fock_conditional_dm", "fock_conditional_dm_batched",
     "fock_conditional_dm_vjp", "fock_conditional_dm_vjp_batched",
     "fk_circuit_triple", "fk_circuit_triple_batched", "fk_mlp_sizes", "fk_mlp_load", "fk_mlp_forward", "fk_mlp_backward", "fk_mlp_train_step",
-    "fk_herald_scores", "fk_diag_set_tuning", "fk_diag_set_engine",
+    "fk_herald_scores", "fk_diag_set_tuning", "fk_diag_set_engine", "fk_diag_set_vjp_split_event",
     "fk_global_size", "fk_global_pattern_index", "fk_global_workspace_size",
     "fock_diag_probs_global_batched", "fock_diag_probs_global_vjp_batched",
     "fk_describe_global_schedule", "fock_diag_probs_stop_batched", "fock_diag_probs_stop_vjp_batched",
@@ -98,6 +98,7 @@ def lib():
         L.fock_pure_amplitudes_vjp_batched.argtypes = [I, P, P, P, I, P, P, P, P, P, U, P, Z, P]
         L.fk_diag_set_tuning.argtypes = [I, I, I]
         L.fk_diag_set_engine.argtypes = [I]
+        L.fk_diag_set_vjp_split_event.argtypes = [P]
         L.fk_herald_scores.argtypes = [I, P, P, I, P, ctypes.c_double, P, P, P, P]
         L.fk_circuit_triple.argtypes = [I, P, ctypes.c_double, P, P, P, P, P, P]
         L.fk_circuit_triple_batched.argtypes = [I, I, P, ctypes.c_double, P, P, P, P, P, P, I]
@@ -552,6 +553,14 @@ FK_ENGINE_FP64, FK_ENGINE_TENSOR = 0, 1
 
 
 def fk_diag_set_engine(engine):
-    """Product engine of the all-detected forward walk (FK_ENGINE_FP64 or
-    FK_ENGINE_TENSOR: exact base-256 digit products on the bf16 tensor cores)."""
+    """Product engine of the all-detected walk (FK_ENGINE_FP64 or
+    FK_ENGINE_TENSOR: exact base-256 digit products on the fp16 tensor cores)."""
     _check(lib().fk_diag_set_engine(int(engine)), "fk_diag_set_engine")
+
+
+def fk_diag_set_vjp_split_event(event=None):
+    """Measurement hook: record `event` (a torch.cuda.Event) between the two
+    launches of every following tensor-engine VJP; None switches it off.
+    The event must outlive the hook."""
+    handle = None if event is None else ctypes.c_void_p(event.cuda_event)
+    _check(lib().fk_diag_set_vjp_split_event(handle), "fk_diag_set_vjp_split_event")
