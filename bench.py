@@ -43,10 +43,10 @@ NCIRC = 16
 # in proportion to them.  Valid only for the kernel source it was measured on
 # (sha256 prefix of csrc/walk_diag.cu) and the engine / tile shape; reported
 # as null once either differs.
-TRAFFIC = {"kernel_sha": "3435c7c4cb1b2b2b", "tuning": ["tensor", 128, 4, 0],
-           "bytes_per_launch": {"diag_forward_kernel": 8 * (495086592 + 854074624),
-                                "diag_vjp_kernel": 8 * (704236288 + 806338560),
-                                "diag_vjp_partials_kernel": 8 * (1734099712 + 140261120)}}
+TRAFFIC = {"kernel_sha": "c16cafc3e648ca4b", "tuning": ["tensor", 128, 4, 0],
+           "bytes_per_launch": {"diag_forward_kernel": 8 * (495703808 + 853363712),
+                                "diag_vjp_kernel": 8 * (704155392 + 803061248),
+                                "diag_vjp_partials_kernel": 8 * (1733271808 + 136535296)}}
 
 FALLBACK_HBM_GBS = 6800.0
 

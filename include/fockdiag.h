@@ -350,7 +350,7 @@ int fk_diag_set_tuning(int tpb, int ch, int blocks_per_sm);
  * of Algorithm 1 is a row of A (restricted to the pivot's modes) times the
  * pivot's reads (eq. recrel with F = G / sqrt(k!)).
  *   FK_ENGINE_FP64:   complex128 DFMA (three real products per term).
- *   FK_ENGINE_TENSOR: the same sums on the bf16 tensor cores: every value is
+ *   FK_ENGINE_TENSOR: the same sums on the fp16 tensor cores: every value is
  *     cut to a 56-bit fixed-point integer relative to a power of two shared
  *     by a row of A or by one pivot's reads, split into seven balanced
  *     base-256 digits (exact in fp16), and the digit products with digit

@@ -9,18 +9,23 @@
 // of a sum carries the same factor sqrt(P!) relative to the original form,
 // so no read needs its own sqrt weight and each write is one complex
 // matrix-vector row times a reciprocal from a table.  Probabilities are
-// G_d = F_d * prod_j d_j!.  All FP arithmetic is IEEE complex128; each
-// complex multiply-accumulate is four DFMAs.
+// G_d = F_d * prod_j d_j!.  Values are IEEE complex128.  Two product engines:
+// FP64 (Gauss's three-multiplication complex product, 3 DFMA per term) and
+// the tensor-core engine (exact base-256 digit products on fp16 MMAs,
+// recombined in int64: the same sums with an error near 2^-53 of the
+// largest term).
 //
 // Parallel structure.  One cooperative persistent launch walks every level
 // s = 0..L-1 (pivot digit sum, Sec. 2.2: pivots of equal weight are
 // independent) for all circuits of the batch; a grid-wide barrier with a
 // time limit separates the phases.  A level is split into tiles of 128
-// pivots of one (anchor K, circuit) segment; a thread owns one pivot: it
-// gathers the pivot's reads into shared memory, runs the 2(M-K) x 2(M-K)
-// complex matrix-vector product against A held in shared memory, and
-// scatters the writes.  Output rows and read columns that no lane of a warp
-// needs are skipped with warp-uniform branches.
+// pivots of one (anchor K, circuit) segment, handed to blocks through a
+// counter; a thread owns one pivot: it takes the pivot's geometry (from a
+// table shared by the circuits when M <= 8), gathers its reads into shared
+// memory, runs the 2(M-K) x 2(M-K) complex matrix-vector product against A
+// held in shared memory, and scatters the writes.  The VJP runs the levels
+// backwards; with the tensor engine its partial dL/dA and dL/db sums are a
+// second launch over all pivots once the walk is done.
 #include <cuda_runtime.h>
 
 #include <mutex>
