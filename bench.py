@@ -43,10 +43,10 @@ NCIRC = 16
 # in proportion to them.  Valid only for the kernel source it was measured on
 # (sha256 prefix of csrc/walk_diag.cu) and the engine / tile shape; reported
 # as null once either differs.
-TRAFFIC = {"kernel_sha": "c16cafc3e648ca4b", "tuning": ["tensor", 128, 4, 0],
-           "bytes_per_launch": {"diag_forward_kernel": 8 * (495703808 + 853363712),
-                                "diag_vjp_kernel": 8 * (704155392 + 803061248),
-                                "diag_vjp_partials_kernel": 8 * (1733271808 + 136535296)}}
+TRAFFIC = {"kernel_sha": "97dc32c248256fc1", "tuning": ["tensor", 128, 4, 0],
+           "bytes_per_launch": {"diag_forward_kernel": 8 * (495558656 + 853413888),
+                                "diag_vjp_kernel": 8 * (703816704 + 802615296),
+                                "diag_vjp_partials_kernel": 8 * (1733378048 + 136373248)}}
 
 FALLBACK_HBM_GBS = 6800.0
 

@@ -287,13 +287,6 @@ struct Walk {
         return fk::unrank(sh.C, sh.M, ltab(sm), k0, dk0, s, rank);
     }
 
-    static __device__ __forceinline__ int64_t diag_index(const DiagShape &sh, const Dig &d, int k0)
-    {
-        int64_t idx = 0;
-        for (int i = k0; i < sh.M; ++i) idx += (int64_t)d(i) * sh.stride[i];
-        return idx;
-    }
-
     // Load A_s (symmetric part, kept modes) and b of one circuit into smem.
     // A is kept as three real planes for Gauss's three-multiplication complex
     // product: Re A, Re A + Im A and Im A - Re A.
@@ -918,11 +911,11 @@ struct Walk {
     }
 
     // Tiles of a phase are numbered circuit-major: circuit c, then segment k
-    // (anchor K for AP; one segment for DP and DIAG), then ceil(count / TPB)
-    // tiles; tiles[k] = prefix over k within one circuit, tiles[nseg] = tiles
-    // per circuit.  Blocks take tiles round robin, so at any moment the grid
+    // (anchor K for AP; one segment for DP), then ceil(count / TPB) tiles;
+    // tiles[k] = prefix over k within one circuit, tiles[nseg] = tiles per
+    // circuit.  Blocks take them in counter order, so at any moment the grid
     // works on one or two circuits and the reads that pivots of different
-    // anchors share stay in L2.  kind: 0 = AP, 1 = DP, 2 = DIAG.
+    // anchors share stay in L2.  kind: 0 = AP, 1 = DP.
     static __device__ int phase_tiles(const DiagArgs &a, Smem &s, int kind, int lev)
     {
         const DiagShape &sh = a.sh;
@@ -933,10 +926,7 @@ struct Walk {
             const int nseg = (kind == 0) ? sh.M : 1;
             for (int k = 0; k < nseg; ++k) {
                 s.tiles[k] = acc;
-                unsigned cnt;
-                if (kind == 0) cnt = level_count(sh, s, k, 1, lev);
-                else if (kind == 1) cnt = level_count(sh, s, 0, 1, lev);
-                else cnt = level_count(sh, s, 0, 0, lev);
+                const unsigned cnt = level_count(sh, s, kind == 0 ? k : 0, 1, lev);
                 acc += (int)((cnt + TPB - 1) / TPB);
             }
             s.tiles[nseg] = acc;
@@ -956,12 +946,8 @@ struct Walk {
         int k = 0;
         while (k + 1 < nseg && r >= s.tiles[k + 1]) ++k;
         t.seg = k;
-        unsigned cnt;
-        if (kind == 0) cnt = level_count(sh, s, k, 1, lev);
-        else if (kind == 1) cnt = level_count(sh, s, 0, 1, lev);
-        else cnt = level_count(sh, s, 0, 0, lev);
         t.rank0 = (unsigned)(r - s.tiles[k]) * TPB;
-        t.count = cnt;
+        t.count = level_count(sh, s, kind == 0 ? k : 0, 1, lev);
         return t;
     }
 
