@@ -229,10 +229,10 @@ static uint64_t encode(const walk_t *w, const int *x)
  * Detected part (Algorithm 1; App. B.2 types).  With excess e_j = x_{2j} -
  * x_{2j+1} over the detected modes j:
  *   e == 0 (diagonal d): K = first detected mode with x_{2K} > 0, w = 2K+1;
- *       P = (d - 1_K) + 1_{2K} is the off-diagonal pivot of line 10 whose
- *       earlier modes are all zero (line 8).
- *   e = +1_j or -1_j (type offset_1): w = 2j or 2j+1; P is the diagonal
- *       pivot of line 5.
+ *       P = (d - 1_K) + 1_{2K} is the off-diagonal pivot of Algorithm 1
+ *       whose earlier modes are all zero.
+ *   e = +1_j or -1_j (type offset_1): w = 2j or 2j+1; P is a diagonal
+ *       pivot of Algorithm 1.
  *   e = +2_K (offset_2): w = 2K; e_K = +1, e_i = +1, K < i (offset_1010):
  *   w = 2i; e_K = +1, e_i = -1, K < i (offset_1001): w = 2i+1.  These are
  *   the writes of the off-diagonal pivot anchored at K.

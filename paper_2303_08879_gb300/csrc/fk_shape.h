@@ -29,10 +29,11 @@
 //
 // Pivots (Algorithm 1):
 //   AP(K) off-diagonal pivot e + 1_{2K}, modes < K zero, e_K in [0, C_K-2]
-//         (lines 6-10).  Reads e (DIAG), T2(K)[e-1_K], P1001(K,n)[e-1_n],
+//         (the off-diagonal pivots of Algorithm 1).  Reads e (DIAG), T2(K)[e-1_K], P1001(K,n)[e-1_n],
 //         P1010(K,n)[e-1_n] (n > K) and, if b != 0, its own value T1K(K)[e];
 //         writes T2(K)[e], DIAG[e+1_K], P1010(K,m)[e], P1001(K,m)[e].
-//   DP    diagonal pivot d with d_0 in [0, C_0-2] (lines 3-5), b != 0 only.
+//   DP    diagonal pivot d with d_0 in [0, C_0-2] (the diagonal pivots of
+//         Algorithm 1), b != 0 only.
 //         Reads T1B(j)[d-1_j], T1K(j)[d-1_j] and its value DIAG[d]; writes
 //         T1K(j)[d], T1B(j)[d].
 // The level of a pivot is its digit sum s = |e| (|d|); level s reads

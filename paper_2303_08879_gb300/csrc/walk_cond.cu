@@ -12,7 +12,7 @@
 // Step 1 (zero photons detected): one block per circuit runs eq. (recrel)
 // over the undetected sub-lattice level by level.  Step 2: the detected
 // levels of Algorithm 1 (diagonal pivots, then off-diagonal pivots), each
-// pivot applied to every u of its block (Algorithm 2, lines 5 and 11); a
+// pivot applied to every u of its block (Algorithm 2); a
 // thread owns one (pivot, u) pair and reads (u, P - 1_l) for detected l,
 // (u - 1_t, P) for undetected t and, when b != 0, (u, P).  All pairs of one
 // detected level are independent.
