@@ -303,6 +303,31 @@ def secondary_rows(torch, fd, inputs, dev, reps=5):
     return rows
 
 
+# ------------------------------------------------------------- multi-rank
+def rank_circuits(rank, n):
+    """The n circuits of rank `rank`: consecutive, disjoint slices of the
+    workload, so the work per GPU is fixed as ranks are added (weak scaling)."""
+    from paper_2303_08879_gb300 import inputs
+    return inputs.workload(WORKLOAD, n, start=rank * n)
+
+
+def max_over_ranks(x, device):
+    """The largest of a per-rank time over all ranks (x itself on one rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, n_per_rank, units_per_circuit, ms):
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time per step."""
+    return world * n_per_rank * units_per_circuit / (ms * 1e-3)
+
+
 def run_gpu(args):
     if not args.no_cpu_baseline and int(os.environ.get("WORLD_SIZE", "1")) == 1:
         import oracle                  # compile the oracle before any CUDA work
@@ -323,7 +348,7 @@ def run_gpu(args):
         if world > 1:
             dist.barrier()
 
-    circs = inputs.workload(WORKLOAD, NCIRC, start=rank * NCIRC)
+    circs = rank_circuits(rank, NCIRC)
     cut = circs[0].cutoffs
     M = len(cut)
     trip = [fd.fk_gaussian_to_triple(c.V, c.mean) for c in circs]
@@ -397,10 +422,7 @@ def run_gpu(args):
                      "diag_vjp_partials_kernel": part_ms}
     else:
         kernel_ms = {"diag_forward_kernel": fwd_ms, "diag_vjp_kernel": vjp_ms}
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dev)
 
     # end to end through the public API, pinned host buffers in and out
     gA_h, gb_h, gc_h = (torch.empty_like(x, device="cpu").pin_memory() for x in (A_h, b_h, c_h))
@@ -421,15 +443,11 @@ def run_gpu(args):
     u1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = u0.elapsed_time(u1) / args.steps
-    if world > 1:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_ms, dev)
     fd.check_workspace(ws, where="e2e steps")
 
     h2d = sum(x.numel() * x.element_size() for x in (A_h, b_h, c_h, w_h))
     d2h = sum(x.numel() * x.element_size() for x in (gA_h, gb_h, gc_h))
-    amps = world * NCIRC * int(np.prod(cut))
     out = None
     if rank == 0:
         flops_fwd = NCIRC * algorithmic_flops(cut)
@@ -478,13 +496,14 @@ def run_gpu(args):
                     "forward": {"achieved": flops_fwd / (fwd_ms * 1e-3) / 1e12,
                                 "frac": flops_fwd / (fwd_ms * 1e-3) / 1e12 / peak}}
         out = {
-            "metric": METRIC, "value": amps / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+            "metric": METRIC, "value": job_rate(world, NCIRC, int(np.prod(cut)), ms), "unit": UNIT,
+            "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
             "data": "synthetic", "config": config_block(),
             "circuits_per_s": world * NCIRC / (ms * 1e-3),
             "kernel_ms": kernel_ms, "vjp_ms": vjp_ms,
-            "e2e": {"value": amps / (e2e_ms * 1e-3), "unit": UNIT,
+            "e2e": {"value": job_rate(world, NCIRC, int(np.prod(cut)), e2e_ms), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             # forward: one launch; VJP: the reverse walk plus (tensor engine) the partial pass
             "gpu_launches": (3 if tuning["engine"] == "tensor" else 2) * args.steps,
