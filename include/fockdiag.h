@@ -224,8 +224,10 @@ int fock_conditional_dm_vjp_batched(int batch, const fk_c128 *d_A, const fk_c128
  * inputs and the probabilities output (device pointers, as above).
  *   - Calls whose workspace would exceed FK_STATIC_WORKSPACE_BYTES return
  *     FK_EWORKSPACE (fk_workspace_size with FK_OP_DIAG gives the need).
- *   - The first call on a GPU looks up the array's device address (with that
- *     GPU current); make that first call before any stream capture.
+ *   - Every call looks up the array's device address in the current GPU's
+ *     context (cudaGetSymbolAddress, which allocates nothing); the first call
+ *     on a GPU may load the library's kernels onto it, so make that first
+ *     call before any stream capture.
  *   - Every call on a GPU shares the one array: calls that overlap on the
  *     GPU (different streams or threads without ordering) race and corrupt
  *     each other.  Calls are otherwise stream-ordered like the others.

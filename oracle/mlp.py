@@ -70,8 +70,12 @@ def forward(params, x, mode="exact"):
     return y, (a0, z1, a1, z2, a2, z3, a3, W1, W2, W3, W4)
 
 
-def backward(params, x, gy, mode="exact"):
-    """Packed gradient of sum(gy * y) with respect to the parameters."""
+def backward(params, x, gy, mode="exact", return_terms=False):
+    """Packed gradient of sum(gy * y) with respect to the parameters.
+
+    With ``return_terms`` also the factors of each weight-gradient sum over
+    the batch, [(g_l, a_{l-1})] for l = 4, 3, 2, 1 (gW_l = g_l^T a_{l-1},
+    gb_l = sum_k g_l[k]), for tests that size tolerances per entry."""
     r = bf16 if mode == "bf16" else (lambda a: np.asarray(a, np.float64))
     _, (a0, z1, a1, z2, a2, z3, a3, W1, W2, W3, W4) = forward(params, x, mode)
     g = r(gy)
@@ -86,7 +90,10 @@ def backward(params, x, gy, mode="exact"):
     g1 = r((g2 @ W2) * dsilu(z1))
     gW1 = g1.T @ a0
     gb1 = g1.sum(0)
-    return np.concatenate([gW1.ravel(), gb1, gW2.ravel(), gb2, gW3.ravel(), gb3, gW4.ravel(), gb4])
+    packed = np.concatenate([gW1.ravel(), gb1, gW2.ravel(), gb2, gW3.ravel(), gb3, gW4.ravel(), gb4])
+    if return_terms:
+        return packed, [(g, a3), (g3, a2), (g2, a1), (g1, a0)]
+    return packed
 
 
 def loss(params, x, t, mode="exact"):

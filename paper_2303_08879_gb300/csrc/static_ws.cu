@@ -4,13 +4,13 @@
 //
 // The array below is device memory reserved when the library is loaded onto a
 // GPU and kept until the process exits.  Host code must not use its name as a
-// pointer: on the host that name only stands in for the device symbol.  The
-// device address is looked up once per GPU with cudaGetSymbolAddress (with
-// that GPU current) and cached; the walk kernel then receives that address
-// exactly as it would receive a caller-supplied workspace.
+// pointer: on the host that name only stands in for the device symbol.  Every
+// call looks the device address up with cudaGetSymbolAddress on the current
+// GPU (a lookup, no allocation), so an address never outlives the context it
+// came from (after cudaDeviceReset the module is loaded again, possibly at
+// another address); the walk kernel then receives that address exactly as it
+// would receive a caller-supplied workspace.
 #include <cuda_runtime.h>
-
-#include <mutex>
 
 #include "fk_internal.h"
 #include "../../include/fockdiag.h"
@@ -21,23 +21,12 @@ constexpr size_t kStaticBytes = (size_t)FK_STATIC_WORKSPACE_BYTES;
 
 static __device__ __align__(256) unsigned char g_static_ws[kStaticBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void *g_addr[kMaxDevices] = {nullptr};
-
-// Device address of g_static_ws on the current GPU (looked up on first use).
+// Device address of g_static_ws in the current GPU's context.
 int static_workspace(void **out)
 {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return FK_ECUDA;
-    if (dev < 0 || dev >= kMaxDevices) return FK_EUNSUPPORTED;
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_static_ws) != cudaSuccess || !p) return FK_ECUDA;
-        g_addr[dev] = p;
-    }
-    *out = g_addr[dev];
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_static_ws) != cudaSuccess || !p) return FK_ECUDA;
+    *out = p;
     return FK_OK;
 }
 

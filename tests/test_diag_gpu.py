@@ -44,10 +44,17 @@ def assert_amp_close(got, ref):
 
 
 def assert_grad_close(got, ref, what):
+    """Every entry within 1e-8 of itself where |ref| > 1e-12 max(1, max|ref|);
+    the structural zeros below that floor within the floor."""
     got = np.asarray(got); ref = np.asarray(ref)
-    scale = max(np.max(np.abs(ref)), 1e-300)
-    err = np.max(np.abs(got - ref)) / scale
-    assert err <= VJP_RTOL, f"{what}: relative error {err:.3e}"
+    floor = 1e-12 * max(1.0, float(np.max(np.abs(ref))))
+    err = np.abs(got - ref)
+    big = np.abs(ref) > floor
+    if big.any():
+        worst = np.max(err[big] / np.abs(ref[big]))
+        assert worst <= VJP_RTOL, f"{what}: per-entry relative error {worst:.3e}"
+    if (~big).any():
+        assert np.max(err[~big]) <= floor, f"{what}: absolute error {np.max(err[~big]):.3e}"
 
 
 def gpu_probs(fd, A, b, c, cut, flags=0):
@@ -149,14 +156,22 @@ def oracle_vjp(A, b, c, cut, gbar_probs):
 
 
 VJP_CASES = [((4, 3), True), ((3, 3, 3), False), ((3, 4, 2), True), ((2, 1, 3), True),
-             ((5,), True), ((2, 2, 2, 2), False), ((4, 4), False)]
+             ((5,), True), ((2, 2, 2, 2), False), ((4, 4), False),
+             # five to nine modes (the 8-mode benchmark's shape class; nine
+             # modes is beyond the tensor engine's compiled shapes)
+             ((2, 3, 2, 2, 3), False), ((3, 2, 2, 2, 2, 3), True), ((2, 2, 2, 2, 2, 2, 2), True),
+             ((2, 2, 2, 2, 2, 2, 2, 3), False), ((2, 2, 2, 2, 2, 2, 2, 3), True),
+             ((3, 3, 2, 2, 2, 2, 2, 2), False), ((2, 2, 2, 2, 2, 2, 2, 2, 2), True)]
 
 
 @pytest.mark.parametrize("cut,withb", VJP_CASES)
 def test_vjp_matches_oracle_gradient(fd, cut, withb):
-    rng = np.random.default_rng(100 + sum(cut))
+    """Every gradient entry against the oracle's closed-form VJP of the full
+    density matrix (Sec. 2.5), FP64 engine."""
+    fd.fk_diag_set_engine(fd.FK_ENGINE_FP64)
+    rng = np.random.default_rng(100 + sum(cut) + 31 * len(cut))
     D = 2 * len(cut)
-    A, b = inputs.random_symmetric(D, rng, with_b=withb)
+    A, b = inputs.random_symmetric(D, rng, scale=0.2 if len(cut) <= 4 else 0.12, with_b=withb)
     c = 0.8 - 0.1j
     gbar = rng.normal(size=cut) + 1j * rng.normal(size=cut)
     rA, rb, rc = oracle_vjp(A, b, c, cut, gbar)

@@ -86,3 +86,36 @@ def test_trained_network_beats_random_starts(prop):
     # the network's picks, verified by the exact walk, beat random picks
     assert np.median(J_mlp) > np.median(J_rnd)
     assert J_mlp.max() > J_rnd.max()
+
+
+def test_heralded_block_does_not_depend_on_detected_cutoffs(prop):
+    """The learned workload's stated detected cutoffs are C = 15, 15 (with the
+    undetected mode at C = 40); the proposal loop walks with C = n* + 1 =
+    (4, 4).  An amplitude is a coefficient of the generating function
+    c exp(z^T A z / 2 + b^T z) (Sec. 2.1), which no cutoff enters, and each is
+    computed from the same parent and reads whatever the box, so the heralded
+    block rho(n* = (3, 3)) and every pattern below (4, 4) agree between the
+    two walks up to rounding order.  Checked on 8 random circuits of the
+    15-parameter family in one batched launch each."""
+    from paper_2303_08879_gb300 import fockdiag as fd
+    task = prop.HeraldTask()
+    theta = task.sample(8, np.random.default_rng(44))
+    A, b, c = task.triples(theta)[:3]
+    Ad = torch.as_tensor(A).cuda(); bd = torch.as_tensor(b).cuda(); cd = torch.as_tensor(c).cuda()
+    blocks = {}
+    for cut in ((4, 4, 40), (15, 15, 40)):
+        rho, _, ws = fd.fock_conditional_dm_batched(Ad, bd, cd, [cut] * 8, task.mask, for_vjp=False)
+        fd.check_workspace(ws)
+        blocks[cut] = [x.cpu().numpy() for x in fd.conditional_blocks(rho, [cut] * 8, task.mask)]
+    for i in range(8):
+        small, big = blocks[(4, 4, 40)][i], blocks[(15, 15, 40)][i]
+        for n0 in range(4):
+            for n1 in range(4):
+                s = small[n0 * 4 + n1]
+                g = big[n0 * 15 + n1]
+                scale = max(float(np.max(np.abs(s))), 1e-300)
+                assert np.max(np.abs(s - g)) <= 1e-13 * scale, (i, n0, n1)
+        # the heralded block itself, entry by entry
+        s, g = small[3 * 4 + 3], big[3 * 15 + 3]
+        big_entries = np.abs(s) > 1e-12 * np.max(np.abs(s))
+        assert np.all(np.abs(s - g)[big_entries] <= 1e-12 * np.abs(s)[big_entries])

@@ -26,20 +26,52 @@ def _blocks(v):
     return out
 
 
+def _rss_tolerance(ref, rss, k=2.0 ** -5, floor=1e-5):
+    """Per-entry bound k * rss + floor * max|ref|.  The GPU and the reference
+    round to bf16 at the same points; they differ by FP32 against FP64
+    accumulation and by the few stored bf16 values that round the other way
+    (one bf16 ulp, 2^-8 relative, of single terms of a sum), so an entry's
+    error is a small multiple of 2^-8 times the root sum of squares of its
+    terms.  A wrong entry (a dropped, swapped or misplaced term or row) is off
+    by the size of the entry itself, which for a sum of B random-sign terms is
+    of the order of that root sum of squares: far above k = 2^-5."""
+    return k * rss + floor * float(np.max(np.abs(ref)))
+
+
+def _assert_entries(got, ref, rss, what):
+    got = np.asarray(got); ref = np.asarray(ref)
+    assert got.shape == ref.shape
+    tol = _rss_tolerance(ref, rss)
+    bad = np.abs(got - ref) > tol
+    assert not bad.any(), (f"{what}: {int(bad.sum())} of {bad.size} entries off, worst "
+                           f"{np.max(np.abs(got - ref) / tol):.2f} x tolerance")
+
+
 @pytest.mark.parametrize("B", [1, 37, 256, 1000, 20000])   # 20000: split-K weight gradients
 def test_forward_backward_match_reference(mlpmod, B):
+    """Every output and every entry of every weight and bias gradient against
+    the CPU reference with the same bf16 rounding points."""
     rng = np.random.default_rng(B)
     p = mlpmod.init_params(B)
     x = rng.uniform(-1, 1, size=(B, om.IN)).astype(np.float32)
     gy = rng.normal(size=(B, om.OUT)).astype(np.float32)
     m = mlpmod.MLP(p, max(B, 64))
     y = m.forward(torch.as_tensor(x)).cpu().numpy()
-    yr, _ = om.forward(p, x, "bf16")
-    assert np.max(np.abs(y - yr)) <= 2e-2 * np.max(np.abs(yr)) + 1e-6
+    yr, cache = om.forward(p, x, "bf16")
+    a3, W4 = cache[6], cache[10]
+    b4 = om.unpack(p)[7]
+    _assert_entries(y, yr, np.sqrt((a3 ** 2) @ (W4 ** 2).T + b4 ** 2), "y")
     g = m.backward(torch.as_tensor(x), torch.as_tensor(gy)).cpu().numpy()
-    gr = om.backward(p, x, gy, "bf16")
-    for a, b in zip(_blocks(g), _blocks(gr)):
-        assert np.linalg.norm(a - b) <= 3e-2 * np.linalg.norm(b) + 1e-6
+    gr, terms = om.backward(p, x, gy, "bf16", return_terms=True)
+    gblocks, rblocks = _blocks(g), _blocks(gr)
+    # block order: W1, b1, W2, b2, W3, b3, W4, b4; terms are listed from layer 4 down
+    for layer, (gl, al) in zip((4, 3, 2, 1), terms):
+        iw = 2 * (layer - 1)
+        shape = (gl.shape[1], al.shape[1])
+        _assert_entries(gblocks[iw].reshape(shape), rblocks[iw].reshape(shape),
+                        np.sqrt((gl ** 2).T @ (al ** 2)), f"grad W{layer}")
+        _assert_entries(gblocks[iw + 1], rblocks[iw + 1], np.sqrt(np.sum(gl ** 2, axis=0)),
+                        f"grad b{layer}")
 
 
 def test_training_reduces_loss(mlpmod):

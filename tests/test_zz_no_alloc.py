@@ -59,10 +59,19 @@ def test_static_workspace_matches_caller_workspace(fd):
         ref, ws = fd.fock_diag_probs_batched(A, b, c, cut, flags=flags, for_vjp=False)
         fd.check_workspace(ws)
         ref = ref.cpu().numpy()
-        for _ in range(2):                          # two calls in a row
-            out = torch.full((3,) + cut, float("nan"), dtype=torch.complex128, device="cuda")
+        outs = [torch.full((3,) + cut, float("nan"), dtype=torch.complex128, device="cuda")
+                for _ in range(3)]
+        rc, st = _static_call(fd, A, b, c, cut, outs[0], flags)   # loads the kernels
+        assert rc == 0 and st == 0
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        for out in outs[1:]:                        # two calls in a row
             rc, st = _static_call(fd, A, b, c, cut, out, flags)
             assert rc == 0 and st == 0
+        torch.cuda.synchronize()
+        # no device memory was allocated by the two calls
+        assert torch.cuda.mem_get_info()[0] == free0
+        for out in outs:
             _close(out.cpu().numpy(), ref)
 
 
