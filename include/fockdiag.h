@@ -54,7 +54,7 @@ typedef enum {
     FK_ENOMEM = 4,         /* host allocation failed */
     FK_ECUDA = 5,          /* a CUDA runtime call or launch failed */
     FK_ETIMEOUT = 6,       /* a device-side barrier wait exceeded its time limit */
-    FK_ENONFINITE = 7,     /* reserved: NaN/Inf in the inputs */
+    FK_ENONFINITE = 7,     /* FK_FLAG_CHECK_FINITE found a NaN or Inf in A, b or c */
     FK_EBZERO = 8          /* FK_FLAG_B_ZERO was given but b has a nonzero entry */
 } fk_status;
 
@@ -78,6 +78,21 @@ typedef enum {
                                   device (FK_EBZERO). */
 #define FK_FLAG_RECOMPUTE 2u   /* VJP: run the forward walk first instead of
                                   reusing the state left in the workspace */
+#define FK_FLAG_ENGINE_FP64   0x10u   /* this call: FP64 product engine of the
+                                         all-detected walk (see fk_diag_set_engine) */
+#define FK_FLAG_ENGINE_TENSOR 0x20u   /* this call: tensor-core product engine
+                                         (M <= 8 after dropping C_j = 1 modes) */
+#define FK_FLAG_CHECK_FINITE  0x40u   /* scan A, b and c on the device before the
+                                         walk; on a NaN or Inf the workspace
+                                         status word becomes FK_ENONFINITE, the
+                                         walk kernels return at once and the
+                                         outputs are left unwritten.  The call
+                                         itself returns FK_OK (the scan is
+                                         stream-ordered); read the status with
+                                         fk_workspace_status. */
+/* Bits 8..17 of flags: a per-call tile shape of the all-detected walk made by
+ * fk_diag_tuning_flags (0 = the process default of fk_diag_set_tuning). */
+#define FK_FLAG_TILE_MASK 0x3ff00u
 
 /* Human-readable text for a status code (static storage). */
 const char *fk_status_string(int status);
@@ -335,20 +350,36 @@ int fock_diag_probs_global_vjp_batched(int batch, const fk_c128 *d_A, const fk_c
 int fk_describe_global_schedule(int M, int n_max, unsigned flags, int64_t *out, int out_len);
 
 /*
- * Tile shape of the all-detected walk kernels, process-wide (the paper has
- * no counterpart: the autotuner in paper_2303_08879_gb300/autotune.py times
- * the shapes on the caller's workload and sets the fastest).  tpb = pivots
- * per tile (64, 128 or 256), ch = output rows per register chunk (4 or 8;
- * compiled pairs: 128/8, 128/4, 64/8, 64/4, 256/8), blocks_per_sm = cap on
- * resident blocks per SM (0 = as many as fit).  tpb = ch = 0 restores the
- * default 128/8.  Workspaces must be sized (fk_workspace_size) after the
- * setting they run with; a VJP launched with a different setting returns
- * FK_EWORKSPACE.
+ * Tile shape of the all-detected walk kernels, process-wide default (the
+ * paper has no counterpart: the autotuner in paper_2303_08879_gb300/
+ * autotune.py times the shapes on the caller's workload and sets the
+ * fastest).  tpb = pivots per tile (64, 128 or 256), ch = output rows per
+ * register chunk (4 or 8; compiled pairs: 128/8, 128/4, 64/8, 64/4, 256/8),
+ * blocks_per_sm = cap on resident blocks per SM (0 = as many as fit).
+ * tpb = ch = 0 restores the default 128/8.  The shape applies to the FP64
+ * engine (the tensor engine has one shape).  Workspaces must be sized
+ * (fk_workspace_size) with the setting and flags they run with; a VJP
+ * launched with a different setting returns FK_EWORKSPACE.
+ *
+ * The process-wide defaults (this call and fk_diag_set_engine) are guarded
+ * by a lock and read once per call.  Callers that share a process and want
+ * different settings pass them per call in `flags` instead: the engine bits
+ * FK_FLAG_ENGINE_* and the tile bits from fk_diag_tuning_flags, which take
+ * precedence over the defaults and involve no shared state.
  */
 int fk_diag_set_tuning(int tpb, int ch, int blocks_per_sm);
 
 /*
- * Product engine of the all-detected forward walk, process-wide.  Each write
+ * Per-call form of fk_diag_set_tuning / fk_diag_set_engine: *flags_out gets
+ * the bits (engine FK_ENGINE_*, tile shape tpb/ch, blocks_per_sm cap) to OR
+ * into the flags of fock_diag_probs*_batched, their VJPs and
+ * fk_workspace_size.  tpb = ch = 0 keeps the process-default shape.
+ * FK_EINVAL for a shape that is not compiled or a cap outside 0..32.
+ */
+int fk_diag_tuning_flags(int engine, int tpb, int ch, int blocks_per_sm, unsigned *flags_out);
+
+/*
+ * Product engine of the all-detected walk, process-wide default.  Each write
  * of Algorithm 1 is a row of A (restricted to the pivot's modes) times the
  * pivot's reads (eq. recrel with F = G / sqrt(k!)).
  *   FK_ENGINE_FP64:   complex128 DFMA (three real products per term).
@@ -367,10 +398,15 @@ int fk_diag_set_tuning(int tpb, int ch, int blocks_per_sm);
  *     its row.  With this engine the VJP is two launches on the stream:
  *     the reverse walk, then the pass that forms the partial sums.  Shapes
  *     with M > 8 use FP64.
- * Returns FK_EINVAL for another value.  Default FK_ENGINE_FP64.
+ *   FK_ENGINE_AUTO:   the tensor engine where it applies (M <= 8 kept
+ *     modes), else FP64.  The default: on GB300 the tensor engine runs the
+ *     8-mode forward + VJP about 2.9 times faster than the best FP64 shape.
+ * Returns FK_EINVAL for another value.  Per call, FK_FLAG_ENGINE_FP64 and
+ * FK_FLAG_ENGINE_TENSOR override this default.
  */
 #define FK_ENGINE_FP64 0
 #define FK_ENGINE_TENSOR 1
+#define FK_ENGINE_AUTO 2
 int fk_diag_set_engine(int engine);
 
 /*

@@ -101,8 +101,9 @@ int build_diag_shape(int M, const int *cutoffs, bool has_b, DiagShape *sh)
     return FK_OK;
 }
 
-int diag_layout(const DiagShape &sh, int batch, bool vjp, DiagLayout *lay)
+int diag_layout(const DiagShape &sh, int batch, bool vjp, unsigned flags, DiagLayout *lay)
 {
+    if (int rc = check_diag_flags(flags)) return rc;
     const size_t B = (size_t)batch, D = 2 * (size_t)sh.M;
     const size_t c16 = 16;
     size_t o = 0;
@@ -121,7 +122,7 @@ int diag_layout(const DiagShape &sh, int batch, bool vjp, DiagLayout *lay)
     if (vjp) {
         int grid = 1, slots = 1;
         if (sh.M > 0) {
-            int rc = diag_grid_size(sh, true, &grid, &slots);
+            int rc = diag_grid_size(sh, true, flags, &grid, &slots);
             if (rc) return rc;
         }
         lay->grid_vjp = grid;
@@ -420,7 +421,7 @@ int fk_workspace_size(int M, const int *cutoffs, const unsigned char *mask, int 
         int rc = build_diag_shape(M, cutoffs, !(flags & FK_FLAG_B_ZERO), &sh);
         if (rc) return rc;
         DiagLayout lay;
-        rc = diag_layout(sh, batch, op == FK_OP_DIAG_VJP, &lay);
+        rc = diag_layout(sh, batch, op == FK_OP_DIAG_VJP, flags, &lay);
         if (rc) return rc;
         *bytes = lay.total;
         return FK_OK;
@@ -532,7 +533,7 @@ int fock_diag_probs_batched(int batch, const fk_c128 *A, const fk_c128 *b, const
     int rc = build_diag_shape(M, cutoffs, !(flags & FK_FLAG_B_ZERO), &sh);
     if (rc) return rc;
     DiagLayout lay;
-    rc = diag_layout(sh, batch, false, &lay);
+    rc = diag_layout(sh, batch, false, flags, &lay);
     if (rc) return rc;
     if (ws_bytes < lay.total || !aligned(ws)) return FK_EWORKSPACE;
     return launch_diag_forward(sh, batch, flags, A, b, c, probs, ws, lay, stream);
@@ -554,7 +555,7 @@ int fock_diag_probs_vjp_batched(int batch, const fk_c128 *A, const fk_c128 *b, c
     int rc = build_diag_shape(M, cutoffs, !(flags & FK_FLAG_B_ZERO), &sh);
     if (rc) return rc;
     DiagLayout lay;
-    rc = diag_layout(sh, batch, true, &lay);
+    rc = diag_layout(sh, batch, true, flags, &lay);
     if (rc) return rc;
     if (ws_bytes < lay.total || !aligned(ws)) return FK_EWORKSPACE;
     if (flags & FK_FLAG_RECOMPUTE) {
@@ -582,6 +583,11 @@ int fk_diag_set_tuning(int tpb, int ch, int blocks_per_sm)
 int fk_diag_set_engine(int engine)
 {
     return set_diag_engine(engine);
+}
+
+int fk_diag_tuning_flags(int engine, int tpb, int ch, int blocks_per_sm, unsigned *flags_out)
+{
+    return diag_tuning_flags(engine, tpb, ch, blocks_per_sm, flags_out);
 }
 
 int fk_diag_set_vjp_split_event(void *event)
@@ -670,7 +676,7 @@ int fk_global_workspace_size(int batch, int M, int n_max, int op, unsigned flags
     int rc = build_global_shape(M, n_max, !(flags & FK_FLAG_B_ZERO), &sh);
     if (rc) return rc;
     DiagLayout lay;
-    rc = diag_layout(sh, batch, op == FK_OP_DIAG_VJP, &lay);
+    rc = diag_layout(sh, batch, op == FK_OP_DIAG_VJP, flags, &lay);
     if (rc) return rc;
     *bytes = lay.total;
     return FK_OK;
@@ -685,7 +691,7 @@ int fock_diag_probs_global_batched(int batch, const fk_c128 *A, const fk_c128 *b
     int rc = build_global_shape(M, n_max, !(flags & FK_FLAG_B_ZERO), &sh);
     if (rc) return rc;
     DiagLayout lay;
-    rc = diag_layout(sh, batch, false, &lay);
+    rc = diag_layout(sh, batch, false, flags, &lay);
     if (rc) return rc;
     if (ws_bytes < lay.total || !aligned(ws)) return FK_EWORKSPACE;
     return launch_diag_forward(sh, batch, flags, A, b, c, probs, ws, lay, stream);
@@ -701,7 +707,7 @@ int fock_diag_probs_global_vjp_batched(int batch, const fk_c128 *A, const fk_c12
     int rc = build_global_shape(M, n_max, !(flags & FK_FLAG_B_ZERO), &sh);
     if (rc) return rc;
     DiagLayout lay;
-    rc = diag_layout(sh, batch, true, &lay);
+    rc = diag_layout(sh, batch, true, flags, &lay);
     if (rc) return rc;
     if (ws_bytes < lay.total || !aligned(ws)) return FK_EWORKSPACE;
     if (flags & FK_FLAG_RECOMPUTE) {
@@ -743,7 +749,7 @@ int fock_diag_probs_stop_batched(int batch, const fk_c128 *A, const fk_c128 *b, 
     int rc = build_diag_shape(M, cutoffs, !(flags & FK_FLAG_B_ZERO), &sh);
     if (rc) return rc;
     DiagLayout lay;
-    rc = diag_layout(sh, batch, false, &lay);
+    rc = diag_layout(sh, batch, false, flags, &lay);
     if (rc) return rc;
     if (ws_bytes < lay.total || !aligned(ws)) return FK_EWORKSPACE;
     const EarlyStop es{eps, levels};
@@ -761,7 +767,7 @@ int fock_diag_probs_stop_vjp_batched(int batch, const fk_c128 *A, const fk_c128 
     int rc = build_diag_shape(M, cutoffs, !(flags & FK_FLAG_B_ZERO), &sh);
     if (rc) return rc;
     DiagLayout lay;
-    rc = diag_layout(sh, batch, true, &lay);
+    rc = diag_layout(sh, batch, true, flags, &lay);
     if (rc) return rc;
     if (ws_bytes < lay.total || !aligned(ws)) return FK_EWORKSPACE;
     const EarlyStop es{eps, nullptr};

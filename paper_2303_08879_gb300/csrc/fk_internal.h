@@ -16,7 +16,9 @@ struct Control {
     unsigned bar_count;  // grid barrier arrivals
     unsigned bar_gen;    // grid barrier generation
     unsigned wait_flag;  // self-test flag that nothing sets
-    int pad[59];
+    int skip;            // set by the input scan (FK_FLAG_CHECK_FINITE) before the walk:
+                         // every walk kernel of the call returns at once
+    int pad[58];
 };
 static_assert(sizeof(Control) == 256, "control block is 256 bytes");
 
@@ -52,7 +54,7 @@ struct DiagLayout {
     size_t ctl, lvl, ctr, As, bs, dig, geo, F, Fbar, scratch, partA, partb, total;
     int grid_vjp, slots_vjp;
 };
-int diag_layout(const DiagShape &sh, int batch, bool vjp, DiagLayout *lay);
+int diag_layout(const DiagShape &sh, int batch, bool vjp, unsigned flags, DiagLayout *lay);
 
 // ------------------------------------------------------- conditional walk
 // Algorithm 2 (Sec. 3.2): undetected modes keep their full (ket, bra) index
@@ -109,14 +111,15 @@ int launch_cond_vjp(const CondPlan &plan, unsigned flags, const void *A, const v
                     const CondLayout &lay, void *stream);
 
 // Tile shape of the all-detected walk (pivots per tile, output rows per
-// register chunk, blocks per SM; 0 = as many as fit).  Process-wide.
+// register chunk, blocks per SM; 0 = as many as fit).  Process-wide default;
+// the flag bits of a call override it.
 int set_diag_tuning(int tpb, int ch, int blocks_per_sm);
 // Product engine of the all-detected forward walk (FK_ENGINE_*).  Process-wide.
 int set_diag_engine(int engine);
 int set_vjp_split_event(void *event);
 
 // Launchers (walk_diag.cu).  All pointers are device pointers.
-int diag_grid_size(const DiagShape &sh, bool vjp, int *grid, int *slots = nullptr);
+int diag_grid_size(const DiagShape &sh, bool vjp, unsigned flags, int *grid, int *slots = nullptr);
 // Early stop on the probability sum (Sec. 2.3): the pivots of a circuit stop
 // once its probabilities with at most `level` photons sum to >= 1 - eps.
 struct EarlyStop {
@@ -131,6 +134,13 @@ int launch_diag_vjp(const DiagShape &sh, int batch, unsigned flags, const void *
                     void *gc, void *ws, const DiagLayout &lay, void *stream,
                     const EarlyStop *es = nullptr);
 int launch_wait_selftest(void *ws, unsigned long long timeout_ns, void *stream);
+// FK_FLAG_CHECK_FINITE: scan n_A, n_b, n_c complex values of A, b, c (device)
+// for NaN or Inf; on one, ctl->status = FK_ENONFINITE and ctl->skip = 1.
+int launch_check_finite(const void *A, int64_t n_A, const void *b, int64_t n_b, const void *c,
+                        int64_t n_c, Control *ctl, void *stream);
+// Validation of the per-call engine and tile bits of flags, and their encoding.
+int check_diag_flags(unsigned flags);
+int diag_tuning_flags(int engine, int tpb, int ch, int bps, unsigned *flags);
 int read_status(const void *ws, void *stream, int *status);
 
 // Default time limit of one grid-barrier wait.

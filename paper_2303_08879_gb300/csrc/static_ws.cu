@@ -43,7 +43,7 @@ extern "C" int fock_diag_probs_static(int batch, const fk_c128 *A, const fk_c128
     int rc = build_diag_shape(M, cutoffs, !(flags & FK_FLAG_B_ZERO), &sh);
     if (rc) return rc;
     DiagLayout lay;
-    rc = diag_layout(sh, batch, false, &lay);
+    rc = diag_layout(sh, batch, false, flags, &lay);
     if (rc) return rc;
     if (lay.total > kStaticBytes) return FK_EWORKSPACE;
     void *ws = nullptr;

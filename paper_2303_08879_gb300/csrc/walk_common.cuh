@@ -68,6 +68,13 @@ __device__ __forceinline__ int ld_status(const Control *ctl)
     return *(volatile const int *)&ctl->status;
 }
 
+// Set before the launch by the input scan of FK_FLAG_CHECK_FINITE and never
+// written by a walk kernel, so every block of a launch reads the same value.
+__device__ __forceinline__ bool skip_walk(const Control *ctl)
+{
+    return *(volatile const int *)&ctl->skip != 0;
+}
+
 // Grid-wide barrier of a cooperative launch.  Every wait is bounded by
 // `timeout_ns`; on expiry the status word becomes FK_ETIMEOUT and all blocks
 // leave.  Returns false once any error is recorded.

@@ -437,6 +437,7 @@ __device__ void pair_forward(const CondArgs &a, CSmem &s, const CTile &tl, int k
 
 __global__ void __launch_bounds__(TPB) cond_forward_kernel(const __grid_constant__ CondArgs a)
 {
+    if (skip_walk(a.ctl)) return;   // the input scan found a NaN or Inf
     CSmem s = carve(a, false);
     build_tables(s);
     prologue(a);
@@ -653,6 +654,7 @@ __device__ void step1_reverse(const CondArgs &a, CSmem &s, int c, bool hb)
 
 __global__ void __launch_bounds__(TPB) cond_vjp_kernel(const __grid_constant__ CondArgs a)
 {
+    if (skip_walk(a.ctl)) return;   // the input scan found a NaN or Inf
     CSmem s = carve(a, true);
     build_tables(s);
     prologue(a);
@@ -956,16 +958,24 @@ int cond_layout(const CondPlan &plan, bool vjp, CondLayout *lay)
     return FK_OK;
 }
 
+static int check_inputs(const CondPlan &plan, unsigned flags, const void *A, const void *b,
+                        const void *c, char *w, const CondLayout &lay, cudaStream_t st)
+{
+    if (!(flags & FK_FLAG_CHECK_FINITE)) return FK_OK;
+    const int64_t D = 2 * (int64_t)plan.M;
+    return launch_check_finite(A, plan.B * D * D, b, plan.B * D, c, plan.B, (Control *)(w + lay.ctl), st);
+}
+
 int launch_cond_forward(const CondPlan &plan, unsigned flags, const void *A, const void *b,
                         const void *c, void *rho, void *ws, const CondLayout &lay, void *stream)
 {
-    (void)flags;
     cudaStream_t st = (cudaStream_t)stream;
     const void *hp = nullptr;
     int rc = pinned_plan(plan, &hp);
     if (rc) return rc;
     char *w = (char *)ws;
     if (cudaMemsetAsync(w + lay.ctl, 0, sizeof(Control), st) != cudaSuccess) return FK_ECUDA;
+    if ((rc = check_inputs(plan, flags, A, b, c, w, lay, st)) != 0) return rc;
     if (cudaMemcpyAsync(w + lay.plan, hp, plan.plan_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
         return FK_ECUDA;
     CondArgs a = make_args(plan, A, b, c, ws, lay);
@@ -981,13 +991,13 @@ int launch_cond_vjp(const CondPlan &plan, unsigned flags, const void *A, const v
                     const void *c, const void *grho, void *gA, void *gb, void *gc, void *ws,
                     const CondLayout &lay, void *stream)
 {
-    (void)flags;
     cudaStream_t st = (cudaStream_t)stream;
     const void *hp = nullptr;
     int rc = pinned_plan(plan, &hp);
     if (rc) return rc;
     char *w = (char *)ws;
     if (cudaMemsetAsync(w + lay.ctl, 0, sizeof(Control), st) != cudaSuccess) return FK_ECUDA;
+    if ((rc = check_inputs(plan, flags, A, b, c, w, lay, st)) != 0) return rc;
     if (cudaMemcpyAsync(w + lay.plan, hp, plan.plan_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
         return FK_ECUDA;
     if (cudaMemsetAsync(w + lay.Fbar, 0, lay.partA - lay.Fbar, st) != cudaSuccess) return FK_ECUDA;

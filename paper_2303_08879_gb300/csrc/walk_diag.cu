@@ -1802,6 +1802,7 @@ struct Walk {
     static __device__ void forward(const DiagArgs &a)
     {
         const DiagShape &sh = a.sh;
+        if (skip_walk(a.ctl)) return;
         Smem s = carve_smem(sh, kFwd);
         build_tables(sh, s);
         prologue(a, s, true);
@@ -1848,6 +1849,7 @@ struct Walk {
     static __device__ void vjp(const DiagArgs &a)
     {
         const DiagShape &sh = a.sh;
+        if (skip_walk(a.ctl)) return;
         Smem s = carve_smem(sh, kVjp);
         build_tables(sh, s);
         prologue(a, s, false);
@@ -1893,7 +1895,7 @@ struct Walk {
     static __device__ void vjp_partials(const DiagArgs &a)
     {
         const DiagShape &sh = a.sh;
-        if (ld_status(a.ctl) != 0) return;   // the walk failed
+        if (skip_walk(a.ctl) || ld_status(a.ctl) != 0) return;   // no walk, or it failed
         Smem s = carve_smem(sh, kPart);
         build_tables(sh, s);
         __syncthreads();
@@ -1995,6 +1997,23 @@ __global__ void fill_int_kernel(int *p, int n, int v)
     if (i < n) p[i] = v;
 }
 
+// NaN or Inf in any of the complex inputs: exponent field all ones.
+__global__ void check_finite_kernel(const unsigned long long *A, int64_t nA, const unsigned long long *b,
+                                    int64_t nb, const unsigned long long *c, int64_t nc, Control *ctl)
+{
+    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
+    constexpr unsigned long long kExp = 0x7ff0000000000000ull;
+    int bad = 0;
+    for (int64_t i = gtid; i < 2 * nA; i += gsz) bad |= (A[i] & kExp) == kExp;
+    for (int64_t i = gtid; i < 2 * nb; i += gsz) bad |= (b[i] & kExp) == kExp;
+    for (int64_t i = gtid; i < 2 * nc; i += gsz) bad |= (c[i] & kExp) == kExp;
+    if (__syncthreads_or(bad) && threadIdx.x == 0) {
+        atomicCAS(&ctl->status, 0, (int)FK_ENONFINITE);
+        atomicExch(&ctl->skip, 1);
+    }
+}
+
 __global__ void wait_selftest_kernel(Control *ctl, unsigned long long timeout_ns)
 {
     if (threadIdx.x != 0) return;
@@ -2065,38 +2084,64 @@ TcVariant tc_variant()
 const TcVariant kTcVariants[] = {tc_variant<1>(), tc_variant<2>()};
 constexpr int kTcMaxModes = 8;
 
+// Process-wide defaults (fk_diag_set_tuning, fk_diag_set_engine), read once
+// per call under the lock; per-call flag bits override them.
 std::mutex g_tune_mu;
-int g_tpb = 128, g_ch = 8, g_bps = 0, g_engine = FK_ENGINE_FP64;
+int g_tpb = 128, g_ch = 8, g_bps = 0, g_engine = FK_ENGINE_AUTO;
 
-const Variant &current_variant(int *bps)
+// The tuning one call runs with.
+struct Tune {
+    int tpb, ch, bps, engine;
+};
+
+constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
+
+Tune resolve_tune(unsigned flags)
 {
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    *bps = g_bps;
+    Tune t;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        t = Tune{g_tpb, g_ch, g_bps, g_engine};
+    }
+    if (flags & FK_FLAG_ENGINE_FP64) t.engine = FK_ENGINE_FP64;
+    if (flags & FK_FLAG_ENGINE_TENSOR) t.engine = FK_ENGINE_TENSOR;
+    const int v = (int)((flags >> 8) & 15u);
+    if (v >= 1 && v <= kNumVariants) {
+        t.tpb = kVariants[v - 1].tpb;
+        t.ch = kVariants[v - 1].ch;
+        t.bps = (int)((flags >> 12) & 63u);
+    }
+    return t;
+}
+
+const Variant &variant_of(const Tune &t)
+{
     for (const Variant &v : kVariants)
-        if (v.tpb == g_tpb && v.ch == g_ch) return v;
+        if (v.tpb == t.tpb && v.ch == t.ch) return v;
     return kVariants[0];
 }
 
-// Kernel, block size, shared memory and partial-sum slots per block for
-// shape sh under the current tuning and engine: the forward (vjp false) or
-// the VJP launch that owns the partial-sum slots (vjp true: the FP64
-// engine's reverse walk, the tensor engine's partial pass).  tc_walk: the
-// tensor engine's reverse walk instead.
-void walk_kernel(const DiagShape &sh, bool vjp, const void **fn, int *tpb, size_t *smem, int *bps,
-                 int *slots_per_block, bool tc_walk = false)
+bool tc_engine_for(const DiagShape &sh, const Tune &t)
 {
-    const Variant &v = current_variant(bps);
-    int engine;
-    {
-        std::lock_guard<std::mutex> lk(g_tune_mu);
-        engine = g_engine;
-    }
-    if (engine == FK_ENGINE_TENSOR && sh.M <= kTcMaxModes) {
-        const TcVariant &t = kTcVariants[(sh.M + 3) / 4 - 1];
+    return t.engine != FK_ENGINE_FP64 && sh.M <= kTcMaxModes;
+}
+
+// Kernel, block size, shared memory and partial-sum slots per block for
+// shape sh under tuning t: the forward (vjp false) or the VJP launch that
+// owns the partial-sum slots (vjp true: the FP64 engine's reverse walk, the
+// tensor engine's partial pass).  tc_walk: the tensor engine's reverse walk
+// instead.
+void walk_kernel(const DiagShape &sh, const Tune &t, bool vjp, const void **fn, int *tpb, size_t *smem,
+                 int *bps, int *slots_per_block, bool tc_walk = false)
+{
+    const Variant &v = variant_of(t);
+    *bps = t.bps;
+    if (tc_engine_for(sh, t)) {
+        const TcVariant &tc = kTcVariants[(sh.M + 3) / 4 - 1];
         const int mode = tc_walk ? kVjp : (vjp ? kPart : kFwd);
-        *fn = tc_walk ? t.vjp : (vjp ? t.part : t.fwd);
+        *fn = tc_walk ? tc.vjp : (vjp ? tc.part : tc.fwd);
         *tpb = 128;
-        *smem = t.smem(sh.M, sh.L, mode, sh.has_b != 0);
+        *smem = tc.smem(sh.M, sh.L, mode, sh.has_b != 0);
         *slots_per_block = 128 / 32;
         return;
     }
@@ -2104,12 +2149,6 @@ void walk_kernel(const DiagShape &sh, bool vjp, const void **fn, int *tpb, size_
     *tpb = v.tpb;
     *smem = v.smem(sh.M, sh.L, vjp ? kVjp : kFwd, sh.has_b != 0);
     *slots_per_block = 1;
-}
-
-bool tc_engine_for(const DiagShape &sh)
-{
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    return g_engine == FK_ENGINE_TENSOR && sh.M <= kTcMaxModes;
 }
 
 }  // namespace
@@ -2128,7 +2167,7 @@ int set_vjp_split_event(void *event)
 
 int set_diag_engine(int engine)
 {
-    if (engine != FK_ENGINE_FP64 && engine != FK_ENGINE_TENSOR) return FK_EINVAL;
+    if (engine != FK_ENGINE_FP64 && engine != FK_ENGINE_TENSOR && engine != FK_ENGINE_AUTO) return FK_EINVAL;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_engine = engine;
     return FK_OK;
@@ -2150,7 +2189,37 @@ int set_diag_tuning(int tpb, int ch, int bps)
     return FK_OK;
 }
 
-int diag_grid_size(const DiagShape &sh, bool vjp, int *grid, int *slots)
+int diag_tuning_flags(int engine, int tpb, int ch, int bps, unsigned *flags)
+{
+    if (!flags) return FK_EINVAL;
+    unsigned f = 0;
+    if (engine == FK_ENGINE_FP64) f |= FK_FLAG_ENGINE_FP64;
+    else if (engine == FK_ENGINE_TENSOR) f |= FK_FLAG_ENGINE_TENSOR;
+    else if (engine != FK_ENGINE_AUTO) return FK_EINVAL;
+    if (bps < 0 || bps > 32) return FK_EINVAL;
+    if (tpb != 0 || ch != 0) {
+        int idx = 0;
+        for (int i = 0; i < kNumVariants; ++i)
+            if (kVariants[i].tpb == tpb && kVariants[i].ch == ch) idx = i + 1;
+        if (idx == 0) return FK_EINVAL;
+        f |= (unsigned)idx << 8 | (unsigned)bps << 12;
+    } else if (bps != 0) {
+        return FK_EINVAL;
+    }
+    *flags = f;
+    return FK_OK;
+}
+
+int check_diag_flags(unsigned flags)
+{
+    if ((flags & FK_FLAG_ENGINE_FP64) && (flags & FK_FLAG_ENGINE_TENSOR)) return FK_EINVAL;
+    const int v = (int)((flags >> 8) & 15u);
+    if (v > kNumVariants || (v == 0 && ((flags >> 12) & 63u) != 0) || ((flags >> 12) & 63u) > 32)
+        return FK_EINVAL;
+    return FK_OK;
+}
+
+int diag_grid_size(const DiagShape &sh, bool vjp, unsigned flags, int *grid, int *slots)
 {
     int sms = 0;
     int rc = device_sms(&sms);
@@ -2158,7 +2227,8 @@ int diag_grid_size(const DiagShape &sh, bool vjp, int *grid, int *slots)
     int bps = 0, tpb = 0, spb = 1;
     size_t smem = 0;
     const void *fn = nullptr;
-    walk_kernel(sh, vjp, &fn, &tpb, &smem, &bps, &spb);
+    const Tune tn = resolve_tune(flags);
+    walk_kernel(sh, tn, vjp, &fn, &tpb, &smem, &bps, &spb);
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return FK_ECUDA;
     int per = 0;
@@ -2205,6 +2275,13 @@ static unsigned long long stop_threshold(double eps)
     return (unsigned long long)((1.0 - eps) * 0x1p56);
 }
 
+static int launch_check_finite(const DiagShape &sh, int batch, const void *A, const void *b,
+                               const void *c, Control *ctl, cudaStream_t st)
+{
+    const int64_t Do = sh.D_orig;
+    return launch_check_finite(A, (int64_t)batch * Do * Do, b, (int64_t)batch * Do, c, batch, ctl, st);
+}
+
 int launch_diag_forward(const DiagShape &sh, int batch, unsigned flags, const void *A,
                         const void *b, const void *c, void *probs, void *ws,
                         const DiagLayout &lay, void *stream, const EarlyStop *es)
@@ -2212,6 +2289,9 @@ int launch_diag_forward(const DiagShape &sh, int batch, unsigned flags, const vo
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemsetAsync((char *)ws + lay.ctl, 0, sizeof(Control), st) != cudaSuccess) return FK_ECUDA;
     if (sh.M == 0) {
+        if ((flags & FK_FLAG_CHECK_FINITE) &&
+            launch_check_finite(sh, batch, A, b, c, (Control *)((char *)ws + lay.ctl), st) != 0)
+            return FK_ECUDA;
         copy_c_kernel<<<(batch + 127) / 128, 128, 0, st>>>((const double2 *)c, (double2 *)probs, batch, 1);
         if (es && es->levels)
             fill_int_kernel<<<(batch + 127) / 128, 128, 0, st>>>(es->levels, batch, 1);
@@ -2219,6 +2299,7 @@ int launch_diag_forward(const DiagShape &sh, int batch, unsigned flags, const vo
     }
     DiagArgs a = make_args(sh, batch, flags, A, b, c, ws, lay);
     a.probs = (double2 *)probs;
+    int rc0 = 0;
     if (es) {
         // unstarted photon numbers stay zero; the per-level sums start from zero
         if (cudaMemsetAsync(probs, 0, (size_t)batch * sh.n_diag * 16, st) != cudaSuccess) return FK_ECUDA;
@@ -2228,14 +2309,17 @@ int launch_diag_forward(const DiagShape &sh, int batch, unsigned flags, const vo
         a.thr = stop_threshold(es->eps);
         a.levels = es->levels;
     }
+    if ((flags & FK_FLAG_CHECK_FINITE) && (rc0 = launch_check_finite(sh, batch, A, b, c, a.ctl, st)) != 0)
+        return rc0;
+    const Tune tn = resolve_tune(flags);
     int grid = 0;
-    int rc = diag_grid_size(sh, false, &grid);
+    int rc = diag_grid_size(sh, false, flags, &grid);
     if (rc) return rc;
     a.grid = grid;
     int bps = 0, tpb = 0, spb = 1;
     size_t smem = 0;
     const void *fn = nullptr;
-    walk_kernel(sh, false, &fn, &tpb, &smem, &bps, &spb);
+    walk_kernel(sh, tn, false, &fn, &tpb, &smem, &bps, &spb);
     return launch_coop(fn, grid, tpb, smem, &a, st);
 }
 
@@ -2271,21 +2355,25 @@ int launch_diag_vjp(const DiagShape &sh, int batch, unsigned flags, const void *
         a.early = 1;
         a.thr = stop_threshold(es->eps);
     }
+    int rc = 0;
+    if ((flags & FK_FLAG_CHECK_FINITE) && (rc = launch_check_finite(sh, batch, A, b, c, a.ctl, st)) != 0)
+        return rc;
+    const Tune tn = resolve_tune(flags);
     int bps = 0, tpb = 0, spb = 1;
     size_t smem = 0;
     const void *fn = nullptr;
-    walk_kernel(sh, true, &fn, &tpb, &smem, &bps, &spb);
+    walk_kernel(sh, tn, true, &fn, &tpb, &smem, &bps, &spb);
     int grid = 0, slots = 0;
-    int rc = diag_grid_size(sh, true, &grid, &slots);
+    rc = diag_grid_size(sh, true, flags, &grid, &slots);
     if (rc) return rc;
     // tuning or engine changed since the layout was sized
     if (grid != lay.grid_vjp || slots != lay.slots_vjp) return FK_EWORKSPACE;
-    if (tc_engine_for(sh)) {
+    if (tc_engine_for(sh, tn)) {
         // the reverse walk (its own grid), then the partial pass that owns the slots
         const void *wfn = nullptr;
         int wtpb = 0, wbps = 0, wspb = 1;
         size_t wsmem = 0;
-        walk_kernel(sh, true, &wfn, &wtpb, &wsmem, &wbps, &wspb, true);
+        walk_kernel(sh, tn, true, &wfn, &wtpb, &wsmem, &wbps, &wspb, true);
         if (cudaFuncSetAttribute(wfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem) != cudaSuccess)
             return FK_ECUDA;
         int per = 0, sms = 0;
@@ -2310,6 +2398,17 @@ int launch_wait_selftest(void *ws, unsigned long long timeout_ns, void *stream)
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemsetAsync(ws, 0, sizeof(Control), st) != cudaSuccess) return FK_ECUDA;
     wait_selftest_kernel<<<1, 32, 0, st>>>((Control *)ws, timeout_ns);
+    return cudaGetLastError() == cudaSuccess ? FK_OK : FK_ECUDA;
+}
+
+int launch_check_finite(const void *A, int64_t n_A, const void *b, int64_t n_b, const void *c,
+                        int64_t n_c, Control *ctl, void *stream)
+{
+    const int64_t n = 2 * (n_A > n_b ? (n_A > n_c ? n_A : n_c) : (n_b > n_c ? n_b : n_c));
+    const int grid = (int)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024);
+    check_finite_kernel<<<grid < 1 ? 1 : grid, 256, 0, (cudaStream_t)stream>>>(
+        (const unsigned long long *)A, n_A, (const unsigned long long *)b, n_b,
+        (const unsigned long long *)c, n_c, ctl);
     return cudaGetLastError() == cudaSuccess ? FK_OK : FK_ECUDA;
 }
 

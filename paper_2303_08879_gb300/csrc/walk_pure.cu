@@ -155,6 +155,7 @@ __device__ void pure_prologue(const PureArgs &a, bool seed)
 
 __global__ void __launch_bounds__(kPureTPB) pure_forward_kernel(const __grid_constant__ PureArgs a)
 {
+    if (skip_walk(a.ctl)) return;   // the input scan found a NaN or Inf
     PureSmem s = carve(a);
     pure_tables(a, s);
     pure_prologue(a, true);
@@ -195,6 +196,7 @@ __global__ void __launch_bounds__(kPureTPB) pure_forward_kernel(const __grid_con
 
 __global__ void __launch_bounds__(kPureTPB) pure_vjp_kernel(const __grid_constant__ PureArgs a)
 {
+    if (skip_walk(a.ctl)) return;   // the input scan found a NaN or Inf
     PureSmem s = carve(a);
     pure_tables(a, s);
     pure_prologue(a, false);
@@ -402,6 +404,10 @@ int run_forward(const PureShape &sh, int batch, unsigned flags, const void *A, c
                 const void *c, void *psi, void *ws, const PureLayout &lay, cudaStream_t st)
 {
     if (cudaMemsetAsync((char *)ws + lay.ctl, 0, sizeof(Control), st) != cudaSuccess) return FK_ECUDA;
+    if ((flags & FK_FLAG_CHECK_FINITE) &&
+        launch_check_finite(A, (int64_t)batch * sh.M * sh.M, b, (int64_t)batch * sh.M, c, batch,
+                            (Control *)((char *)ws + lay.ctl), st) != FK_OK)
+        return FK_ECUDA;
     PureArgs a = pure_args(sh, batch, flags, A, b, c, ws, lay);
     a.psi = (double2 *)psi;
     int grid = 0;
@@ -471,6 +477,10 @@ int fock_pure_amplitudes_vjp_batched(int batch, const fk_c128 *A, const fk_c128 
         if (rc) return rc;
     }
     if (cudaMemsetAsync((char *)ws + lay.ctl, 0, sizeof(Control), st) != cudaSuccess) return FK_ECUDA;
+    if ((flags & FK_FLAG_CHECK_FINITE) &&
+        launch_check_finite(A, (int64_t)batch * sh.M * sh.M, b, (int64_t)batch * sh.M, c, batch,
+                            (Control *)((char *)ws + lay.ctl), st) != FK_OK)
+        return FK_ECUDA;
     if (cudaMemsetAsync((char *)ws + lay.Fbar, 0, lay.total - lay.Fbar, st) != cudaSuccess) return FK_ECUDA;
     PureArgs a = pure_args(sh, batch, flags, A, b, c, ws, lay);
     a.gpsi = (const double2 *)grad_psi;

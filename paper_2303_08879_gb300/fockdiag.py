@@ -18,10 +18,14 @@ LIB_PATH = os.path.join(_HERE, "libfockdiag.so")
 
 FK_OK = 0
 FK_ETIMEOUT = 6
+FK_ENONFINITE = 7
 FK_EBZERO = 8
 FK_OP_DIAG, FK_OP_DIAG_VJP, FK_OP_COND, FK_OP_COND_VJP = 1, 2, 3, 4
 FK_FLAG_B_ZERO = 1
 FK_FLAG_RECOMPUTE = 2
+FK_FLAG_ENGINE_FP64 = 0x10
+FK_FLAG_ENGINE_TENSOR = 0x20
+FK_FLAG_CHECK_FINITE = 0x40
 
 # every symbol the header declares
 EXPORTS = [
@@ -37,7 +41,7 @@ EXPORTS = [
     "fock_diag_probs_global_batched", "fock_diag_probs_global_vjp_batched",
     "fk_describe_global_schedule", "fock_diag_probs_stop_batched", "fock_diag_probs_stop_vjp_batched",
     "fk_gaussian_to_pure_triple", "fk_pure_workspace_size", "fock_pure_amplitudes_batched",
-    "fock_pure_amplitudes_vjp_batched",
+    "fock_pure_amplitudes_vjp_batched", "fk_diag_tuning_flags",
 ]
 
 
@@ -98,6 +102,7 @@ def lib():
         L.fock_pure_amplitudes_vjp_batched.argtypes = [I, P, P, P, I, P, P, P, P, P, U, P, Z, P]
         L.fk_diag_set_tuning.argtypes = [I, I, I]
         L.fk_diag_set_engine.argtypes = [I]
+        L.fk_diag_tuning_flags.argtypes = [I, I, I, I, ctypes.POINTER(ctypes.c_uint)]
         L.fk_diag_set_vjp_split_event.argtypes = [P]
         L.fk_herald_scores.argtypes = [I, P, P, I, P, ctypes.c_double, P, P, P, P]
         L.fk_circuit_triple.argtypes = [I, P, ctypes.c_double, P, P, P, P, P, P]
@@ -549,13 +554,23 @@ def fk_diag_set_tuning(tpb=0, ch=0, blocks_per_sm=0):
     _check(lib().fk_diag_set_tuning(int(tpb), int(ch), int(blocks_per_sm)), "fk_diag_set_tuning")
 
 
-FK_ENGINE_FP64, FK_ENGINE_TENSOR = 0, 1
+FK_ENGINE_FP64, FK_ENGINE_TENSOR, FK_ENGINE_AUTO = 0, 1, 2
 
 
 def fk_diag_set_engine(engine):
-    """Product engine of the all-detected walk (FK_ENGINE_FP64 or
-    FK_ENGINE_TENSOR: exact base-256 digit products on the fp16 tensor cores)."""
+    """Process-default product engine of the all-detected walk (FK_ENGINE_FP64,
+    FK_ENGINE_TENSOR: exact base-256 digit products on the fp16 tensor cores,
+    or FK_ENGINE_AUTO, the default: tensor for up to 8 kept modes)."""
     _check(lib().fk_diag_set_engine(int(engine)), "fk_diag_set_engine")
+
+
+def fk_diag_tuning_flags(engine=FK_ENGINE_AUTO, tpb=0, ch=0, blocks_per_sm=0):
+    """Flag bits that select engine and tile shape for one call (OR them into
+    `flags`); they take precedence over the process defaults."""
+    out = ctypes.c_uint(0)
+    _check(lib().fk_diag_tuning_flags(int(engine), int(tpb), int(ch), int(blocks_per_sm),
+                                      ctypes.byref(out)), "fk_diag_tuning_flags")
+    return int(out.value)
 
 
 def fk_diag_set_vjp_split_event(event=None):

@@ -83,7 +83,7 @@ def main():
     fd.check_workspace(ws)
     out["state_vector"] = {"amplitudes_per_state": int(np.prod(cut)), "forward_ms": fwd,
                            "vjp_ms": vjp, "engine": "fp64"}
-    fd.fk_diag_set_engine(fd.FK_ENGINE_FP64)
+    fd.fk_diag_set_engine(fd.FK_ENGINE_AUTO)
     print(json.dumps(out))
 
 

@@ -140,7 +140,7 @@ def main(argv):
             out[f"fig10_time_slopes_{name}"] = {
                 k: slope(cs, [r[k] for r in tt])
                 for k in ("forward_ms_per_circuit", "vjp_ms_per_circuit", "workspace_bytes_per_circuit")}
-        fd.fk_diag_set_engine(fd.FK_ENGINE_FP64)
+        fd.fk_diag_set_engine(fd.FK_ENGINE_AUTO)
     print(json.dumps(out))
 
 

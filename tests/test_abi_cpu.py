@@ -133,3 +133,27 @@ def test_pure_triple_matches_oracle(fd):
     lossy = inputs.make_circuit(2, rng, r_range=(0.4, 0.5), eta_range=(0.5, 0.6), cutoffs=(2, 2))
     with pytest.raises(fd.FockError):
         fd.fk_gaussian_to_pure_triple(lossy.V, lossy.mean)
+
+
+def test_per_call_tuning_flags(fd):
+    """Engine and tile bits for one call: encoded by fk_diag_tuning_flags,
+    validated on the host (uncompiled shapes, caps outside 0..32, both engine
+    bits at once) before any device work."""
+    assert fd.fk_diag_tuning_flags(fd.FK_ENGINE_AUTO) == 0
+    assert fd.fk_diag_tuning_flags(fd.FK_ENGINE_FP64) == fd.FK_FLAG_ENGINE_FP64
+    assert fd.fk_diag_tuning_flags(fd.FK_ENGINE_TENSOR) == fd.FK_FLAG_ENGINE_TENSOR
+    f = fd.fk_diag_tuning_flags(fd.FK_ENGINE_FP64, 64, 4, 3)
+    assert f & fd.FK_FLAG_ENGINE_FP64 and (f >> 8) & 15 == 4 and (f >> 12) & 63 == 3
+    for bad in ((3, 0, 0, 0), (0, 96, 8, 0), (0, 128, 8, 33), (0, 0, 0, 2), (0, 128, 2, 0)):
+        with pytest.raises(fd.FockError):
+            fd.fk_diag_tuning_flags(*bad)
+    L = fd.lib()
+    need = ctypes.c_size_t(0)
+    cut = (ctypes.c_int * 2)(3, 3)
+    both = fd.FK_FLAG_ENGINE_FP64 | fd.FK_FLAG_ENGINE_TENSOR
+    for flags in (both, 9 << 8, (1 << 8) | (40 << 12)):
+        assert L.fk_workspace_size(2, cut, None, 1, fd.FK_OP_DIAG, flags, ctypes.byref(need)) == 1
+    # the tile bits select the FP64 shape only; the forward layout does not depend on them
+    ok = [L.fk_workspace_size(2, cut, None, 1, fd.FK_OP_DIAG, fl, ctypes.byref(need)) for fl in
+          (0, fd.fk_diag_tuning_flags(fd.FK_ENGINE_FP64, 256, 8, 0), fd.FK_FLAG_CHECK_FINITE)]
+    assert ok == [0, 0, 0]

@@ -21,10 +21,14 @@ RTOL, ATOL, VJP_RTOL = 1e-10, 1e-12, 1e-8
 
 @pytest.fixture(scope="module")
 def fd():
+    """The FP64 product engine for this module (the library defaults to the
+    tensor engine up to 8 modes; test_tensor_engine_gpu.py covers that one)."""
     from paper_2303_08879_gb300 import build
     build.build()
     from paper_2303_08879_gb300 import fockdiag
-    return fockdiag
+    fockdiag.fk_diag_set_engine(fockdiag.FK_ENGINE_FP64)
+    yield fockdiag
+    fockdiag.fk_diag_set_engine(fockdiag.FK_ENGINE_AUTO)
 
 
 def cuda(x):
@@ -168,7 +172,6 @@ VJP_CASES = [((4, 3), True), ((3, 3, 3), False), ((3, 4, 2), True), ((2, 1, 3), 
 def test_vjp_matches_oracle_gradient(fd, cut, withb):
     """Every gradient entry against the oracle's closed-form VJP of the full
     density matrix (Sec. 2.5), FP64 engine."""
-    fd.fk_diag_set_engine(fd.FK_ENGINE_FP64)
     rng = np.random.default_rng(100 + sum(cut) + 31 * len(cut))
     D = 2 * len(cut)
     A, b = inputs.random_symmetric(D, rng, scale=0.2 if len(cut) <= 4 else 0.12, with_b=withb)

@@ -74,7 +74,7 @@ def test_stop_matches_definition(fd, engine, eps):
         p, levels, ws = fd.fock_diag_probs_stop_batched(cuda(A[None]), cuda(b[None]), cuda([c]), cut, eps)
         fd.check_workspace(ws)
     finally:
-        fd.fk_diag_set_engine(0)
+        fd.fk_diag_set_engine(fd.FK_ENGINE_AUTO)
     assert int(levels[0]) == lv
     got = p[0].cpu().numpy()
     want = stopped(ref, lv)
@@ -130,7 +130,7 @@ def test_stop_vjp_matches_oracle(fd, engine):
         gA, gb, gc = fd.fock_diag_probs_stop_vjp_batched(Ad, bd, cd, cut, eps, cuda(gbar[None]), ws)
         fd.check_workspace(ws)
     finally:
-        fd.fk_diag_set_engine(0)
+        fd.fk_diag_set_engine(fd.FK_ENGINE_AUTO)
     assert int(levels[0]) == lv
     for got, want, what in ((gA[0], rA, "A"), (gb[0], rb, "b")):
         got = got.cpu().numpy()

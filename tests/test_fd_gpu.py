@@ -100,4 +100,4 @@ def test_vjp_matches_central_differences_full_size(fd, circuit, engine):
             g = gc.real if part == "re" else gc.imag
             assert abs(q - g) <= FD_RTOL * max(abs(gc), 1e-300), (part, q, g)
     finally:
-        fd.fk_diag_set_engine(fd.FK_ENGINE_FP64)
+        fd.fk_diag_set_engine(fd.FK_ENGINE_AUTO)

@@ -72,7 +72,7 @@ def test_global_forward_matches_oracle(fd, engine, M, n, withb):
             fd.check_workspace(ws)
             assert_amp_close(p0[0].cpu().numpy(), ref)
     finally:
-        fd.fk_diag_set_engine(0)
+        fd.fk_diag_set_engine(fd.FK_ENGINE_AUTO)
 
 
 def test_global_gbs_batch_matches_oracle(fd):
@@ -87,7 +87,7 @@ def test_global_gbs_batch_matches_oracle(fd):
         p, ws = fd.fock_diag_probs_global_batched(cuda(A), cuda(b), cuda(c), 6, flags=fd.FK_FLAG_B_ZERO)
         fd.check_workspace(ws)
     finally:
-        fd.fk_diag_set_engine(0)
+        fd.fk_diag_set_engine(fd.FK_ENGINE_AUTO)
     got = p.cpu().numpy()
     pats = patterns(8, 6)
     rng = np.random.default_rng(5)
@@ -131,4 +131,4 @@ def test_global_vjp_matches_oracle(fd, engine, M, n, withb):
             assert np.max(np.abs(got - ref)) / scale <= VJP_RTOL, what
         assert abs(gc[0].item() - rc) <= VJP_RTOL * abs(rc)
     finally:
-        fd.fk_diag_set_engine(0)
+        fd.fk_diag_set_engine(fd.FK_ENGINE_AUTO)

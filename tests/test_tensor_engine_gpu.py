@@ -28,7 +28,7 @@ def fd():
     from paper_2303_08879_gb300 import fockdiag
     fockdiag.fk_diag_set_engine(fockdiag.FK_ENGINE_TENSOR)
     yield fockdiag
-    fockdiag.fk_diag_set_engine(fockdiag.FK_ENGINE_FP64)
+    fockdiag.fk_diag_set_engine(fockdiag.FK_ENGINE_AUTO)
 
 
 def cuda(x):
