@@ -14,6 +14,31 @@
 
 namespace fk {
 
+static std::vector<int64_t> level_hist(const std::vector<int> &ext, int L);
+static std::vector<int> extents(const DiagShape &sh, int k0, int a, int da, int m, int dm);
+
+// Tile bounds of a shape (see DiagShape::max_phase_tiles): AP(K) pivots of
+// level s are the vectors of family K (extents C_K - 1, C_K+1, ...) with digit
+// sum s; the DP pivots are those of family 0.
+static void set_tile_bounds(DiagShape *sh)
+{
+    const int tpbs[3] = {64, 128, 256};
+    for (int i = 0; i < 3; ++i) sh->max_phase_tiles[i] = 0;
+    sh->all_tiles128 = 0;
+    if (sh->M == 0) return;
+    std::vector<std::vector<int64_t>> h(sh->M);
+    for (int K = 0; K < sh->M; ++K) h[K] = level_hist(extents(*sh, K, K, 1, -1, 0), sh->L);
+    for (int s = 0; s < sh->L; ++s) {
+        for (int i = 0; i < 3; ++i) {
+            int64_t t = 0;
+            for (int K = 0; K < sh->M; ++K) t += (h[K][s] + tpbs[i] - 1) / tpbs[i];
+            if (t > sh->max_phase_tiles[i]) sh->max_phase_tiles[i] = t;
+        }
+        for (int K = 0; K < sh->M; ++K) sh->all_tiles128 += (h[K][s] + 127) / 128;
+        if (sh->has_b) sh->all_tiles128 += (h[0][s] + 127) / 128;
+    }
+}
+
 int build_diag_shape(int M, const int *cutoffs, bool has_b, DiagShape *sh)
 {
     if (M < 1 || !cutoffs || !sh) return FK_EINVAL;
@@ -98,6 +123,7 @@ int build_diag_shape(int M, const int *cutoffs, bool has_b, DiagShape *sh)
         ap += box_size(*sh, K, K, 1, -1, 0);
     }
     sh->n_ap = ap;
+    set_tile_bounds(sh);
     return FK_OK;
 }
 
@@ -122,7 +148,7 @@ int diag_layout(const DiagShape &sh, int batch, bool vjp, unsigned flags, DiagLa
     if (vjp) {
         int grid = 1, slots = 1;
         if (sh.M > 0) {
-            int rc = diag_grid_size(sh, true, flags, &grid, &slots);
+            int rc = diag_grid_size(sh, true, flags, batch, &grid, &slots);
             if (rc) return rc;
         }
         lay->grid_vjp = grid;
@@ -347,6 +373,7 @@ int build_global_shape(int M, int n_max, bool has_b, DiagShape *sh)
         ap += sh->fam[K];
     }
     sh->n_ap = ap;
+    set_tile_bounds(sh);
     return FK_OK;
 }
 

@@ -119,7 +119,12 @@ int set_diag_engine(int engine);
 int set_vjp_split_event(void *event);
 
 // Launchers (walk_diag.cu).  All pointers are device pointers.
-int diag_grid_size(const DiagShape &sh, bool vjp, unsigned flags, int *grid, int *slots = nullptr);
+// Grid of a walk launch: as many blocks as fit on the GPU, but no more than
+// the batch has tiles in its largest phase (all phases for the tensor
+// engine's barrier-free partial pass), so small problems wait at grid
+// barriers of few blocks.
+int diag_grid_size(const DiagShape &sh, bool vjp, unsigned flags, int batch, int *grid,
+                   int *slots = nullptr);
 // Early stop on the probability sum (Sec. 2.3): the pivots of a circuit stop
 // once its probabilities with at most `level` photons sum to >= 1 - eps.
 struct EarlyStop {

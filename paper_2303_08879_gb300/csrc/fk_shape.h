@@ -80,6 +80,12 @@ struct DiagShape {
     int64_t lm_t1[FK_MAXM];   // level-major T1 pair of mode j (b != 0): T1B at even, T1K at odd
     int64_t circ_alloc;       // level-major amplitudes allocated per circuit (>= circ_size)
     int64_t stride[FK_MAXM];  // DIAG strides S_j = prod_{i>j} C_i
+    // Work bounds per circuit for sizing the grid of small problems: the
+    // largest number of pivot tiles in one phase (any level, AP or DP) for
+    // 64-, 128- and 256-pivot tiles, and the tiles of every AP and DP phase
+    // together at 128 pivots (the barrier-free partial pass).
+    int64_t max_phase_tiles[3];
+    int64_t all_tiles128;
 };
 
 // Dense index of digits `dig` in the box over modes k0..M-1 whose extents are

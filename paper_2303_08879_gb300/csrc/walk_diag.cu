@@ -717,55 +717,68 @@ struct Walk {
     // field of its reads) and its adjoints by the inverse, which leaves every
     // product unchanged; the adjoints then share a power of two per row w
     // over the 32 pivots, so each term is exact relative to the largest
-    // product of its row.  Real form with K = (pivot t, re/im) = 64:
-    //   A[w][(t,0)] = Yr, A[w][(t,1)] = Yi;  B[(t,0)][2j] = Xr, B[(t,1)][2j] = Xi,
-    //   B[(t,0)][2j+1] = -Xi, B[(t,1)][2j+1] = Xr,
-    // so column 2j of A B is Re P[w][j] and column 2j+1 is Im P[w][j].
-    // The result is added to the warp's own slot (single writer).
+    // product of its row.  Real form with K = (pivot t, re/im) = 64 and the
+    // re/im split on the rows: M tile mt holds rows (w = 8 mt + r, re) at r
+    // and (w, im) at r + 8, r < 8;
+    //   A[(w,re)][(t,0)] = Yr, A[(w,re)][(t,1)] = Yi,
+    //   A[(w,im)][(t,0)] = Yi, A[(w,im)][(t,1)] = -Yr,
+    //   B[(t,0)][j] = Xr_j, B[(t,1)][j] = Xi_j,
+    // so row (w,re) of A B is Re P[w][:] and row (w,im) is Im P[w][:].  A lane
+    // converts (Yr, Yi) once per (row, pivot) and derives the (Yi, -Yr)
+    // fragment by a half swap and a sign flip (digits negate exactly), and
+    // converts each read once.  The result is added to the warp's own slot
+    // (single writer).
     static __device__ void tc_partials(const DiagArgs &a, const Smem &s, int circ, int row0, int N)
     {
-        constexpr int NT = 2 * KS;   // N tiles over the 2N real columns (N <= 8 KS)
+        constexpr int TT = KS > 1 ? 2 : 1;   // M and N tiles of 8 complex rows / columns (N <= 8 TT)
         const int lane = threadIdx.x & 31, grp = lane >> 2, tig = lane & 3, warp = threadIdx.x >> 5;
-        const int D = 2 * a.sh.M, nnt = (2 * N + 7) >> 3;
+        const int D = 2 * a.sh.M, nt_used = (N + 7) >> 3;
         const double *wx = s.wb + (size_t)warp * XS * WBS;
         const double *wy = s.wy + (size_t)warp * XS * WBS;
         const int *ef = s.wf + warp * 32;
         const int *gy = s.wg + warp * 32;
         const size_t slot = (size_t)blockIdx.x * (TPB / 32) + warp;
         double *pA = (double *)(a.partA + ((size_t)circ * a.slots + slot) * D * D);
-        float acc[NDIG][NT][4];
+        float acc[NDIG][TT][TT][4];
 #pragma unroll
         for (int d = 0; d < NDIG; ++d)
 #pragma unroll
-            for (int nt = 0; nt < NT; ++nt)
+            for (int mt = 0; mt < TT; ++mt)
 #pragma unroll
-                for (int q = 0; q < 4; ++q) acc[d][nt][q] = 0.f;
-        // A rows of this lane: w0 = grp, w1 = grp + 8
-        const int g0 = grp < N ? gy[grp] : 0, g1 = grp + 8 < N ? gy[grp + 8] : 0;
+                for (int nt = 0; nt < TT; ++nt)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[d][mt][nt][q] = 0.f;
+        // row exponent of this lane's row w = 8 mt + grp in each M tile
+        int gw[TT];
+#pragma unroll
+        for (int mt = 0; mt < TT; ++mt) gw[mt] = 8 * mt + grp < N ? gy[8 * mt + grp] : 0;
 #pragma unroll 1
         for (int ks = 0; ks < 4; ++ks) {
             const int t0 = 8 * ks + tig, t1 = t0 + 4;
             const int e0 = ef[t0], e1 = ef[t1];
-            uint32_t aq[NDIG][4];
+            uint32_t aq[NDIG][TT][2];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int w = grp + 8 * (k & 1), t = (k & 2) ? t1 : t0, e = (k & 2) ? e1 : e0;
-                const int g = (k & 1) ? g1 : g0;
-                double yr = 0.0, yi = 0.0;
-                if (w < N && g != 0 && e != 0) {
-                    yr = wy[(2 * w) * WBS + t];
-                    yi = wy[(2 * w + 1) * WBS + t];
+            for (int mt = 0; mt < TT; ++mt) {
+                const int w = 8 * mt + grp;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int t = h ? t1 : t0, e = h ? e1 : e0;
+                    double yr = 0.0, yi = 0.0;
+                    if (mt < nt_used && w < N && gw[mt] != 0 && e != 0) {
+                        yr = wy[(2 * w) * WBS + t];
+                        yi = wy[(2 * w + 1) * WBS + t];
+                    }
+                    const int fm = gw[mt] - e + 1022;
+                    uint32_t wd[NDIG];
+                    digit_words(to_fixed_rel(yr, fm), to_fixed_rel(yi, fm), wd);
+#pragma unroll
+                    for (int sl = 0; sl < NDIG; ++sl) aq[sl][mt][h] = wd[sl];   // (Yr, Yi)
                 }
-                const int fm = g - e + 1022;
-                uint32_t wd[NDIG];
-                digit_words(to_fixed_rel(yr, fm), to_fixed_rel(yi, fm), wd);
-#pragma unroll
-                for (int sl = 0; sl < NDIG; ++sl) aq[sl][k] = wd[sl];
             }
 #pragma unroll
-            for (int nt = 0; nt < NT; ++nt) {
-                if (nt >= nnt) continue;
-                const int n = 8 * nt + grp, j = n >> 1, im = n & 1;
+            for (int nt = 0; nt < TT; ++nt) {
+                if (nt >= nt_used) continue;
+                const int j = 8 * nt + grp;
                 uint32_t bq[NDIG][2];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
@@ -776,35 +789,49 @@ struct Walk {
                         xi = wx[(2 * j + 1) * WBS + t];
                     }
                     uint32_t wd[NDIG];
-                    digit_words(to_fixed(im ? -xi : xr, e), to_fixed(im ? xr : xi, e), wd);
+                    digit_words(to_fixed(xr, e), to_fixed(xi, e), wd);
 #pragma unroll
                     for (int sl = 0; sl < NDIG; ++sl) bq[sl][h] = wd[sl];
                 }
 #pragma unroll
-                for (int sa = 0; sa < NDIG; ++sa)
+                for (int mt = 0; mt < TT; ++mt) {
+                    if (mt >= nt_used) continue;
 #pragma unroll
-                    for (int u = 0; u + sa < NDIG; ++u) mma_f16(acc[sa + u][nt], aq[sa], bq[u]);
+                    for (int sa = 0; sa < NDIG; ++sa) {
+                        // register order of the A fragment: (row r, k lo), (row r + 8, k lo),
+                        // (row r, k hi), (row r + 8, k hi); rows (w, im) carry (Yi, -Yr)
+                        const uint32_t x0 = aq[sa][mt][0], x1 = aq[sa][mt][1];
+                        const uint32_t af[4] = {x0, __byte_perm(x0, 0u, 0x1032) ^ 0x80000000u, x1,
+                                                __byte_perm(x1, 0u, 0x1032) ^ 0x80000000u};
+#pragma unroll
+                        for (int u = 0; u + sa < NDIG; ++u) mma_f16(acc[sa + u][mt][nt], af, bq[u]);
+                    }
+                }
             }
         }
 #pragma unroll
-        for (int nt = 0; nt < NT; ++nt) {
-            if (nt >= nnt) continue;
+        for (int mt = 0; mt < TT; ++mt) {
+            const int w = 8 * mt + grp;
+            if (mt >= nt_used || w >= N || gw[mt] < 26) continue;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int w = grp + 8 * (q >> 1), n = 8 * nt + 2 * tig + (q & 1), j = n >> 1;
-                const int g = (q >> 1) ? g1 : g0;
-                if (w < N && j < N && g >= 26) {
-                    float a7[NDIG][4];
+            for (int nt = 0; nt < TT; ++nt) {
+                if (nt >= nt_used) continue;
 #pragma unroll
-                    for (int d = 0; d < NDIG; ++d) a7[d][0] = acc[d][nt][q];
-                    const long long Y = combine_digits_wide(a7, 0);
-                    const double v = scale2(__ll2double_rn(Y), g - 1074);
-                    double *dst = pA + 2 * ((size_t)(row0 + w) * D + row0 + j) + (n & 1);
-                    // reduction without return: the warp does not wait for the
-                    // old value.  The slot has one warp as its only writer and
-                    // its updates are ordered by the warp's barriers between
-                    // tiles, so the sum order is fixed.
-                    atomicAdd(dst, v);
+                for (int q = 0; q < 4; ++q) {
+                    const int j = 8 * nt + 2 * tig + (q & 1), im = q >> 1;
+                    if (j < N) {
+                        float a7[NDIG][4];
+#pragma unroll
+                        for (int d = 0; d < NDIG; ++d) a7[d][0] = acc[d][mt][nt][q];
+                        const long long Y = combine_digits_wide(a7, 0);
+                        const double v = scale2(__ll2double_rn(Y), gw[mt] - 1074);
+                        double *dst = pA + 2 * ((size_t)(row0 + w) * D + row0 + j) + im;
+                        // reduction without return: the warp does not wait for the
+                        // old value.  The slot has one warp as its only writer and
+                        // its updates are ordered by the warp's barriers between
+                        // tiles, so the sum order is fixed.
+                        atomicAdd(dst, v);
+                    }
                 }
             }
         }
@@ -2219,7 +2246,16 @@ int check_diag_flags(unsigned flags)
     return FK_OK;
 }
 
-int diag_grid_size(const DiagShape &sh, bool vjp, unsigned flags, int *grid, int *slots)
+// Blocks a launch of shape sh and `batch` circuits can keep busy: the tiles
+// of its largest phase, or of all phases for the tensor engine's partial pass.
+static int64_t useful_blocks(const DiagShape &sh, int batch, int tpb, bool all_phases)
+{
+    const int i = tpb <= 64 ? 0 : (tpb <= 128 ? 1 : 2);
+    const int64_t t = all_phases ? sh.all_tiles128 : sh.max_phase_tiles[i];
+    return t < 1 ? 1 : (int64_t)batch * t;
+}
+
+int diag_grid_size(const DiagShape &sh, bool vjp, unsigned flags, int batch, int *grid, int *slots)
 {
     int sms = 0;
     int rc = device_sms(&sms);
@@ -2235,8 +2271,11 @@ int diag_grid_size(const DiagShape &sh, bool vjp, unsigned flags, int *grid, int
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, tpb, smem) != cudaSuccess) return FK_ECUDA;
     if (per < 1) return FK_EUNSUPPORTED;
     if (bps > 0 && bps < per) per = bps;
-    *grid = per * sms;
-    if (slots) *slots = per * sms * spb;
+    int64_t g = (int64_t)per * sms;
+    const int64_t useful = useful_blocks(sh, batch, tpb, vjp && tc_engine_for(sh, tn));
+    if (useful < g) g = useful;
+    *grid = (int)g;
+    if (slots) *slots = (int)g * spb;
     return FK_OK;
 }
 
@@ -2313,7 +2352,7 @@ int launch_diag_forward(const DiagShape &sh, int batch, unsigned flags, const vo
         return rc0;
     const Tune tn = resolve_tune(flags);
     int grid = 0;
-    int rc = diag_grid_size(sh, false, flags, &grid);
+    int rc = diag_grid_size(sh, false, flags, batch, &grid);
     if (rc) return rc;
     a.grid = grid;
     int bps = 0, tpb = 0, spb = 1;
@@ -2364,7 +2403,7 @@ int launch_diag_vjp(const DiagShape &sh, int batch, unsigned flags, const void *
     const void *fn = nullptr;
     walk_kernel(sh, tn, true, &fn, &tpb, &smem, &bps, &spb);
     int grid = 0, slots = 0;
-    rc = diag_grid_size(sh, true, flags, &grid, &slots);
+    rc = diag_grid_size(sh, true, flags, batch, &grid, &slots);
     if (rc) return rc;
     // tuning or engine changed since the layout was sized
     if (grid != lay.grid_vjp || slots != lay.slots_vjp) return FK_EWORKSPACE;
@@ -2381,7 +2420,8 @@ int launch_diag_vjp(const DiagShape &sh, int batch, unsigned flags, const void *
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, wfn, wtpb, wsmem) != cudaSuccess) return FK_ECUDA;
         if (per < 1) return FK_EUNSUPPORTED;
         DiagArgs w = a;
-        w.grid = per * sms;
+        const int64_t useful = useful_blocks(sh, batch, wtpb, false);
+        w.grid = (int)((int64_t)per * sms < useful ? (int64_t)per * sms : useful);
         if ((rc = launch_coop(wfn, w.grid, wtpb, wsmem, &w, st)) != 0) return rc;
         void *ev = nullptr;
         {
