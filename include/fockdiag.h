@@ -350,6 +350,41 @@ int fock_diag_probs_global_vjp_batched(int batch, const fk_c128 *d_A, const fk_c
 int fk_describe_global_schedule(int M, int n_max, unsigned flags, int64_t *out, int out_len);
 
 /*
+ * Per-circuit cutoffs in one launch (Algorithm 1, Sec. 3.1.3, for a batch of
+ * circuits of different shapes, e.g. a sweep over GBS circuits whose modes
+ * are cut at different photon numbers).  host_cutoffs is [batch][M] (C >= 1;
+ * a circuit with fewer modes gives its unused modes cutoff 1 and they are
+ * dropped from its walk, rule R1 of the walk: their indices stay 0).  All
+ * circuits share M and the input layout of fock_diag_probs_batched: A
+ * [batch][2M][2M], b [batch][2M], c [batch] (device).  Outputs are packed in
+ * the caller's order: circuit i's probabilities, row-major over its own
+ * cutoffs (mode 0 slowest, prod_j C_ij values), start at out_offsets[i]
+ * (fk_multi_workspace_size writes out_offsets[0..batch], the total last).
+ * Circuits that share a shape form a group with its own storage; every
+ * phase of the walk hands out the tiles of all groups through one counter,
+ * so all shapes advance level by level in the same cooperative launch.
+ * flags: FK_FLAG_B_ZERO (all circuits), FK_FLAG_ENGINE_*, tile bits,
+ * FK_FLAG_CHECK_FINITE; the VJP also FK_FLAG_RECOMPUTE.  The VJP takes
+ * d_grad_probs in the packed layout and writes grad_A, grad_b, grad_c as the
+ * one-shape VJP.  The launch plan (grouping, offsets, tile tables) is built
+ * on the host once per (batch, M, cutoffs, flags, tuning) and kept for the
+ * life of the process in pinned memory, so the calls can be captured in a
+ * CUDA graph; each call copies it into the workspace.  Errors as for
+ * fock_diag_probs_batched; FK_EUNSUPPORTED when a phase holds 2^30 tiles or
+ * more.
+ */
+int fk_multi_workspace_size(int batch, int M, const int *host_cutoffs, int op, unsigned flags,
+                            size_t *bytes, int64_t *host_out_offsets);
+int fock_diag_probs_multi_batched(int batch, const fk_c128 *d_A, const fk_c128 *d_b, const fk_c128 *d_c,
+                                  int M, const int *host_cutoffs, fk_c128 *d_probs, unsigned flags,
+                                  void *d_ws, size_t ws_bytes, void *stream);
+int fock_diag_probs_multi_vjp_batched(int batch, const fk_c128 *d_A, const fk_c128 *d_b,
+                                      const fk_c128 *d_c, int M, const int *host_cutoffs,
+                                      const fk_c128 *d_grad_probs, fk_c128 *d_grad_A, fk_c128 *d_grad_b,
+                                      fk_c128 *d_grad_c, unsigned flags, void *d_ws, size_t ws_bytes,
+                                      void *stream);
+
+/*
  * Tile shape of the all-detected walk kernels, process-wide default (the
  * paper has no counterpart: the autotuner in paper_2303_08879_gb300/
  * autotune.py times the shapes on the caller's workload and sets the

@@ -18,7 +18,9 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfockdiag.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cpp", "circuit.cpp", "walk_diag.cu", "walk_cond.cu", "mlp.cu", "herald.cu", "probe.cu", "static_ws.cu",
-           "walk_pure.cu"]
+           "walk_pure.cu", "multi.cpp", "walk_diag_tc1.cu", "walk_diag_tc2.cu"]
+# walk_diag_fp64.cu once per FP64 tile shape (pivots per tile, rows per chunk)
+FP64_SHAPES = [(128, 8), (128, 4), (64, 8), (64, 4), (256, 8)]
 
 
 def nvcc() -> str:
@@ -47,12 +49,15 @@ def build(verbose: bool = False, extra_flags=()) -> str:
     cc = nvcc()
     jobs = []
     objs = []
-    for src in SOURCES:
+    units = [(src, src + ".o", []) for src in SOURCES]
+    units += [("walk_diag_fp64.cu", f"walk_diag_fp64_{t}_{c}.o", [f"-DFK_TPB={t}", f"-DFK_CH={c}"])
+              for t, c in FP64_SHAPES]
+    for src, oname, defs in units:
         path = os.path.join(CSRC, src)
-        obj = os.path.join(BUILD, src + ".o")
+        obj = os.path.join(BUILD, oname)
         objs.append(obj)
         if _stale(obj, [path, __file__] + headers):
-            cmd = [cc] + _flags(extra_flags) + ["-c", path, "-o", obj]
+            cmd = [cc] + _flags(extra_flags) + defs + ["-c", path, "-o", obj]
             if src.endswith(".cu"):
                 cmd += ["-Xptxas", "-v"] if verbose else []
             jobs.append(cmd)
@@ -61,6 +66,8 @@ def build(verbose: bool = False, extra_flags=()) -> str:
         r = subprocess.run(cmd, capture_output=True, text=True)
         return cmd, r
 
+    # the heaviest units first, so the parallel build ends soon after them
+    jobs.sort(key=lambda c: 0 if "walk_diag" in c[-3] else 1)
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 1))) as ex:
         for cmd, r in ex.map(run, jobs):
             if verbose or r.returncode:

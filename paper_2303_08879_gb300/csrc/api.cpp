@@ -841,3 +841,53 @@ int fk_gaussian_to_pure_triple(int M, const double *V, const double *mean, fk_c1
 }
 
 }  // extern "C"
+
+// ----------------------------------------------- per-circuit cutoffs (several shapes)
+extern "C" {
+
+int fk_multi_workspace_size(int batch, int M, const int *cutoffs, int op, unsigned flags, size_t *bytes,
+                            int64_t *out_offsets)
+{
+    if (!bytes || (op != FK_OP_DIAG && op != FK_OP_DIAG_VJP)) return FK_EINVAL;
+    const MultiPlan *p = nullptr;
+    int rc = get_multi_plan(batch, M, cutoffs, flags, &p);
+    if (rc) return rc;
+    *bytes = op == FK_OP_DIAG_VJP ? p->total_vjp : p->total_fwd;
+    if (out_offsets)
+        for (int i = 0; i <= batch; ++i) out_offsets[i] = p->out_offsets[i];
+    return FK_OK;
+}
+
+int fock_diag_probs_multi_batched(int batch, const fk_c128 *A, const fk_c128 *b, const fk_c128 *c, int M,
+                                  const int *cutoffs, fk_c128 *probs, unsigned flags, void *ws,
+                                  size_t ws_bytes, void *stream)
+{
+    if (batch < 1 || !A || !b || !c || !probs || !ws) return FK_EINVAL;
+    const MultiPlan *p = nullptr;
+    int rc = get_multi_plan(batch, M, cutoffs, flags, &p);
+    if (rc) return rc;
+    if (ws_bytes < p->total_fwd || !aligned(ws)) return FK_EWORKSPACE;
+    return launch_multi_forward(*p, flags, A, b, c, probs, ws, stream);
+}
+
+int fock_diag_probs_multi_vjp_batched(int batch, const fk_c128 *A, const fk_c128 *b, const fk_c128 *c,
+                                      int M, const int *cutoffs, const fk_c128 *gprobs, fk_c128 *gA,
+                                      fk_c128 *gb, fk_c128 *gc, unsigned flags, void *ws, size_t ws_bytes,
+                                      void *stream)
+{
+    if (batch < 1 || !A || !b || !c || !gprobs || !gA || !gb || !gc || !ws) return FK_EINVAL;
+    const MultiPlan *p = nullptr;
+    int rc = get_multi_plan(batch, M, cutoffs, flags, &p);
+    if (rc) return rc;
+    if (ws_bytes < p->total_vjp || !aligned(ws)) return FK_EWORKSPACE;
+    if (flags & FK_FLAG_RECOMPUTE) {
+        // the forward's probabilities land in the adjoint region, which the
+        // VJP either clears (b != 0) or overwrites before reading (b = 0)
+        if ((size_t)p->n_out * 16 > p->total_vjp - p->off_vjp) return FK_EWORKSPACE;
+        rc = launch_multi_forward(*p, flags, A, b, c, (char *)ws + p->off_vjp, ws, stream);
+        if (rc) return rc;
+    }
+    return launch_multi_vjp(*p, flags, A, b, c, gprobs, gA, gb, gc, ws, stream);
+}
+
+}  // extern "C"

@@ -5,6 +5,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "fk_shape.h"
 
 namespace fk {
@@ -48,6 +50,20 @@ inline size_t diag_geo_bytes(const DiagShape &sh)
 {
     return sh.M >= 1 && sh.M <= 8 ? (size_t)sh.n_ap * kGeoInts * sizeof(int) : 0;
 }
+
+// One group of a launch of several all-detected shapes (circuits with
+// different cutoffs in one launch): the circuits that share a shape (the same
+// kept cutoffs and kept modes), where their state lives in the workspace
+// (byte offsets), and where their caller indices and output offsets start in
+// the launch's tables.
+struct DiagGroup {
+    DiagShape sh;
+    int B;                    // circuits of the group
+    int first;                // first entry in the launch's cidx / oidx tables
+    int slots;                // partial-sum slots per circuit (VJP)
+    int pad;
+    int64_t As, bs, dig, geo, F, Fbar, scratch, partA, partb;
+};
 
 // Workspace layout of the all-detected walk for `batch` circuits.
 struct DiagLayout {
@@ -110,6 +126,24 @@ int launch_cond_vjp(const CondPlan &plan, unsigned flags, const void *A, const v
                     const void *c, const void *grho, void *gA, void *gb, void *gc, void *ws,
                     const CondLayout &lay, void *stream);
 
+// Compiled kernels of the all-detected walk (walk_diag_fp64.cu,
+// walk_diag_tc1.cu, walk_diag_tc2.cu): pivots per tile, output rows per
+// register chunk (FP64) or K steps (tensor engine), the kernels and their
+// shared-memory size function (M, L, mode, has_b).
+struct WalkKernels {
+    int tpb, ch, ks;
+    const void *fwd, *vjp, *part;
+    size_t (*smem)(int, int, int, bool);
+};
+constexpr int kNumFp64Shapes = 5;         // 128/8, 128/4, 64/8, 64/4, 256/8
+const WalkKernels *fp64_walk_kernels_128_8();
+const WalkKernels *fp64_walk_kernels_128_4();
+const WalkKernels *fp64_walk_kernels_64_8();
+const WalkKernels *fp64_walk_kernels_64_4();
+const WalkKernels *fp64_walk_kernels_256_8();
+const WalkKernels *tc1_walk_kernels();    // M <= 4
+const WalkKernels *tc2_walk_kernels();    // M <= 8
+
 // Tile shape of the all-detected walk (pivots per tile, output rows per
 // register chunk, blocks per SM; 0 = as many as fit).  Process-wide default;
 // the flag bits of a call override it.
@@ -138,6 +172,38 @@ int launch_diag_vjp(const DiagShape &sh, int batch, unsigned flags, const void *
                     const void *b, const void *c, const void *gprobs, void *gA, void *gb,
                     void *gc, void *ws, const DiagLayout &lay, void *stream,
                     const EarlyStop *es = nullptr);
+// Several shapes in one launch: the plan (host-side, cached per batch shape
+// and grid) and its launchers.  The plan's device image, copied into the
+// workspace by every call, is DiagGroup[G] | int cidx[B] | int64 oidx[B] |
+// int gtiles[L][2][G + 1] (per level and phase kind (AP 0, DP 1), prefix sums
+// over the groups of their tiles).
+struct MultiPlan {
+    int B, M, G, L;           // circuits, caller's modes, groups, levels (largest group)
+    DiagShape env;            // largest kept M and L over the groups, has_b (kernel choice, smem)
+    int grid_fwd;             // forward grid
+    int grid, slots_pb;       // VJP grid (the partial-sum pass for the tensor engine) and
+                              // partial-sum slots per block it was laid out for
+    int64_t n_out;            // packed outputs (sum over circuits of prod C)
+    size_t off_plan, plan_bytes, off_views, off_ctr, total_fwd;
+    size_t off_vjp, off_scratch, off_part, total_vjp;   // VJP regions: Fbar | scratch | partials
+    const void *host_plan;    // the device image (host copy)
+    std::vector<int64_t> out_offsets;   // [B + 1]
+};
+int get_multi_plan(int batch, int M, const int *cutoffs, unsigned flags, const MultiPlan **plan);
+int multi_pinned_plan(const MultiPlan &plan, const void **out);
+// The process-default tuning resolved with the flag bits of a call (engine,
+// tpb, ch, blocks-per-SM cap): part of the key of cached launch plans.
+void tuning_key(unsigned flags, int out[4]);
+// Kernel variant and grid of a several-shape launch (the envelope selects the
+// variant): the grid is capped at useful[0..2] blocks (tiles of the largest
+// phases at 64/128/256 pivots, summed over the circuits) or, for the tensor
+// engine's partial pass, useful[3] (all its tiles).  *tpb = pivots per tile.
+int multi_geometry(const DiagShape &env, unsigned flags, bool vjp, const int64_t useful[4], int *grid,
+                   int *slots_pb, int *tpb);
+int launch_multi_forward(const MultiPlan &p, unsigned flags, const void *A, const void *b, const void *c,
+                         void *probs, void *ws, void *stream);
+int launch_multi_vjp(const MultiPlan &p, unsigned flags, const void *A, const void *b, const void *c,
+                     const void *gprobs, void *gA, void *gb, void *gc, void *ws, void *stream);
 int launch_wait_selftest(void *ws, unsigned long long timeout_ns, void *stream);
 // FK_FLAG_CHECK_FINITE: scan n_A, n_b, n_c complex values of A, b, c (device)
 // for NaN or Inf; on one, ctl->status = FK_ENONFINITE and ctl->skip = 1.

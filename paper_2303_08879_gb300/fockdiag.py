@@ -42,6 +42,7 @@ EXPORTS = [
     "fk_describe_global_schedule", "fock_diag_probs_stop_batched", "fock_diag_probs_stop_vjp_batched",
     "fk_gaussian_to_pure_triple", "fk_pure_workspace_size", "fock_pure_amplitudes_batched",
     "fock_pure_amplitudes_vjp_batched", "fk_diag_tuning_flags",
+    "fk_multi_workspace_size", "fock_diag_probs_multi_batched", "fock_diag_probs_multi_vjp_batched",
 ]
 
 
@@ -103,6 +104,9 @@ def lib():
         L.fk_diag_set_tuning.argtypes = [I, I, I]
         L.fk_diag_set_engine.argtypes = [I]
         L.fk_diag_tuning_flags.argtypes = [I, I, I, I, ctypes.POINTER(ctypes.c_uint)]
+        L.fk_multi_workspace_size.argtypes = [I, I, P, I, U, ctypes.POINTER(Z), P]
+        L.fock_diag_probs_multi_batched.argtypes = [I, P, P, P, I, P, P, U, P, Z, P]
+        L.fock_diag_probs_multi_vjp_batched.argtypes = [I, P, P, P, I, P, P, P, P, P, U, P, Z, P]
         L.fk_diag_set_vjp_split_event.argtypes = [P]
         L.fk_herald_scores.argtypes = [I, P, P, I, P, ctypes.c_double, P, P, P, P]
         L.fk_circuit_triple.argtypes = [I, P, ctypes.c_double, P, P, P, P, P, P]
@@ -280,6 +284,78 @@ def fock_diag_probs_vjp_batched(A, b, c, cutoffs, grad_probs, ws, flags=0, strea
                                            _ptr(grad_probs), _ptr(gA), _ptr(gb), _ptr(gc), flags,
                                            _ptr(ws), ws.numel(), _stream(stream))
     _check(st, "fock_diag_probs_vjp_batched")
+    return gA, gb, gc
+
+
+# ------------------------------------------- per-circuit cutoffs, one launch
+def _multi_cut(cutoffs):
+    cut = np.ascontiguousarray(np.asarray(cutoffs, dtype=np.int32))
+    if cut.ndim != 2:
+        raise ValueError("cutoffs must be [batch][M]")
+    return cut, cut.shape[0], cut.shape[1]
+
+
+def fk_multi_workspace_size(cutoffs, op=FK_OP_DIAG_VJP, flags=0):
+    """(bytes, out_offsets[B + 1]) of a launch whose circuits have their own cutoffs."""
+    cut, B, M = _multi_cut(cutoffs)
+    n = ctypes.c_size_t(0)
+    offs = np.zeros(B + 1, np.int64)
+    _check(lib().fk_multi_workspace_size(B, M, cut.ctypes.data, op, flags, ctypes.byref(n),
+                                         offs.ctypes.data), "fk_multi_workspace_size")
+    return int(n.value), offs
+
+
+def multi_blocks(probs, cutoffs):
+    """Per-circuit views [*cutoffs[i]] of the packed output."""
+    cut, B, M = _multi_cut(cutoffs)
+    out, off = [], 0
+    for i in range(B):
+        n = int(np.prod(cut[i]))
+        out.append(probs[off:off + n].view(*(int(x) for x in cut[i])))
+        off += n
+    return out
+
+
+def fock_diag_probs_multi_batched(A, b, c, cutoffs, probs=None, flags=0, ws=None, stream=None,
+                                  for_vjp=True):
+    """p(n) of a batch whose circuits have different cutoffs (cutoffs [B][M];
+    unused modes of a circuit get cutoff 1), in one launch.  Returns
+    (probs packed [sum_i prod C_i], offsets [B + 1], ws)."""
+    for n, t in (("A", A), ("b", b), ("c", c)):
+        _need_cuda_c128(n, t)
+    cut, B, M = _multi_cut(cutoffs)
+    if A.shape != (B, 2 * M, 2 * M) or b.shape != (B, 2 * M) or c.shape != (B,):
+        raise ValueError("shapes must be A[B,2M,2M], b[B,2M], c[B]")
+    need, offs = fk_multi_workspace_size(cut, FK_OP_DIAG_VJP if for_vjp else FK_OP_DIAG, flags)
+    if probs is None:
+        probs = torch.empty(int(offs[-1]), dtype=torch.complex128, device=A.device)
+    _need_cuda_c128("probs", probs)
+    if ws is None:
+        ws = workspace(need, A.device)
+    st = lib().fock_diag_probs_multi_batched(B, _ptr(A), _ptr(b), _ptr(c), M, cut.ctypes.data, _ptr(probs),
+                                             flags, _ptr(ws), ws.numel(), _stream(stream))
+    _check(st, "fock_diag_probs_multi_batched")
+    return probs, offs, ws
+
+
+def fock_diag_probs_multi_vjp_batched(A, b, c, cutoffs, grad_probs, ws, flags=0, stream=None, out=None):
+    """(grad_A, grad_b, grad_c) of a per-circuit-cutoff batch; grad_probs packed
+    like the forward's output.  ws = the forward's workspace, or None to
+    recompute the forward."""
+    for n, t in (("A", A), ("b", b), ("c", c), ("grad_probs", grad_probs)):
+        _need_cuda_c128(n, t)
+    cut, B, M = _multi_cut(cutoffs)
+    if out is None:
+        gA = torch.empty_like(A); gb = torch.empty_like(b); gc = torch.empty_like(c)
+    else:
+        gA, gb, gc = out
+    if ws is None:
+        ws = workspace(fk_multi_workspace_size(cut, FK_OP_DIAG_VJP, flags)[0], A.device)
+        flags |= FK_FLAG_RECOMPUTE
+    st = lib().fock_diag_probs_multi_vjp_batched(B, _ptr(A), _ptr(b), _ptr(c), M, cut.ctypes.data,
+                                                 _ptr(grad_probs), _ptr(gA), _ptr(gb), _ptr(gc), flags,
+                                                 _ptr(ws), ws.numel(), _stream(stream))
+    _check(st, "fock_diag_probs_multi_vjp_batched")
     return gA, gb, gc
 
 
