@@ -51,10 +51,29 @@ struct CondArgs {
     unsigned long long timeout_ns;
 };
 
+// Positions (in the detected structure) of one pivot's reads and writes;
+// every thread of a tile shares the pivot, so thread 0 computes them once per
+// tile into shared memory.
+struct PGeom {
+    int64_t yP;                 // pivot position
+    int64_t ia;                 // AP pivot: its entry in the diagonal-read scratch
+    int64_t yr[2 * FK_MAXM];    // read positions, column j
+    int64_t yw[2 * FK_MAXM];    // write positions, row i
+    int den[2 * FK_MAXM];       // P_w + 1 of row i
+    unsigned vmask, nmask;      // valid detected reads / needed writes
+    int N;                      // rows = detected read columns
+    int row0;                   // first detected lattice index of rows/cols (2K or 0)
+    double fdiag;               // prod d_j! of the diagonal written by row 1 (AP)
+};
+
 struct CSmem {
     double *inv, *fact, *sqf;   // 1/v, v!, sqrt(v!)
     double2 *Ar, *br;           // current circuit's reduced A (Dmax x Dmax) and b
-    double2 *R, *Y, *FP;        // [Dmax][RS], [Dmax][RS], [RS]
+    double *A3;                 // [3][Dmax][Dmax]: Re A, Re A + Im A, Im A - Re A
+    double *R3, *Y3;            // [3][Dmax][RS] reads (Re x, Im x, Re x + Im x), scaled
+                                // output adjoints (Re y, Im y, Re y + Im y)
+    double2 *FP;                // [RS] pivot values (VJP)
+    PGeom *geo;                 // the current tile's pivot
     int *ctiles;                // [MAXB + 1] tile prefix over circuits
     int loaded;
 };
@@ -63,8 +82,11 @@ __host__ __device__ inline size_t cond_smem_bytes(int Dmax, bool vjp)
 {
     size_t n = 3 * kTabN * sizeof(double);
     n += (size_t)Dmax * Dmax * sizeof(double2) + (size_t)Dmax * sizeof(double2);
-    n += (size_t)Dmax * RS * sizeof(double2);    // at most 2M matrix columns per pivot
-    if (vjp) n += (size_t)Dmax * RS * sizeof(double2) + RS * sizeof(double2);
+    n += 3 * (size_t)Dmax * Dmax * sizeof(double);
+    n += 3 * (size_t)Dmax * RS * sizeof(double);    // at most 2M matrix columns per pivot
+    if (vjp) n += 3 * (size_t)Dmax * RS * sizeof(double) + RS * sizeof(double2);
+    n = (n + 15) & ~(size_t)15;
+    n += sizeof(PGeom);
     n += (MAXB + 1) * sizeof(int);
     return n + 64;
 }
@@ -74,21 +96,44 @@ __device__ CSmem carve(const CondArgs &a, bool vjp)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CSmem s;
     unsigned char *p = smem_raw;
+    const size_t Dm = (size_t)a.Dmax;
     s.inv = (double *)p; p += kTabN * sizeof(double);
     s.fact = (double *)p; p += kTabN * sizeof(double);
     s.sqf = (double *)p; p += kTabN * sizeof(double);
-    s.Ar = (double2 *)p; p += (size_t)a.Dmax * a.Dmax * sizeof(double2);
-    s.br = (double2 *)p; p += (size_t)a.Dmax * sizeof(double2);
-    s.R = (double2 *)p; p += (size_t)a.Dmax * RS * sizeof(double2);
+    s.Ar = (double2 *)p; p += Dm * Dm * sizeof(double2);
+    s.br = (double2 *)p; p += Dm * sizeof(double2);
+    s.A3 = (double *)p; p += 3 * Dm * Dm * sizeof(double);
+    s.R3 = (double *)p; p += 3 * Dm * RS * sizeof(double);
     if (vjp) {
-        s.Y = (double2 *)p; p += (size_t)a.Dmax * RS * sizeof(double2);
+        s.Y3 = (double *)p; p += 3 * Dm * RS * sizeof(double);
         s.FP = (double2 *)p; p += RS * sizeof(double2);
     } else {
-        s.Y = s.FP = nullptr;
+        s.Y3 = nullptr;
+        s.FP = nullptr;
     }
+    p = smem_raw + ((p - smem_raw + 15) & ~(size_t)15);
+    s.geo = (PGeom *)p; p += sizeof(PGeom);
     s.ctiles = (int *)p;
     s.loaded = -1;
     return s;
+}
+
+// Plane k (0: Re, 1: Im, 2: Re + Im) of column j of a per-thread buffer.
+__device__ __forceinline__ double &pl(double *buf, int Dm, int k, int j, int t)
+{
+    return buf[((size_t)k * Dm + j) * RS + t];
+}
+
+__device__ __forceinline__ void put3(double *buf, int Dm, int j, int t, double2 v)
+{
+    pl(buf, Dm, 0, j, t) = v.x;
+    pl(buf, Dm, 1, j, t) = v.y;
+    pl(buf, Dm, 2, j, t) = v.x + v.y;
+}
+
+__device__ __forceinline__ double2 get2(double *buf, int Dm, int j, int t)
+{
+    return make_double2(pl(buf, Dm, 0, j, t), pl(buf, Dm, 1, j, t));
 }
 
 __device__ void build_tables(CSmem &s)
@@ -112,7 +157,13 @@ __device__ void load_circuit(const CondArgs &a, CSmem &s, int c)
     if (s.loaded == c) return;
     __syncthreads();
     const int Dm = a.Dmax;
-    for (int e = threadIdx.x; e < Dm * Dm; e += blockDim.x) s.Ar[e] = a.Ar[(size_t)c * Dm * Dm + e];
+    for (int e = threadIdx.x; e < Dm * Dm; e += blockDim.x) {
+        const double2 v = a.Ar[(size_t)c * Dm * Dm + e];
+        s.Ar[e] = v;
+        s.A3[e] = v.x;
+        s.A3[Dm * Dm + e] = v.x + v.y;
+        s.A3[2 * Dm * Dm + e] = v.y - v.x;
+    }
     for (int e = threadIdx.x; e < Dm; e += blockDim.x) s.br[e] = a.br[(size_t)c * Dm + e];
     __syncthreads();
     s.loaded = c;
@@ -277,21 +328,10 @@ __device__ CTile decode(const CondArgs &a, const CSmem &s, int kind, int lev, in
 }
 
 // ----------------------------------------------------- pivot geometry
-// Positions (in the detected structure) of one pivot's reads and writes.
-struct PGeom {
-    int64_t yP;             // pivot position
-    int64_t yr[2 * FK_MAXM];    // read positions, column j
-    int64_t yw[2 * FK_MAXM];    // write positions, row i
-    int den[2 * FK_MAXM];       // P_w + 1 of row i
-    unsigned vmask, nmask;      // valid detected reads / needed writes
-    int N;                      // rows = detected read columns
-    int row0;                   // first detected lattice index of rows/cols (2K or 0)
-    double fdiag;               // prod d_j! of the diagonal written by row 1 (AP)
-};
-
 __device__ PGeom ap_geom(const DiagShape &ds, const Dig &e, int K, const CSmem &s)
 {
     PGeom g;
+    g.ia = ds.off_ap[K] + box_index(ds, e, K, K, 1, -1, 0);
     const int M = ds.M;
     g.N = 2 * (M - K);
     g.row0 = 2 * K;
@@ -330,6 +370,7 @@ __device__ PGeom dp_geom(const DiagShape &ds, const Dig &d)
 {
     PGeom g;
     const int M = ds.M;
+    g.ia = 0;
     g.N = 2 * M;
     g.row0 = 0;
     g.fdiag = 0.0;
@@ -364,66 +405,88 @@ __device__ __forceinline__ int col_index(const PGeom &g, int Db, int j)
     return j < g.N ? g.row0 + j : Db + (j - g.N);
 }
 
+// The current tile's pivot geometry, computed once by thread 0.
+__device__ const PGeom &tile_geometry(const CondArgs &a, CSmem &s, const CTile &tl, int kind, int lev)
+{
+    const CondCirc &cc = a.plan[tl.circ];
+    const DiagShape &ds = cc.dsh;
+    __syncthreads();   // the previous tile's readers are done
+    if (threadIdx.x == 0) {
+        const int K = kind == 0 ? tl.seg : 0;
+        const Dig e = unrank(ds.C, ds.M, ltab(a, cc), K, 1, lev, tl.rank);
+        *s.geo = kind == 0 ? ap_geom(ds, e, K, s) : dp_geom(ds, e);
+    }
+    __syncthreads();
+    return *s.geo;
+}
+
 // -------------------------------------------------------------- forward
 // One (pivot, u) pair per thread: rows = detected writes, columns = detected
-// reads then undetected reads, plus the b-term on the pivot value.
+// reads then undetected reads, plus the b-term on the pivot value.  Gauss's
+// three-multiplication complex product (A in the planes Re A, Re A + Im A,
+// Im A - Re A; reads as Re x, Im x, Re x + Im x): three DFMA per term.
 template <bool HASB>
 __device__ void pair_forward(const CondArgs &a, CSmem &s, const CTile &tl, int kind, int lev)
 {
     const CondCirc &cc = a.plan[tl.circ];
     const DiagShape &ds = cc.dsh;
     load_circuit(a, s, tl.circ);
-    const int t = threadIdx.x;
+    const PGeom &g = tile_geometry(a, s, tl, kind, lev);
+    const int t = threadIdx.x, Dm = a.Dmax;
     const int u = tl.chunk * TPB + t;
     const bool act = u < cc.U2;
-    const LevelTab W = ltab(a, cc);
-    const Dig e = (kind == 0) ? unrank(ds.C, ds.M, W, tl.seg, 1, lev, tl.rank)
-                              : unrank(ds.C, ds.M, W, 0, 1, lev, tl.rank);
-    const PGeom g = (kind == 0) ? ap_geom(ds, e, tl.seg, s) : dp_geom(ds, e);
-    const int Db = 2 * ds.M, tU = 2 * cc.nU, NC = g.N + tU;
+    const int Db = 2 * ds.M, tU = 2 * cc.nU, N = g.N, NC = N + tU, row0 = g.row0;
+    const unsigned vmask = g.vmask, nm = g.nmask;   // uniform: every thread of the tile shares the pivot
+    const int64_t yP = g.yP;
     const double2 *F = a.F + cc.off_F;
     unsigned umask = 0;
     double2 PV = czero();
     if (act) {
-        for (int j = 0; j < g.N; ++j)
-            s.R[j * RS + t] = ((g.vmask >> j) & 1u) ? __ldcg(F + g.yr[j] * cc.U2 + u) : czero();
+        for (int j = 0; j < N; ++j)
+            put3(s.R3, Dm, j, t, ((vmask >> j) & 1u) ? __ldcg(F + g.yr[j] * cc.U2 + u) : czero());
         for (int q = 0; q < tU; ++q) {
             double2 v = czero();
             if (udigit(cc, u, q) >= 1) {
                 umask |= 1u << q;
-                v = __ldcg(F + g.yP * cc.U2 + u - cc.ustride[q]);
+                v = __ldcg(F + yP * cc.U2 + u - cc.ustride[q]);
             }
-            s.R[(g.N + q) * RS + t] = v;
+            put3(s.R3, Dm, N + q, t, v);
         }
-        if (HASB) PV = __ldcg(F + g.yP * cc.U2 + u);
+        if (HASB) PV = __ldcg(F + yP * cc.U2 + u);
     } else {
-        for (int j = 0; j < NC; ++j) s.R[j * RS + t] = czero();
+        for (int j = 0; j < NC; ++j) put3(s.R3, Dm, j, t, czero());
     }
-    const unsigned cm = __reduce_or_sync(0xffffffffu, act ? (g.vmask | (umask << g.N)) : 0u);
-    const unsigned nm = g.nmask;   // uniform: every thread of the tile shares the pivot
+    const unsigned cm = __reduce_or_sync(0xffffffffu, act ? (vmask | (umask << N)) : 0u);
     double2 *Fw = a.F + cc.off_F;
+    const size_t DD = (size_t)Dm * Dm;
+    const double *Ar = s.A3, *Ap = s.A3 + DD, *Am = s.A3 + 2 * DD;
     constexpr int CH = 8;
-    for (int i0 = 0; i0 < g.N; i0 += CH) {
+    for (int i0 = 0; i0 < N; i0 += CH) {
         if (((nm >> i0) & 0xffu) == 0) continue;
-        double2 acc[CH];
+        double p1[CH], p2[CH], p3[CH];
 #pragma unroll
-        for (int ii = 0; ii < CH; ++ii)
-            acc[ii] = (HASB && i0 + ii < g.N) ? cmul(s.br[g.row0 + i0 + ii], PV) : czero();
+        for (int ii = 0; ii < CH; ++ii) p1[ii] = p2[ii] = p3[ii] = 0.0;
         for (int j = 0; j < NC; ++j) {
             if (!((cm >> j) & 1u)) continue;
-            const double2 x = s.R[j * RS + t];
+            const double xr = pl(s.R3, Dm, 0, j, t), xi = pl(s.R3, Dm, 1, j, t), xs = pl(s.R3, Dm, 2, j, t);
             const int cj = col_index(g, Db, j);
 #pragma unroll
             for (int ii = 0; ii < CH; ++ii)
-                if (i0 + ii < g.N && ((nm >> (i0 + ii)) & 1u))
-                    acc[ii] = cfma(s.Ar[(g.row0 + i0 + ii) * a.Dmax + cj], x, acc[ii]);
+                if (i0 + ii < N && ((nm >> (i0 + ii)) & 1u)) {
+                    const size_t o = (size_t)(row0 + i0 + ii) * Dm + cj;
+                    p1[ii] = fma(Ar[o], xs, p1[ii]);
+                    p2[ii] = fma(Ap[o], xi, p2[ii]);
+                    p3[ii] = fma(Am[o], xr, p3[ii]);
+                }
         }
         if (!act) continue;
 #pragma unroll
         for (int ii = 0; ii < CH; ++ii) {
             const int i = i0 + ii;
-            if (i < g.N && ((nm >> i) & 1u)) {
-                const double2 v = rscale(acc[ii], s.inv[g.den[i]]);
+            if (i < N && ((nm >> i) & 1u)) {
+                double2 acc = make_double2(p1[ii] - p2[ii], p1[ii] + p3[ii]);
+                if (HASB) acc = cadd(acc, cmul(s.br[row0 + i], PV));
+                const double2 v = rscale(acc, s.inv[g.den[i]]);
                 Fw[g.yw[i] * cc.U2 + u] = v;
                 if (kind == 0 && i == 1) {          // a diagonal of the detected modes
                     int ket, bra;
@@ -471,68 +534,68 @@ __device__ void pair_reverse(const CondArgs &a, CSmem &s, const CTile &tl, int k
     const CondCirc &cc = a.plan[tl.circ];
     const DiagShape &ds = cc.dsh;
     load_circuit(a, s, tl.circ);
+    const PGeom &g = tile_geometry(a, s, tl, kind, lev);
     const int t = threadIdx.x;
     const int u = tl.chunk * TPB + t;
     const bool act = u < cc.U2;
-    const LevelTab W = ltab(a, cc);
-    const int K = (kind == 0) ? tl.seg : 0;
-    const Dig e = (kind == 0) ? unrank(ds.C, ds.M, W, K, 1, lev, tl.rank)
-                              : unrank(ds.C, ds.M, W, 0, 1, lev, tl.rank);
-    const PGeom g = (kind == 0) ? ap_geom(ds, e, K, s) : dp_geom(ds, e);
-    const int Db = 2 * ds.M, tU = 2 * cc.nU, NC = g.N + tU, Dm = a.Dmax;
+    const int Db = 2 * ds.M, tU = 2 * cc.nU, N = g.N, NC = N + tU, Dm = a.Dmax, row0 = g.row0;
+    const unsigned vmask = g.vmask, nm = g.nmask;
+    const int64_t yP = g.yP;
     const double2 *F = a.F + cc.off_F;
     double2 *Fb = a.Fbar + cc.off_F;
-    unsigned umask = 0, upmask = 0;
+    unsigned upmask = 0;
     if (act) {
-        for (int j = 0; j < g.N; ++j)
-            s.R[j * RS + t] = ((g.vmask >> j) & 1u) ? __ldcg(F + g.yr[j] * cc.U2 + u) : czero();
+        for (int j = 0; j < N; ++j)
+            put3(s.R3, Dm, j, t, ((vmask >> j) & 1u) ? __ldcg(F + g.yr[j] * cc.U2 + u) : czero());
         for (int q = 0; q < tU; ++q) {
             const int dq = udigit(cc, u, q);
             double2 v = czero();
-            if (dq >= 1) {
-                umask |= 1u << q;
-                v = __ldcg(F + g.yP * cc.U2 + u - cc.ustride[q]);
-            }
+            if (dq >= 1) v = __ldcg(F + yP * cc.U2 + u - cc.ustride[q]);
             if (dq + 1 < cc.CU[q >> 1]) upmask |= 1u << q;
-            s.R[(g.N + q) * RS + t] = v;
+            put3(s.R3, Dm, N + q, t, v);
         }
-        for (int i = 0; i < g.N; ++i)
-            s.Y[i * RS + t] = ((g.nmask >> i) & 1u)
-                                  ? rscale(__ldcg(Fb + g.yw[i] * cc.U2 + u), s.inv[g.den[i]])
-                                  : czero();
-        s.FP[t] = HASB ? __ldcg(F + g.yP * cc.U2 + u) : czero();
+        for (int i = 0; i < N; ++i)
+            put3(s.Y3, Dm, i, t, ((nm >> i) & 1u) ? rscale(__ldcg(Fb + g.yw[i] * cc.U2 + u), s.inv[g.den[i]])
+                                                   : czero());
+        s.FP[t] = HASB ? __ldcg(F + yP * cc.U2 + u) : czero();
     } else {
-        for (int j = 0; j < NC; ++j) s.R[j * RS + t] = czero();
-        for (int i = 0; i < g.N; ++i) s.Y[i * RS + t] = czero();
+        for (int j = 0; j < NC; ++j) put3(s.R3, Dm, j, t, czero());
+        for (int i = 0; i < N; ++i) put3(s.Y3, Dm, i, t, czero());
         s.FP[t] = czero();
     }
-    const unsigned nm = g.nmask;
-    // detected reads
+    // detected reads: Rbar_j = sum_i conj(A_{w_i l_j}) y_i, with y = yr + i yi,
+    // ys = yr + yi:  Re = sum Ar ys + sum (Ai - Ar) yi,  Im = sum Ar ys - sum (Ar + Ai) yr
+    const size_t DD = (size_t)Dm * Dm;
+    const double *Ar = s.A3, *Ap = s.A3 + DD, *Am = s.A3 + 2 * DD;
     constexpr int CH = 8;
-    for (int j0 = 0; j0 < g.N; j0 += CH) {
-        if (((g.vmask >> j0) & 0xffu) == 0) continue;
-        double2 acc[CH];
+    for (int j0 = 0; j0 < N; j0 += CH) {
+        if (((vmask >> j0) & 0xffu) == 0) continue;
+        double p1[CH], q2[CH], q3[CH];
 #pragma unroll
-        for (int jj = 0; jj < CH; ++jj) acc[jj] = czero();
-        for (int i = 0; i < g.N; ++i) {
+        for (int jj = 0; jj < CH; ++jj) p1[jj] = q2[jj] = q3[jj] = 0.0;
+        for (int i = 0; i < N; ++i) {
             if (!((nm >> i) & 1u)) continue;
-            const double2 y = s.Y[i * RS + t];
+            const double yr = pl(s.Y3, Dm, 0, i, t), yi = pl(s.Y3, Dm, 1, i, t), ys = pl(s.Y3, Dm, 2, i, t);
 #pragma unroll
             for (int jj = 0; jj < CH; ++jj)
-                if (j0 + jj < g.N && ((g.vmask >> (j0 + jj)) & 1u))
-                    acc[jj] = cfma_conj(s.Ar[(g.row0 + i) * Dm + g.row0 + j0 + jj], y, acc[jj]);
+                if (j0 + jj < N && ((vmask >> (j0 + jj)) & 1u)) {
+                    const size_t o = (size_t)(row0 + i) * Dm + row0 + j0 + jj;
+                    p1[jj] = fma(Ar[o], ys, p1[jj]);
+                    q2[jj] = fma(Am[o], yi, q2[jj]);
+                    q3[jj] = fma(Ap[o], yr, q3[jj]);
+                }
         }
         if (!act) continue;
 #pragma unroll
         for (int jj = 0; jj < CH; ++jj) {
             const int j = j0 + jj;
-            if (j < g.N && ((g.vmask >> j) & 1u)) {
+            if (j < N && ((vmask >> j) & 1u)) {
+                const double2 acc = make_double2(p1[jj] + q2[jj], p1[jj] - q3[jj]);
                 if (kind == 0 && j == 0) {
-                    const int64_t ia = ds.off_ap[K] + box_index(ds, e, K, K, 1, -1, 0);
-                    a.scratch[cc.off_scratch + ia * cc.U2 + u] = acc[jj];
+                    a.scratch[cc.off_scratch + g.ia * cc.U2 + u] = acc;
                 } else {
                     double2 *dst = Fb + g.yr[j] * cc.U2 + u;
-                    *dst = cadd(__ldcg(dst), acc[jj]);
+                    *dst = cadd(__ldcg(dst), acc);
                 }
             }
         }
@@ -541,39 +604,51 @@ __device__ void pair_reverse(const CondArgs &a, CSmem &s, const CTile &tl, int k
     if (act) {
         double2 pv = czero();
         if (HASB)
-            for (int i = 0; i < g.N; ++i)
-                if ((nm >> i) & 1u) pv = cfma_conj(s.br[g.row0 + i], s.Y[i * RS + t], pv);
+            for (int i = 0; i < N; ++i)
+                if ((nm >> i) & 1u) pv = cfma_conj(s.br[row0 + i], get2(s.Y3, Dm, i, t), pv);
         for (int q = 0; q < tU; ++q) {
             if (!((upmask >> q) & 1u)) continue;
             const int un = u + cc.ustride[q];
-            for (int i = 0; i < g.N; ++i) {
+            for (int i = 0; i < N; ++i) {
                 if (!((nm >> i) & 1u)) continue;
                 const double2 yn = rscale(__ldcg(Fb + g.yw[i] * cc.U2 + un), s.inv[g.den[i]]);
-                pv = cfma_conj(s.Ar[(g.row0 + i) * Dm + Db + q], yn, pv);
+                pv = cfma_conj(s.Ar[(row0 + i) * Dm + Db + q], yn, pv);
             }
         }
-        double2 *dst = Fb + g.yP * cc.U2 + u;
+        double2 *dst = Fb + yP * cc.U2 + u;
         *dst = cadd(__ldcg(dst), pv);
     }
-    // dL/dA (rows = detected writes, columns = all reads) and dL/db partials
+    // dL/dA (rows = detected writes, columns = all reads) and dL/db partials:
+    // one warp per entry, lanes over the tile's pairs, a fixed butterfly sum
     __syncthreads();
+    const int lane = t & 31, warp = t >> 5;
     double2 *pA = a.partA + ((size_t)tl.circ * a.grid + blockIdx.x) * Dm * Dm;
-    for (int ent = threadIdx.x; ent < g.N * NC; ent += blockDim.x) {
+    for (int ent = warp; ent < N * NC; ent += TPB / 32) {
         const int i = ent / NC, j = ent % NC;
         if (!((nm >> i) & 1u)) continue;
-        if (j < g.N && !((g.vmask >> j) & 1u)) continue;
+        if (j < N && !((vmask >> j) & 1u)) continue;
         double2 acc = czero();
-        for (int tt = 0; tt < TPB; ++tt) acc = cfma_conj(s.R[j * RS + tt], s.Y[i * RS + tt], acc);
-        double2 &d = pA[(g.row0 + i) * Dm + col_index(g, Db, j)];
-        d = cadd(d, acc);
+        for (int tt = lane; tt < TPB; tt += 32) acc = cfma_conj(get2(s.R3, Dm, j, tt), get2(s.Y3, Dm, i, tt), acc);
+        for (int o = 16; o > 0; o >>= 1) {
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+        }
+        if (lane == 0) {
+            double2 &d = pA[(row0 + i) * Dm + col_index(g, Db, j)];
+            d = cadd(d, acc);
+        }
     }
     if (HASB) {
         double2 *pb = a.partb + ((size_t)tl.circ * a.grid + blockIdx.x) * Dm;
-        for (int i = threadIdx.x; i < g.N; i += blockDim.x) {
+        for (int i = warp; i < N; i += TPB / 32) {
             if (!((nm >> i) & 1u)) continue;
             double2 acc = czero();
-            for (int tt = 0; tt < TPB; ++tt) acc = cfma_conj(s.FP[tt], s.Y[i * RS + tt], acc);
-            pb[g.row0 + i] = cadd(pb[g.row0 + i], acc);
+            for (int tt = lane; tt < TPB; tt += 32) acc = cfma_conj(s.FP[tt], get2(s.Y3, Dm, i, tt), acc);
+            for (int o = 16; o > 0; o >>= 1) {
+                acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+                acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+            }
+            if (lane == 0) pb[row0 + i] = cadd(pb[row0 + i], acc);
         }
     }
     __syncthreads();
