@@ -46,7 +46,7 @@ NCIRC = 16
 # each walk kernel on this 16-circuit workload, captured with ncu on a
 # 2-circuit launch and scaled by 8: circuits share no data, so traffic grows
 # in proportion to them.  Valid only for the kernel source it was measured on
-# (sha256 prefix of csrc/walk_diag.cu) and the engine / tile shape; reported
+# (sha256 prefix of csrc/walk_diag_impl.cuh) and the engine / tile shape; reported
 # as null once either differs.
 TRAFFIC = {"kernel_sha": "97dc32c248256fc1", "tuning": ["tensor", 128, 4, 0],
            "bytes_per_launch": {"diag_forward_kernel": 8 * (495558656 + 853413888),
@@ -66,7 +66,8 @@ def measured_hbm_gbs():
 
 
 def kernel_sha():
-    with open(os.path.join(ROOT, "paper_2303_08879_gb300", "csrc", "walk_diag.cu"), "rb") as f:
+    """sha256 prefix of the walk kernels' source (csrc/walk_diag_impl.cuh)."""
+    with open(os.path.join(ROOT, "paper_2303_08879_gb300", "csrc", "walk_diag_impl.cuh"), "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
