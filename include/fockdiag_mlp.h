@@ -68,6 +68,22 @@ int fk_herald_scores(int batch, const fk_c128 *d_rho, const int64_t *d_offsets, 
                      const fk_c128 *d_target, double lambda, double *d_P, double *d_F,
                      fk_c128 *d_grad_rho, void *stream);
 
+/*
+ * The tensor-core GEMM the 256-wide layers of the model run on (exposed for
+ * its own tests; the paper has no counterpart): d_C [M][N] fp32 =
+ * d_A [M][K] d_B [N][K]^T, both operands bf16 row-major (K contiguous), on
+ * the fifth-generation tensor cores (tcgen05.mma, fp32 accumulation in
+ * tensor memory, operand tiles loaded by TMA).  N must be a multiple of 256
+ * and K of 8 (TMA row strides are multiples of 16 bytes); base pointers
+ * 16-byte aligned.  ksplit > 1 splits K over CTAs into d_partials
+ * [ceil(K / k_slice)][M][N] fp32 (at most ksplit slices) summed in a fixed
+ * order into d_C.  d_status (device int, may be NULL) becomes FK_ETIMEOUT if
+ * a wait inside the kernel ran out (the kernel then returns without
+ * writing).  FK_EINVAL for bad sizes, FK_ECUDA for a failed launch.
+ */
+int fk_tc_gemm_bf16(int M, int N, int K, const void *d_A, const void *d_B, float *d_C,
+                    float *d_partials, int ksplit, int *d_status, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

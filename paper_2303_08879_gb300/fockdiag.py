@@ -43,6 +43,7 @@ EXPORTS = [
     "fk_gaussian_to_pure_triple", "fk_pure_workspace_size", "fock_pure_amplitudes_batched",
     "fock_pure_amplitudes_vjp_batched", "fk_diag_tuning_flags",
     "fk_multi_workspace_size", "fock_diag_probs_multi_batched", "fock_diag_probs_multi_vjp_batched",
+    "fk_tc_gemm_bf16",
 ]
 
 
@@ -105,6 +106,7 @@ def lib():
         L.fk_diag_set_engine.argtypes = [I]
         L.fk_diag_tuning_flags.argtypes = [I, I, I, I, ctypes.POINTER(ctypes.c_uint)]
         L.fk_multi_workspace_size.argtypes = [I, I, P, I, U, ctypes.POINTER(Z), P]
+        L.fk_tc_gemm_bf16.argtypes = [I, I, I, P, P, P, P, I, P, P]
         L.fock_diag_probs_multi_batched.argtypes = [I, P, P, P, I, P, P, U, P, Z, P]
         L.fock_diag_probs_multi_vjp_batched.argtypes = [I, P, P, P, I, P, P, P, P, P, U, P, Z, P]
         L.fk_diag_set_vjp_split_event.argtypes = [P]
