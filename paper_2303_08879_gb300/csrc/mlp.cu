@@ -1,7 +1,9 @@
 // mlp.cu -- the learned proposal model: a 15 -> 256 -> 256 -> 256 -> 2
 // multilayer perceptron with BF16 weights and activations, FP32 accumulation
-// on the tensor cores (mma.sync m16n8k16), SiLU hidden activations, an MSE
-// loss and Adam on FP32 master weights.  It predicts, from 15 circuit
+// on the tensor cores, SiLU hidden activations, an MSE loss and Adam on FP32
+// master weights.  The 256 x 256 layers (forward, input gradients and weight
+// gradients) run on the tcgen05 GEMM of mlp_tc.cu; the 16-wide first and
+// last layers on a small mma.sync GEMM.  It predicts, from 15 circuit
 // parameters, two scores of the state the circuit heralds; the exact
 // recurrence checks every proposal it makes.
 //
@@ -9,12 +11,14 @@
 //   master[P]  packed W1 b1 W2 b2 W3 b3 W4 b4 (W row-major [out][in])
 //   adam_m[P], adam_v[P]
 //   W1h [256][16] bf16 (input padded 15 -> 16), W2h, W3h [256][256] bf16,
-//   W4h [16][256] bf16 (output padded 2 -> 16)
+//   W4h [16][256] bf16 (output padded 2 -> 16), W2t, W3t: W2h, W3h transposed
+//   (the B operands, K-major, of the input-gradient GEMMs)
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <stdint.h>
 
+#include "mlp_tc.h"
 #include "../../include/fockdiag.h"
 #include "../../include/fockdiag_mlp.h"
 
@@ -27,7 +31,7 @@ constexpr int64_t OW1 = 0, OB1 = OW1 + NW1, OW2 = OB1 + H, OB2 = OW2 + NW2, OW3 
                   OB3 = OW3 + NW3, OW4 = OB3 + H, OB4 = OW4 + NW4, NPARAM = OB4 + OUT;
 
 struct StateLayout {
-    size_t master, m, v, w1h, w2h, w3h, w4h, total;
+    size_t master, m, v, w1h, w2h, w3h, w4h, w2t, w3t, total;
 };
 
 size_t al(size_t x) { return (x + 255) / 256 * 256; }
@@ -43,6 +47,8 @@ StateLayout state_layout()
     s.w2h = o; o = al(o + (size_t)H * H * 2);
     s.w3h = o; o = al(o + (size_t)H * H * 2);
     s.w4h = o; o = al(o + (size_t)OUTP * H * 2);
+    s.w2t = o; o = al(o + (size_t)H * H * 2);
+    s.w3t = o; o = al(o + (size_t)H * H * 2);
     s.total = o;
     return s;
 }
@@ -50,7 +56,9 @@ StateLayout state_layout()
 // Workspace per batch: activations (bf16) and pre-activations (fp32) of the
 // three hidden layers, the padded input, the output, and backward buffers.
 struct WsLayout {
-    size_t x, z1, a1, z2, a2, z3, a3, y, g3, g2, g1, gy, gp, loss, wpart, bpart, total;
+    size_t x, z1, a1, z2, a2, z3, a3, y, g3, g2, g1, gy, gp, loss, wpart, bpart;
+    size_t a1t, a2t, g2t, g3t, status, total;   // transposed [H][ldT] copies (weight-gradient operands)
+    int64_t ldT;
 };
 
 // The weight gradients contract over the batch: from 1024 samples on their
@@ -58,6 +66,9 @@ struct WsLayout {
 // in a fixed order (the output tiles alone give 4-16 CTAs).
 constexpr int kBiasRows = 4096;   // batch rows per block of the bias-gradient sums
 int ksplit(int B) { return B >= 1024 ? (B / 512 < 32 ? B / 512 : 32) : 1; }
+// K slices of the tcgen05 weight-gradient GEMMs (K = batch): about 1024
+// samples per CTA, at most 128 slices.
+int tc_ksplit(int B) { return B >= 2048 ? (B / 1024 < 128 ? B / 1024 : 128) : 1; }
 
 WsLayout ws_layout(int B)
 {
@@ -78,8 +89,15 @@ WsLayout ws_layout(int B)
     w.g1 = o; o = al(o + b * H * 2);
     w.gp = o; o = al(o + NPARAM * 4);
     w.loss = o; o = al(o + 64);
-    w.wpart = o; o = al(o + (size_t)ksplit(B) * H * H * 4);
+    const int slices = fk::tc_gemm_slices(B, tc_ksplit(B));
+    w.wpart = o; o = al(o + (size_t)(ksplit(B) > slices ? ksplit(B) : slices) * H * H * 4);
     w.bpart = o; o = al(o + (size_t)((B + kBiasRows - 1) / kBiasRows) * H * 4);
+    w.ldT = (b + 7) / 8 * 8;
+    w.a1t = o; o = al(o + (size_t)H * w.ldT * 2);
+    w.a2t = o; o = al(o + (size_t)H * w.ldT * 2);
+    w.g2t = o; o = al(o + (size_t)H * w.ldT * 2);
+    w.g3t = o; o = al(o + (size_t)H * w.ldT * 2);
+    w.status = o; o = al(o + 64);
     w.total = o;
     return w;
 }
@@ -243,21 +261,51 @@ __global__ void pack_input(const float *x, __nv_bfloat16 *xp, int B)
     xp[i] = __float2bfloat16(k < IN ? x[(int64_t)b * IN + k] : 0.f);
 }
 
-// bf16 working copies of the master weights (padded shapes)
+// bf16 working copies of the master weights (padded shapes), and the
+// transposes of W2 and W3
 __global__ void refresh_bf16(const float *master, __nv_bfloat16 *w1, __nv_bfloat16 *w2,
-                             __nv_bfloat16 *w3, __nv_bfloat16 *w4)
+                             __nv_bfloat16 *w3, __nv_bfloat16 *w4, __nv_bfloat16 *w2t, __nv_bfloat16 *w3t)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < (int64_t)H * INP) {
         const int r = (int)(i / INP), k = (int)(i % INP);
         w1[i] = __float2bfloat16(k < IN ? master[OW1 + (int64_t)r * IN + k] : 0.f);
     }
-    if (i < NW2) w2[i] = __float2bfloat16(master[OW2 + i]);
-    if (i < NW3) w3[i] = __float2bfloat16(master[OW3 + i]);
+    if (i < NW2) {
+        const __nv_bfloat16 v2 = __float2bfloat16(master[OW2 + i]);
+        const __nv_bfloat16 v3 = __float2bfloat16(master[OW3 + i]);
+        w2[i] = v2;
+        w3[i] = v3;
+        const int64_t t = (i % H) * H + i / H;
+        w2t[t] = v2;
+        w3t[t] = v3;
+    }
     if (i < (int64_t)OUTP * H) {
         const int r = (int)(i / H);
         w4[i] = __float2bfloat16(r < OUT ? master[OW4 + i] : 0.f);
     }
+}
+
+// out[c][r] = in[r][c] for a [rows][H] bf16 matrix (out leading dimension
+// ldo), through a 32 x 33 shared tile.
+__global__ void transpose_bf16(const __nv_bfloat16 *in, int rows, __nv_bfloat16 *out, int64_t ldo)
+{
+    __shared__ __nv_bfloat16 t[32][33];
+    const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+    for (int y = threadIdx.y; y < 32; y += 8) {
+        const int r = r0 + y, c = c0 + threadIdx.x;
+        t[y][threadIdx.x] = r < rows ? in[(int64_t)r * H + c] : __float2bfloat16(0.f);
+    }
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += 8) {
+        const int c = c0 + y, r = r0 + threadIdx.x;
+        if (r < rows) out[(int64_t)c * ldo + r] = t[threadIdx.x][y];
+    }
+}
+
+void transpose(const __nv_bfloat16 *in, int rows, __nv_bfloat16 *out, int64_t ldo, cudaStream_t st)
+{
+    transpose_bf16<<<dim3((rows + 31) / 32, H / 32), dim3(32, 8), 0, st>>>(in, rows, out, ldo);
 }
 
 // dL/dy for L = mean_b sum_j (y_bj - t_bj)^2 / OUT, as bf16 (padded), and
@@ -337,9 +385,12 @@ __global__ void adam_kernel(float *w, float *m, float *v, const float *g, int64_
 
 struct Ptrs {
     float *master, *m, *v;
-    __nv_bfloat16 *w1, *w2, *w3, *w4;
+    __nv_bfloat16 *w1, *w2, *w3, *w4, *w2t, *w3t;
     __nv_bfloat16 *x, *a1, *a2, *a3, *gy, *g3, *g2, *g1;
+    __nv_bfloat16 *a1t, *a2t, *g2t, *g3t;
     float *z1, *z2, *z3, *y, *gp, *loss, *wpart, *bpart;
+    int *status;
+    int64_t ldT;
 };
 
 Ptrs ptrs(void *state, void *ws, int B)
@@ -355,6 +406,14 @@ Ptrs ptrs(void *state, void *ws, int B)
     p.w2 = (__nv_bfloat16 *)(S + s.w2h);
     p.w3 = (__nv_bfloat16 *)(S + s.w3h);
     p.w4 = (__nv_bfloat16 *)(S + s.w4h);
+    p.w2t = (__nv_bfloat16 *)(S + s.w2t);
+    p.w3t = (__nv_bfloat16 *)(S + s.w3t);
+    p.a1t = (__nv_bfloat16 *)(W + w.a1t);
+    p.a2t = (__nv_bfloat16 *)(W + w.a2t);
+    p.g2t = (__nv_bfloat16 *)(W + w.g2t);
+    p.g3t = (__nv_bfloat16 *)(W + w.g3t);
+    p.status = (int *)(W + w.status);
+    p.ldT = w.ldT;
     p.x = (__nv_bfloat16 *)(W + w.x);
     p.z1 = (float *)(W + w.z1);
     p.a1 = (__nv_bfloat16 *)(W + w.a1);
@@ -385,13 +444,33 @@ GemmArgs fwd_layer(int B, const __nv_bfloat16 *X, int K, const __nv_bfloat16 *W,
     return g;
 }
 
-int forward(const Ptrs &p, int B, const float *x, cudaStream_t st)
+// Layer l = 2, 3 on the tcgen05 GEMM: z = a_in W^T + b, act = SiLU(z), and
+// with actT the transposed activations for the weight gradients.
+int hidden_tc(const Ptrs &p, int B, const __nv_bfloat16 *ain, const __nv_bfloat16 *W, const float *bias,
+              float *z, __nv_bfloat16 *act, __nv_bfloat16 *actT, cudaStream_t st)
 {
+    fk::TcEpilogue e{};
+    e.kind = fk::TC_EPI_HIDDEN;
+    e.ldo = H;
+    e.ldT = p.ldT;
+    e.bias = bias;
+    e.z = z;
+    e.act = act;
+    e.actT = actT;
+    e.status = p.status;
+    return fk::tc_gemm(B, H, H, ain, H, W, H, 1, e, st);
+}
+
+// train: also the transposed activations the weight gradients need
+int forward(const Ptrs &p, int B, const float *x, cudaStream_t st, bool train = false)
+{
+    if (cudaMemsetAsync(p.status, 0, sizeof(int), st) != cudaSuccess) return FK_ECUDA;
     pack_input<<<(B * INP + 255) / 256, 256, 0, st>>>(x, p.x, B);
     int rc;
     if ((rc = gemm(fwd_layer(B, p.x, INP, p.w1, H, p.master + OB1, p.z1, p.a1, EPI_HIDDEN, H), st))) return rc;
-    if ((rc = gemm(fwd_layer(B, p.a1, H, p.w2, H, p.master + OB2, p.z2, p.a2, EPI_HIDDEN, H), st))) return rc;
-    if ((rc = gemm(fwd_layer(B, p.a2, H, p.w3, H, p.master + OB3, p.z3, p.a3, EPI_HIDDEN, H), st))) return rc;
+    if (train) transpose(p.a1, B, p.a1t, p.ldT, st);
+    if ((rc = hidden_tc(p, B, p.a1, p.w2, p.master + OB2, p.z2, p.a2, train ? p.a2t : nullptr, st))) return rc;
+    if ((rc = hidden_tc(p, B, p.a2, p.w3, p.master + OB3, p.z3, p.a3, nullptr, st))) return rc;
     GemmArgs g = fwd_layer(B, p.a3, H, p.w4, OUTP, p.master + OB4, p.y, nullptr, EPI_OUT, OUT);
     g.ldo = OUTP;
     return gemm(g, st);
@@ -418,34 +497,42 @@ int backward(const Ptrs &p, int B, cudaStream_t st)
     g.B = p.w4; g.sbn = 1; g.sbk = H;             // B(n=h, k=j) = W4[j][h]
     g.epi = EPI_BACK_HIDDEN; g.act = p.g3; g.zprev = p.z3; g.ldo = H; g.nvalid = H;
     if ((rc = gemm(g, st))) return rc;
-    const __nv_bfloat16 *gin[3] = {p.g3, p.g2, p.g1};
-    const __nv_bfloat16 *ain[3] = {p.a2, p.a1, p.x};
-    const __nv_bfloat16 *Wl[3] = {p.w3, p.w2, p.w1};
-    const float *zp[3] = {p.z2, p.z1, nullptr};
-    __nv_bfloat16 *gout[3] = {p.g2, p.g1, nullptr};
-    const int64_t ow[3] = {OW3, OW2, OW1}, ob[3] = {OB3, OB2, OB1};
-    const int Kin[3] = {H, H, INP};
-    for (int l = 0; l < 3; ++l) {
-        // dL/dW = g^T a_in  ([H][Kin]); layer 1 stores only the 15 real inputs
-        g = GemmArgs{};
-        g.M = H; g.N = Kin[l]; g.K = B;
-        g.A = gin[l]; g.sam = 1; g.sak = H;
-        g.B = ain[l]; g.sbn = 1; g.sbk = Kin[l];
-        g.epi = EPI_WGRAD; g.wgrad = p.gp + ow[l];
-        g.ldo = (l == 2) ? IN : Kin[l];
-        g.nvalid = (l == 2) ? IN : Kin[l];
-        g.ksplit = ksplit(B); g.wpart = p.wpart;
-        if ((rc = gemm(g, st))) return rc;
-        bias_grad(gin[l], B, H, H, p.bpart, p.gp + ob[l], st);
-        if (gout[l]) {
-            g = GemmArgs{};
-            g.M = B; g.N = H; g.K = H;
-            g.A = gin[l]; g.sam = H; g.sak = 1;
-            g.B = Wl[l]; g.sbn = 1; g.sbk = H;    // B(n, k) = W[k][n]
-            g.epi = EPI_BACK_HIDDEN; g.act = gout[l]; g.zprev = zp[l]; g.ldo = H; g.nvalid = H;
-            if ((rc = gemm(g, st))) return rc;
-        }
+    transpose(p.g3, B, p.g3t, p.ldT, st);
+    // layers 3 and 2 on the tcgen05 GEMM: dL/dW = g^T a_in (K = batch, split
+    // over CTAs, fixed-order sum), then dL/dz_in = (g W) * silu'(z_in)
+    const __nv_bfloat16 *gT[2] = {p.g3t, p.g2t}, *aT[2] = {p.a2t, p.a1t}, *gl[2] = {p.g3, p.g2};
+    const __nv_bfloat16 *Wt[2] = {p.w3t, p.w2t};
+    const float *zp[2] = {p.z2, p.z1};
+    __nv_bfloat16 *gout[2] = {p.g2, p.g1}, *goutT[2] = {p.g2t, nullptr};
+    const int64_t ow[2] = {OW3, OW2}, ob[2] = {OB3, OB2};
+    for (int l = 0; l < 2; ++l) {
+        fk::TcEpilogue e{};
+        e.kind = fk::TC_EPI_PARTIAL;
+        e.ldo = H;
+        e.out = p.wpart;
+        e.sum_to = p.gp + ow[l];
+        e.status = p.status;
+        if ((rc = fk::tc_gemm(H, H, B, gT[l], p.ldT, aT[l], p.ldT, tc_ksplit(B), e, st))) return rc;
+        bias_grad(gl[l], B, H, H, p.bpart, p.gp + ob[l], st);
+        fk::TcEpilogue b{};
+        b.kind = fk::TC_EPI_BACK_HIDDEN;
+        b.ldo = H;
+        b.ldT = p.ldT;
+        b.act = gout[l];
+        b.actT = goutT[l];
+        b.zprev = zp[l];
+        b.status = p.status;
+        if ((rc = fk::tc_gemm(B, H, H, gl[l], H, Wt[l], H, 1, b, st))) return rc;
     }
+    // layer 1: dL/dW1 = g1^T x (the 15 real inputs), dL/db1
+    g = GemmArgs{};
+    g.M = H; g.N = INP; g.K = B;
+    g.A = p.g1; g.sam = 1; g.sak = H;
+    g.B = p.x; g.sbn = 1; g.sbk = INP;
+    g.epi = EPI_WGRAD; g.wgrad = p.gp + OW1; g.ldo = IN; g.nvalid = IN;
+    g.ksplit = ksplit(B); g.wpart = p.wpart;
+    if ((rc = gemm(g, st))) return rc;
+    bias_grad(p.g1, B, H, H, p.bpart, p.gp + OB1, st);
     return FK_OK;
 }
 
@@ -476,7 +563,8 @@ int fk_mlp_load(void *state, const float *master, void *stream)
     const int64_t n = NW2;
     refresh_bf16<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
         (const float *)(S + s.master), (__nv_bfloat16 *)(S + s.w1h), (__nv_bfloat16 *)(S + s.w2h),
-        (__nv_bfloat16 *)(S + s.w3h), (__nv_bfloat16 *)(S + s.w4h));
+        (__nv_bfloat16 *)(S + s.w3h), (__nv_bfloat16 *)(S + s.w4h), (__nv_bfloat16 *)(S + s.w2t),
+        (__nv_bfloat16 *)(S + s.w3t));
     return cudaGetLastError() == cudaSuccess ? FK_OK : FK_ECUDA;
 }
 
@@ -503,7 +591,7 @@ int fk_mlp_backward(const void *state, int batch, const float *x, const float *g
     if (ws_bytes < ws_layout(batch).total) return FK_EWORKSPACE;
     cudaStream_t st = (cudaStream_t)stream;
     Ptrs p = ptrs((void *)state, ws, batch);
-    int rc = forward(p, batch, x, st);
+    int rc = forward(p, batch, x, st, true);
     if (rc) return rc;
     // upstream gradient [B][OUT] fp32 -> padded bf16
     if (cudaMemsetAsync(p.gy, 0, (size_t)batch * OUTP * 2, st) != cudaSuccess) return FK_ECUDA;
@@ -522,7 +610,7 @@ int fk_mlp_train_step(void *state, int batch, const float *x, const float *targe
     if (ws_bytes < ws_layout(batch).total) return FK_EWORKSPACE;
     cudaStream_t st = (cudaStream_t)stream;
     Ptrs p = ptrs(state, ws, batch);
-    int rc = forward(p, batch, x, st);
+    int rc = forward(p, batch, x, st, true);
     if (rc) return rc;
     if (cudaMemsetAsync(p.loss, 0, 4, st) != cudaSuccess) return FK_ECUDA;
     loss_grad<<<(batch * OUTP + 255) / 256, 256, 0, st>>>(p.y, target, p.gy, p.loss, batch);
@@ -530,7 +618,8 @@ int fk_mlp_train_step(void *state, int batch, const float *x, const float *targe
     const float c1 = 1.f - powf(beta1, (float)step), c2 = 1.f - powf(beta2, (float)step);
     adam_kernel<<<(unsigned)((NPARAM + 255) / 256), 256, 0, st>>>(p.master, p.m, p.v, p.gp, NPARAM,
                                                                   lr, beta1, beta2, eps, c1, c2);
-    refresh_bf16<<<(unsigned)((NW2 + 255) / 256), 256, 0, st>>>(p.master, p.w1, p.w2, p.w3, p.w4);
+    refresh_bf16<<<(unsigned)((NW2 + 255) / 256), 256, 0, st>>>(p.master, p.w1, p.w2, p.w3, p.w4, p.w2t,
+                                                                p.w3t);
     if (loss && cudaMemcpyAsync(loss, p.loss, 4, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         return FK_ECUDA;
     return cudaGetLastError() == cudaSuccess ? FK_OK : FK_ECUDA;
