@@ -101,3 +101,31 @@ class MLP:
                                            self.ws.numel(), fd._stream(None)),
                   "fk_mlp_train_step")
         return self.loss_buf
+
+
+def _main(argv):
+    """python -m paper_2303_08879_gb300.mlp [batch] [steps]: training steps of
+    the model on random data (CUDA-event timed), for profiling the GEMMs."""
+    import time
+    batch = int(argv[0]) if argv else 65536
+    steps = int(argv[1]) if len(argv) > 1 else 10
+    dev = torch.device("cuda")
+    m = MLP(init_params(0), batch, dev)
+    gen = torch.Generator(device=dev).manual_seed(0)
+    X = torch.rand((batch, IN), device=dev, generator=gen) * 2 - 1
+    Y = torch.rand((batch, OUT), device=dev, generator=gen)
+    for _ in range(3):
+        m.train_step(X, Y)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        m.train_step(X, Y)
+    e1.record()
+    torch.cuda.synchronize()
+    print(f"batch {batch}: {e0.elapsed_time(e1) / steps:.4f} ms per training step")
+
+
+if __name__ == "__main__":
+    import sys
+    _main(sys.argv[1:])

@@ -3,7 +3,9 @@ tensor-core engine where it applies): the probability-sum early stop
 (Sec. 2.3), the global photon-number cutoff and the state-vector walk of pure
 states (Sec. 2.2), each forward and VJP.
 
-    python -m paper_2303_08879_gb300.rows
+    python -m paper_2303_08879_gb300.rows [--cond]
+
+--cond runs only the 64-circuit conditional workload (forward + VJP, twice).
 """
 from __future__ import annotations
 
@@ -26,7 +28,34 @@ def _time(fn, reps=5, warmup=2):
     return e0.elapsed_time(e1) / reps
 
 
+def cond_once(reps=2):
+    """The 64-circuit conditional workload, forward + VJP, reps times (for
+    profiling the conditional-walk kernels)."""
+    import torch
+    from . import fockdiag as fd
+    from . import inputs
+    mask = (1, 1, 0)
+    circs = inputs.workload("cond_m3_batch64")
+    cuts = [cc.cutoffs for cc in circs]
+    trip = [fd.fk_gaussian_to_triple(cc.V, cc.mean) for cc in circs]
+    A = torch.tensor(np.stack([t[0] for t in trip]), device="cuda")
+    b = torch.tensor(np.stack([t[1] for t in trip]), device="cuda")
+    c = torch.tensor(np.array([t[2] for t in trip], np.complex128), device="cuda")
+    rho, offs, ws = fd.fock_conditional_dm_batched(A, b, c, cuts, mask)
+    g = torch.ones_like(rho)
+    for _ in range(reps):
+        fd.fock_conditional_dm_batched(A, b, c, cuts, mask, rho=rho, ws=ws)
+        fd.fock_conditional_dm_vjp_batched(A, b, c, cuts, mask, g, ws)
+    torch.cuda.synchronize()
+    fd.check_workspace(ws)
+    print(json.dumps({"conditional_outputs": int(offs[-1]), "reps": reps}))
+
+
 def main():
+    import sys
+    if "--cond" in sys.argv:
+        cond_once()
+        return
     import torch
     from . import fockdiag as fd
     from . import inputs
