@@ -5,8 +5,9 @@
 // One CTA computes a 128 x 256 tile of C (the 128 TMEM lanes are the rows,
 // 256 fp32 TMEM columns the columns).  The K loop runs in steps of 64 bf16
 // (one 128-byte row per tile row): warp 0 (one lane) loads the A and B tiles
-// of a step with TMA (cp.async.bulk.tensor, 128-byte swizzle) into a 4-stage
-// ring of shared memory, warp 1 (one lane) issues four tcgen05.mma of K = 16
+// of a step with TMA (cp.async.bulk.tensor, 128-byte swizzle) into a 2-stage
+// ring of shared memory (about 97 KB, so two CTAs share an SM and one's
+// epilogue overlaps the other's loads), warp 1 (one lane) issues four tcgen05.mma of K = 16
 // per step and frees the stage with tcgen05.commit; when the last MMA has
 // landed every warp reads its 32 TMEM lanes (tcgen05.ld) and applies the
 // layer's epilogue.  A K range split over blockIdx.z (the weight gradients,
@@ -31,7 +32,7 @@ namespace fk {
 
 namespace {
 
-constexpr int TBM = 128, TBN = 256, TBK = 64, STAGES = 4, TPB_TC = 128;
+constexpr int TBM = 128, TBN = 256, TBK = 64, STAGES = 2, TPB_TC = 128;
 constexpr uint32_t A_BYTES = TBM * TBK * 2, B_BYTES = TBN * TBK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr uint32_t TMEM_COLS = 256;
 constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 1024 /* alignment */ + 256 /* barriers */;
@@ -226,35 +227,78 @@ __global__ void __launch_bounds__(TPB_TC, 1)
 #pragma unroll
                 for (int i = 0; i < 32; ++i) v[i] = 0.f;
             }
-            if (m >= g.M) continue;
             const int n = n0 + c0;
-            if (n >= g.N) continue;
+            if (m >= g.M || n >= g.N) continue;
+            const int nv = min(32, g.N - n);
             const int64_t o = (int64_t)m * e.ldo + n;
+            // whole 32-column runs of rows with 16-byte aligned starts use vector accesses
+            const bool vec = nv == 32 && (e.ldo % 8) == 0;
             switch (e.kind) {
-            case TC_EPI_HIDDEN: {
+            case TC_EPI_HIDDEN:
+            case TC_EPI_OUT: {
+                const bool hid = e.kind == TC_EPI_HIDDEN;
+                float zz[32];
+                __nv_bfloat16 aa[32];
 #pragma unroll
                 for (int i = 0; i < 32; ++i) {
-                    const float z = v[i] + e.bias[n + i];
-                    e.z[o + i] = z;
-                    const __nv_bfloat16 a = __float2bfloat16(silu(z));
-                    e.act[o + i] = a;
-                    if (e.actT) e.actT[(int64_t)(n + i) * e.ldT + m] = a;
+                    zz[i] = i < nv ? v[i] + e.bias[n + i] : 0.f;
+                    aa[i] = __float2bfloat16(silu(zz[i]));
                 }
+                if (vec) {
+                    float4 *zd = (float4 *)(e.z + o);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) zd[q] = make_float4(zz[4 * q], zz[4 * q + 1], zz[4 * q + 2], zz[4 * q + 3]);
+                    if (hid) {
+                        uint4 *ad = (uint4 *)(e.act + o);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) ad[q] = *(const uint4 *)&aa[8 * q];
+                    }
+                } else {
+                    for (int i = 0; i < nv; ++i) {
+                        e.z[o + i] = zz[i];
+                        if (hid) e.act[o + i] = aa[i];
+                    }
+                }
+                if (hid && e.actT)
+                    for (int i = 0; i < nv; ++i) e.actT[(int64_t)(n + i) * e.ldT + m] = aa[i];
                 break;
             }
             case TC_EPI_BACK_HIDDEN: {
+                float zp[32];
+                if (vec) {
+                    const float4 *zs = (const float4 *)(e.zprev + o);
 #pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    const __nv_bfloat16 a = __float2bfloat16(v[i] * dsilu(e.zprev[o + i]));
-                    e.act[o + i] = a;
-                    if (e.actT) e.actT[(int64_t)(n + i) * e.ldT + m] = a;
+                    for (int q = 0; q < 8; ++q) {
+                        const float4 t = zs[q];
+                        zp[4 * q] = t.x; zp[4 * q + 1] = t.y; zp[4 * q + 2] = t.z; zp[4 * q + 3] = t.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) zp[i] = i < nv ? e.zprev[o + i] : 0.f;
                 }
+                __nv_bfloat16 aa[32];
+#pragma unroll
+                for (int i = 0; i < 32; ++i) aa[i] = __float2bfloat16(v[i] * dsilu(zp[i]));
+                if (vec) {
+                    uint4 *ad = (uint4 *)(e.act + o);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) ad[q] = *(const uint4 *)&aa[8 * q];
+                } else {
+                    for (int i = 0; i < nv; ++i) e.act[o + i] = aa[i];
+                }
+                if (e.actT)
+                    for (int i = 0; i < nv; ++i) e.actT[(int64_t)(n + i) * e.ldT + m] = aa[i];
                 break;
             }
             case TC_EPI_PARTIAL: {
                 float *dst = e.out + (int64_t)blockIdx.z * g.M * e.ldo + o;
+                if (vec) {
 #pragma unroll
-                for (int i = 0; i < 32; ++i) dst[i] = v[i];
+                    for (int q = 0; q < 8; ++q)
+                        ((float4 *)dst)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                } else {
+                    for (int i = 0; i < nv; ++i) dst[i] = v[i];
+                }
                 break;
             }
             default: break;
@@ -314,7 +358,7 @@ int make_map(CUtensorMap *map, const void *ptr, int rows, int cols, int64_t ld, 
 int tc_gemm(int M, int N, int K, const void *A, int64_t lda, const void *B, int64_t ldb, int ksplit,
             const TcEpilogue &e, void *stream)
 {
-    if (M < 1 || N < 1 || K < 1 || (N % TBN) != 0 || ksplit < 1) return FK_EINVAL;
+    if (M < 1 || N < 1 || K < 1 || (N > TBN && (N % TBN) != 0) || ksplit < 1) return FK_EINVAL;
     CUtensorMap ma, mb;
     int rc = make_map(&ma, A, M, K, lda, TBM);
     if (rc) return rc;
@@ -333,7 +377,7 @@ int tc_gemm(int M, int N, int K, const void *A, int64_t lda, const void *B, int6
     g.kper = ((K + ksplit - 1) / ksplit + TBK - 1) / TBK * TBK;
     g.e = e;
     const int zs = (K + g.kper - 1) / g.kper;
-    const dim3 grid(N / TBN, (M + TBM - 1) / TBM, zs);
+    const dim3 grid((N + TBN - 1) / TBN, (M + TBM - 1) / TBM, zs);
     cudaStream_t st = (cudaStream_t)stream;
     tc_gemm_kernel<<<grid, TPB_TC, SMEM_BYTES, st>>>(ma, mb, g);
     if (cudaGetLastError() != cudaSuccess) return FK_ECUDA;
