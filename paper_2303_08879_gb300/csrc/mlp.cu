@@ -69,7 +69,6 @@ struct WsLayout {
 // The weight gradients contract over the batch (K): their K range is split
 // over CTAs (about 1024 samples each, at most 128 slices) into a scratch
 // array summed in a fixed order, since the output tiles alone give 1-2 CTAs.
-constexpr int kBiasRows = 4096;   // batch rows per block of the bias-gradient sums
 int tc_ksplit(int B) { return B >= 2048 ? (B / 1024 < 128 ? B / 1024 : 128) : 1; }
 
 WsLayout ws_layout(int B)
@@ -93,7 +92,7 @@ WsLayout ws_layout(int B)
     w.loss = o; o = al(o + 64);
     const int slices = fk::tc_gemm_slices(B, tc_ksplit(B));
     w.wpart = o; o = al(o + (size_t)slices * H * H * 4);
-    w.bpart = o; o = al(o + (size_t)((B + kBiasRows - 1) / kBiasRows) * H * 4);
+    w.bpart = o; o = al(o + (size_t)((B + 8191) / 8192) * H * 4);
     w.ldT = (b + 7) / 8 * 8;
     w.a1t = o; o = al(o + (size_t)H * w.ldT * 2);
     w.a2t = o; o = al(o + (size_t)H * w.ldT * 2);
@@ -197,31 +196,46 @@ __global__ void pack_grad(const float *gy, __nv_bfloat16 *out, __nv_bfloat16 *ou
     outt[(int64_t)j * ldT + b] = v;
 }
 
-// bias gradients: column sums of a [B][ld] bf16 gradient (first n columns).
-// Block (x: 32 columns, y: kBiasRows rows), 32 x 8 threads; the 8 row
-// strands are summed in a fixed order, then the row blocks (second kernel).
-__global__ void bias_grad_part(const __nv_bfloat16 *g, int B, int ld, int n, float *part)
+// bias gradients: row sums of a transposed bf16 gradient gT [rows][ldT]
+// (the first B entries of each row).  Block (r, s) sums the 8192-entry
+// slice s of row r with 16-byte loads and a fixed-order tree; a second pass
+// adds the slices in order.
+constexpr int kBiasSlice = 8192;
+
+__global__ void bias_grad_part(const __nv_bfloat16 *gT, int B, int64_t ldT, float *part, int rows)
 {
-    __shared__ float red[8][33];
-    const int j = blockIdx.x * 32 + threadIdx.x;
-    const int b0 = blockIdx.y * kBiasRows, b1 = min(B, b0 + kBiasRows);
-    float s = 0.f;
-    if (j < n)
-        for (int b = b0 + threadIdx.y; b < b1; b += 8) s += __bfloat162float(g[(int64_t)b * ld + j]);
-    red[threadIdx.y][threadIdx.x] = s;
-    __syncthreads();
-    if (threadIdx.y == 0 && j < n) {
-        float t = 0.f;
-        for (int y = 0; y < 8; ++y) t += red[y][threadIdx.x];
-        part[(int64_t)blockIdx.y * n + j] = t;
+    __shared__ float red[256];
+    const int r = blockIdx.x, s = blockIdx.y;
+    const int64_t b0 = (int64_t)s * kBiasSlice;
+    const __nv_bfloat16 *row = gT + (int64_t)r * ldT;
+    float acc = 0.f;
+    // 32 entries per thread: four runs of 8
+    for (int k = 0; k < 4; ++k) {
+        const int64_t b = b0 + (int64_t)(k * 256 + threadIdx.x) * 8;
+        if (b + 8 <= B && ((ldT & 7) == 0)) {
+            const uint4 w = *(const uint4 *)(row + b);
+            const __nv_bfloat16 *h = (const __nv_bfloat16 *)&w;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) acc += __bfloat162float(h[i]);
+        } else {
+            for (int i = 0; i < 8; ++i)
+                if (b + i < B) acc += __bfloat162float(row[b + i]);
+        }
     }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[(int64_t)s * rows + r] = red[0];
 }
 
-void bias_grad(const __nv_bfloat16 *g, int B, int ld, int n, float *part, float *out, cudaStream_t st)
+void bias_grad(const __nv_bfloat16 *gT, int B, int64_t ldT, int rows, float *part, float *out, cudaStream_t st)
 {
-    const int rb = (B + kBiasRows - 1) / kBiasRows;
-    bias_grad_part<<<dim3((n + 31) / 32, rb), dim3(32, 8), 0, st>>>(g, B, ld, n, part);
-    sum_slices<<<(n + 255) / 256, 256, 0, st>>>(part, rb, n, out);
+    const int slices = (B + kBiasSlice - 1) / kBiasSlice;
+    bias_grad_part<<<dim3(rows, slices), 256, 0, st>>>(gT, B, ldT, part, rows);
+    sum_slices<<<(rows + 255) / 256, 256, 0, st>>>(part, slices, rows, out);
 }
 
 __global__ void adam_kernel(float *w, float *m, float *v, const float *g, int64_t n, float lr,
@@ -362,19 +376,19 @@ int backward(const Ptrs &p, int B, cudaStream_t st)
     int rc;
     // layer 4: dL/dW4 = gy^T a3 ([2][H]), dL/db4, dL/dz3 = (gy W4) * silu'(z3)
     if ((rc = wgrad(p, B, p.gyt, OUT, p.a3t, H, p.gp + OW4, st))) return rc;
-    bias_grad(p.gy, B, OUTP, OUT, p.bpart, p.gp + OB4, st);
+    bias_grad(p.gyt, B, p.ldT, OUT, p.bpart, p.gp + OB4, st);
     if ((rc = back_hidden(p, B, p.gy, OUTP, p.w4t, p.z3, p.g3, p.g3t, st))) return rc;
     // layer 3
     if ((rc = wgrad(p, B, p.g3t, H, p.a2t, H, p.gp + OW3, st))) return rc;
-    bias_grad(p.g3, B, H, H, p.bpart, p.gp + OB3, st);
+    bias_grad(p.g3t, B, p.ldT, H, p.bpart, p.gp + OB3, st);
     if ((rc = back_hidden(p, B, p.g3, H, p.w3t, p.z2, p.g2, p.g2t, st))) return rc;
     // layer 2
     if ((rc = wgrad(p, B, p.g2t, H, p.a1t, H, p.gp + OW2, st))) return rc;
-    bias_grad(p.g2, B, H, H, p.bpart, p.gp + OB2, st);
+    bias_grad(p.g2t, B, p.ldT, H, p.bpart, p.gp + OB2, st);
     if ((rc = back_hidden(p, B, p.g2, H, p.w2t, p.z1, p.g1, p.g1t, st))) return rc;
     // layer 1: the 15 real inputs of W1
     if ((rc = wgrad(p, B, p.g1t, H, p.xt, IN, p.gp + OW1, st))) return rc;
-    bias_grad(p.g1, B, H, H, p.bpart, p.gp + OB1, st);
+    bias_grad(p.g1t, B, p.ldT, H, p.bpart, p.gp + OB1, st);
     return FK_OK;
 }
 

@@ -2,15 +2,15 @@
 // tensor cores: C = A B^T with A [M][K] and B [N][K] bf16 (both K-major, rows
 // of K contiguous), fp32 accumulation in tensor memory.
 //
-// One CTA computes a 128 x 256 tile of C (the 128 TMEM lanes are the rows,
-// 256 fp32 TMEM columns the columns).  The K loop runs in steps of 64 bf16
+// One CTA of 8 warps computes a 128 x 256 tile of C (the 128 TMEM lanes are
+// the rows, 256 fp32 TMEM columns the columns).  The K loop runs in steps of 64 bf16
 // (one 128-byte row per tile row): warp 0 (one lane) loads the A and B tiles
 // of a step with TMA (cp.async.bulk.tensor, 128-byte swizzle) into a 2-stage
 // ring of shared memory (about 97 KB, so two CTAs share an SM and one's
 // epilogue overlaps the other's loads), warp 1 (one lane) issues four tcgen05.mma of K = 16
 // per step and frees the stage with tcgen05.commit; when the last MMA has
-// landed every warp reads its 32 TMEM lanes (tcgen05.ld) and applies the
-// layer's epilogue.  A K range split over blockIdx.z (the weight gradients,
+// landed every warp reads 32 TMEM lanes of half the columns (tcgen05.ld) and
+// applies the layer's epilogue.  A K range split over blockIdx.z (the weight gradients,
 // whose K is the batch) writes fp32 partials that a second kernel sums in a
 // fixed order.
 //
@@ -32,7 +32,7 @@ namespace fk {
 
 namespace {
 
-constexpr int TBM = 128, TBN = 256, TBK = 64, STAGES = 2, TPB_TC = 128;
+constexpr int TBM = 128, TBN = 256, TBK = 64, STAGES = 2, TPB_TC = 256;
 constexpr uint32_t A_BYTES = TBM * TBK * 2, B_BYTES = TBN * TBK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr uint32_t TMEM_COLS = 256;
 constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 1024 /* alignment */ + 256 /* barriers */;
@@ -217,12 +217,15 @@ __global__ void __launch_bounds__(TPB_TC, 1)
     const bool aborted = *(volatile int *)&s_abort != 0;
     if (aborted && threadIdx.x == 0 && g.e.status) atomicCAS(g.e.status, 0, (int)FK_ETIMEOUT);
     if (!aborted) {
-        const int m = m0 + warp * 32 + lane;
+        // warp w reads TMEM lanes 32 (w % 4) .. + 31 (the lanes its quarter may
+        // access); warps w and w + 4 take the two halves of the columns
+        const int q = warp & 3, half = warp >> 2;
+        const int m = m0 + q * 32 + lane;
         const TcEpilogue &e = g.e;
-        for (int c0 = 0; c0 < TBN; c0 += 32) {
+        for (int c0 = half * (TBN / 2); c0 < (half + 1) * (TBN / 2); c0 += 32) {
             float v[32];
             if (nk > 0) {
-                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
             } else {
 #pragma unroll
                 for (int i = 0; i < 32; ++i) v[i] = 0.f;
