@@ -98,6 +98,11 @@ struct CondCirc {
     int64_t off_rho;                  // its block of the output (elements)
     int64_t off_scratch;              // its VJP scratch (elements): dsh.n_ap * U2
     int64_t n_patterns;               // detected patterns (= dsh.n_diag)
+    int64_t geo_off;                  // first record of this circuit's pivot geometry table
+    int gp_off;                       // its pivot prefix per (kind, level) in the plan's tables:
+                                      // [2][dsh.L + 1] unsigned, off-diagonal pivots of every
+                                      // level first, then the diagonal pivots
+    int pad_geo;
 };
 
 struct CondPlan {
@@ -105,12 +110,13 @@ struct CondPlan {
     int Dmax;                         // 2 M
     int Lmax;                         // max detected levels over circuits
     int64_t F_total, scratch_total, rho_total;
+    int64_t geo_total;                // pivot geometry records of every circuit
     size_t plan_bytes;                // CondCirc[B] followed by the level tables
     const void *host_plan;            // pinned host copy (kept for the life of the process)
 };
 
 struct CondLayout {
-    size_t ctl, plan, Ar, br, F, Fbar, scratch, partA, partb, total;
+    size_t ctl, plan, Ar, br, geo, F, Fbar, scratch, partA, partb, total;
     int grid_vjp;
 };
 

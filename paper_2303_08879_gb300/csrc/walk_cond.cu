@@ -37,6 +37,8 @@ constexpr int TPB = kCondTPB;
 constexpr int RS = TPB + 1;
 constexpr int MAXB = 1024;                        // circuits per launch
 
+struct PGeom;
+
 struct CondArgs {
     int B, Md, Dmax, grid, Lmax, D_orig;
     const CondCirc *plan;
@@ -45,6 +47,7 @@ struct CondArgs {
     double2 *rho;
     Control *ctl;
     double2 *Ar, *br, *F;
+    PGeom *geo;                     // pivot geometry of every circuit (built by the prologue)
     const double2 *grho;
     double2 *Fbar, *scratch, *partA, *partb;
     double2 *gA, *gb, *gc;
@@ -301,6 +304,7 @@ __device__ int phase_tiles(const CondArgs &a, CSmem &s, int kind, int lev)
 struct CTile {
     int circ, seg, chunk;
     unsigned rank;
+    unsigned pbase;     // pivots of the segments before seg in this phase of the circuit
 };
 
 __device__ CTile decode(const CondArgs &a, const CSmem &s, int kind, int lev, int tile)
@@ -316,12 +320,16 @@ __device__ CTile decode(const CondArgs &a, const CSmem &s, int kind, int lev, in
     int rem = tile - s.ctiles[lo];
     const int nseg = (kind == 0) ? cc.dsh.M : 1;
     int k = 0;
+    unsigned pb = 0;
     for (; k < nseg; ++k) {
-        const int n = (int)seg_count(a, cc, kind, k, lev) * cc.nchunk;
+        const unsigned c = seg_count(a, cc, kind, k, lev);
+        const int n = (int)c * cc.nchunk;
         if (rem < n) break;
         rem -= n;
+        pb += c;
     }
     t.seg = k;
+    t.pbase = pb;
     t.rank = (unsigned)(rem / cc.nchunk);
     t.chunk = rem % cc.nchunk;
     return t;
@@ -405,19 +413,45 @@ __device__ __forceinline__ int col_index(const PGeom &g, int Db, int j)
     return j < g.N ? g.row0 + j : Db + (j - g.N);
 }
 
-// The current tile's pivot geometry, computed once by thread 0.
-__device__ const PGeom &tile_geometry(const CondArgs &a, CSmem &s, const CTile &tl, int kind, int lev)
+// Record of pivot `rank` of segment `seg` of phase (kind, lev) in circuit c's
+// geometry table: AP pivots of every level first, then DP pivots.
+__device__ __forceinline__ int64_t geo_index(const CondArgs &a, const CondCirc &cc, int kind, int lev,
+                                             unsigned pbase, unsigned rank)
+{
+    const unsigned *pre = a.Wall + cc.gp_off;
+    return cc.geo_off + (int64_t)pre[kind * (cc.dsh.L + 1) + lev] + pbase + rank;
+}
+
+// The pivot geometry of every circuit, once per launch: one block per
+// circuit, a thread per pivot of each (kind, level, segment).
+__device__ void build_geo(const CondArgs &a, const CSmem &s)
+{
+    for (int c = blockIdx.x; c < a.B; c += gridDim.x) {
+        const CondCirc &cc = a.plan[c];
+        const DiagShape &ds = cc.dsh;
+        if (ds.M == 0) continue;
+        const LevelTab W = ltab(a, cc);
+        for (int kind = 0; kind < 2; ++kind)
+            for (int lev = 0; lev < ds.L; ++lev) {
+                unsigned pb = 0;
+                const int nseg = kind == 0 ? ds.M : 1;
+                for (int k = 0; k < nseg; ++k) {
+                    const unsigned cnt = seg_count(a, cc, kind, k, lev);
+                    for (unsigned r = threadIdx.x; r < cnt; r += blockDim.x) {
+                        const Dig e = unrank(ds.C, ds.M, W, kind == 0 ? k : 0, 1, lev, r);
+                        a.geo[geo_index(a, cc, kind, lev, pb, r)] = kind == 0 ? ap_geom(ds, e, k, s) : dp_geom(ds, e);
+                    }
+                    pb += cnt;
+                }
+            }
+    }
+}
+
+// The current tile's pivot geometry (shared by every thread of the tile).
+__device__ __forceinline__ const PGeom &tile_geometry(const CondArgs &a, const CTile &tl, int kind, int lev)
 {
     const CondCirc &cc = a.plan[tl.circ];
-    const DiagShape &ds = cc.dsh;
-    __syncthreads();   // the previous tile's readers are done
-    if (threadIdx.x == 0) {
-        const int K = kind == 0 ? tl.seg : 0;
-        const Dig e = unrank(ds.C, ds.M, ltab(a, cc), K, 1, lev, tl.rank);
-        *s.geo = kind == 0 ? ap_geom(ds, e, K, s) : dp_geom(ds, e);
-    }
-    __syncthreads();
-    return *s.geo;
+    return a.geo[geo_index(a, cc, kind, lev, tl.pbase, tl.rank)];
 }
 
 // -------------------------------------------------------------- forward
@@ -431,7 +465,7 @@ __device__ void pair_forward(const CondArgs &a, CSmem &s, const CTile &tl, int k
     const CondCirc &cc = a.plan[tl.circ];
     const DiagShape &ds = cc.dsh;
     load_circuit(a, s, tl.circ);
-    const PGeom &g = tile_geometry(a, s, tl, kind, lev);
+    const PGeom &g = tile_geometry(a, tl, kind, lev);
     const int t = threadIdx.x, Dm = a.Dmax;
     const int u = tl.chunk * TPB + t;
     const bool act = u < cc.U2;
@@ -504,6 +538,7 @@ __global__ void __launch_bounds__(TPB) cond_forward_kernel(const __grid_constant
     CSmem s = carve(a, false);
     build_tables(s);
     prologue(a);
+    build_geo(a, s);
     if (!grid_sync(a.ctl, gridDim.x, a.timeout_ns)) return;
     const bool hb = *(volatile int *)&a.ctl->has_b != 0;
     for (int c = blockIdx.x; c < a.B; c += gridDim.x) step1_forward(a, s, c, hb);
@@ -534,7 +569,7 @@ __device__ void pair_reverse(const CondArgs &a, CSmem &s, const CTile &tl, int k
     const CondCirc &cc = a.plan[tl.circ];
     const DiagShape &ds = cc.dsh;
     load_circuit(a, s, tl.circ);
-    const PGeom &g = tile_geometry(a, s, tl, kind, lev);
+    const PGeom &g = tile_geometry(a, tl, kind, lev);
     const int t = threadIdx.x;
     const int u = tl.chunk * TPB + t;
     const bool act = u < cc.U2;
@@ -733,6 +768,7 @@ __global__ void __launch_bounds__(TPB) cond_vjp_kernel(const __grid_constant__ C
     CSmem s = carve(a, true);
     build_tables(s);
     prologue(a);
+    build_geo(a, s);
     if (!grid_sync(a.ctl, gridDim.x, a.timeout_ns)) return;
     const bool hb = *(volatile int *)&a.ctl->has_b != 0;
     for (int lev = a.Lmax; lev >= 0; --lev) {
@@ -812,7 +848,7 @@ int build_plan(int B, int M, const int *cut, const unsigned char *mask, PlanEntr
     for (int j = 0; j < M; ++j) Md += mask[j] ? 1 : 0;
     std::vector<CondCirc> cc(B);
     std::vector<unsigned> tabs;
-    int64_t offF = 0, offR = 0, offS = 0;
+    int64_t offF = 0, offR = 0, offS = 0, offG = 0;
     int Lmax = 0;
     for (int c = 0; c < B; ++c) {
         CondCirc &x = cc[c];
@@ -884,6 +920,24 @@ int build_plan(int B, int M, const int *cut, const unsigned char *mask, PlanEntr
                 W[(size_t)i * x.Wn + t2] = acc;
             }
         tabs.insert(tabs.end(), W.begin(), W.end());
+        // pivot prefix per (kind, level): AP(K) pivots of level s are the vectors
+        // over modes K.. with digit K < C_K - 1 summing to s; DP pivots those of K = 0
+        auto fam_count = [&](int K, int lev) {
+            int64_t n = 0;
+            for (int v = 0; v < ds.C[K] - 1 && v <= lev; ++v) n += W[(size_t)(K + 1) * x.Wn + lev - v];
+            return n;
+        };
+        x.gp_off = (int)tabs.size();
+        int64_t npiv = 0;
+        for (int kind = 0; kind < 2; ++kind)
+            for (int lev = 0; lev <= ds.L; ++lev) {
+                if (npiv >= (int64_t(1) << 32)) return FK_EUNSUPPORTED;
+                tabs.push_back((unsigned)npiv);
+                if (lev < ds.L && Mw > 0)
+                    for (int K = 0; K < (kind == 0 ? Mw : 1); ++K) npiv += fam_count(K, lev);
+            }
+        x.geo_off = offG;
+        offG += npiv;
         x.n_patterns = ds.n_diag;
         x.off_F = offF;
         x.off_rho = offR;
@@ -902,6 +956,7 @@ int build_plan(int B, int M, const int *cut, const unsigned char *mask, PlanEntr
     p.plan.F_total = offF;
     p.plan.scratch_total = offS;
     p.plan.rho_total = offR;
+    p.plan.geo_total = offG;
     const size_t nb = sizeof(CondCirc) * B + sizeof(unsigned) * tabs.size();
     p.bytes.resize(nb);
     std::memcpy(p.bytes.data(), cc.data(), sizeof(CondCirc) * B);
@@ -965,6 +1020,7 @@ CondArgs make_args(const CondPlan &plan, const void *A, const void *b, const voi
     a.Ar = (double2 *)(w + lay.Ar);
     a.br = (double2 *)(w + lay.br);
     a.F = (double2 *)(w + lay.F);
+    a.geo = (PGeom *)(w + lay.geo);
     a.timeout_ns = kBarrierTimeoutNs;
     return a;
 }
@@ -1015,6 +1071,7 @@ int cond_layout(const CondPlan &plan, bool vjp, CondLayout *lay)
     lay->plan = o; o = align_up(o + plan.plan_bytes);
     lay->Ar = o; o = align_up(o + B * D * D * c16);
     lay->br = o; o = align_up(o + B * D * c16);
+    lay->geo = o; o = align_up(o + (size_t)plan.geo_total * sizeof(PGeom));
     lay->F = o; o = align_up(o + (size_t)plan.F_total * c16);
     lay->grid_vjp = 0;
     if (vjp) {

@@ -43,12 +43,19 @@ def cond_once(reps=2):
     c = torch.tensor(np.array([t[2] for t in trip], np.complex128), device="cuda")
     rho, offs, ws = fd.fock_conditional_dm_batched(A, b, c, cuts, mask)
     g = torch.ones_like(rho)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    fwd = vjp = 0.0
     for _ in range(reps):
+        ev[0].record()
         fd.fock_conditional_dm_batched(A, b, c, cuts, mask, rho=rho, ws=ws)
+        ev[1].record()
         fd.fock_conditional_dm_vjp_batched(A, b, c, cuts, mask, g, ws)
-    torch.cuda.synchronize()
+        ev[2].record()
+        torch.cuda.synchronize()
+        fwd += ev[0].elapsed_time(ev[1]); vjp += ev[1].elapsed_time(ev[2])
     fd.check_workspace(ws)
-    print(json.dumps({"conditional_outputs": int(offs[-1]), "reps": reps}))
+    print(json.dumps({"conditional_outputs": int(offs[-1]), "reps": reps, "forward_ms": fwd / reps,
+                      "vjp_ms": vjp / reps}))
 
 
 def main():
