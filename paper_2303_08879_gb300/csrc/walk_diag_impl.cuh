@@ -106,9 +106,6 @@ struct Smem {
     int *wg;          // tensor-core VJP: per-warp [32] row exponents of the partial dL/dA
     int *idx;         // [M][TPB] box indices per pivot
     int *tiles;       // [M + 2] tile prefix sums of the current phase
-    int64_t *wcum;    // partial pass: [TPB / 32][3][M] level offsets of each warp's level
-    int *tpre;        // partial pass: [L + 1][M + 1] 32-pivot tile prefix over K per circuit,
-                      // then [L + 2] prefix over levels of the launch's tiles
     int loaded_circ;
     int multi_key;    // several shapes: (group, level, kind) the tables hold, or -1
 };
@@ -165,7 +162,7 @@ struct Walk {
     // pass.  Absent regions have offset kNone.
     static constexpr size_t kNone = ~(size_t)0;
     struct SmemPlan {
-        size_t S, cum, inv, bs, fA, wb, wy, FP, wf, wg, Af, A3, R3, Y3, idx, tiles, wcum, tpre, bytes;
+        size_t S, cum, inv, bs, fA, wb, wy, FP, wf, wg, Af, A3, R3, Y3, idx, tiles, bytes;
     };
 
     static __host__ __device__ SmemPlan smem_plan(int M, int L, int mode, bool has_b)
@@ -205,14 +202,6 @@ struct Walk {
             q.idx = n; n += (size_t)M * TPB * sizeof(int); al();
         }
         q.tiles = n; n += (M + 2) * sizeof(int);
-        q.wcum = q.tpre = kNone;
-        if (TC && mode == kPart) {
-            // warp-scheduled partial pass: each warp's level offsets (three rows of M),
-            // and the 32-pivot tile prefix sums of every level ([L + 1][M + 1] + [L + 2])
-            al();
-            q.wcum = n; n += (size_t)(TPB / 32) * 3 * M * sizeof(int64_t);
-            q.tpre = n; n += ((size_t)(L + 1) * (M + 1) + (L + 2)) * sizeof(int);
-        }
         q.bytes = n + 64;
         return q;
     }
@@ -249,8 +238,6 @@ struct Walk {
         s.Y3 = (double *)at(q.Y3);
         s.idx = (int *)at(q.idx);
         s.tiles = (int *)at(q.tiles);
-        s.wcum = (int64_t *)at(q.wcum);
-        s.tpre = (int *)at(q.tpre);
         s.loaded_circ = -1;
         s.multi_key = -1;
         return s;
@@ -1944,70 +1931,21 @@ struct Walk {
         build_tables(sh, s);
         __syncthreads();
         const int hb = *(volatile int *)&a.ctl->has_b;
-        const int L = sh.L, M = sh.M, W = M + 1;
-        // 32-pivot tiles: per level and anchor, then over levels for the whole launch
-        int *tk = s.tpre, *tl = s.tpre + (size_t)(L + 1) * W;
-        if (threadIdx.x == 0) {
-            int acc = 0;
-            for (int lev = 0; lev <= L; ++lev) {
-                int t = 0;
-                for (int K = 0; K < M; ++K) {
-                    tk[lev * W + K] = t;
-                    if (lev < L) t += (int)((level_count(sh, s, K, 1, lev) + 31) / 32);
-                }
-                tk[lev * W + M] = t;
-                tl[lev] = acc;
-                acc += a.B * t;
-            }
-            tl[L + 1] = acc;
-        }
-        __syncthreads();
-        // each warp takes 32-pivot tiles of any level from one counter, with no
-        // block-wide barrier between tiles; its level offsets live in its own rows
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        Smem w = s;
-        w.cum0 = s.wcum + (size_t)warp * 3 * M;
-        w.cum1 = w.cum0 + M;
-        w.cum2 = w.cum0 + 2 * M;
-        int *ctr = a.ctr + 2 * (L + 1);
-        const int total = tl[L + 1];
-        int cur = -1;
-        for (;;) {
-            int g = 0;
-            if (lane == 0) g = atomicAdd(ctr, 1);
-            g = __shfl_sync(0xffffffffu, g, 0);
-            if (g >= total) break;
-            int lev = 0;
-            while (tl[lev + 1] <= g) ++lev;
-            if (lev != cur) {
-                if (lane == 0) phase_offsets(sh, w, lev);
-                __syncwarp();
-                cur = lev;
-            }
-            const int Tc = tk[lev * W + M], loc = g - tl[lev];
-            TileId t;
-            t.circ = loc / Tc;
-            const int r = loc - t.circ * Tc;
-            int K = 0;
-            while (K + 1 < M && r >= tk[lev * W + K + 1]) ++K;
-            t.seg = K;
-            // pivot rank0 + lane of the level; the tile functions add threadIdx.x
-            t.rank0 = (unsigned)(r - tk[lev * W + K]) * 32u - (unsigned)(warp * 32);
-            t.count = level_count(sh, s, K, 1, lev);
-            if (!pivots_run(a, t.circ, lev)) continue;
-            if (hb) ap_partial_tile<true>(a, w, t, K, lev);
-            else ap_partial_tile<false>(a, w, t, K, lev);
-        }
-        __syncthreads();
-        if (hb) {
-            // the diagonal pivots (b != 0): block tiles of 128 per level, as in the walk
-            int *dctr = a.ctr + 2 * (L + 1);
-            for (int lev = 0; lev < L; ++lev) {
+        int *ctr = a.ctr + 2 * (sh.L + 1);
+        for (int lev = 0; lev < sh.L; ++lev) {
+            const int nt = phase_tiles(a, s, 0, lev);
+            run_tiles(ctr + 2 * lev + 1, nt, [&](int tile) {
+                const TileId tl = decode_tile(a, s, 0, lev, tile);
+                if (!pivots_run(a, tl.circ, lev)) return;
+                if (hb) ap_partial_tile<true>(a, s, tl, tl.seg, lev);
+                else ap_partial_tile<false>(a, s, tl, tl.seg, lev);
+            });
+            if (hb) {
                 const int nd = phase_tiles(a, s, 1, lev);
-                run_tiles(dctr + 2 * lev + 2, nd, [&](int tile) {
-                    const TileId td = decode_tile(a, s, 1, lev, tile);
-                    if (!pivots_run(a, td.circ, lev)) return;
-                    dp_partial_tile(a, s, td, lev);
+                run_tiles(ctr + 2 * lev, nd, [&](int tile) {
+                    const TileId tl = decode_tile(a, s, 1, lev, tile);
+                    if (!pivots_run(a, tl.circ, lev)) return;
+                    dp_partial_tile(a, s, tl, lev);
                 });
             }
         }
