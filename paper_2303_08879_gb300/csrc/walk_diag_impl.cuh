@@ -108,7 +108,6 @@ struct Smem {
     int *tiles;       // [M + 2] tile prefix sums of the current phase
     int loaded_circ;
     int multi_key;    // several shapes: (group, level, kind) the tables hold, or -1
-    int run_circ[2], run_lev[2], run_val[2];   // early stop: the last decision per level parity
 };
 
 // ---------------------------------------------------------------- geometry
@@ -241,7 +240,6 @@ struct Walk {
         s.tiles = (int *)at(q.tiles);
         s.loaded_circ = -1;
         s.multi_key = -1;
-        s.run_circ[0] = s.run_circ[1] = -1;
         return s;
     }
 
@@ -907,24 +905,6 @@ struct Walk {
         return cum < a.thr;
     }
 
-    // The same decision kept per thread for the last (circuit, level) asked of
-    // each level parity (a reverse tile asks for its level and the one above).
-    // A decision never changes once it can be asked: the slots up to `lev` are
-    // final before any tile of level lev runs, and the reverse walk reads the
-    // forward's slots.  The tiles of a block come circuit by circuit, so the
-    // slots are summed about once per circuit and phase instead of per tile.
-    static __device__ __forceinline__ bool pivots_run(const DiagArgs &a, Smem &s, int circ, int lev)
-    {
-        if (!a.early) return lev < a.sh.L;
-        const int k = lev & 1;
-        if (s.run_circ[k] != circ || s.run_lev[k] != lev) {
-            s.run_val[k] = pivots_run(a, circ, lev) ? 1 : 0;
-            s.run_circ[k] = circ;
-            s.run_lev[k] = lev;
-        }
-        return s.run_val[k] != 0;
-    }
-
     // Block-wide sum of v added to lvl[circ][n] (thread 0).
     static __device__ void add_level_prob(const DiagArgs &a, int circ, int n, double v)
     {
@@ -1495,7 +1475,7 @@ struct Walk {
         double2 *Fb = a.Fbar + (size_t)tl.circ * sh.circ_alloc;
         const unsigned r = tl.rank0 + t;
         const bool act = r < tl.count;
-        const bool up = pivots_run(a, s, tl.circ, lev + 1);   // level lev + 1 ran in reverse
+        const bool up = pivots_run(a, tl.circ, lev + 1);   // level lev + 1 ran in reverse
         Dig e;
         ApGeom g{};
         if (act) {
@@ -1656,7 +1636,7 @@ struct Walk {
         double2 *Fb = a.Fbar + (size_t)tl.circ * sh.circ_alloc;
         const unsigned r = tl.rank0 + t;
         const bool act = r < tl.count;
-        const bool up = pivots_run(a, s, tl.circ, lev + 1);   // level lev + 1 ran in reverse
+        const bool up = pivots_run(a, tl.circ, lev + 1);   // level lev + 1 ran in reverse
         Dig e;
         ApGeom g{};
         if (act) {
@@ -1763,7 +1743,7 @@ struct Walk {
         const double2 *Fb = a.Fbar + (size_t)tl.circ * sh.circ_alloc;
         const unsigned r = tl.rank0 + t;
         const bool act = r < tl.count;
-        const bool up = pivots_run(a, s, tl.circ, lev + 1);
+        const bool up = pivots_run(a, tl.circ, lev + 1);
         int fx = 0;
         double2 FPv = make_double2(0, 0);
         if (act) {
@@ -1868,7 +1848,7 @@ struct Walk {
                 const int nt = phase_tiles(a, s, 1, lev);
                 run_tiles(a.ctr + 2 * lev, nt, [&](int tile) {
                     const TileId tl = decode_tile(a, s, 1, lev, tile);
-                    if (!pivots_run(a, s, tl.circ, lev)) return;
+                    if (!pivots_run(a, tl.circ, lev)) return;
                     dp_forward_tile(a, s, tl, lev);
                 });
                 if (!grid_sync(a.ctl, gridDim.x, a.timeout_ns)) return;
@@ -1876,7 +1856,7 @@ struct Walk {
             const int nt = phase_tiles(a, s, 0, lev);
             run_tiles(a.ctr + 2 * lev + 1, nt, [&](int tile) {
                 const TileId tl = decode_tile(a, s, 0, lev, tile);
-                if (!pivots_run(a, s, tl.circ, lev)) return;
+                if (!pivots_run(a, tl.circ, lev)) return;
                 if (a.early) {
                     if (hb) ap_forward_tile<true, true>(a, s, tl, tl.seg, lev);
                     else ap_forward_tile<false, true>(a, s, tl, tl.seg, lev);
@@ -1915,7 +1895,7 @@ struct Walk {
                 const int nt = phase_tiles(a, s, 0, lev);
                 run_tiles(a.ctr + 2 * lev + 1, nt, [&](int tile) {
                     const TileId tl = decode_tile(a, s, 0, lev, tile);
-                    if (!pivots_run(a, s, tl.circ, lev)) return;
+                    if (!pivots_run(a, tl.circ, lev)) return;
                     if constexpr (TC) {
                         if (hb) ap_reverse_tile_tc<true>(a, s, tl, tl.seg, lev);
                         else ap_reverse_tile_tc<false>(a, s, tl, tl.seg, lev);
@@ -1930,7 +1910,7 @@ struct Walk {
                 const int nt = phase_tiles(a, s, 1, lev);
                 run_tiles(a.ctr + 2 * lev, nt, [&](int tile) {
                     const TileId tl = decode_tile(a, s, 1, lev, tile);
-                    if (!pivots_run(a, s, tl.circ, lev)) return;
+                    if (!pivots_run(a, tl.circ, lev)) return;
                     if constexpr (TC) dp_reverse_tile_tc(a, s, tl, lev);
                     else dp_reverse_tile(a, s, tl, lev);
                 });
@@ -1956,7 +1936,7 @@ struct Walk {
             const int nt = phase_tiles(a, s, 0, lev);
             run_tiles(ctr + 2 * lev + 1, nt, [&](int tile) {
                 const TileId tl = decode_tile(a, s, 0, lev, tile);
-                if (!pivots_run(a, s, tl.circ, lev)) return;
+                if (!pivots_run(a, tl.circ, lev)) return;
                 if (hb) ap_partial_tile<true>(a, s, tl, tl.seg, lev);
                 else ap_partial_tile<false>(a, s, tl, tl.seg, lev);
             });
@@ -1964,7 +1944,7 @@ struct Walk {
                 const int nd = phase_tiles(a, s, 1, lev);
                 run_tiles(ctr + 2 * lev, nd, [&](int tile) {
                     const TileId tl = decode_tile(a, s, 1, lev, tile);
-                    if (!pivots_run(a, s, tl.circ, lev)) return;
+                    if (!pivots_run(a, tl.circ, lev)) return;
                     dp_partial_tile(a, s, tl, lev);
                 });
             }
