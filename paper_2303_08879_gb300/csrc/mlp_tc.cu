@@ -218,10 +218,17 @@ __global__ void __launch_bounds__(TPB_TC, 1)
     if (aborted && threadIdx.x == 0 && g.e.status) atomicCAS(g.e.status, 0, (int)FK_ETIMEOUT);
     if (!aborted) {
         // warp w reads TMEM lanes 32 (w % 4) .. + 31 (the lanes its quarter may
-        // access); warps w and w + 4 take the two halves of the columns
+        // access); warps w and w + 4 take the two halves of the columns.  A lane
+        // holds one row of a 32-column chunk; row-major outputs go through the
+        // warp's 32 x 33 staging tile in the (now idle) operand ring, so that each
+        // store instruction writes one contiguous row; the transposed outputs are
+        // written straight from the lane-per-row layout, which is already coalesced.
         const int q = warp & 3, half = warp >> 2;
-        const int m = m0 + q * 32 + lane;
+        const int mrow0 = m0 + q * 32, m = mrow0 + lane;
         const TcEpilogue &e = g.e;
+        float *fst = (float *)(smem_raw + (base - smem_u32(smem_raw))) + warp * (32 * 33 * 3 / 2 + 16);
+        unsigned short *hst = (unsigned short *)(fst + 32 * 33);
+        const int mrows = min(32, g.M - mrow0);
         for (int c0 = half * (TBN / 2); c0 < (half + 1) * (TBN / 2); c0 += 32) {
             float v[32];
             if (nk > 0) {
@@ -231,77 +238,57 @@ __global__ void __launch_bounds__(TPB_TC, 1)
                 for (int i = 0; i < 32; ++i) v[i] = 0.f;
             }
             const int n = n0 + c0;
-            if (m >= g.M || n >= g.N) continue;
+            if (mrows <= 0 || n >= g.N) continue;
             const int nv = min(32, g.N - n);
-            const int64_t o = (int64_t)m * e.ldo + n;
-            // whole 32-column runs of rows with 16-byte aligned starts use vector accesses
-            const bool vec = nv == 32 && (e.ldo % 8) == 0;
+            const bool in = m < g.M;
+            __syncwarp();
             switch (e.kind) {
             case TC_EPI_HIDDEN:
             case TC_EPI_OUT: {
                 const bool hid = e.kind == TC_EPI_HIDDEN;
-                float zz[32];
-                __nv_bfloat16 aa[32];
 #pragma unroll
                 for (int i = 0; i < 32; ++i) {
-                    zz[i] = i < nv ? v[i] + e.bias[n + i] : 0.f;
-                    aa[i] = __float2bfloat16(silu(zz[i]));
+                    const float z = i < nv ? v[i] + e.bias[n + i] : 0.f;
+                    const __nv_bfloat16 a = __float2bfloat16(silu(z));
+                    fst[lane * 33 + i] = z;
+                    hst[lane * 33 + i] = __bfloat16_as_ushort(a);
+                    if (hid && e.actT && in && i < nv) e.actT[(int64_t)(n + i) * e.ldT + m] = a;
                 }
-                if (vec) {
-                    float4 *zd = (float4 *)(e.z + o);
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) zd[q] = make_float4(zz[4 * q], zz[4 * q + 1], zz[4 * q + 2], zz[4 * q + 3]);
-                    if (hid) {
-                        uint4 *ad = (uint4 *)(e.act + o);
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) ad[q] = *(const uint4 *)&aa[8 * q];
+                __syncwarp();
+                if (lane < nv)
+                    for (int r = 0; r < mrows; ++r) {
+                        const int64_t o = (int64_t)(mrow0 + r) * e.ldo + n + lane;
+                        e.z[o] = fst[r * 33 + lane];
+                        if (hid) e.act[o] = __ushort_as_bfloat16(hst[r * 33 + lane]);
                     }
-                } else {
-                    for (int i = 0; i < nv; ++i) {
-                        e.z[o + i] = zz[i];
-                        if (hid) e.act[o + i] = aa[i];
-                    }
-                }
-                if (hid && e.actT)
-                    for (int i = 0; i < nv; ++i) e.actT[(int64_t)(n + i) * e.ldT + m] = aa[i];
                 break;
             }
             case TC_EPI_BACK_HIDDEN: {
-                float zp[32];
-                if (vec) {
-                    const float4 *zs = (const float4 *)(e.zprev + o);
+                // z_prev rows in, coalesced, through the staging tile
+                if (lane < nv)
+                    for (int r = 0; r < mrows; ++r)
+                        fst[r * 33 + lane] = e.zprev[(int64_t)(mrow0 + r) * e.ldo + n + lane];
+                __syncwarp();
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const float4 t = zs[q];
-                        zp[4 * q] = t.x; zp[4 * q + 1] = t.y; zp[4 * q + 2] = t.z; zp[4 * q + 3] = t.w;
-                    }
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) zp[i] = i < nv ? e.zprev[o + i] : 0.f;
+                for (int i = 0; i < 32; ++i) {
+                    const __nv_bfloat16 a = __float2bfloat16(v[i] * dsilu(fst[lane * 33 + i]));
+                    hst[lane * 33 + i] = __bfloat16_as_ushort(a);
+                    if (e.actT && in && i < nv) e.actT[(int64_t)(n + i) * e.ldT + m] = a;
                 }
-                __nv_bfloat16 aa[32];
-#pragma unroll
-                for (int i = 0; i < 32; ++i) aa[i] = __float2bfloat16(v[i] * dsilu(zp[i]));
-                if (vec) {
-                    uint4 *ad = (uint4 *)(e.act + o);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) ad[q] = *(const uint4 *)&aa[8 * q];
-                } else {
-                    for (int i = 0; i < nv; ++i) e.act[o + i] = aa[i];
-                }
-                if (e.actT)
-                    for (int i = 0; i < nv; ++i) e.actT[(int64_t)(n + i) * e.ldT + m] = aa[i];
+                __syncwarp();
+                if (lane < nv)
+                    for (int r = 0; r < mrows; ++r)
+                        e.act[(int64_t)(mrow0 + r) * e.ldo + n + lane] = __ushort_as_bfloat16(hst[r * 33 + lane]);
                 break;
             }
             case TC_EPI_PARTIAL: {
-                float *dst = e.out + (int64_t)blockIdx.z * g.M * e.ldo + o;
-                if (vec) {
 #pragma unroll
-                    for (int q = 0; q < 8; ++q)
-                        ((float4 *)dst)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-                } else {
-                    for (int i = 0; i < nv; ++i) dst[i] = v[i];
-                }
+                for (int i = 0; i < 32; ++i) fst[lane * 33 + i] = v[i];
+                __syncwarp();
+                float *dst = e.out + (int64_t)blockIdx.z * g.M * e.ldo;
+                if (lane < nv)
+                    for (int r = 0; r < mrows; ++r)
+                        dst[(int64_t)(mrow0 + r) * e.ldo + n + lane] = fst[r * 33 + lane];
                 break;
             }
             default: break;
