@@ -747,29 +747,32 @@ struct Walk {
     // field of its reads) and its adjoints by the inverse, which leaves every
     // product unchanged; the adjoints then share a power of two per row w
     // over the 32 pivots, so each term is exact relative to the largest
-    // product of its row.  Real form with K = (pivot t, re/im) = 64:
-    //   A[w][(t,0)] = Yr, A[w][(t,1)] = Yi;  B[(t,0)][2j] = Xr, B[(t,1)][2j] = Xi,
-    //   B[(t,0)][2j+1] = -Xi, B[(t,1)][2j+1] = Xr,
-    // so column 2j of A B is Re P[w][j] and column 2j+1 is Im P[w][j].
-    // The result is added to the warp's own slot (single writer).
+    // product of its row.  Real form with K = (pivot t, re/im) = 64 and two
+    // accumulators per output:
+    //   A[w][(t,0)] = Yr, A[w][(t,1)] = Yi;
+    //   Re P = A [Xr; Xi],  Im P = A [-Xi; Xr]  (column j of each B).
+    // Each read is converted once; the digits of (-Xi, Xr) are those of
+    // (Xr, Xi) with the halves swapped and the low half negated (a balanced
+    // digit negates exactly in fp16).  The result is added to the warp's own
+    // slot (single writer).
     static __device__ void tc_partials(const DiagArgs &a, const Smem &s, int circ, int row0, int N)
     {
-        constexpr int NT = 2 * KS;   // N tiles over the 2N real columns (N <= 8 KS)
+        constexpr int NT = KS;   // N tiles of 8 columns j (N <= 8 KS)
         const int lane = threadIdx.x & 31, grp = lane >> 2, tig = lane & 3, warp = threadIdx.x >> 5;
-        const int D = 2 * a.sh.M, nnt = (2 * N + 7) >> 3;
+        const int D = 2 * a.sh.M, nnt = (N + 7) >> 3;
         const double *wx = s.wb + (size_t)warp * XS * WBS;
         const double *wy = s.wy + (size_t)warp * XS * WBS;
         const int *ef = s.wf + warp * 32;
         const int *gy = s.wg + warp * 32;
         const size_t slot = (size_t)blockIdx.x * (TPB / 32) + warp;
         double *pA = (double *)(a.partA + ((size_t)circ * a.slots + slot) * D * D);
-        float acc[NDIG][NT][4];
+        float ar[NDIG][NT][4], ai[NDIG][NT][4];
 #pragma unroll
         for (int d = 0; d < NDIG; ++d)
 #pragma unroll
             for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
-                for (int q = 0; q < 4; ++q) acc[d][nt][q] = 0.f;
+                for (int q = 0; q < 4; ++q) ar[d][nt][q] = ai[d][nt][q] = 0.f;
         // A rows of this lane: w0 = grp, w1 = grp + 8
         const int g0 = grp < N ? gy[grp] : 0, g1 = grp + 8 < N ? gy[grp + 8] : 0;
 #pragma unroll 1
@@ -795,7 +798,7 @@ struct Walk {
 #pragma unroll
             for (int nt = 0; nt < NT; ++nt) {
                 if (nt >= nnt) continue;
-                const int n = 8 * nt + grp, j = n >> 1, im = n & 1;
+                const int j = 8 * nt + grp;
                 uint32_t bq[NDIG][2];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
@@ -806,14 +809,20 @@ struct Walk {
                         xi = wx[(2 * j + 1) * WBS + t];
                     }
                     uint32_t wd[NDIG];
-                    digit_words(to_fixed(im ? -xi : xr, e), to_fixed(im ? xr : xi, e), wd);
+                    digit_words(to_fixed(xr, e), to_fixed(xi, e), wd);
 #pragma unroll
                     for (int sl = 0; sl < NDIG; ++sl) bq[sl][h] = wd[sl];
                 }
 #pragma unroll
-                for (int sa = 0; sa < NDIG; ++sa)
+                for (int u = 0; u < NDIG; ++u) {
+                    const uint32_t bi[2] = {__byte_perm(bq[u][0], 0u, 0x1032) ^ 0x8000u,
+                                            __byte_perm(bq[u][1], 0u, 0x1032) ^ 0x8000u};
 #pragma unroll
-                    for (int u = 0; u + sa < NDIG; ++u) mma_f16(acc[sa + u][nt], aq[sa], bq[u]);
+                    for (int sa = 0; sa + u < NDIG; ++sa) {
+                        mma_f16(ar[sa + u][nt], aq[sa], bq[u]);
+                        mma_f16(ai[sa + u][nt], aq[sa], bi);
+                    }
+                }
             }
         }
 #pragma unroll
@@ -821,20 +830,23 @@ struct Walk {
             if (nt >= nnt) continue;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const int w = grp + 8 * (q >> 1), n = 8 * nt + 2 * tig + (q & 1), j = n >> 1;
+                const int w = grp + 8 * (q >> 1), j = 8 * nt + 2 * tig + (q & 1);
                 const int g = (q >> 1) ? g1 : g0;
                 if (w < N && j < N && g >= 26) {
                     float a7[NDIG][4];
 #pragma unroll
-                    for (int d = 0; d < NDIG; ++d) a7[d][0] = acc[d][nt][q];
-                    const long long Y = combine_digits_wide(a7, 0);
-                    const double v = scale2(__ll2double_rn(Y), g - 1074);
-                    double *dst = pA + 2 * ((size_t)(row0 + w) * D + row0 + j) + (n & 1);
-                    // reduction without return: the warp does not wait for the
-                    // old value.  The slot has one warp as its only writer and
-                    // its updates are ordered by the warp's barriers between
-                    // tiles, so the sum order is fixed.
-                    atomicAdd(dst, v);
+                    for (int d = 0; d < NDIG; ++d) a7[d][0] = ar[d][nt][q];
+                    const long long Yr = combine_digits_wide(a7, 0);
+#pragma unroll
+                    for (int d = 0; d < NDIG; ++d) a7[d][0] = ai[d][nt][q];
+                    const long long Yi = combine_digits_wide(a7, 0);
+                    double *dst = pA + 2 * ((size_t)(row0 + w) * D + row0 + j);
+                    // reductions without return: the warp does not wait for
+                    // the old values.  The slot has one warp as its only
+                    // writer and its updates are ordered by the warp's
+                    // barriers between tiles, so the sum order is fixed.
+                    atomicAdd(dst, scale2(__ll2double_rn(Yr), g - 1074));
+                    atomicAdd(dst + 1, scale2(__ll2double_rn(Yi), g - 1074));
                 }
             }
         }
@@ -1973,31 +1985,56 @@ struct Walk {
             a.gb[cix(a, (int)(e / Do)) * Do + e % Do] = make_double2(0, 0);
     }
 
+    // Sum of a double2 over the 32 lanes (xor butterfly: a fixed order, so
+    // the result does not depend on timing).
+    static __device__ __forceinline__ double2 warp_sum2(double2 v)
+    {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+            v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+        }
+        return v;
+    }
+
+    // One warp per gradient entry: the lanes sum interleaved subsets of the
+    // slots (all loads independent), then a butterfly joins them.
     static __device__ void reduce_grads(const DiagArgs &a, int hb)
     {
         const DiagShape &sh = a.sh;
-        const int D = 2 * sh.M, Do = sh.D_orig;
+        const int D = 2 * sh.M, Do = sh.D_orig, lane = threadIdx.x & 31;
+        const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+        const int64_t nA = (int64_t)a.B * D * D, nb = (int64_t)a.B * D;
+        for (int64_t e = gw; e < nA + nb; e += nw) {
+            if (e < nA) {
+                const int c = (int)(e / (D * D));
+                const int w = (int)((e / D) % D), l = (int)(e % D);
+                double2 x = make_double2(0, 0), y = make_double2(0, 0);
+                const double2 *pA = a.partA + (size_t)c * a.slots * D * D;
+                for (int blk = lane; blk < a.slots; blk += 32) {
+                    x = cadd(x, __ldcg(pA + (size_t)blk * D * D + (size_t)w * D + l));
+                    y = cadd(y, __ldcg(pA + (size_t)blk * D * D + (size_t)l * D + w));
+                }
+                x = warp_sum2(x);
+                y = warp_sum2(y);
+                if (lane == 0) {
+                    const int ow = 2 * sh.mode_map[w / 2] + (w & 1), ol = 2 * sh.mode_map[l / 2] + (l & 1);
+                    a.gA[cix(a, c) * Do * Do + (size_t)ow * Do + ol] =
+                        make_double2(0.5 * (x.x + y.x), 0.5 * (x.y + y.y));
+                }
+            } else {
+                const int64_t f = e - nA;
+                const int c = (int)(f / D), w = (int)(f % D);
+                double2 x = make_double2(0, 0);
+                for (int blk = lane; blk < a.slots; blk += 32)
+                    x = cadd(x, __ldcg(a.partb + ((size_t)c * a.slots + blk) * D + w));
+                x = warp_sum2(x);
+                if (lane == 0) a.gb[cix(a, c) * Do + 2 * sh.mode_map[w / 2] + (w & 1)] = x;
+            }
+        }
         const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
         const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
-        for (int64_t e = gtid; e < (int64_t)a.B * D * D; e += gsz) {
-            const int c = (int)(e / (D * D));
-            const int w = (int)((e / D) % D), l = (int)(e % D);
-            double2 x = make_double2(0, 0), y = make_double2(0, 0);
-            for (int blk = 0; blk < a.slots; ++blk) {
-                const double2 *pA = a.partA + ((size_t)c * a.slots + blk) * D * D;
-                x = cadd(x, pA[(size_t)w * D + l]);
-                y = cadd(y, pA[(size_t)l * D + w]);
-            }
-            const int ow = 2 * sh.mode_map[w / 2] + (w & 1), ol = 2 * sh.mode_map[l / 2] + (l & 1);
-            a.gA[cix(a, c) * Do * Do + (size_t)ow * Do + ol] = make_double2(0.5 * (x.x + y.x), 0.5 * (x.y + y.y));
-        }
-        for (int64_t e = gtid; e < (int64_t)a.B * D; e += gsz) {
-            const int c = (int)(e / D), w = (int)(e % D);
-            double2 x = make_double2(0, 0);
-            for (int blk = 0; blk < a.slots; ++blk) x = cadd(x, a.partb[((size_t)c * a.slots + blk) * D + w]);
-            const int ow = 2 * sh.mode_map[w / 2] + (w & 1);
-            a.gb[cix(a, c) * Do + ow] = x;
-        }
         for (int64_t c = gtid; c < a.B; c += gsz) a.gc[cix(a, (int)c)] = vacuum_adjoint(a, (int)c, hb != 0);
     }
 
