@@ -81,7 +81,7 @@ typedef enum {
 #define FK_FLAG_ENGINE_FP64   0x10u   /* this call: FP64 product engine of the
                                          all-detected walk (see fk_diag_set_engine) */
 #define FK_FLAG_ENGINE_TENSOR 0x20u   /* this call: tensor-core product engine
-                                         (M <= 8 after dropping C_j = 1 modes) */
+                                         (M <= 12 after dropping C_j = 1 modes) */
 #define FK_FLAG_CHECK_FINITE  0x40u   /* scan A, b and c on the device before the
                                          walk; on a NaN or Inf the workspace
                                          status word becomes FK_ENONFINITE, the
@@ -431,11 +431,13 @@ int fk_diag_tuning_flags(int engine, int tpb, int ch, int blocks_per_sm, unsigne
  *     pivot's power of two from its reads to its adjoints (products
  *     unchanged), so each term is exact relative to the largest product of
  *     its row.  With this engine the VJP is two launches on the stream:
- *     the reverse walk, then the pass that forms the partial sums.  Shapes
- *     with M > 8 use FP64.
- *   FK_ENGINE_AUTO:   the tensor engine where it applies (M <= 8 kept
+ *     the reverse walk, then the pass that forms the partial sums.  Kept
+ *     modes: up to 12 (one, two or three 16-row K steps); shapes with
+ *     M > 12 use FP64.
+ *   FK_ENGINE_AUTO:   the tensor engine where it applies (M <= 12 kept
  *     modes), else FP64.  The default: on GB300 the tensor engine runs the
- *     8-mode forward + VJP about 2.9 times faster than the best FP64 shape.
+ *     8-mode forward + VJP about 3 times faster than the best FP64 shape
+ *     and the 12-mode one about 3.9 times faster.
  * Returns FK_EINVAL for another value.  Per call, FK_FLAG_ENGINE_FP64 and
  * FK_FLAG_ENGINE_TENSOR override this default.
  */

@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfockdiag.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cpp", "circuit.cpp", "walk_diag.cu", "walk_cond.cu", "mlp.cu", "herald.cu", "probe.cu", "static_ws.cu",
-           "walk_pure.cu", "multi.cpp", "walk_diag_tc1.cu", "walk_diag_tc2.cu", "mlp_tc.cu"]
+           "walk_pure.cu", "multi.cpp", "walk_diag_tc1.cu", "walk_diag_tc2.cu", "walk_diag_tc3.cu", "mlp_tc.cu"]
 # walk_diag_fp64.cu once per FP64 tile shape (pivots per tile, rows per chunk)
 FP64_SHAPES = [(128, 8), (128, 4), (64, 8), (64, 4), (256, 8)]
 

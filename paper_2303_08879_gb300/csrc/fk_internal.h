@@ -34,12 +34,12 @@ int build_diag_shape(int M, const int *cutoffs, bool has_b, DiagShape *sh);
 // describes): every pattern with n_1 + ... + n_M < n_max, no per-mode cutoff.
 int build_global_shape(int M, int n_max, bool has_b, DiagShape *sh);
 
-// Per-circuit digit fragments of A for the tensor-core engine (M <= 8): the
+// Per-circuit digit fragments of A for the tensor-core engine (M <= 12): the
 // 2D row exponent fields (padded to 256 bytes), then the fp16 digit fragments
-// of the real form of A (up to 2 x 2 tiles x 7 digits x 32 lanes x 16 bytes).
-constexpr size_t kDigFragBytes = 2 * 2 * 7 * 32 * 16;
+// of the real form of A (up to 3 x 3 tiles x 7 digits x 32 lanes x 16 bytes).
+constexpr size_t kDigFragBytes = 3 * 3 * 7 * 32 * 16;
 constexpr size_t kDigBytes = 256 + kDigFragBytes;
-inline size_t diag_digit_bytes(int M) { return M <= 8 ? kDigBytes : 0; }
+inline size_t diag_digit_bytes(int M) { return M <= 12 ? kDigBytes : 0; }
 
 // Geometry of every AP(K) pivot (M <= 8), shared by all circuits of a launch:
 // 12 ints per pivot, indexed like the VJP scratch (off_ap[K] + level offset
@@ -149,6 +149,7 @@ const WalkKernels *fp64_walk_kernels_64_4();
 const WalkKernels *fp64_walk_kernels_256_8();
 const WalkKernels *tc1_walk_kernels();    // M <= 4
 const WalkKernels *tc2_walk_kernels();    // M <= 8
+const WalkKernels *tc3_walk_kernels();    // M <= 12
 
 // Tile shape of the all-detected walk (pivots per tile, output rows per
 // register chunk, blocks per SM; 0 = as many as fit).  Process-wide default;

@@ -87,13 +87,13 @@ int device_sms(int *sms)
 }
 
 // Compiled tile shapes (pivots per tile, output rows per register chunk) of
-// the FP64 engine and the tensor-core kernels by KS = ceil(M / 4) (M <= 8;
+// the FP64 engine and the tensor-core kernels by KS = ceil(M / 4) (M <= 12;
 // 128 pivots per tile; the VJP is two launches: the reverse walk, then the
 // partial pass).
 using Variant = WalkKernels;
 struct VariantTable {
     Variant v[kNumFp64Shapes];
-    const Variant *tc[2] = {nullptr, nullptr};
+    const Variant *tc[3] = {nullptr, nullptr, nullptr};
     VariantTable()
     {
         v[0] = *fp64_walk_kernels_128_8();
@@ -103,6 +103,7 @@ struct VariantTable {
         v[4] = *fp64_walk_kernels_256_8();
         tc[0] = tc1_walk_kernels();
         tc[1] = tc2_walk_kernels();
+        tc[2] = tc3_walk_kernels();
     }
 };
 const VariantTable &tables()
@@ -110,7 +111,7 @@ const VariantTable &tables()
     static const VariantTable t;
     return t;
 }
-constexpr int kTcMaxModes = 8;
+constexpr int kTcMaxModes = 12;
 
 // Process-wide defaults (fk_diag_set_tuning, fk_diag_set_engine), read once
 // per call under the lock; per-call flag bits override them.

@@ -665,7 +665,8 @@ struct Walk {
                     const int ra = 16 * mt + grp + 8 * (q >> 1), r = ra - r0;
                     const int pc = nt * 8 + 2 * tig + (q & 1);
                     if (r >= 0 && r < n2) {
-                        const long long Y = combine_digits(acc, q);
+                        // up to 7 x 16 KS x 2^14 per diagonal: below 2^22 for KS <= 2
+                        const long long Y = KS > 2 ? combine_digits_wide(acc, q) : combine_digits(acc, q);
                         out[r * WBS + pc] = scale2(__ll2double_rn(Y), s.fA[ra] + ((q & 1) ? fx1 : fx0));
                     }
                 }
@@ -759,94 +760,99 @@ struct Walk {
     {
         constexpr int NT = KS;   // N tiles of 8 columns j (N <= 8 KS)
         const int lane = threadIdx.x & 31, grp = lane >> 2, tig = lane & 3, warp = threadIdx.x >> 5;
-        const int D = 2 * a.sh.M, nnt = (N + 7) >> 3;
+        const int D = 2 * a.sh.M, nnt = (N + 7) >> 3, nmt = KS > 2 ? (N + 15) >> 4 : 1;
         const double *wx = s.wb + (size_t)warp * XS * WBS;
         const double *wy = s.wy + (size_t)warp * XS * WBS;
         const int *ef = s.wf + warp * 32;
         const int *gy = s.wg + warp * 32;
         const size_t slot = (size_t)blockIdx.x * (TPB / 32) + warp;
         double *pA = (double *)(a.partA + ((size_t)circ * a.slots + slot) * D * D);
-        float ar[NDIG][NT][4], ai[NDIG][NT][4];
-#pragma unroll
-        for (int d = 0; d < NDIG; ++d)
-#pragma unroll
-            for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) ar[d][nt][q] = ai[d][nt][q] = 0.f;
-        // A rows of this lane: w0 = grp, w1 = grp + 8
-        const int g0 = grp < N ? gy[grp] : 0, g1 = grp + 8 < N ? gy[grp + 8] : 0;
+        // rows w of the m16 tile mt (one tile up to 16 rows, two beyond)
 #pragma unroll 1
-        for (int ks = 0; ks < 4; ++ks) {
-            const int t0 = 8 * ks + tig, t1 = t0 + 4;
-            const int e0 = ef[t0], e1 = ef[t1];
-            uint32_t aq[NDIG][4];
+        for (int mt = 0; mt < nmt; ++mt) {
+            float ar[NDIG][NT][4], ai[NDIG][NT][4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int w = grp + 8 * (k & 1), t = (k & 2) ? t1 : t0, e = (k & 2) ? e1 : e0;
-                const int g = (k & 1) ? g1 : g0;
-                double yr = 0.0, yi = 0.0;
-                if (w < N && g != 0 && e != 0) {
-                    yr = wy[(2 * w) * WBS + t];
-                    yi = wy[(2 * w + 1) * WBS + t];
+            for (int d = 0; d < NDIG; ++d)
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) ar[d][nt][q] = ai[d][nt][q] = 0.f;
+            // A rows of this lane: w0 = 16 mt + grp, w1 = w0 + 8
+            const int w0 = 16 * mt + grp, w1 = w0 + 8;
+            const int g0 = w0 < N ? gy[w0] : 0, g1 = w1 < N ? gy[w1] : 0;
+#pragma unroll 1
+            for (int ks = 0; ks < 4; ++ks) {
+                const int t0 = 8 * ks + tig, t1 = t0 + 4;
+                const int e0 = ef[t0], e1 = ef[t1];
+                uint32_t aq[NDIG][4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int w = (k & 1) ? w1 : w0, t = (k & 2) ? t1 : t0, e = (k & 2) ? e1 : e0;
+                    const int g = (k & 1) ? g1 : g0;
+                    double yr = 0.0, yi = 0.0;
+                    if (w < N && g != 0 && e != 0) {
+                        yr = wy[(2 * w) * WBS + t];
+                        yi = wy[(2 * w + 1) * WBS + t];
+                    }
+                    const int fm = g - e + 1022;
+                    uint32_t wd[NDIG];
+                    digit_words(to_fixed_rel(yr, fm), to_fixed_rel(yi, fm), wd);
+#pragma unroll
+                    for (int sl = 0; sl < NDIG; ++sl) aq[sl][k] = wd[sl];
                 }
-                const int fm = g - e + 1022;
-                uint32_t wd[NDIG];
-                digit_words(to_fixed_rel(yr, fm), to_fixed_rel(yi, fm), wd);
 #pragma unroll
-                for (int sl = 0; sl < NDIG; ++sl) aq[sl][k] = wd[sl];
+                for (int nt = 0; nt < NT; ++nt) {
+                    if (nt >= nnt) continue;
+                    const int j = 8 * nt + grp;
+                    uint32_t bq[NDIG][2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int t = h ? t1 : t0, e = h ? e1 : e0;
+                        double xr = 0.0, xi = 0.0;
+                        if (j < N) {
+                            xr = wx[(2 * j) * WBS + t];
+                            xi = wx[(2 * j + 1) * WBS + t];
+                        }
+                        uint32_t wd[NDIG];
+                        digit_words(to_fixed(xr, e), to_fixed(xi, e), wd);
+#pragma unroll
+                        for (int sl = 0; sl < NDIG; ++sl) bq[sl][h] = wd[sl];
+                    }
+#pragma unroll
+                    for (int u = 0; u < NDIG; ++u) {
+                        const uint32_t bi[2] = {__byte_perm(bq[u][0], 0u, 0x1032) ^ 0x8000u,
+                                                __byte_perm(bq[u][1], 0u, 0x1032) ^ 0x8000u};
+#pragma unroll
+                        for (int sa = 0; sa + u < NDIG; ++sa) {
+                            mma_f16(ar[sa + u][nt], aq[sa], bq[u]);
+                            mma_f16(ai[sa + u][nt], aq[sa], bi);
+                        }
+                    }
+                }
             }
 #pragma unroll
             for (int nt = 0; nt < NT; ++nt) {
                 if (nt >= nnt) continue;
-                const int j = 8 * nt + grp;
-                uint32_t bq[NDIG][2];
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int t = h ? t1 : t0, e = h ? e1 : e0;
-                    double xr = 0.0, xi = 0.0;
-                    if (j < N) {
-                        xr = wx[(2 * j) * WBS + t];
-                        xi = wx[(2 * j + 1) * WBS + t];
+                for (int q = 0; q < 4; ++q) {
+                    const int w = (q >> 1) ? w1 : w0, j = 8 * nt + 2 * tig + (q & 1);
+                    const int g = (q >> 1) ? g1 : g0;
+                    if (w < N && j < N && g >= 26) {
+                        float a7[NDIG][4];
+#pragma unroll
+                        for (int d = 0; d < NDIG; ++d) a7[d][0] = ar[d][nt][q];
+                        const long long Yr = combine_digits_wide(a7, 0);
+#pragma unroll
+                        for (int d = 0; d < NDIG; ++d) a7[d][0] = ai[d][nt][q];
+                        const long long Yi = combine_digits_wide(a7, 0);
+                        double *dst = pA + 2 * ((size_t)(row0 + w) * D + row0 + j);
+                        // reductions without return: the warp does not wait for
+                        // the old values.  The slot has one warp as its only
+                        // writer and its updates are ordered by the warp's
+                        // barriers between tiles, so the sum order is fixed.
+                        atomicAdd(dst, scale2(__ll2double_rn(Yr), g - 1074));
+                        atomicAdd(dst + 1, scale2(__ll2double_rn(Yi), g - 1074));
                     }
-                    uint32_t wd[NDIG];
-                    digit_words(to_fixed(xr, e), to_fixed(xi, e), wd);
-#pragma unroll
-                    for (int sl = 0; sl < NDIG; ++sl) bq[sl][h] = wd[sl];
-                }
-#pragma unroll
-                for (int u = 0; u < NDIG; ++u) {
-                    const uint32_t bi[2] = {__byte_perm(bq[u][0], 0u, 0x1032) ^ 0x8000u,
-                                            __byte_perm(bq[u][1], 0u, 0x1032) ^ 0x8000u};
-#pragma unroll
-                    for (int sa = 0; sa + u < NDIG; ++sa) {
-                        mma_f16(ar[sa + u][nt], aq[sa], bq[u]);
-                        mma_f16(ai[sa + u][nt], aq[sa], bi);
-                    }
-                }
-            }
-        }
-#pragma unroll
-        for (int nt = 0; nt < NT; ++nt) {
-            if (nt >= nnt) continue;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int w = grp + 8 * (q >> 1), j = 8 * nt + 2 * tig + (q & 1);
-                const int g = (q >> 1) ? g1 : g0;
-                if (w < N && j < N && g >= 26) {
-                    float a7[NDIG][4];
-#pragma unroll
-                    for (int d = 0; d < NDIG; ++d) a7[d][0] = ar[d][nt][q];
-                    const long long Yr = combine_digits_wide(a7, 0);
-#pragma unroll
-                    for (int d = 0; d < NDIG; ++d) a7[d][0] = ai[d][nt][q];
-                    const long long Yi = combine_digits_wide(a7, 0);
-                    double *dst = pA + 2 * ((size_t)(row0 + w) * D + row0 + j);
-                    // reductions without return: the warp does not wait for
-                    // the old values.  The slot has one warp as its only
-                    // writer and its updates are ordered by the warp's
-                    // barriers between tiles, so the sum order is fixed.
-                    atomicAdd(dst, scale2(__ll2double_rn(Yr), g - 1074));
-                    atomicAdd(dst + 1, scale2(__ll2double_rn(Yi), g - 1074));
                 }
             }
         }
@@ -999,8 +1005,9 @@ struct Walk {
     // level `lev`, rank r in family K): the ranks of e - 1_m (m > K) within
     // their level, the offset of T2(K)[e - 1_K] within level lev - 1 of family
     // K and of DIAG[e + 1_K] within level lev + 1 of the DIAG family.
+    static constexpr int kRel = KS > 2 ? FK_MAXM - 1 : 7;   // modes after K an AP pivot reads
     struct ApRel {
-        int idx[7];       // idx[m - K - 1] for m = K+1..M-1 (M <= 8)
+        int idx[kRel];    // idx[m - K - 1] for m = K+1..M-1
         int rt2, wdiag;
     };
 
@@ -1016,7 +1023,7 @@ struct Walk {
         int64_t pre = Pf(s, K, t - 1, eK);
         t -= eK;
 #pragma unroll
-        for (int i = 0; i < 7; ++i) {
+        for (int i = 0; i < kRel; ++i) {
             const int m = K + 1 + i;
             q.idx[i] = 0;
             if (m >= sh.M) continue;
@@ -1029,7 +1036,7 @@ struct Walk {
         return q;
     }
 
-    // AP(K) pivot e of level `lev` with rank r in family K (M <= 8):
+    // AP(K) pivot e of level `lev` with rank r in family K (M <= 4 KS):
     // addresses of its reads and writes from its relative geometry; the ranks
     // of e - 1_m (m > K) go to s.idx[m][thread].  ap_geom below is the same
     // computation for any M.
@@ -1053,7 +1060,7 @@ struct Walk {
         g.vmask = 1u | (eK >= 1 ? 2u : 0u);
         g.nmask = 2u | (eK <= sh.C[K] - 3 ? 1u : 0u);
 #pragma unroll
-        for (int i = 0; i < 7; ++i) {
+        for (int i = 0; i < kRel; ++i) {
             const int m = K + 1 + i;
             if (m >= sh.M) continue;
             const int em = e(m);
@@ -2256,21 +2263,21 @@ struct Walk {
 };
 
 template <int TPB, int CH, int KS>
-__global__ void __launch_bounds__(TPB, (KS > 0 ? 4 : 1)) diag_forward_kernel(const __grid_constant__ DiagArgs a)
+__global__ void __launch_bounds__(TPB, (KS > 2 ? 2 : (KS > 0 ? 4 : 1))) diag_forward_kernel(const __grid_constant__ DiagArgs a)
 {
     if (a.G == 0) Walk<TPB, CH, KS>::forward(a);
     else if (!skip_walk(a.ctl)) Walk<TPB, CH, KS>::forward_multi(a);
 }
 
 template <int TPB, int CH, int KS>
-__global__ void __launch_bounds__(TPB, (KS > 0 ? 4 : 1)) diag_vjp_kernel(const __grid_constant__ DiagArgs a)
+__global__ void __launch_bounds__(TPB, (KS > 2 ? 2 : (KS > 0 ? 4 : 1))) diag_vjp_kernel(const __grid_constant__ DiagArgs a)
 {
     if (a.G == 0) Walk<TPB, CH, KS>::vjp(a);
     else if (!skip_walk(a.ctl)) Walk<TPB, CH, KS>::vjp_multi(a);
 }
 
 template <int TPB, int CH, int KS>
-__global__ void __launch_bounds__(TPB, (KS > 0 ? 3 : 1)) diag_vjp_partials_kernel(const __grid_constant__ DiagArgs a)
+__global__ void __launch_bounds__(TPB, (KS > 2 ? 2 : (KS > 0 ? 3 : 1))) diag_vjp_partials_kernel(const __grid_constant__ DiagArgs a)
 {
     if constexpr (KS > 0) {
         if (a.G == 0) Walk<TPB, CH, KS>::vjp_partials(a);

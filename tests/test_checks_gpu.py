@@ -184,10 +184,10 @@ def test_check_finite_flag_pure_walk(fd):
     assert fd.fk_workspace_status(ws) == fd.FK_ENONFINITE
 
 
-def test_default_engine_is_tensor_up_to_eight_modes(fd):
+def test_default_engine_is_tensor_up_to_twelve_modes(fd):
     """With nothing set, an 8-mode call runs the tensor engine (its VJP
     workspace is the tensor engine's, and its forward is bit-identical to a
-    call that asks for the tensor engine); 9 modes run FP64."""
+    call that asks for the tensor engine); so do 9 and 12 modes."""
     fd.fk_diag_set_engine(fd.FK_ENGINE_AUTO)
     cut = (3, 2, 2, 2, 2, 2, 2, 3)
     ws_auto = fd.fk_workspace_size(8, cut, 2, fd.FK_OP_DIAG_VJP, 0)
@@ -206,9 +206,11 @@ def test_default_engine_is_tensor_up_to_eight_modes(fd):
     ref = oracle.full_dm_probs(A, b, 0.9, cut)
     assert_amp_close(p2[0].cpu().numpy(), ref)
     assert_amp_close(p0[0].cpu().numpy(), ref)
-    cut9 = (2,) * 9
-    assert fd.fk_workspace_size(9, cut9, 1, fd.FK_OP_DIAG_VJP, 0) == \
-        fd.fk_workspace_size(9, cut9, 1, fd.FK_OP_DIAG_VJP, fd.FK_FLAG_ENGINE_FP64)
+    for m in (9, 12):
+        cutm = (2,) * m
+        ws_auto = fd.fk_workspace_size(m, cutm, 1, fd.FK_OP_DIAG_VJP, 0)
+        assert ws_auto == fd.fk_workspace_size(m, cutm, 1, fd.FK_OP_DIAG_VJP, fd.FK_FLAG_ENGINE_TENSOR)
+        assert ws_auto != fd.fk_workspace_size(m, cutm, 1, fd.FK_OP_DIAG_VJP, fd.FK_FLAG_ENGINE_FP64)
 
 
 def test_per_call_tile_flags_override_process_default(fd):

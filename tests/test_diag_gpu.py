@@ -22,7 +22,7 @@ RTOL, ATOL, VJP_RTOL = 1e-10, 1e-12, 1e-8
 @pytest.fixture(scope="module")
 def fd():
     """The FP64 product engine for this module (the library defaults to the
-    tensor engine up to 8 modes; test_tensor_engine_gpu.py covers that one)."""
+    tensor engine up to 12 modes; test_tensor_engine_gpu.py covers that one)."""
     from paper_2303_08879_gb300 import build
     build.build()
     from paper_2303_08879_gb300 import fockdiag

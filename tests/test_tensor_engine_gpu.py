@@ -151,13 +151,31 @@ def test_tensor_gbs_m8_c6_batch16_matches_fp64_engine(fd):
             assert_amp_close(got[ci][n], ref)
 
 
-def test_tensor_more_than_eight_modes_uses_fp64(fd):
-    """M = 9 is beyond the compiled tensor shapes and runs in FP64."""
-    rng = np.random.default_rng(9)
-    cut = (2, 2, 2, 2, 2, 2, 2, 2, 2)
-    A, b = inputs.random_symmetric(18, rng, scale=0.1, with_b=True)
+WIDE_CASES = [((2,) * 9, True), ((3, 2, 2, 2, 2, 2, 2, 2, 2), False), ((2, 2, 3, 2, 2, 2, 2, 2, 2, 2), True),
+              ((2,) * 11, False), ((2,) * 12, True), ((2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 3), False)]
+
+
+@pytest.mark.parametrize("cut,withb", WIDE_CASES)
+def test_tensor_nine_to_twelve_modes_match_oracle(fd, cut, withb):
+    """9 to 12 kept modes: three 16-row K steps (KS = 3), outputs from more
+    than 16 rows of A per pivot."""
+    rng = np.random.default_rng(5 * sum(cut) + len(cut))
+    A, b = inputs.random_symmetric(2 * len(cut), rng, scale=0.1, with_b=withb)
     ref = oracle.Walk(A, b, 0.5, cut).all_probs()
     got, _ = gpu_probs(fd, A, b, 0.5, cut)
+    assert_amp_close(got[0], ref)
+    if not withb:
+        got0, _ = gpu_probs(fd, A, b, 0.5, cut, flags=fd.FK_FLAG_B_ZERO)
+        assert_amp_close(got0[0], ref)
+
+
+def test_tensor_nine_modes_many_tiles_ragged(fd):
+    """KS = 3 with several tiles per level and ragged tails."""
+    rng = np.random.default_rng(19)
+    cut = (4, 3, 3, 3, 2, 3, 2, 2, 3)
+    A, b = inputs.random_symmetric(18, rng, scale=0.1, with_b=True)
+    ref = oracle.Walk(A, b, 0.7, cut).all_probs()
+    got, _ = gpu_probs(fd, A, b, 0.7, cut)
     assert_amp_close(got[0], ref)
 
 
@@ -177,7 +195,11 @@ VJP_CASES = [((4, 3), True), ((3, 3, 3), False), ((3, 4, 2), True), ((2, 1, 3), 
              ((2, 3, 2, 2, 3), False), ((2, 3, 2, 2, 3), True), ((3, 2, 2, 2, 2, 3), True),
              ((3, 2, 2, 2, 2, 3), False), ((2, 2, 2, 2, 2, 2, 2), True),
              ((2, 2, 2, 2, 2, 2, 2, 3), False), ((2, 2, 2, 2, 2, 2, 2, 3), True),
-             ((3, 3, 2, 2, 2, 2, 2, 2), False), ((2, 2, 1, 3, 2, 2, 2, 2, 2), False)]
+             ((3, 3, 2, 2, 2, 2, 2, 2), False), ((2, 2, 1, 3, 2, 2, 2, 2, 2), False),
+             # nine and ten kept modes: three K steps; the partial dL/dA of the
+             # K = 0 family has 18 or 20 rows (two m16 tiles)
+             ((2,) * 9, False), ((2,) * 9, True), ((3, 2, 2, 2, 2, 2, 2, 2, 2), True),
+             ((2, 2, 2, 2, 2, 2, 2, 2, 2, 2), False), ((2, 3, 2, 2, 2, 2, 2, 2, 2, 2), True)]
 
 
 @pytest.mark.parametrize("cut,withb", VJP_CASES)
