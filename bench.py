@@ -48,10 +48,10 @@ NCIRC = 16
 # in proportion to them.  Valid only for the kernel source it was measured on
 # (sha256 prefix of csrc/walk_diag_impl.cuh) and the engine / tile shape; reported
 # as null once either differs.
-TRAFFIC = {"kernel_sha": "faf3ff0e782a5a12", "tuning": ["tensor", 128, 4, 0],
-           "bytes_per_launch": {"diag_forward_kernel": 8 * (496301312 + 853497600),
-                                "diag_vjp_kernel": 8 * (703872512 + 802632192),
-                                "diag_vjp_partials_kernel": 8 * (1735206144 + 139661568)}}
+TRAFFIC = {"kernel_sha": "db0f40ce25e6d667", "tuning": ["tensor", 128, 4, 0],
+           "bytes_per_launch": {"diag_forward_kernel": 8 * (496171008 + 853766400),
+                                "diag_vjp_kernel": 8 * (703233280 + 802750720),
+                                "diag_vjp_partials_kernel": 8 * (1727779072 + 133031680)}}
 
 FALLBACK_HBM_GBS = 6800.0
 

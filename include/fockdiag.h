@@ -473,6 +473,38 @@ int fk_selftest_wait_timeout(void *d_ws, size_t ws_bytes, unsigned long long tim
                              void *stream);
 
 /*
+ * Debug-checks build (the paper has no counterpart; these stand in for a
+ * memory checker).  The library built with -DFK_DEBUG_CHECKS
+ * (libfockdiag_debug.so) checks the index of every amplitude, adjoint,
+ * scratch, output and pivot-geometry access of the all-detected walk
+ * (Algorithm 1 and its reverse walk) against the storage box of its
+ * type (DIAG, T2(K), the P1010/P1001 pairs of anchor K, the T1 pairs,
+ * AP(K) scratch; the App. B.2 types), and those of the conditional walk
+ * (Algorithm 2) against its circuit's amplitude, scratch and output
+ * arrays.  A violation is counted in the
+ * workspace's control block, the first one with its source line, index and
+ * box; the access is redirected to the first entry of that box, so nothing
+ * outside the buffers is touched.  The normal build compiles the checks
+ * out.
+ *
+ * fk_debug_checks: 1 in the debug-checks build, 0 otherwise.
+ * fk_workspace_debug: out[5] = {violations, source line of the first,
+ *   its index, box start, box end} of the last walk call on d_ws
+ *   (host array; synchronises `stream`).  Always zeros in the normal build.
+ * fk_debug_set_trace: registers a device buffer of 1 + 2 capacity 64-bit
+ *   words (process-wide; NULL and 0 unregister it) for per-level device
+ *   timestamps: after each grid barrier of the walk kernels, word 0 is
+ *   incremented and a record (tag, %globaltimer ns) appended while room is
+ *   left; tag = kernel << 24 | level << 8 | phase, kernel 1 = forward,
+ *   2 = reverse walk, 3 = final gradient reduction, phase 0 = off-diagonal
+ *   pivots, 1 = diagonal pivots.  The caller zeroes word 0.  Returns
+ *   FK_EUNSUPPORTED in the normal build.
+ */
+int fk_debug_checks(void);
+int fk_workspace_debug(const void *d_ws, void *stream, long long *out);
+int fk_debug_set_trace(unsigned long long *d_buf, int capacity);
+
+/*
  * Schedule description (host only, no device work): for the all-detected
  * walk of one circuit writes
  *   out[0] = amplitudes stored, out[1] = pivots applied, out[2] = levels,

@@ -16,6 +16,10 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfockdiag.so")
+# the debug-checks variant (-DFK_DEBUG_CHECKS: storage-box checks of every
+# walk access and per-level timestamps), built on request only
+BUILD_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(HERE, "libfockdiag_debug.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cpp", "circuit.cpp", "walk_diag.cu", "walk_cond.cu", "mlp.cu", "herald.cu", "probe.cu", "static_ws.cu",
            "walk_pure.cu", "multi.cpp", "walk_diag_tc1.cu", "walk_diag_tc2.cu", "walk_diag_tc3.cu", "mlp_tc.cu"]
@@ -42,8 +46,12 @@ def _stale(obj, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(verbose: bool = False, extra_flags=()) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, extra_flags=(), debug: bool = False) -> str:
+    """Compile the library (``debug``: the debug-checks variant) and return its path."""
+    build_dir, lib_path = (BUILD_DEBUG, LIB_DEBUG) if debug else (BUILD, LIB)
+    if debug:
+        extra_flags = list(extra_flags) + ["-DFK_DEBUG_CHECKS"]
+    os.makedirs(build_dir, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers += [os.path.join(ROOT, "include", h) for h in os.listdir(os.path.join(ROOT, "include"))]
     cc = nvcc()
@@ -54,7 +62,7 @@ def build(verbose: bool = False, extra_flags=()) -> str:
               for t, c in FP64_SHAPES]
     for src, oname, defs in units:
         path = os.path.join(CSRC, src)
-        obj = os.path.join(BUILD, oname)
+        obj = os.path.join(build_dir, oname)
         objs.append(obj)
         if _stale(obj, [path, __file__] + headers):
             cmd = [cc] + _flags(extra_flags) + defs + ["-c", path, "-o", obj]
@@ -74,16 +82,16 @@ def build(verbose: bool = False, extra_flags=()) -> str:
                 sys.stderr.write(" ".join(cmd) + "\n" + r.stdout + r.stderr)
             if r.returncode:
                 raise RuntimeError(f"nvcc failed on {cmd[-3]}")
-    if jobs or not os.path.exists(LIB) or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if jobs or not os.path.exists(lib_path) or _stale(lib_path, objs):
+        tmp = lib_path + f".tmp{os.getpid()}"
         cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode:
             sys.stderr.write(r.stdout + r.stderr)
-            raise RuntimeError("link of libfockdiag.so failed")
-        os.replace(tmp, LIB)
-    return LIB
+            raise RuntimeError(f"link of {os.path.basename(lib_path)} failed")
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":
-    print(build(verbose="-v" in sys.argv))
+    print(build(verbose="-v" in sys.argv, debug="--debug" in sys.argv))

@@ -628,6 +628,26 @@ int fk_workspace_status(const void *ws, void *stream, int *status)
     return read_status(ws, stream, status);
 }
 
+int fk_debug_checks(void)
+{
+#ifdef FK_DEBUG_CHECKS
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+int fk_workspace_debug(const void *ws, void *stream, long long *out)
+{
+    if (!ws || !out) return FK_EINVAL;
+    return read_debug(ws, stream, out);
+}
+
+int fk_debug_set_trace(unsigned long long *d_buf, int capacity)
+{
+    return set_debug_trace(d_buf, capacity);
+}
+
 int fk_selftest_wait_timeout(void *ws, size_t ws_bytes, unsigned long long timeout_ns, void *stream)
 {
     if (!ws || ws_bytes < sizeof(Control) || !aligned(ws)) return FK_EWORKSPACE;

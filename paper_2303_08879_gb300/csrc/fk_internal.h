@@ -20,7 +20,12 @@ struct Control {
     unsigned wait_flag;  // self-test flag that nothing sets
     int skip;            // set by the input scan (FK_FLAG_CHECK_FINITE) before the walk:
                          // every walk kernel of the call returns at once
-    int pad[58];
+    // debug-checks build (FK_DEBUG_CHECKS): accesses outside their storage box
+    int dbg_count;       // how many
+    int dbg_site;        // source line of the first one
+    long long dbg_index; // its index and the box [dbg_lo, dbg_hi) it had to lie in
+    long long dbg_lo, dbg_hi;
+    int pad[50];
 };
 static_assert(sizeof(Control) == 256, "control block is 256 bytes");
 
@@ -220,6 +225,10 @@ int launch_check_finite(const void *A, int64_t n_A, const void *b, int64_t n_b, 
 int check_diag_flags(unsigned flags);
 int diag_tuning_flags(int engine, int tpb, int ch, int bps, unsigned *flags);
 int read_status(const void *ws, void *stream, int *status);
+// Debug-checks build: the control block's access-violation record
+// (count, source line, index, box start, box end) and the trace buffer.
+int read_debug(const void *ws, void *stream, long long *out);
+int set_debug_trace(void *buf, int capacity);
 
 // Default time limit of one grid-barrier wait.
 constexpr unsigned long long kBarrierTimeoutNs = 20ull * 1000ull * 1000ull * 1000ull;

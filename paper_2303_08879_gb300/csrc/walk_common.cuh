@@ -110,6 +110,80 @@ __device__ __forceinline__ bool grid_sync(Control *ctl, unsigned nblocks,
     return s_ok != 0;
 }
 
+// ------------------------------------------------------------ debug checks
+// Built with -DFK_DEBUG_CHECKS (a separate library, libfockdiag_debug.so),
+// every index of an amplitude, adjoint, scratch, output or geometry access is
+// checked against the storage box it must lie in.  A violation is counted in
+// the launch's control block (the first one with its source line, index and
+// box) and the access is redirected to the first entry of the same box, so
+// the check itself never reads or writes outside the buffers.  The normal
+// build compiles the checks away.
+#ifdef FK_DEBUG_CHECKS
+__device__ __forceinline__ Control *&dbg_ctl()
+{
+    __shared__ Control *p;
+    return p;
+}
+
+// Called by every thread at kernel entry, before the first checked access.
+__device__ __forceinline__ void dbg_begin(Control *ctl)
+{
+    if (threadIdx.x == 0) dbg_ctl() = ctl;
+    __syncthreads();
+}
+
+static __device__ __noinline__ void dbg_record(long long i, long long lo, long long hi, int site)
+{
+    Control *ctl = dbg_ctl();
+    if (atomicAdd(&ctl->dbg_count, 1) == 0) {
+        ctl->dbg_site = site;
+        ctl->dbg_index = i;
+        ctl->dbg_lo = lo;
+        ctl->dbg_hi = hi;
+    }
+}
+#define FK_DBG_BEGIN(ctl) ::fk::dbg_begin(ctl)
+#else
+#define FK_DBG_BEGIN(ctl) ((void)0)
+#endif
+
+// Index i of an access that must lie in [lo, hi) (see above).
+__device__ __forceinline__ int64_t in_box(int64_t i, int64_t lo, int64_t hi, int site)
+{
+#ifdef FK_DEBUG_CHECKS
+    if (i < lo || i >= hi) {
+        dbg_record(i, lo, hi, site);
+        return lo;
+    }
+#else
+    (void)lo;
+    (void)hi;
+    (void)site;
+#endif
+    return i;
+}
+#define FK_BOX(i, lo, hi) ::fk::in_box((int64_t)(i), (int64_t)(lo), (int64_t)(hi), __LINE__)
+
+// Per-level device timestamps of the debug-checks build: after each grid
+// barrier of a walk, thread 0 of block 0 appends (tag, %globaltimer) to a
+// caller-registered buffer (word 0: the number of records).
+__device__ __forceinline__ void trace_mark(unsigned long long *buf, int cap, unsigned tag)
+{
+#ifdef FK_DEBUG_CHECKS
+    if (buf != nullptr && blockIdx.x == 0 && threadIdx.x == 0) {
+        const unsigned long long n = atomicAdd(buf, 1ull);
+        if ((long long)n < (long long)cap) {
+            buf[1 + 2 * n] = tag;
+            buf[2 + 2 * n] = gtimer();
+        }
+    }
+#else
+    (void)buf;
+    (void)cap;
+    (void)tag;
+#endif
+}
+
 // Up to 16 digits of at most 8 bits, packed in two registers.
 struct Dig {
     uint64_t lo = 0, hi = 0;

@@ -172,6 +172,25 @@ __device__ void load_circuit(const CondArgs &a, CSmem &s, int c)
     s.loaded = c;
 }
 
+// Checked indices (debug-checks build, see walk_common.cuh): amplitude
+// (y, u) of circuit cc in F / Fbar, with y a position of the detected
+// structure and u a point of the u-block; an entry of its output block; of
+// its diagonal-read scratch.
+__device__ __forceinline__ int64_t fpos(const CondCirc &cc, int64_t y, int64_t u)
+{
+    return FK_BOX(FK_BOX(y, 0, cc.dsh.circ_size) * cc.U2 + FK_BOX(u, 0, cc.U2), 0, cc.dsh.circ_size * cc.U2);
+}
+
+__device__ __forceinline__ int64_t rpos(const CondCirc &cc, int64_t i)
+{
+    return cc.off_rho + FK_BOX(i, 0, cc.n_patterns * cc.NUo * cc.NUo);
+}
+
+__device__ __forceinline__ int64_t spos(const CondCirc &cc, int64_t ia, int64_t u)
+{
+    return cc.off_scratch + FK_BOX(FK_BOX(ia, 0, cc.dsh.n_ap) * cc.U2 + u, 0, cc.dsh.n_ap * cc.U2);
+}
+
 // u-block digit t of flat index u.
 __device__ __forceinline__ int udigit(const CondCirc &cc, int u, int t)
 {
@@ -250,18 +269,18 @@ __device__ void step1_forward(const CondArgs &a, CSmem &s, int c, bool hb)
             } else {
                 const int P = u - cc.ustride[w];
                 const int Pw = dig[w] - 1;
-                double2 acc = hb ? cmul(s.br[Db + w], __ldcg(F + P)) : czero();
+                double2 acc = hb ? cmul(s.br[Db + w], __ldcg(F + fpos(cc, 0, P))) : czero();
                 for (int t = 0; t < tU; ++t) {
                     const int Pt = dig[t] - (t == w ? 1 : 0);
                     if (Pt <= 0) continue;
-                    acc = cfma(s.Ar[(Db + w) * a.Dmax + Db + t], __ldcg(F + P - cc.ustride[t]), acc);
+                    acc = cfma(s.Ar[(Db + w) * a.Dmax + Db + t], __ldcg(F + fpos(cc, 0, P - cc.ustride[t])), acc);
                 }
                 v = rscale(acc, s.inv[Pw + 1]);
             }
-            F[u] = v;
+            F[fpos(cc, 0, u)] = v;
             int ket, bra;
             const double f = uscale(cc, s, u, &ket, &bra);
-            a.rho[cc.off_rho + (int64_t)ket * cc.NUo + bra] = rscale(v, f);
+            a.rho[rpos(cc, (int64_t)ket * cc.NUo + bra)] = rscale(v, f);
         }
         __syncthreads();
     }
@@ -477,16 +496,16 @@ __device__ void pair_forward(const CondArgs &a, CSmem &s, const CTile &tl, int k
     double2 PV = czero();
     if (act) {
         for (int j = 0; j < N; ++j)
-            put3(s.R3, Dm, j, t, ((vmask >> j) & 1u) ? __ldcg(F + g.yr[j] * cc.U2 + u) : czero());
+            put3(s.R3, Dm, j, t, ((vmask >> j) & 1u) ? __ldcg(F + fpos(cc, g.yr[j], u)) : czero());
         for (int q = 0; q < tU; ++q) {
             double2 v = czero();
             if (udigit(cc, u, q) >= 1) {
                 umask |= 1u << q;
-                v = __ldcg(F + yP * cc.U2 + u - cc.ustride[q]);
+                v = __ldcg(F + fpos(cc, yP, u - cc.ustride[q]));
             }
             put3(s.R3, Dm, N + q, t, v);
         }
-        if (HASB) PV = __ldcg(F + yP * cc.U2 + u);
+        if (HASB) PV = __ldcg(F + fpos(cc, yP, u));
     } else {
         for (int j = 0; j < NC; ++j) put3(s.R3, Dm, j, t, czero());
     }
@@ -521,11 +540,11 @@ __device__ void pair_forward(const CondArgs &a, CSmem &s, const CTile &tl, int k
                 double2 acc = make_double2(p1[ii] - p2[ii], p1[ii] + p3[ii]);
                 if (HASB) acc = cadd(acc, cmul(s.br[row0 + i], PV));
                 const double2 v = rscale(acc, s.inv[g.den[i]]);
-                Fw[g.yw[i] * cc.U2 + u] = v;
+                Fw[fpos(cc, g.yw[i], u)] = v;
                 if (kind == 0 && i == 1) {          // a diagonal of the detected modes
                     int ket, bra;
                     const double f = uscale(cc, s, u, &ket, &bra) * g.fdiag;
-                    a.rho[cc.off_rho + (g.yw[1] * cc.NUo + ket) * cc.NUo + bra] = rscale(v, f);
+                    a.rho[rpos(cc, (g.yw[1] * cc.NUo + ket) * cc.NUo + bra)] = rscale(v, f);
                 }
             }
         }
@@ -534,6 +553,7 @@ __device__ void pair_forward(const CondArgs &a, CSmem &s, const CTile &tl, int k
 
 __global__ void __launch_bounds__(TPB) cond_forward_kernel(const __grid_constant__ CondArgs a)
 {
+    FK_DBG_BEGIN(a.ctl);
     if (skip_walk(a.ctl)) return;   // the input scan found a NaN or Inf
     CSmem s = carve(a, false);
     build_tables(s);
@@ -581,18 +601,18 @@ __device__ void pair_reverse(const CondArgs &a, CSmem &s, const CTile &tl, int k
     unsigned upmask = 0;
     if (act) {
         for (int j = 0; j < N; ++j)
-            put3(s.R3, Dm, j, t, ((vmask >> j) & 1u) ? __ldcg(F + g.yr[j] * cc.U2 + u) : czero());
+            put3(s.R3, Dm, j, t, ((vmask >> j) & 1u) ? __ldcg(F + fpos(cc, g.yr[j], u)) : czero());
         for (int q = 0; q < tU; ++q) {
             const int dq = udigit(cc, u, q);
             double2 v = czero();
-            if (dq >= 1) v = __ldcg(F + yP * cc.U2 + u - cc.ustride[q]);
+            if (dq >= 1) v = __ldcg(F + fpos(cc, yP, u - cc.ustride[q]));
             if (dq + 1 < cc.CU[q >> 1]) upmask |= 1u << q;
             put3(s.R3, Dm, N + q, t, v);
         }
         for (int i = 0; i < N; ++i)
-            put3(s.Y3, Dm, i, t, ((nm >> i) & 1u) ? rscale(__ldcg(Fb + g.yw[i] * cc.U2 + u), s.inv[g.den[i]])
+            put3(s.Y3, Dm, i, t, ((nm >> i) & 1u) ? rscale(__ldcg(Fb + fpos(cc, g.yw[i], u)), s.inv[g.den[i]])
                                                    : czero());
-        s.FP[t] = HASB ? __ldcg(F + yP * cc.U2 + u) : czero();
+        s.FP[t] = HASB ? __ldcg(F + fpos(cc, yP, u)) : czero();
     } else {
         for (int j = 0; j < NC; ++j) put3(s.R3, Dm, j, t, czero());
         for (int i = 0; i < N; ++i) put3(s.Y3, Dm, i, t, czero());
@@ -627,9 +647,9 @@ __device__ void pair_reverse(const CondArgs &a, CSmem &s, const CTile &tl, int k
             if (j < N && ((vmask >> j) & 1u)) {
                 const double2 acc = make_double2(p1[jj] + q2[jj], p1[jj] - q3[jj]);
                 if (kind == 0 && j == 0) {
-                    a.scratch[cc.off_scratch + g.ia * cc.U2 + u] = acc;
+                    a.scratch[spos(cc, g.ia, u)] = acc;
                 } else {
-                    double2 *dst = Fb + g.yr[j] * cc.U2 + u;
+                    double2 *dst = Fb + fpos(cc, g.yr[j], u);
                     *dst = cadd(__ldcg(dst), acc);
                 }
             }
@@ -646,11 +666,11 @@ __device__ void pair_reverse(const CondArgs &a, CSmem &s, const CTile &tl, int k
             const int un = u + cc.ustride[q];
             for (int i = 0; i < N; ++i) {
                 if (!((nm >> i) & 1u)) continue;
-                const double2 yn = rscale(__ldcg(Fb + g.yw[i] * cc.U2 + un), s.inv[g.den[i]]);
+                const double2 yn = rscale(__ldcg(Fb + fpos(cc, g.yw[i], un)), s.inv[g.den[i]]);
                 pv = cfma_conj(s.Ar[(row0 + i) * Dm + Db + q], yn, pv);
             }
         }
-        double2 *dst = Fb + yP * cc.U2 + u;
+        double2 *dst = Fb + fpos(cc, yP, u);
         *dst = cadd(__ldcg(dst), pv);
     }
     // dL/dA (rows = detected writes, columns = all reads) and dL/db partials:
@@ -709,14 +729,14 @@ __device__ void diag_reverse(const CondArgs &a, CSmem &s, const CTile &tl, int l
     }
     int ket, bra;
     f *= uscale(cc, s, u, &ket, &bra);
-    double2 acc = rscale(a.grho[cc.off_rho + (idx * cc.NUo + ket) * cc.NUo + bra], f);
+    double2 acc = rscale(a.grho[rpos(cc, (idx * cc.NUo + ket) * cc.NUo + bra)], f);
     const int kmax = fnz < ds.M ? fnz : ds.M - 1;
     for (int K = 0; K <= kmax; ++K)
         if (d(K) <= ds.C[K] - 2) {
             const int64_t ia = ds.off_ap[K] + box_index(ds, d, K, K, 1, -1, 0);
-            acc = cadd(acc, __ldcg(a.scratch + cc.off_scratch + ia * cc.U2 + u));
+            acc = cadd(acc, __ldcg(a.scratch + spos(cc, ia, u)));
         }
-    double2 *dst = a.Fbar + cc.off_F + idx * cc.U2 + u;
+    double2 *dst = a.Fbar + cc.off_F + fpos(cc, idx, u);
     *dst = cadd(__ldcg(dst), acc);
 }
 
@@ -736,7 +756,7 @@ __device__ void step1_reverse(const CondArgs &a, CSmem &s, int c, bool hb)
         for (int u = 0; u < cc.U2; ++u) {
             int ket, bra;
             const double f = uscale(cc, s, u, &ket, &bra);
-            Fb[u] = cadd(Fb[u], rscale(a.grho[cc.off_rho + (int64_t)ket * cc.NUo + bra], f));
+            Fb[fpos(cc, 0, u)] = cadd(Fb[u], rscale(a.grho[rpos(cc, (int64_t)ket * cc.NUo + bra)], f));
         }
     }
     for (int u = cc.U2 - 1; u >= 1; --u) {
@@ -748,14 +768,14 @@ __device__ void step1_reverse(const CondArgs &a, CSmem &s, int c, bool hb)
         const int P = u - cc.ustride[w];
         const double2 y = rscale(Fb[u], s.inv[dig[w]]);
         if (hb) {
-            Fb[P] = cfma_conj(s.br[Db + w], y, Fb[P]);
+            Fb[fpos(cc, 0, P)] = cfma_conj(s.br[Db + w], y, Fb[P]);
             pb[Db + w] = cfma_conj(F[P], y, pb[Db + w]);
         }
         for (int q = 0; q < tU; ++q) {
             const int Pq = dig[q] - (q == w ? 1 : 0);
             if (Pq <= 0) continue;
             const int r = P - cc.ustride[q];
-            Fb[r] = cfma_conj(s.Ar[(Db + w) * Dm + Db + q], y, Fb[r]);
+            Fb[fpos(cc, 0, r)] = cfma_conj(s.Ar[(Db + w) * Dm + Db + q], y, Fb[r]);
             double2 &dA = pA[(Db + w) * Dm + Db + q];
             dA = cfma_conj(F[r], y, dA);
         }
@@ -764,6 +784,7 @@ __device__ void step1_reverse(const CondArgs &a, CSmem &s, int c, bool hb)
 
 __global__ void __launch_bounds__(TPB) cond_vjp_kernel(const __grid_constant__ CondArgs a)
 {
+    FK_DBG_BEGIN(a.ctl);
     if (skip_walk(a.ctl)) return;   // the input scan found a NaN or Inf
     CSmem s = carve(a, true);
     build_tables(s);

@@ -185,7 +185,33 @@ void walk_kernel(const DiagShape &sh, const Tune &t, bool vjp, const void **fn, 
 namespace {
 std::mutex g_split_mu;
 void *g_split_event = nullptr;   // cudaEvent_t recorded between the two VJP launches
+// debug-checks build: caller-registered buffer of per-level timestamps
+std::mutex g_trace_mu;
+unsigned long long *g_trace = nullptr;
+int g_trace_cap = 0;
+
+void attach_trace(DiagArgs &a)
+{
+    std::lock_guard<std::mutex> lk(g_trace_mu);
+    a.trace = g_trace;
+    a.trace_cap = g_trace_cap;
+}
 }  // namespace
+
+int set_debug_trace(void *buf, int capacity)
+{
+#ifdef FK_DEBUG_CHECKS
+    if (capacity < 0 || (buf == nullptr && capacity != 0)) return FK_EINVAL;
+    std::lock_guard<std::mutex> lk(g_trace_mu);
+    g_trace = (unsigned long long *)buf;
+    g_trace_cap = buf ? capacity : 0;
+    return FK_OK;
+#else
+    (void)buf;
+    (void)capacity;
+    return FK_EUNSUPPORTED;
+#endif
+}
 
 int set_vjp_split_event(void *event)
 {
@@ -308,6 +334,7 @@ static DiagArgs make_args(const DiagShape &sh, int batch, unsigned flags, const 
     a.F = (double2 *)(w + lay.F);
     a.lvl = (unsigned long long *)(w + lay.lvl);
     a.timeout_ns = kBarrierTimeoutNs;
+    attach_trace(a);
     return a;
 }
 
@@ -487,6 +514,7 @@ static DiagArgs multi_args(const MultiPlan &p, unsigned flags, const void *A, co
     a.ctl = (Control *)w;
     a.ctr = (int *)(w + p.off_ctr);
     a.timeout_ns = kBarrierTimeoutNs;
+    attach_trace(a);
     a.G = p.G;
     const unsigned char *img = (const unsigned char *)(w + p.off_plan);
     a.grp = (const DiagGroup *)img;
@@ -623,6 +651,20 @@ int read_status(const void *ws, void *stream, int *status)
     if (cudaMemcpyAsync(&v, ws, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return FK_ECUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return FK_ECUDA;
     *status = v;
+    return FK_OK;
+}
+
+int read_debug(const void *ws, void *stream, long long *out)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    Control c;
+    if (cudaMemcpyAsync(&c, ws, sizeof(Control), cudaMemcpyDeviceToHost, st) != cudaSuccess) return FK_ECUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return FK_ECUDA;
+    out[0] = c.dbg_count;
+    out[1] = c.dbg_site;
+    out[2] = c.dbg_index;
+    out[3] = c.dbg_lo;
+    out[4] = c.dbg_hi;
     return FK_OK;
 }
 

@@ -80,6 +80,9 @@ struct DiagArgs {
     const int *cidx;              // caller's circuit index of each local circuit (null: identity)
     const int64_t *oidx;          // output offset of each local circuit (null: circ * n_diag)
     char *wsbase;
+    // debug-checks build: per-level timestamps (see trace_mark), or null
+    unsigned long long *trace;
+    int trace_cap;
 };
 
 // ------------------------------------------------------------ shared memory
@@ -139,6 +142,10 @@ struct DpGeom {
     int64_t l00, l0m; // family-0 offsets of levels s and s - 1
     unsigned vmask, nmask;
 };
+
+// Trace tags (debug-checks build): kernel in bits 24.., level in bits 8..23,
+// phase (0 = AP, 1 = DP) in bit 0.
+constexpr unsigned kTraceFwd = 1u << 24, kTraceVjp = 2u << 24, kTraceFinish = 3u << 24;
 
 // Shared-memory layouts of the walk kernels (see Walk::smem_plan).
 constexpr int kFwd = 0, kVjp = 1, kPart = 2;
@@ -485,19 +492,23 @@ struct Walk {
     // Biased fixed point U = round(v * 2^(1076 - fmax)) + 0x0080808080808080:
     // |round(...)| < 2^54, so 0 < U < 2^56 and byte k of U minus 128 is the
     // k-th balanced base-256 digit.  fmax < 26 (values below 2^-997) gives 0.
+    // With ND < 7 digits the point moves 8 (7 - ND) bits up (|round| <
+    // 2^(8 ND - 2)) and the bias keeps ND bytes of 0x80.
+    template <int ND = NDIG>
     static __device__ __forceinline__ uint64_t to_fixed(double v, int fmax)
     {
+        constexpr int sh = 8 * (NDIG - ND);
         const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
         const int f = (hi >> 20) & 0x7ff;
         long long X = 0;
         if (f != 0 && fmax >= 26) {
             const unsigned long long m =
                 ((unsigned long long)((hi & 0xfffffu) | 0x100000u) << 32) | lo;
-            const int q = min(fmax - f, 63);
+            const int q = min(fmax - f + sh, 63);
             X = (long long)((((m << 2) >> q) + 1ull) >> 1);
             if (hi >> 31) X = -X;
         }
-        return (uint64_t)(X + 0x0080808080808080ll);
+        return (uint64_t)(X + (0x0080808080808080ll >> sh));
     }
 
     // The seven digits of a pair (lo, hi) of biased fixed points as packed
@@ -506,7 +517,8 @@ struct Walk {
     // one byte permute places each as the low mantissa byte of an fp16 with
     // exponent field 25 (the value 1024 + byte), and one packed fp16
     // subtraction of 1152 leaves byte - 128, the balanced digit, exactly.
-    static __device__ __forceinline__ void digit_words(uint64_t lo, uint64_t hi, uint32_t (&w)[NDIG])
+    template <int ND = NDIG>
+    static __device__ __forceinline__ void digit_words(uint64_t lo, uint64_t hi, uint32_t (&w)[ND])
     {
         const uint32_t l0 = (uint32_t)lo, l1 = (uint32_t)(lo >> 32);
         const uint32_t h0 = (uint32_t)hi, h1 = (uint32_t)(hi >> 32);
@@ -514,8 +526,8 @@ struct Walk {
         const uint32_t t[4] = {__byte_perm(l0, h0, 0x5140), __byte_perm(l0, h0, 0x7362),
                                __byte_perm(l1, h1, 0x5140), __byte_perm(l1, h1, 0x7362)};
 #pragma unroll
-        for (int sl = 0; sl < NDIG; ++sl) {
-            const int k = NDIG - 1 - sl;
+        for (int sl = 0; sl < ND; ++sl) {
+            const int k = ND - 1 - sl;
             const uint32_t v = __byte_perm(t[k >> 1], 0x64646464u, (k & 1) ? 0x4342 : 0x4140);
             uint32_t d;
             asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(d) : "r"(v), "r"(0x64806480u));
@@ -698,13 +710,15 @@ struct Walk {
         return (long long)(Y - bias);
     }
 
-    // The same for partial sums below 2^23 in magnitude (conversions to int).
-    static __device__ __forceinline__ long long combine_digits_wide(const float (&acc)[NDIG][4], int q)
+    // The same for partial sums below 2^23 in magnitude (conversions to int),
+    // for ND diagonals: sum_d acc_d 256^(ND - 2 - d), the last one floored.
+    template <int ND = NDIG>
+    static __device__ __forceinline__ long long combine_digits_wide(const float (&acc)[ND][4], int q)
     {
         long long Y = __float2int_rn(acc[0][q]);
 #pragma unroll
-        for (int d = 1; d < NDIG - 1; ++d) Y = Y * 256 + __float2int_rn(acc[d][q]);
-        return Y + (long long)(__float2int_rn(acc[NDIG - 1][q]) >> 8);
+        for (int d = 1; d < ND - 1; ++d) Y = Y * 256 + __float2int_rn(acc[d][q]);
+        return Y + (long long)(__float2int_rn(acc[ND - 1][q]) >> 8);
     }
 
     // Forward rows row0 + i (i < N) of A x for this warp's pivots (reads in
@@ -725,20 +739,22 @@ struct Walk {
     }
 
     // Biased fixed point of v relative to exponent field fm >= field(v)
-    // (no flush: the caller checks the scale).
+    // (no flush: the caller checks the scale), ND digits as in to_fixed.
+    template <int ND = NDIG>
     static __device__ __forceinline__ uint64_t to_fixed_rel(double v, int fm)
     {
+        constexpr int sh = 8 * (NDIG - ND);
         const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
         const int f = (hi >> 20) & 0x7ff;
         long long X = 0;
         if (f != 0) {
             const unsigned long long m =
                 ((unsigned long long)((hi & 0xfffffu) | 0x100000u) << 32) | lo;
-            const int q = min(max(fm - f, 0), 63);
+            const int q = min(max(fm - f, 0) + sh, 63);
             X = (long long)((((m << 2) >> q) + 1ull) >> 1);
             if (hi >> 31) X = -X;
         }
-        return (uint64_t)(X + 0x0080808080808080ll);
+        return (uint64_t)(X + (0x0080808080808080ll >> sh));
     }
 
     // Partial dL/dA of this warp's 32 pivots on the tensor cores:
@@ -756,6 +772,14 @@ struct Walk {
     // (Xr, Xi) with the halves swapped and the low half negated (a balanced
     // digit negates exactly in fp16).  The result is added to the warp's own
     // slot (single writer).
+    //
+    // These sums feed no recurrence, so they take NDP = 6 digits (21 digit
+    // pairs): a term's error is below 2^-45 of the largest product of its row
+    // in the tile, under the rounding of the FP64 additions that follow (about
+    // 60 tiles per slot, then the slots), so the gradient is as accurate as
+    // an FP64 sum of the same terms.
+    static constexpr int NDP = 6;
+
     static __device__ void tc_partials(const DiagArgs &a, const Smem &s, int circ, int row0, int N)
     {
         constexpr int NT = KS;   // N tiles of 8 columns j (N <= 8 KS)
@@ -770,9 +794,9 @@ struct Walk {
         // rows w of the m16 tile mt (one tile up to 16 rows, two beyond)
 #pragma unroll 1
         for (int mt = 0; mt < nmt; ++mt) {
-            float ar[NDIG][NT][4], ai[NDIG][NT][4];
+            float ar[NDP][NT][4], ai[NDP][NT][4];
 #pragma unroll
-            for (int d = 0; d < NDIG; ++d)
+            for (int d = 0; d < NDP; ++d)
 #pragma unroll
                 for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
@@ -784,7 +808,7 @@ struct Walk {
             for (int ks = 0; ks < 4; ++ks) {
                 const int t0 = 8 * ks + tig, t1 = t0 + 4;
                 const int e0 = ef[t0], e1 = ef[t1];
-                uint32_t aq[NDIG][4];
+                uint32_t aq[NDP][4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const int w = (k & 1) ? w1 : w0, t = (k & 2) ? t1 : t0, e = (k & 2) ? e1 : e0;
@@ -795,16 +819,16 @@ struct Walk {
                         yi = wy[(2 * w + 1) * WBS + t];
                     }
                     const int fm = g - e + 1022;
-                    uint32_t wd[NDIG];
-                    digit_words(to_fixed_rel(yr, fm), to_fixed_rel(yi, fm), wd);
+                    uint32_t wd[NDP];
+                    digit_words<NDP>(to_fixed_rel<NDP>(yr, fm), to_fixed_rel<NDP>(yi, fm), wd);
 #pragma unroll
-                    for (int sl = 0; sl < NDIG; ++sl) aq[sl][k] = wd[sl];
+                    for (int sl = 0; sl < NDP; ++sl) aq[sl][k] = wd[sl];
                 }
 #pragma unroll
                 for (int nt = 0; nt < NT; ++nt) {
                     if (nt >= nnt) continue;
                     const int j = 8 * nt + grp;
-                    uint32_t bq[NDIG][2];
+                    uint32_t bq[NDP][2];
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         const int t = h ? t1 : t0, e = h ? e1 : e0;
@@ -813,17 +837,17 @@ struct Walk {
                             xr = wx[(2 * j) * WBS + t];
                             xi = wx[(2 * j + 1) * WBS + t];
                         }
-                        uint32_t wd[NDIG];
-                        digit_words(to_fixed(xr, e), to_fixed(xi, e), wd);
+                        uint32_t wd[NDP];
+                        digit_words<NDP>(to_fixed<NDP>(xr, e), to_fixed<NDP>(xi, e), wd);
 #pragma unroll
-                        for (int sl = 0; sl < NDIG; ++sl) bq[sl][h] = wd[sl];
+                        for (int sl = 0; sl < NDP; ++sl) bq[sl][h] = wd[sl];
                     }
 #pragma unroll
-                    for (int u = 0; u < NDIG; ++u) {
+                    for (int u = 0; u < NDP; ++u) {
                         const uint32_t bi[2] = {__byte_perm(bq[u][0], 0u, 0x1032) ^ 0x8000u,
                                                 __byte_perm(bq[u][1], 0u, 0x1032) ^ 0x8000u};
 #pragma unroll
-                        for (int sa = 0; sa + u < NDIG; ++sa) {
+                        for (int sa = 0; sa + u < NDP; ++sa) {
                             mma_f16(ar[sa + u][nt], aq[sa], bq[u]);
                             mma_f16(ai[sa + u][nt], aq[sa], bi);
                         }
@@ -838,20 +862,22 @@ struct Walk {
                     const int w = (q >> 1) ? w1 : w0, j = 8 * nt + 2 * tig + (q & 1);
                     const int g = (q >> 1) ? g1 : g0;
                     if (w < N && j < N && g >= 26) {
-                        float a7[NDIG][4];
+                        float a6[NDP][4];
 #pragma unroll
-                        for (int d = 0; d < NDIG; ++d) a7[d][0] = ar[d][nt][q];
-                        const long long Yr = combine_digits_wide(a7, 0);
+                        for (int d = 0; d < NDP; ++d) a6[d][0] = ar[d][nt][q];
+                        const long long Yr = combine_digits_wide<NDP>(a6, 0);
 #pragma unroll
-                        for (int d = 0; d < NDIG; ++d) a7[d][0] = ai[d][nt][q];
-                        const long long Yi = combine_digits_wide(a7, 0);
+                        for (int d = 0; d < NDP; ++d) a6[d][0] = ai[d][nt][q];
+                        const long long Yi = combine_digits_wide<NDP>(a6, 0);
                         double *dst = pA + 2 * ((size_t)(row0 + w) * D + row0 + j);
                         // reductions without return: the warp does not wait for
                         // the old values.  The slot has one warp as its only
                         // writer and its updates are ordered by the warp's
                         // barriers between tiles, so the sum order is fixed.
-                        atomicAdd(dst, scale2(__ll2double_rn(Yr), g - 1074));
-                        atomicAdd(dst + 1, scale2(__ll2double_rn(Yi), g - 1074));
+                        // Scale: Y carries the product of the two fixed points
+                        // over 2^(8 NDP), i.e. 2^(1074 - 8 (7 - NDP) - g).
+                        atomicAdd(dst, scale2(__ll2double_rn(Yr), g - 1074 + 8 * (NDIG - NDP)));
+                        atomicAdd(dst + 1, scale2(__ll2double_rn(Yi), g - 1074 + 8 * (NDIG - NDP)));
                     }
                 }
             }
@@ -1051,7 +1077,7 @@ struct Walk {
         g.lk0 = s.cum0[K];
         g.lkm = s.cum1[K];
         g.wt2 = sh.lm_t2[K] + g.lk0 + r;
-        g.fp = sh.has_b ? sh.lm_t1[K] + 2 * (s.cum0[0] + r) + 1 : 0;
+        g.fp = sh.has_b ? box_t1(sh, K, sh.lm_t1[K] + 2 * (s.cum0[0] + r) + 1) : 0;
         int64_t pout = sh.stride[K];
         for (int i = K; i < sh.M; ++i) pout += (int64_t)e(i) * sh.stride[i];
         g.pout = pout;
@@ -1083,7 +1109,7 @@ struct Walk {
         g.lk0 = s.cum0[K];
         g.lkm = s.cum1[K];
         g.wt2 = sh.lm_t2[K] + g.lk0 + r;
-        g.fp = sh.has_b ? sh.lm_t1[K] + 2 * (s.cum0[0] + r) + 1 : 0;
+        g.fp = sh.has_b ? box_t1(sh, K, sh.lm_t1[K] + 2 * (s.cum0[0] + r) + 1) : 0;
         int64_t pout = sh.stride[K];
         for (int i = K; i < sh.M; ++i) pout += (int64_t)e(i) * sh.stride[i];
         g.pout = pout;
@@ -1117,7 +1143,7 @@ struct Walk {
             e = unrank(sh, s, K, 1, lev, r);
             return ap_geom(sh, e, K, s, lev, (int64_t)r);
         }
-        const int4 *rec = (const int4 *)(a.geo + (size_t)(sh.off_ap[K] + s.cum0[K] + r) * kGeoInts);
+        const int4 *rec = (const int4 *)(a.geo + (size_t)box_ap(sh, K, sh.off_ap[K] + s.cum0[K] + r) * kGeoInts);
         const int4 w0 = __ldcg(rec), w1 = __ldcg(rec + 1), w2 = __ldcg(rec + 2);
         e.lo = (uint64_t)(unsigned)w0.x | ((uint64_t)(unsigned)w0.y << 32);
         e.hi = 0;
@@ -1140,7 +1166,7 @@ struct Walk {
             q = ap_rel(sh, e, K, s, lev, (int64_t)r);
             return ap_assemble<false>(sh, e, K, s, lev, (int64_t)r, q);
         }
-        const int4 *rec = (const int4 *)(a.geo + (size_t)(sh.off_ap[K] + s.cum0[K] + r) * kGeoInts);
+        const int4 *rec = (const int4 *)(a.geo + (size_t)box_ap(sh, K, sh.off_ap[K] + s.cum0[K] + r) * kGeoInts);
         const int4 w0 = __ldcg(rec), w1 = __ldcg(rec + 1), w2 = __ldcg(rec + 2);
         e.lo = (uint64_t)(unsigned)w0.x | ((uint64_t)(unsigned)w0.y << 32);
         e.hi = 0;
@@ -1166,7 +1192,7 @@ struct Walk {
                 for (int64_t r = gtid; r < cnt; r += gsz) {
                     const Dig e = unrank(sh, s, K, 1, lev, (unsigned)r);
                     const ApRel q = ap_rel(sh, e, K, s, lev, r);
-                    int4 *rec = (int4 *)(a.geo + (size_t)(off + r) * kGeoInts);
+                    int4 *rec = (int4 *)(a.geo + (size_t)box_ap(sh, K, off + r) * kGeoInts);
                     rec[0] = make_int4((int)(unsigned)e.lo, (int)(unsigned)(e.lo >> 32), q.idx[0], q.idx[1]);
                     rec[1] = make_int4(q.idx[2], q.idx[3], q.idx[4], q.idx[5]);
                     rec[2] = make_int4(q.idx[6], q.rt2, q.wdiag, 0);
@@ -1182,15 +1208,40 @@ struct Walk {
         return sh.lm_p[K] + 2 * (int64_t)(m - K - 1) * sh.fam[K];
     }
 
+    // Storage boxes of one circuit's amplitude array for the debug checks:
+    // DIAG [0, n_diag); T2(K) and the P pairs (K, m) in family K; the T1
+    // pair of mode q in family 0.
+    static __device__ __forceinline__ int64_t box_diag(const DiagShape &sh, int64_t i)
+    {
+        return FK_BOX(i, 0, sh.n_diag);
+    }
+    static __device__ __forceinline__ int64_t box_t2(const DiagShape &sh, int K, int64_t i)
+    {
+        return FK_BOX(i, sh.lm_t2[K], sh.lm_t2[K] + sh.fam[K]);
+    }
+    static __device__ __forceinline__ int64_t box_pair(const DiagShape &sh, int K, int m, int64_t i)
+    {
+        return FK_BOX(i, pair_base(sh, K, m), pair_base(sh, K, m) + 2 * sh.fam[K]);
+    }
+    static __device__ __forceinline__ int64_t box_t1(const DiagShape &sh, int q, int64_t i)
+    {
+        return FK_BOX(i, sh.lm_t1[q], sh.lm_t1[q] + 2 * sh.fam[0]);
+    }
+    // AP(K) pivots: VJP scratch entries and geometry records
+    static __device__ __forceinline__ int64_t box_ap(const DiagShape &sh, int K, int64_t i)
+    {
+        return FK_BOX(i, sh.off_ap[K], sh.off_ap[K] + sh.fam[K]);
+    }
+
     // Address (within the circuit's amplitude array) of AP read column j.
     static __device__ __forceinline__ int64_t ap_read_addr(const DiagShape &sh, const ApGeom &g, int K,
                                                     int j, const Smem &s)
     {
-        if (j == 0) return g.rd;
-        if (j == 1) return g.rt2;
+        if (j == 0) return box_diag(sh, g.rd);
+        if (j == 1) return box_t2(sh, K, g.rt2);
         const int m = K + j / 2;
         const int64_t rk = s.idx[m * TPB + threadIdx.x];
-        return pair_base(sh, K, m) + 2 * (g.lkm + rk) + ((j & 1) ? 0 : 1);
+        return box_pair(sh, K, m, pair_base(sh, K, m) + 2 * (g.lkm + rk) + ((j & 1) ? 0 : 1));
     }
 
     // The same with the ranks of e - 1_m in registers (q.idx[m - K - 1]); j is
@@ -1198,10 +1249,10 @@ struct Walk {
     static __device__ __forceinline__ int64_t ap_read_addr_q(const DiagShape &sh, const ApGeom &g, int K,
                                                              int j, const ApRel &q)
     {
-        if (j == 0) return g.rd;
-        if (j == 1) return g.rt2;
+        if (j == 0) return box_diag(sh, g.rd);
+        if (j == 1) return box_t2(sh, K, g.rt2);
         const int m = K + j / 2;
-        return pair_base(sh, K, m) + 2 * (g.lkm + q.idx[j / 2 - 1]) + ((j & 1) ? 0 : 1);
+        return box_pair(sh, K, m, pair_base(sh, K, m) + 2 * (g.lkm + q.idx[j / 2 - 1]) + ((j & 1) ? 0 : 1));
     }
 
     // Address of AP write row i and its scale index P_w + 1.
@@ -1209,11 +1260,11 @@ struct Walk {
                                                      const Dig &e, int K, int i, const Smem &s,
                                                      int *den)
     {
-        if (i == 0) { *den = e(K) + 2; return g.wt2; }
-        if (i == 1) { *den = e(K) + 1; return g.wdiag; }
+        if (i == 0) { *den = e(K) + 2; return box_t2(sh, K, g.wt2); }
+        if (i == 1) { *den = e(K) + 1; return box_diag(sh, g.wdiag); }
         const int m = K + i / 2;
         *den = e(m) + 1;
-        return pair_base(sh, K, m) + 2 * (g.lk0 + g.r) + (i & 1);
+        return box_pair(sh, K, m, pair_base(sh, K, m) + 2 * (g.lk0 + g.r) + (i & 1));
     }
 
     // DP pivot d of level `lev` with rank r in family 0; ranks of d - 1_q go
@@ -1223,7 +1274,7 @@ struct Walk {
     {
         DpGeom g;
         g.r = r;
-        g.rdiag = cum_full(s, lev) + r;
+        g.rdiag = box_diag(sh, cum_full(s, lev) + r);
         g.l00 = s.cum0[0];
         g.l0m = s.cum1[0];
         g.vmask = 0;
@@ -1252,7 +1303,7 @@ struct Walk {
                                                     const Smem &s)
     {
         const int q = j / 2;
-        return sh.lm_t1[q] + 2 * (g.l0m + s.idx[q * TPB + threadIdx.x]) + (j & 1);
+        return box_t1(sh, q, sh.lm_t1[q] + 2 * (g.l0m + s.idx[q * TPB + threadIdx.x]) + (j & 1));
     }
 
     static __device__ __forceinline__ int64_t dp_write_addr(const DiagShape &sh, const DpGeom &g,
@@ -1260,7 +1311,7 @@ struct Walk {
     {
         const int q = i / 2;
         *den = d(q) + 1;
-        return sh.lm_t1[q] + 2 * (g.l00 + g.r) + ((i & 1) ? 0 : 1);
+        return box_t1(sh, q, sh.lm_t1[q] + 2 * (g.l00 + g.r) + ((i & 1) ? 0 : 1));
     }
 
     // ---------------------------------------------------------------- prologue
@@ -1352,7 +1403,7 @@ struct Walk {
             F[addr] = v;
             if (i == 1) {
                 const double2 p = rscale(v, fe * (double)(e(K) + 1));
-                a.probs[oix(a, tl.circ) + (sh.global ? g.wdiag : g.pout)] = p;
+                a.probs[oix(a, tl.circ) + box_diag(sh, sh.global ? g.wdiag : g.pout)] = p;
                 if (EARLY) psum += p.x;
             }
         });
@@ -1459,13 +1510,13 @@ struct Walk {
         double fe = 1.0;
         for (int i = K; i < sh.M; ++i) fe *= s.fact[e(i)];
         const int xK = e(K) + 1;
-        double2 acc = rscale(a.gprobs[oix(a, circ) + (sh.global ? g.wdiag : g.pout)],
+        double2 acc = rscale(a.gprobs[oix(a, circ) + box_diag(sh, sh.global ? g.wdiag : g.pout)],
                              fe * (double)xK);
         if (pivots_run(a, circ, lev + 1)) {
             const double2 *sc = a.scratch + (size_t)circ * sh.n_ap;
             const int64_t rx = g.wdiag - cum_full(s, lev + 1);
             for (int k = 0; k <= K; ++k)
-                if (k < K || xK <= sh.C[K] - 2) acc = cadd(acc, __ldcg(sc + sh.off_ap[k] + s.cum2[k] + rx));
+                if (k < K || xK <= sh.C[K] - 2) acc = cadd(acc, __ldcg(sc + box_ap(sh, k, sh.off_ap[k] + s.cum2[k] + rx)));
         }
         if (HASB) acc = cadd(acc, __ldcg(a.Fbar + (size_t)circ * sh.circ_alloc + g.wdiag));
         return acc;
@@ -1532,7 +1583,7 @@ struct Walk {
             if (!act || !((g.vmask >> j) & 1u)) return;
             if (j == 0) {
                 const int64_t ia = g.lk0 + g.r;
-                a.scratch[(size_t)tl.circ * sh.n_ap + sh.off_ap[K] + ia] = acc;
+                a.scratch[(size_t)tl.circ * sh.n_ap + box_ap(sh, K, sh.off_ap[K] + ia)] = acc;
             } else {
                 // T2 and P1010/P1001 values have this pivot as their only
                 // reader, so their adjoint is this one term
@@ -1694,7 +1745,7 @@ struct Walk {
                 const double2 acc = make_double2(wy[(2 * j) * WBS + lane], wy[(2 * j + 1) * WBS + lane]);
                 if (j == 0) {
                     const int64_t ia = g.lk0 + g.r;
-                    a.scratch[(size_t)tl.circ * sh.n_ap + sh.off_ap[K] + ia] = acc;
+                    a.scratch[(size_t)tl.circ * sh.n_ap + box_ap(sh, K, sh.off_ap[K] + ia)] = acc;
                 } else {
                     Fb[ap_read_addr(sh, g, K, j, s)] = acc;   // the value's only reader
                 }
@@ -1871,6 +1922,7 @@ struct Walk {
                     dp_forward_tile(a, s, tl, lev);
                 });
                 if (!grid_sync(a.ctl, gridDim.x, a.timeout_ns)) return;
+                trace_mark(a.trace, a.trace_cap, kTraceFwd | (lev << 8) | 1u);
             }
             const int nt = phase_tiles(a, s, 0, lev);
             run_tiles(a.ctr + 2 * lev + 1, nt, [&](int tile) {
@@ -1885,6 +1937,7 @@ struct Walk {
                 }
             });
             if ((lev + 1 < sh.L || a.early) && !grid_sync(a.ctl, gridDim.x, a.timeout_ns)) return;
+            trace_mark(a.trace, a.trace_cap, kTraceFwd | (lev << 8));
         }
         if (a.early && a.levels != nullptr && blockIdx.x == 0) {
             // photon numbers completed: 0 .. (first level whose pivots did not run)
@@ -1924,6 +1977,7 @@ struct Walk {
                     }
                 });
                 if (!grid_sync(a.ctl, gridDim.x, a.timeout_ns)) return;
+                trace_mark(a.trace, a.trace_cap, kTraceVjp | (lev << 8));
             }
             if (hb && lev < sh.L) {
                 const int nt = phase_tiles(a, s, 1, lev);
@@ -1934,6 +1988,7 @@ struct Walk {
                     else dp_reverse_tile(a, s, tl, lev);
                 });
                 if (!grid_sync(a.ctl, gridDim.x, a.timeout_ns)) return;
+                trace_mark(a.trace, a.trace_cap, kTraceVjp | (lev << 8) | 1u);
             }
         }
         if constexpr (!TC) finish_vjp(a, hb);   // the tensor engine's partial pass finishes
@@ -1978,6 +2033,7 @@ struct Walk {
     {
         zero_grads(a);
         if (!grid_sync(a.ctl, gridDim.x, a.timeout_ns)) return;
+        trace_mark(a.trace, a.trace_cap, kTraceFinish);
         reduce_grads(a, hb);
     }
 
@@ -2265,6 +2321,7 @@ struct Walk {
 template <int TPB, int CH, int KS>
 __global__ void __launch_bounds__(TPB, (KS > 2 ? 2 : (KS > 0 ? 4 : 1))) diag_forward_kernel(const __grid_constant__ DiagArgs a)
 {
+    FK_DBG_BEGIN(a.ctl);
     if (a.G == 0) Walk<TPB, CH, KS>::forward(a);
     else if (!skip_walk(a.ctl)) Walk<TPB, CH, KS>::forward_multi(a);
 }
@@ -2272,6 +2329,7 @@ __global__ void __launch_bounds__(TPB, (KS > 2 ? 2 : (KS > 0 ? 4 : 1))) diag_for
 template <int TPB, int CH, int KS>
 __global__ void __launch_bounds__(TPB, (KS > 2 ? 2 : (KS > 0 ? 4 : 1))) diag_vjp_kernel(const __grid_constant__ DiagArgs a)
 {
+    FK_DBG_BEGIN(a.ctl);
     if (a.G == 0) Walk<TPB, CH, KS>::vjp(a);
     else if (!skip_walk(a.ctl)) Walk<TPB, CH, KS>::vjp_multi(a);
 }
@@ -2279,6 +2337,7 @@ __global__ void __launch_bounds__(TPB, (KS > 2 ? 2 : (KS > 0 ? 4 : 1))) diag_vjp
 template <int TPB, int CH, int KS>
 __global__ void __launch_bounds__(TPB, (KS > 2 ? 2 : (KS > 0 ? 3 : 1))) diag_vjp_partials_kernel(const __grid_constant__ DiagArgs a)
 {
+    FK_DBG_BEGIN(a.ctl);
     if constexpr (KS > 0) {
         if (a.G == 0) Walk<TPB, CH, KS>::vjp_partials(a);
         else Walk<TPB, CH, KS>::vjp_partials_multi(a);

@@ -14,7 +14,9 @@ import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libfockdiag.so")
+# FOCKDIAG_LIB selects another build of the same ABI (the debug-checks
+# library libfockdiag_debug.so)
+LIB_PATH = os.environ.get("FOCKDIAG_LIB") or os.path.join(_HERE, "libfockdiag.so")
 
 FK_OK = 0
 FK_ETIMEOUT = 6
@@ -43,7 +45,7 @@ EXPORTS = [
     "fk_gaussian_to_pure_triple", "fk_pure_workspace_size", "fock_pure_amplitudes_batched",
     "fock_pure_amplitudes_vjp_batched", "fk_diag_tuning_flags",
     "fk_multi_workspace_size", "fock_diag_probs_multi_batched", "fock_diag_probs_multi_vjp_batched",
-    "fk_tc_gemm_bf16",
+    "fk_tc_gemm_bf16", "fk_debug_checks", "fk_workspace_debug", "fk_debug_set_trace",
 ]
 
 
@@ -86,6 +88,9 @@ def lib():
         L.fock_diag_probs_vjp_batched.argtypes = [I, P, P, P, I, P, P, P, P, P, U, P, Z, P]
         L.fk_workspace_status.argtypes = [P, P, ctypes.POINTER(I)]
         L.fk_selftest_wait_timeout.argtypes = [P, Z, ctypes.c_ulonglong, P]
+        L.fk_debug_checks.restype = I
+        L.fk_workspace_debug.argtypes = [P, P, P]
+        L.fk_debug_set_trace.argtypes = [P, I]
         L.fk_describe_diag_schedule.argtypes = [I, P, U, P, I]
         L.fk_measure_fp64_fma_rate.argtypes = [P, Z, ctypes.POINTER(ctypes.c_double), P]
         L.fock_diag_probs_static.argtypes = [I, P, P, P, I, P, P, U, P, ctypes.POINTER(I)]
@@ -531,6 +536,28 @@ def fk_workspace_status(ws, stream=None):
     st = lib().fk_workspace_status(_ptr(ws), _stream(stream), ctypes.byref(v))
     _check(st, "fk_workspace_status")
     return int(v.value)
+
+
+def fk_debug_checks():
+    """True for the debug-checks build (libfockdiag_debug.so)."""
+    return bool(lib().fk_debug_checks())
+
+
+def fk_workspace_debug(ws, stream=None):
+    """Access-violation record of the debug-checks build: (count, source
+    line of the first, its index, box start, box end)."""
+    out = (ctypes.c_longlong * 5)()
+    _check(lib().fk_workspace_debug(_ptr(ws), _stream(stream), out), "fk_workspace_debug")
+    return tuple(int(v) for v in out)
+
+
+def fk_debug_set_trace(buf):
+    """Register a zeroed device int64 tensor of 1 + 2 n words for per-level
+    timestamps (debug-checks build); None unregisters it."""
+    if buf is None:
+        _check(lib().fk_debug_set_trace(None, 0), "fk_debug_set_trace")
+        return
+    _check(lib().fk_debug_set_trace(_ptr(buf), (buf.numel() - 1) // 2), "fk_debug_set_trace")
 
 
 def check_workspace(ws, stream=None, where="device"):
