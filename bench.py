@@ -426,39 +426,61 @@ def secondary_rows(torch, fd, inputs, dev, fp64_peak, reps=5):
     circs = inputs.workload("cond_m3_batch64")
     cuts = [cc.cutoffs for cc in circs]
     A, b, c = _triples(fd, circs, dev)
-    rho, offs, ws = fd.fock_conditional_dm_batched(A, b, c, cuts, mask)
-    g = torch.randn(rho.shape, dtype=torch.float64, device=dev).to(torch.complex128)
-    out = tuple(torch.empty_like(x) for x in (A, b, c))
-    for _ in range(3):
-        fd.fock_conditional_dm_batched(A, b, c, cuts, mask, rho=rho, ws=ws)
-        fd.fock_conditional_dm_vjp_batched(A, b, c, cuts, mask, g, ws, out=out)
-    torch.cuda.synchronize()
-    t0, t1, t2 = ev(), ev(), ev()
-    fwd = vjp = 0.0
-    for _ in range(reps):
-        t0.record()
-        fd.fock_conditional_dm_batched(A, b, c, cuts, mask, rho=rho, ws=ws)
-        t1.record()
-        fd.fock_conditional_dm_vjp_batched(A, b, c, cuts, mask, g, ws, out=out)
-        t2.record()
+    hbm, _ = measured_hbm_gbs()
+
+    def time_cond(flags):
+        rho, offs, ws = fd.fock_conditional_dm_batched(A, b, c, cuts, mask, flags=flags)
+        g = torch.randn(rho.shape, dtype=torch.float64, device=dev).to(torch.complex128)
+        out = tuple(torch.empty_like(x) for x in (A, b, c))
+        for _ in range(3):
+            fd.fock_conditional_dm_batched(A, b, c, cuts, mask, rho=rho, ws=ws, flags=flags)
+            fd.fock_conditional_dm_vjp_batched(A, b, c, cuts, mask, g, ws, out=out, flags=flags)
         torch.cuda.synchronize()
-        fwd += t0.elapsed_time(t1); vjp += t1.elapsed_time(t2)
-    fd.check_workspace(ws, where="conditional rows")
-    fwd /= reps; vjp /= reps
-    n_out = int(offs[-1])
+        t0, t1, t2 = ev(), ev(), ev()
+        fwd = vjp = 0.0
+        for _ in range(reps):
+            t0.record()
+            fd.fock_conditional_dm_batched(A, b, c, cuts, mask, rho=rho, ws=ws, flags=flags)
+            t1.record()
+            fd.fock_conditional_dm_vjp_batched(A, b, c, cuts, mask, g, ws, out=out, flags=flags)
+            t2.record()
+            torch.cuda.synchronize()
+            fwd += t0.elapsed_time(t1); vjp += t1.elapsed_time(t2)
+        fd.check_workspace(ws, where="conditional rows")
+        n_out = int(offs[-1])
+        del rho, ws, g
+        return fwd / reps, vjp / reps, n_out
+
+    fwd, vjp, n_out = time_cond(fd.FK_FLAG_ENGINE_TENSOR)
+    fwd64, vjp64, _ = time_cond(fd.FK_FLAG_ENGINE_FP64)
     f_fwd = sum(counts.cond_flops(cu, mask) for cu in cuts)
+    n_amp = sum(counts.cond_amplitudes(cu, mask) for cu in cuts)
+    # algorithmic bytes: 16 B written + 16 B read per walk amplitude and 16 B
+    # per output (forward); the VJP reads the value and writes and reads the
+    # adjoint (48 B) plus 16 B per upstream gradient
+    b_fwd = 32 * n_amp + 16 * n_out
+    b_vjp = 48 * n_amp + 16 * n_out
     rows["conditional_walk"] = {
         "workload": "cond_m3_batch64: 64 circuits, modes 0,1 detected (C 10..20), mode 2 "
                     "undetected (C 20..30), b != 0",
-        "forward_ms": fwd, "vjp_ms": vjp, "outputs": n_out,
-        "outputs_per_s": n_out / ((fwd + vjp) * 1e-3), "engine": "fp64",
+        "engine": "tensor", "forward_ms": fwd, "vjp_ms": vjp, "outputs": n_out,
+        "walk_amplitudes": n_amp,
+        "outputs_per_s": n_out / ((fwd + vjp) * 1e-3),
         "circuits_per_s": 64 / ((fwd + vjp) * 1e-3),
-        "roofline": {"bound": "alu", "achieved": f_fwd / (fwd * 1e-3) / 1e12, "peak": fp64_peak,
-                     "unit": "TFLOP/s", "frac": f_fwd / (fwd * 1e-3) / 1e12 / fp64_peak,
-                     "algorithmic_flops_forward": f_fwd,
-                     "vjp_frac": 2 * f_fwd / (vjp * 1e-3) / 1e12 / fp64_peak,
-                     "note": "forward kernel; the VJP performs two complex MACs per term"}}
-    del rho, ws, g
+        "roofline": {"bound": "hbm", "achieved": b_vjp / (vjp * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                     "frac": b_vjp / (vjp * 1e-3) / 1e9 / hbm, "kernel": "cond_vjp_kernel",
+                     "algorithmic_bytes_per_launch": b_vjp,
+                     "forward": {"achieved": b_fwd / (fwd * 1e-3) / 1e9,
+                                 "frac": b_fwd / (fwd * 1e-3) / 1e9 / hbm,
+                                 "algorithmic_bytes_per_launch": b_fwd},
+                     "fp64_equivalent": {"unit": "TFLOP/s", "peak": fp64_peak,
+                                         "algorithmic_flops_forward": f_fwd,
+                                         "forward_frac": f_fwd / (fwd * 1e-3) / 1e12 / fp64_peak,
+                                         "vjp_frac": 2 * f_fwd / (vjp * 1e-3) / 1e12 / fp64_peak,
+                                         "note": "the VJP performs two complex MACs per term"}},
+        "fp64_engine": {"forward_ms": fwd64, "vjp_ms": vjp64,
+                        "forward_frac_of_fp64_peak": f_fwd / (fwd64 * 1e-3) / 1e12 / fp64_peak,
+                        "vjp_frac_of_fp64_peak": 2 * f_fwd / (vjp64 * 1e-3) / 1e12 / fp64_peak}}
     # BF16 MLP training step (15-256-256-256-2, forward + backward + Adam): the
     # training batch (2048) and a large batch (65536) for the GEMM roofline
     from paper_2303_08879_gb300.mlp import MLP, init_params, IN, HIDDEN, OUT
@@ -492,7 +514,6 @@ def secondary_rows(torch, fd, inputs, dev, fp64_peak, reps=5):
         "roofline": {"bound": "tensor", "batch": 65536, "achieved": tf, "peak": peak,
                      "unit": "TFLOP/s", "frac": tf / peak, "peak_source": src}}
     torch.cuda.empty_cache()
-    hbm, _ = measured_hbm_gbs()
     rows["config1_latency"] = config1_row(torch, fd, inputs, dev, fp64_peak)
     torch.cuda.empty_cache()
     rows["config5_large"] = config5_row(torch, fd, inputs, dev, fp64_peak, hbm)

@@ -22,7 +22,8 @@ BUILD_DEBUG = os.path.join(HERE, "_build_debug")
 LIB_DEBUG = os.path.join(HERE, "libfockdiag_debug.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cpp", "circuit.cpp", "walk_diag.cu", "walk_cond.cu", "mlp.cu", "herald.cu", "probe.cu", "static_ws.cu",
-           "walk_pure.cu", "multi.cpp", "walk_diag_tc1.cu", "walk_diag_tc2.cu", "walk_diag_tc3.cu", "mlp_tc.cu"]
+           "walk_pure.cu", "multi.cpp", "walk_diag_tc1.cu", "walk_diag_tc2.cu", "walk_diag_tc3.cu", "mlp_tc.cu",
+           "walk_cond_k0.cu", "walk_cond_k1.cu", "walk_cond_k2.cu", "walk_cond_k3.cu"]
 # walk_diag_fp64.cu once per FP64 tile shape (pivots per tile, rows per chunk)
 FP64_SHAPES = [(128, 8), (128, 4), (64, 8), (64, 4), (256, 8)]
 
@@ -75,7 +76,7 @@ def build(verbose: bool = False, extra_flags=(), debug: bool = False) -> str:
         return cmd, r
 
     # the heaviest units first, so the parallel build ends soon after them
-    jobs.sort(key=lambda c: 0 if "walk_diag" in c[-3] else 1)
+    jobs.sort(key=lambda c: 0 if ("walk_diag" in c[-3] or "walk_cond_k" in c[-3]) else 1)
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 1))) as ex:
         for cmd, r in ex.map(run, jobs):
             if verbose or r.returncode:

@@ -116,3 +116,14 @@ def cond_terms(cutoffs, detected):
 
 def cond_flops(cutoffs, detected):
     return 8 * cond_terms(cutoffs, detected)
+
+
+def cond_amplitudes(cutoffs, detected):
+    """Amplitudes the conditional walk of one circuit stores (b != 0): the
+    u-block of every position of the detected Algorithm-1 structure with its
+    offset_1 amplitudes, the vacuum position included (U2 (1 + writes))."""
+    det = [int(c) for c, d in zip(cutoffs, detected) if d]
+    und = [int(c) for c, d in zip(cutoffs, detected) if not d and int(c) >= 2]
+    U2 = _prod(c * c for c in und)
+    return U2 * (1 + diag_terms_writes(det, has_b=True)[1])
+

@@ -466,17 +466,12 @@ int fk_workspace_size(int M, const int *cutoffs, const unsigned char *mask, int 
 int fk_conditional_workspace_size(int batch, int M, const int *cutoffs, const unsigned char *mask,
                                   int op, unsigned flags, size_t *bytes, int64_t *rho_offsets)
 {
-    (void)flags;
     if (!bytes || (op != FK_OP_COND && op != FK_OP_COND_VJP)) return FK_EINVAL;
     const CondPlan *plan = nullptr;
     int rc = get_cond_plan(batch, M, cutoffs, mask, &plan);
     if (rc) return rc;
     CondLayout lay;
-    if (op == FK_OP_COND_VJP) {
-        rc = cond_layout(*plan, true, &lay);
-    } else {
-        rc = cond_layout(*plan, false, &lay);
-    }
+    rc = cond_layout(*plan, op == FK_OP_COND_VJP, flags, &lay);
     if (rc) return rc;
     *bytes = lay.total;
     if (rho_offsets) {
@@ -504,7 +499,7 @@ int fock_conditional_dm_batched(int batch, const fk_c128 *A, const fk_c128 *b, c
     int rc = get_cond_plan(batch, M, cutoffs, mask, &plan);
     if (rc) return rc;
     CondLayout lay;
-    rc = cond_layout(*plan, false, &lay);
+    rc = cond_layout(*plan, false, flags, &lay);
     if (rc) return rc;
     if (ws_bytes < lay.total || !aligned(ws)) return FK_EWORKSPACE;
     return launch_cond_forward(*plan, flags, A, b, c, rho, ws, lay, stream);
@@ -529,7 +524,7 @@ int fock_conditional_dm_vjp_batched(int batch, const fk_c128 *A, const fk_c128 *
     int rc = get_cond_plan(batch, M, cutoffs, mask, &plan);
     if (rc) return rc;
     CondLayout lay;
-    rc = cond_layout(*plan, true, &lay);
+    rc = cond_layout(*plan, true, flags, &lay);
     if (rc) return rc;
     if (ws_bytes < lay.total || !aligned(ws)) return FK_EWORKSPACE;
     if (flags & FK_FLAG_RECOMPUTE) {

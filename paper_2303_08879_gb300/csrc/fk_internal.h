@@ -121,16 +121,20 @@ struct CondPlan {
 };
 
 struct CondLayout {
-    size_t ctl, plan, Ar, br, geo, F, Fbar, scratch, partA, partb, total;
+    size_t ctl, plan, Ar, br, geo, dig, F, Fbar, scratch, partA, partb, total;
     int grid_vjp;
+    int ks;            // product engine: 0 = FP64, 1..3 = tensor engine with KS K steps
 };
 
 // Returns the cached plan of (batch, M, cutoffs[batch][M], mask); the pinned
 // host copy stays valid for the life of the process (graph replays copy it).
 int get_cond_plan(int batch, int M, const int *cutoffs, const unsigned char *mask,
                   const CondPlan **plan);
-int cond_layout(const CondPlan &plan, bool vjp, CondLayout *lay);
-int cond_grid_size(const CondPlan &plan, bool vjp, int *grid);
+// Workspace layout of a conditional call; flags select the product engine
+// (FK_FLAG_ENGINE_FP64 / FK_FLAG_ENGINE_TENSOR, default the tensor engine).
+int cond_layout(const CondPlan &plan, bool vjp, unsigned flags, CondLayout *lay);
+int cond_engine_ks(const CondPlan &plan, unsigned flags, int *ks);
+int cond_grid_size(const CondPlan &plan, bool vjp, int ks, int *grid);
 int launch_cond_forward(const CondPlan &plan, unsigned flags, const void *A, const void *b,
                         const void *c, void *rho, void *ws, const CondLayout &lay, void *stream);
 int launch_cond_vjp(const CondPlan &plan, unsigned flags, const void *A, const void *b,

@@ -119,16 +119,17 @@ def main():
                              "forward": fwd, "vjp": debug_record(ws)})
     # conditional states (Algorithm 2): two undetected-mode layouts, b != 0,
     # against the oracle's full density matrix
-    for cut, mask, seed in (((3, 4, 3), (1, 1, 0), 7), ((3, 2, 3, 3), (0, 0, 1, 1), 8)):
+    for (cut, mask, seed), (fl, ename) in [(case, e) for case in (((3, 4, 3), (1, 1, 0), 7), ((3, 2, 3, 3), (0, 0, 1, 1), 8))
+                                           for e in ((fd.FK_FLAG_ENGINE_TENSOR, "tensor"), (fd.FK_FLAG_ENGINE_FP64, "fp64"))]:
         rng = np.random.default_rng(seed)
         A1, b1 = inputs.random_symmetric(2 * len(cut), rng, with_b=True)
         ref = oracle.full_dm_conditional(A1, b1, 0.6, cut, mask)
         A = cuda(A1[None]); b = cuda(b1[None]); c = cuda(np.array([0.6 + 0.0j]))
-        rho, offs, ws = fd.fock_conditional_dm_batched(A, b, c, [cut], mask)
+        rho, offs, ws = fd.fock_conditional_dm_batched(A, b, c, [cut], mask, flags=fl)
         fwd = debug_record(ws)
         got = fd.conditional_blocks(rho, [cut], mask)[0].cpu().numpy()
-        g = fd.fock_conditional_dm_vjp_batched(A, b, c, [cut], mask, torch.ones_like(rho), ws)
-        out["cases"].append({"what": f"conditional {cut} mask {mask}", "status": fd.fk_workspace_status(ws),
+        g = fd.fock_conditional_dm_vjp_batched(A, b, c, [cut], mask, torch.ones_like(rho), ws, flags=fl)
+        out["cases"].append({"what": f"conditional {ename} {cut} mask {mask}", "status": fd.fk_workspace_status(ws),
                              "forward": fwd, "vjp": debug_record(ws),
                              "probs_err": errors(got, ref, 1e-12),
                              "finite": bool(all(torch.isfinite(torch.view_as_real(x)).all() for x in g))})

@@ -71,3 +71,14 @@ def test_cond_terms_small_case_by_enumeration():
             step1 += 1 + sum(1 for v in P if v >= 1)
     nzsum = sum((k >= 1) + (l >= 1) for k in range(CU) for l in range(CU))
     assert counts.cond_terms(cut, det) == step1 + CU * CU * dt + dw * nzsum
+
+
+def test_cond_amplitudes_small_case_by_enumeration():
+    """Stored amplitudes of the conditional walk: every u of the u-block at
+    the vacuum position and at every detected amplitude the walk writes."""
+    cut, det = (3, 2, 3), (1, 1, 0)
+    _, dw = brute_terms_writes((3, 2), True)
+    assert counts.cond_amplitudes(cut, det) == 9 * (1 + dw)
+    assert counts.cond_amplitudes((4, 3, 2, 5), (1, 0, 1, 0)) == \
+        (3 * 3 * 5 * 5) * (1 + brute_terms_writes((4, 2), True)[1])
+

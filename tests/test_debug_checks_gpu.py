@@ -36,7 +36,7 @@ def test_debug_build_is_loaded(report):
 
 
 def test_no_access_leaves_its_storage_box(report):
-    assert len(report["cases"]) == 16
+    assert len(report["cases"]) == 18
     for case in report["cases"]:
         assert case["status"] == 0, case
         assert case["forward"]["violations"] == 0, case
@@ -53,7 +53,7 @@ def test_checked_walks_match_the_oracle(report):
         assert c["gradA_err"][0] <= 1e-8 and c["gradA_err"][1] <= 1.0, c
         assert c["gradb_err"][0] <= 1e-8 and c["gradb_err"][1] <= 1.0, c
     cond = [c for c in report["cases"] if c["what"].startswith("conditional")]
-    assert len(cond) == 2
+    assert len(cond) == 4
     for c in cond:
         assert c["probs_err"][0] <= 1e-10 and c["probs_err"][1] <= 1.0, c
 
