@@ -201,9 +201,10 @@ int fock_diag_probs_vjp_batched(int batch, const fk_c128 *d_A, const fk_c128 *d_
  * At most 1024 circuits per call, FK_MAX_MODES detected and 4 undetected
  * modes with cutoff > 1.  The walk stays in the workspace for the VJP.
  * Product engine (flags, here and in the VJP): the tensor-core digits by
- * default when 2 M <= 24 (M <= 12 caller modes), FP64 beyond;
- * FK_FLAG_ENGINE_FP64 selects FP64, FK_FLAG_ENGINE_TENSOR the tensor engine
- * (FK_EUNSUPPORTED above 12 modes).  The workspace size depends on the
+ * default up to M = 11 caller modes (the real form of [[A, b], [b^T, 0]]
+ * fits three 16-row K steps), FP64 beyond; FK_FLAG_ENGINE_FP64 selects
+ * FP64, FK_FLAG_ENGINE_TENSOR the tensor engine (FK_EUNSUPPORTED above 11
+ * modes).  The workspace size depends on the
  * engine: query fk_conditional_workspace_size with the same flags.
  */
 int fk_conditional_workspace_size(int batch, int M, const int *host_cutoffs,

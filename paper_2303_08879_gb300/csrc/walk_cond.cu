@@ -250,8 +250,8 @@ const void *cond_kernel(int ks, bool vjp)
 }  // namespace
 
 // Product engine of a conditional call: FK_FLAG_ENGINE_FP64 -> FP64 (0);
-// otherwise the tensor engine with KS = ceil(2 Dmax / 16) K steps when
-// KS <= 3 (up to 12 modes), FP64 beyond (FK_FLAG_ENGINE_TENSOR there:
+// otherwise the tensor engine with KS = ceil(2 (Dmax + 1) / 16) K steps when
+// KS <= 3 (up to 11 modes), FP64 beyond (FK_FLAG_ENGINE_TENSOR there:
 // FK_EUNSUPPORTED).
 int cond_engine_ks(const CondPlan &plan, unsigned flags, int *ks)
 {
@@ -260,7 +260,7 @@ int cond_engine_ks(const CondPlan &plan, unsigned flags, int *ks)
         *ks = 0;
         return FK_OK;
     }
-    const int k = (2 * plan.Dmax + 15) / 16;
+    const int k = cond_ks(plan.Dmax);
     if (k > 3) {
         if (flags & FK_FLAG_ENGINE_TENSOR) return FK_EUNSUPPORTED;
         *ks = 0;

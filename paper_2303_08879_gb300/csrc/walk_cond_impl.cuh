@@ -93,6 +93,13 @@ struct CSmem {
 
 constexpr int kCWBS = 34;       // column stride (doubles) of a tensor-engine per-warp buffer
 
+// K steps of 16 real rows the tensor engine needs for Dmax reduced indices:
+// the real form of the augmented (Dmax + 1) x (Dmax + 1) matrix [[A, b], [b^T, 0]].
+__host__ __device__ inline int cond_ks(int Dmax)
+{
+    return (2 * (Dmax + 1) + 15) / 16;
+}
+
 // Shared-memory plan (host sizing and device carving use the same one).
 // KS = 0: the FP64 engine; KS > 0: the tensor engine with 16 KS real rows.
 struct CondSmemPlan {
@@ -217,7 +224,7 @@ __device__ void load_circuit(const CondArgs &a, CSmem &s, int c)
     for (int e = threadIdx.x; e < Dm; e += blockDim.x) s.br[e] = a.br[(size_t)c * Dm + e];
     if (s.Af != nullptr) {
         // tensor engine: the digit fragments and row exponents written by the prologue
-        const int KS = (2 * Dm + 15) / 16;
+        const int KS = cond_ks(Dm);
         const unsigned char *src = a.dig + (size_t)c * kDigBytes;
         const uint4 *gf = (const uint4 *)(src + 256);
         for (int e = threadIdx.x; e < KS * KS * kNDig * 32; e += blockDim.x) s.Af[e] = __ldcg(gf + e);
@@ -627,26 +634,33 @@ __device__ void pair_forward(const CondArgs &a, CSmem &s, const CTile &tl, int k
 // pivot: the products use the aligned 16 x 16 tiles of R that these rows and
 // columns meet, with zeros for the inputs outside.
 
-// Entry (w, l) of the symmetric part of circuit c's A on the reduced indices
-// (the arithmetic of the prologue's copy).
+// Entry (w, l) of the augmented symmetric matrix [[A_s, b], [b^T, 0]] of
+// circuit c on the reduced indices, index Dred standing for the pivot value
+// (the arithmetic of the prologue's copies of A_s and b).
 __device__ __forceinline__ double2 red_entry(const CondArgs &a, const CondCirc &cc, int c, int w, int l)
 {
-    const int Do = a.D_orig, ow = cc.red_to_orig[w], ol = cc.red_to_orig[l];
+    const int Do = a.D_orig, Dr = cc.Dred;
+    if (w == Dr && l == Dr) return czero();
+    if (w == Dr || l == Dr) return a.b[(size_t)c * Do + cc.red_to_orig[w == Dr ? l : w]];
+    const int ow = cc.red_to_orig[w], ol = cc.red_to_orig[l];
     const double2 x = a.A[(size_t)c * Do * Do + (size_t)ow * Do + ol];
     const double2 y = a.A[(size_t)c * Do * Do + (size_t)ol * Do + ow];
     return make_double2(0.5 * (x.x + y.x), 0.5 * (x.y + y.y));
 }
 
-// Digit fragments of every circuit's R (one block per circuit): the row
-// exponent fields (largest over the complex row) first, then the seven
-// digit planes in the register order of the A operand of mma m16n8k16.
+// Digit fragments of every circuit's augmented R (one block per circuit):
+// the row exponent fields (largest over the complex row) first, then the
+// seven digit planes in the register order of the A operand of mma
+// m16n8k16.  With b folded in as the column (and row) of the pivot value,
+// the forward's b-term b_w G_P and the reverse walk's pivot-value adjoint
+// sum_w conj(b_w) ybar_w come out of the same exact products.
 template <int KS>
 __device__ void build_cond_digits(const CondArgs &a, CSmem &s)
 {
     constexpr int P = 16 * KS;
     for (int c = blockIdx.x; c < a.B; c += gridDim.x) {
         const CondCirc &cc = a.plan[c];
-        const int Dr = cc.Dred;
+        const int Dr = cc.Dred + 1;   // augmented
         int *gA = (int *)(a.dig + (size_t)c * kDigBytes);
         uint32_t *Af = (uint32_t *)(a.dig + (size_t)c * kDigBytes + 256);
         __syncthreads();
@@ -907,15 +921,17 @@ __device__ void pair_forward_tc(const CondArgs &a, CSmem &s, const CTile &tl, in
     } else {
         for (int j = 0; j < NC; ++j) wb[(2 * j) * kCWBS] = wb[(2 * j + 1) * kCWBS] = 0.0;
     }
+    // the pivot value as the read of column Dred (b in the augmented matrix)
+    wb[(2 * NC) * kCWBS] = PV.x;
+    wb[(2 * NC + 1) * kCWBS] = PV.y;
     __syncwarp();
     double *wbw = s.wx + (size_t)(t >> 5) * 16 * KS * kCWBS;
-    cond_products<KS, false>(s, row0, 2 * N, 2 * NC, wbw, wbw);
+    cond_products<KS, false>(s, row0, 2 * N, 2 * (NC + 1), wbw, wbw);
     if (act) {
         double2 *Fw = a.F + cc.off_F;
         for (int i = 0; i < N; ++i) {
             if (!((nm >> i) & 1u)) continue;
-            double2 acc = make_double2(wb[(2 * i) * kCWBS], wb[(2 * i + 1) * kCWBS]);
-            if (HASB) acc = cadd(acc, cmul(s.br[row0 + i], PV));
+            const double2 acc = make_double2(wb[(2 * i) * kCWBS], wb[(2 * i + 1) * kCWBS]);
             const double2 val = rscale(acc, s.inv[g.den[i]]);
             Fw[fpos(cc, g.yw[i], u)] = val;
             if (kind == 0 && i == 1) {          // a diagonal of the detected modes
@@ -1018,14 +1034,16 @@ __device__ void pair_reverse_tc(const CondArgs &a, CSmem &s, const CTile &tl, in
             atomicAdd(&pb[row0 + w].y, acc.y);
         }
     }
-    double2 pv = czero();
-    if (HASB && act)
-        for (int i = 0; i < N; ++i)
-            if ((nm >> i) & 1u) pv = cfma_conj(s.br[row0 + i], make_double2(wyl[(2 * i) * kCWBS], wyl[(2 * i + 1) * kCWBS]), pv);
     __syncwarp();
+    // conj(M)^T Y on the augmented matrix, rows [row0, Dred]: the detected
+    // read adjoints (j < N), the values this pair sends to the pivot
+    // positions u - 1_t through its undetected reads (N <= j < NC), and the
+    // b-term of its own pivot-value adjoint (j = NC)
     double *wyw = s.wy + (size_t)warp * 16 * KS * kCWBS;
-    cond_products<KS, true>(s, row0, 2 * N, 2 * N, wyw, wyw);
+    cond_products<KS, true>(s, row0, 2 * (NC + 1), 2 * N, wyw, wyw);
+    __syncthreads();   // the tile's products are visible to every warp
     if (act) {
+        double2 pv = make_double2(wyl[(2 * NC) * kCWBS], wyl[(2 * NC + 1) * kCWBS]);
         for (int j = 0; j < N; ++j) {
             if (!((vmask >> j) & 1u)) continue;
             const double2 acc = make_double2(wyl[(2 * j) * kCWBS], wyl[(2 * j + 1) * kCWBS]);
@@ -1036,8 +1054,16 @@ __device__ void pair_reverse_tc(const CondArgs &a, CSmem &s, const CTile &tl, in
                 *dst = cadd(__ldcg(dst), acc);
             }
         }
+        // the pivot position (u, P) pulls from the pairs u + 1_t: from the
+        // tile's products when that pair is in the tile, else in FP64
         for (int q = 0; q < tU; ++q) {
             if (!((upmask >> q) & 1u)) continue;
+            const int tn = t + cc.ustride[q];
+            if (tn < TPB) {
+                const double *src = s.wy + (size_t)(tn >> 5) * 16 * KS * kCWBS + (tn & 31);
+                pv = cadd(pv, make_double2(src[(2 * (N + q)) * kCWBS], src[(2 * (N + q) + 1) * kCWBS]));
+                continue;
+            }
             const int un = u + cc.ustride[q];
             for (int i = 0; i < N; ++i) {
                 if (!((nm >> i) & 1u)) continue;
@@ -1048,7 +1074,7 @@ __device__ void pair_reverse_tc(const CondArgs &a, CSmem &s, const CTile &tl, in
         double2 *dst = Fb + fpos(cc, yP, u);
         *dst = cadd(__ldcg(dst), pv);
     }
-    __syncwarp();
+    __syncthreads();   // every warp has read the buffers before the next tile
 }
 
 // KS = 0: the FP64 engine; KS = 1..3: the tensor engine with 16 KS real rows.
