@@ -777,105 +777,113 @@ __device__ __forceinline__ void cond_products(const CSmem &s, int row0, int nrow
 
 // Partial dL/dA of this warp's 32 pairs, P[w][j] = sum_t Y_w(t) conj(X_j(t))
 // for rows w < N and read columns j < NC (reduced indices row0 + w and
-// row0 + j), on six-digit products as in the all-detected walk's partial
-// pass: each pair's reads are scaled by 2^(1022 - e_t) and its adjoints by
-// the inverse, the adjoints share one power of two per row over the warp;
-// real form with K = (pair, re/im), Re P from B = [Xr; Xi] and Im P from the
-// same digits with the halves swapped and the low one negated.  The result
-// is added to the warp's own slot (single writer, fixed order).
+// row0 + j), on six-digit products (the reading of the all-detected walk's
+// partial pass): each pair's reads are scaled by 2^(1022 - e_t) and its
+// adjoints by the inverse, and the adjoints share one power of two per row
+// over the warp.  The matrices are small here (N <= 2 Md rows), so the real
+// parts go into the MMA's M and N dimensions and the pairs into K: rows
+// (w, Re/Im of Y) = the warp buffer's rows of Y, columns (j, Re/Im of X) =
+// its rows of X, K = 16 pairs per MMA.  Re P = Yr Xr + Yi Xi and
+// Im P = Yi Xr - Yr Xi then join the accumulators of lanes 4 apart (the
+// Re/Im rows of one w), exactly in int64.  Each diagonal sums at most
+// 6 x 32 products below 2^14, so the fp32 accumulators stay below 2^22.
+// The result is added to the warp's own slot (single writer, fixed order).
 template <int KS>
 __device__ void cond_partials(const CondArgs &a, const CSmem &s, int circ, int row0, int N, int NC)
 {
-    constexpr int NDP = 6, NT = KS;
+    constexpr int NDP = 6, NT = 2 * KS;   // N tiles of 8 real columns (2 NC <= 16 KS)
     const int lane = threadIdx.x & 31, grp = lane >> 2, tig = lane & 3, warp = threadIdx.x >> 5;
-    const int Dm = a.Dmax, nnt = (NC + 7) >> 3, nmt = KS > 2 ? (N + 15) >> 4 : 1;
+    const int Dm = a.Dmax, nmt = (2 * N + 15) >> 4, nnt = (2 * NC + 7) >> 3;
     const double *wx = s.wx + (size_t)warp * 16 * KS * kCWBS;
     const double *wy = s.wy + (size_t)warp * 16 * KS * kCWBS;
     const int *ef = s.wf + warp * 32;
     const int *gy = s.wg + warp * 32;
     const size_t slot = (size_t)blockIdx.x * a.spb + warp;
     double *pA = (double *)(a.partA + ((size_t)circ * a.slots + slot) * Dm * Dm);
+    const int ri = grp & 1;   // Re (0) or Im (1) part of Y on this lane's rows
 #pragma unroll 1
     for (int mt = 0; mt < nmt; ++mt) {
-        float ar[NDP][NT][4], ai[NDP][NT][4];
+        float acc[NDP][NT][4];
 #pragma unroll
         for (int d = 0; d < NDP; ++d)
 #pragma unroll
             for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
-                for (int q = 0; q < 4; ++q) ar[d][nt][q] = ai[d][nt][q] = 0.f;
-        const int w0 = 16 * mt + grp, w1 = w0 + 8;
+                for (int q = 0; q < 4; ++q) acc[d][nt][q] = 0.f;
+        // this lane's rows of Y: real rows ra0 = 16 mt + grp and ra1 = ra0 + 8
+        const int ra0 = 16 * mt + grp, ra1 = ra0 + 8;
+        const int w0 = ra0 >> 1, w1 = ra1 >> 1;
         const int g0 = w0 < N ? gy[w0] : 0, g1 = w1 < N ? gy[w1] : 0;
 #pragma unroll 1
-        for (int ks = 0; ks < 4; ++ks) {
-            const int t0 = 8 * ks + tig, t1 = t0 + 4;
-            const int e0 = ef[t0], e1 = ef[t1];
+        for (int ks = 0; ks < 2; ++ks) {
+            // pairs of the k-step: 16 ks + 2 tig (+1) and 16 ks + 2 tig + 8 (+1)
+            const int tA = 16 * ks + 2 * tig, tB = tA + 8;
+            const int eA0 = ef[tA], eA1 = ef[tA + 1], eB0 = ef[tB], eB1 = ef[tB + 1];
             uint32_t aq[NDP][4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const int w = (k & 1) ? w1 : w0, t = (k & 2) ? t1 : t0, e = (k & 2) ? e1 : e0;
-                const int g = (k & 1) ? g1 : g0;
-                double yr = 0.0, yi = 0.0;
-                if (w < N && g != 0 && e != 0) {
-                    yr = wy[(2 * w) * kCWBS + t];
-                    yi = wy[(2 * w + 1) * kCWBS + t];
+                // A operand registers: k bit 0 = row half, bit 1 = K half
+                const int ra = (k & 1) ? ra1 : ra0, w = (k & 1) ? w1 : w0, g = (k & 1) ? g1 : g0;
+                const int t = (k & 2) ? tB : tA;
+                const int e0 = (k & 2) ? eB0 : eA0, e1 = (k & 2) ? eB1 : eA1;
+                double y0 = 0.0, y1 = 0.0;
+                if (w < N && g != 0) {
+                    if (e0 != 0) y0 = wy[ra * kCWBS + t];
+                    if (e1 != 0) y1 = wy[ra * kCWBS + t + 1];
                 }
-                const int fm = g - e + 1022;
                 uint32_t wd[NDP];
-                digit_words<NDP>(to_fixed_rel<NDP>(yr, fm), to_fixed_rel<NDP>(yi, fm), wd);
+                digit_words<NDP>(to_fixed_rel<NDP>(y0, g - e0 + 1022), to_fixed_rel<NDP>(y1, g - e1 + 1022), wd);
 #pragma unroll
                 for (int sl = 0; sl < NDP; ++sl) aq[sl][k] = wd[sl];
             }
 #pragma unroll
             for (int nt = 0; nt < NT; ++nt) {
                 if (nt >= nnt) continue;
-                const int j = 8 * nt + grp;
+                const int n = 8 * nt + grp;   // B column = real row of X
                 uint32_t bq[NDP][2];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const int t = h ? t1 : t0, e = h ? e1 : e0;
-                    double xr = 0.0, xi = 0.0;
-                    if (j < NC) {
-                        xr = wx[(2 * j) * kCWBS + t];
-                        xi = wx[(2 * j + 1) * kCWBS + t];
+                    const int t = h ? tB : tA;
+                    const int e0 = h ? eB0 : eA0, e1 = h ? eB1 : eA1;
+                    double x0 = 0.0, x1 = 0.0;
+                    if (n < 2 * NC) {
+                        x0 = wx[n * kCWBS + t];
+                        x1 = wx[n * kCWBS + t + 1];
                     }
                     uint32_t wd[NDP];
-                    digit_words<NDP>(to_fixed<NDP>(xr, e), to_fixed<NDP>(xi, e), wd);
+                    digit_words<NDP>(to_fixed<NDP>(x0, e0), to_fixed<NDP>(x1, e1), wd);
 #pragma unroll
                     for (int sl = 0; sl < NDP; ++sl) bq[sl][h] = wd[sl];
                 }
 #pragma unroll
-                for (int u = 0; u < NDP; ++u) {
-                    const uint32_t bi[2] = {__byte_perm(bq[u][0], 0u, 0x1032) ^ 0x8000u,
-                                            __byte_perm(bq[u][1], 0u, 0x1032) ^ 0x8000u};
+                for (int u = 0; u < NDP; ++u)
 #pragma unroll
-                    for (int sa = 0; sa + u < NDP; ++sa) {
-                        mma_f16(ar[sa + u][nt], aq[sa], bq[u]);
-                        mma_f16(ai[sa + u][nt], aq[sa], bi);
-                    }
-                }
+                    for (int sa = 0; sa + u < NDP; ++sa) mma_f16(acc[sa + u][nt], aq[sa], bq[u]);
             }
         }
 #pragma unroll
         for (int nt = 0; nt < NT; ++nt) {
             if (nt >= nnt) continue;
+            const int j = 4 * nt + tig;   // columns 2 tig (Re X) and 2 tig + 1 (Im X) of the tile
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int w = (q >> 1) ? w1 : w0, j = 8 * nt + 2 * tig + (q & 1);
-                const int g = (q >> 1) ? g1 : g0;
+            for (int h = 0; h < 2; ++h) {
+                const int w = h ? w1 : w0, g = h ? g1 : g0;
+                float t6[NDP][4];
+#pragma unroll
+                for (int d = 0; d < NDP; ++d) {
+                    t6[d][0] = acc[d][nt][2 * h];
+                    t6[d][1] = acc[d][nt][2 * h + 1];
+                }
+                const long long v0 = combine_digits<NDP>(t6, 0);   // Y_ri X_re
+                const long long v1 = combine_digits<NDP>(t6, 1);   // Y_ri X_im
+                // the other part of Y of the same w sits on the lane 4 apart
+                const long long o1 = __shfl_xor_sync(0xffffffffu, v1, 4);
+                const long long y = ri ? v0 - o1 : v0 + o1;   // Im P = Yi Xr - Yr Xi, Re P = Yr Xr + Yi Xi
                 if (w < N && j < NC && g >= 26) {
-                    float a6[NDP][4];
-#pragma unroll
-                    for (int d = 0; d < NDP; ++d) a6[d][0] = ar[d][nt][q];
-                    const long long Yr = combine_digits_wide<NDP>(a6, 0);
-#pragma unroll
-                    for (int d = 0; d < NDP; ++d) a6[d][0] = ai[d][nt][q];
-                    const long long Yi = combine_digits_wide<NDP>(a6, 0);
-                    double *dst = pA + 2 * ((size_t)(row0 + w) * Dm + row0 + j);
-                    // Y carries the product of the two fixed points over 2^48:
-                    // scale 2^(g - 1066)
-                    atomicAdd(dst, scale2(__ll2double_rn(Yr), g - 1074 + 8 * (kNDig - NDP)));
-                    atomicAdd(dst + 1, scale2(__ll2double_rn(Yi), g - 1074 + 8 * (kNDig - NDP)));
+                    // reductions without return into the warp's own slot; Y
+                    // carries the product of the two fixed points over 2^48
+                    double *dst = pA + 2 * ((size_t)(row0 + w) * Dm + row0 + j) + ri;
+                    atomicAdd(dst, scale2(__ll2double_rn(y), g - 1074 + 8 * (kNDig - NDP)));
                 }
             }
         }

@@ -808,6 +808,21 @@ struct Walk {
         return cum < a.thr;
     }
 
+    // The same, the sum split over the 32 lanes of a warp whose lanes all ask
+    // for the same (circ, lev) (integer sums: the same decision, in two loads
+    // per lane instead of lev + 1).
+    static __device__ __forceinline__ bool pivots_run_w(const DiagArgs &a, int circ, int lev)
+    {
+        if (!a.early) return lev < a.sh.L;
+        if (lev >= a.sh.L) return false;
+        const unsigned long long *l = a.lvl + (size_t)circ * (a.sh.L + 2);
+        unsigned long long cum = 0;
+        for (int n = threadIdx.x & 31; n <= lev; n += 32) cum += __ldcg(l + n);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cum += __shfl_xor_sync(0xffffffffu, cum, o);
+        return cum < a.thr;
+    }
+
     // Block-wide sum of v added to lvl[circ][n] (thread 0).
     static __device__ void add_level_prob(const DiagArgs &a, int circ, int n, double v)
     {
@@ -1363,7 +1378,7 @@ struct Walk {
     // the DIAG values.
     template <bool HASB>
     static __device__ __forceinline__ double2 diag_adjoint(const DiagArgs &a, const Smem &s, int circ, int K,
-                                                           int lev, const ApGeom &g, const Dig &e)
+                                                           int lev, const ApGeom &g, const Dig &e, bool up)
     {
         const DiagShape &sh = a.sh;
         double fe = 1.0;
@@ -1371,7 +1386,7 @@ struct Walk {
         const int xK = e(K) + 1;
         double2 acc = rscale(a.gprobs[oix(a, circ) + box_diag(sh, sh.global ? g.wdiag : g.pout)],
                              fe * (double)xK);
-        if (pivots_run(a, circ, lev + 1)) {
+        if (up) {   // level lev + 1 ran: its AP pivots left the scratch slots
             const double2 *sc = a.scratch + (size_t)circ * sh.n_ap;
             const int64_t rx = g.wdiag - cum_full(s, lev + 1);
             for (int k = 0; k <= K; ++k)
@@ -1404,7 +1419,7 @@ struct Walk {
         double2 *Fb = a.Fbar + (size_t)tl.circ * sh.circ_alloc;
         const unsigned r = tl.rank0 + t;
         const bool act = r < tl.count;
-        const bool up = pivots_run(a, tl.circ, lev + 1);   // level lev + 1 ran in reverse
+        const bool up = pivots_run_w(a, tl.circ, lev + 1);   // level lev + 1 ran in reverse
         Dig e;
         ApGeom g{};
         if (act) {
@@ -1421,7 +1436,7 @@ struct Walk {
                     const int64_t addr = ap_write_addr(sh, g, e, K, i, s, &den);
                     // T2 and P values of a level whose pivots did not run have no
                     // reader: their adjoint is zero (Fbar is not cleared for b = 0)
-                    const double2 y = i == 1 ? diag_adjoint<HASB>(a, s, tl.circ, K, lev, g, e)
+                    const double2 y = i == 1 ? diag_adjoint<HASB>(a, s, tl.circ, K, lev, g, e, up)
                                       : up ? __ldcg(Fb + addr) : make_double2(0, 0);
                     v = rscale(y, s.inv[den]);
                 }
@@ -1565,7 +1580,7 @@ struct Walk {
         double2 *Fb = a.Fbar + (size_t)tl.circ * sh.circ_alloc;
         const unsigned r = tl.rank0 + t;
         const bool act = r < tl.count;
-        const bool up = pivots_run(a, tl.circ, lev + 1);   // level lev + 1 ran in reverse
+        const bool up = pivots_run_w(a, tl.circ, lev + 1);   // level lev + 1 ran in reverse
         Dig e;
         ApGeom g{};
         if (act) {
@@ -1578,7 +1593,7 @@ struct Walk {
                     const int64_t addr = ap_write_addr(sh, g, e, K, i, s, &den);
                     double2 y;
                     if (i == 1) {
-                        y = diag_adjoint<HASB>(a, s, tl.circ, K, lev, g, e);
+                        y = diag_adjoint<HASB>(a, s, tl.circ, K, lev, g, e, up);
                         Fb[addr] = y;   // complete: the partial pass reads it back
                     } else {
                         // T2 and P values of a level whose pivots did not run have no
@@ -1672,7 +1687,7 @@ struct Walk {
         const double2 *Fb = a.Fbar + (size_t)tl.circ * sh.circ_alloc;
         const unsigned r = tl.rank0 + t;
         const bool act = r < tl.count;
-        const bool up = pivots_run(a, tl.circ, lev + 1);
+        const bool up = pivots_run_w(a, tl.circ, lev + 1);
         int fx = 0;
         double2 FPv = make_double2(0, 0);
         if (act) {
@@ -1826,7 +1841,7 @@ struct Walk {
                 const int nt = phase_tiles(a, s, 0, lev);
                 run_tiles(a.ctr + 2 * lev + 1, nt, [&](int tile) {
                     const TileId tl = decode_tile(a, s, 0, lev, tile);
-                    if (!pivots_run(a, tl.circ, lev)) return;
+                    if (!pivots_run_w(a, tl.circ, lev)) return;
                     if constexpr (TC) {
                         if (hb) ap_reverse_tile_tc<true>(a, s, tl, tl.seg, lev);
                         else ap_reverse_tile_tc<false>(a, s, tl, tl.seg, lev);
@@ -1842,7 +1857,7 @@ struct Walk {
                 const int nt = phase_tiles(a, s, 1, lev);
                 run_tiles(a.ctr + 2 * lev, nt, [&](int tile) {
                     const TileId tl = decode_tile(a, s, 1, lev, tile);
-                    if (!pivots_run(a, tl.circ, lev)) return;
+                    if (!pivots_run_w(a, tl.circ, lev)) return;
                     if constexpr (TC) dp_reverse_tile_tc(a, s, tl, lev);
                     else dp_reverse_tile(a, s, tl, lev);
                 });
@@ -1869,7 +1884,7 @@ struct Walk {
             const int nt = phase_tiles(a, s, 0, lev);
             run_tiles(ctr + 2 * lev + 1, nt, [&](int tile) {
                 const TileId tl = decode_tile(a, s, 0, lev, tile);
-                if (!pivots_run(a, tl.circ, lev)) return;
+                if (!pivots_run_w(a, tl.circ, lev)) return;
                 if (hb) ap_partial_tile<true>(a, s, tl, tl.seg, lev);
                 else ap_partial_tile<false>(a, s, tl, tl.seg, lev);
             });
@@ -1877,7 +1892,7 @@ struct Walk {
                 const int nd = phase_tiles(a, s, 1, lev);
                 run_tiles(ctr + 2 * lev, nd, [&](int tile) {
                     const TileId tl = decode_tile(a, s, 1, lev, tile);
-                    if (!pivots_run(a, tl.circ, lev)) return;
+                    if (!pivots_run_w(a, tl.circ, lev)) return;
                     dp_partial_tile(a, s, tl, lev);
                 });
             }

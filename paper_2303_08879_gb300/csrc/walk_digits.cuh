@@ -104,20 +104,24 @@ __device__ __forceinline__ void mma_f16(float *c, const uint32_t *a, const uint3
 // pattern is 0x4B400000 + acc_d, so the integers come from one add each;
 // the constant those offsets contribute is removed at the end (modulo
 // 2^64, where the true sum fits).
+template <int ND = kNDig>
 __host__ __device__ constexpr unsigned long long combine_bias()
 {
     unsigned long long y = kMagicBits;
-    for (int d = 1; d < kNDig - 1; ++d) y = (y << 8) + kMagicBits;
+    for (int d = 1; d < ND - 1; ++d) y = (y << 8) + kMagicBits;
     return y + (kMagicBits >> 8);
 }
 
-__device__ __forceinline__ long long combine_digits(const float (&acc)[kNDig][4], int q)
+// ND diagonals (ND = 7 above; 6 for the partial sums), each below 2^22:
+// sum_d acc_d 256^(ND - 2 - d), the last one floored.
+template <int ND = kNDig>
+__device__ __forceinline__ long long combine_digits(const float (&acc)[ND][4], int q)
 {
     unsigned long long Y = __float_as_uint(acc[0][q] + 12582912.0f);
 #pragma unroll
-    for (int d = 1; d < kNDig - 1; ++d) Y = (Y << 8) + __float_as_uint(acc[d][q] + 12582912.0f);
-    Y += __float_as_uint(acc[kNDig - 1][q] + 12582912.0f) >> 8;
-    constexpr unsigned long long bias = combine_bias();
+    for (int d = 1; d < ND - 1; ++d) Y = (Y << 8) + __float_as_uint(acc[d][q] + 12582912.0f);
+    Y += __float_as_uint(acc[ND - 1][q] + 12582912.0f) >> 8;
+    constexpr unsigned long long bias = combine_bias<ND>();
     return (long long)(Y - bias);
 }
 
