@@ -374,9 +374,25 @@ __device__ int phase_tiles(const CondArgs &a, CSmem &s, int kind, int lev)
         s.ctiles[c + 1] = n;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        s.ctiles[0] = 0;
-        for (int c = 0; c < a.B; ++c) s.ctiles[c + 1] += s.ctiles[c];
+    // prefix sums over the circuits by warp 0: each lane a contiguous run of
+    // entries, then an exclusive scan of the runs' totals across the lanes
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x, per = (a.B + 31) / 32;
+        const int lo = 1 + lane * per, hi = min(lo + per, a.B + 1);
+        int run = 0;
+        for (int c = lo; c < hi; ++c) {
+            run += s.ctiles[c];
+            s.ctiles[c] = run;
+        }
+        int ex = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, ex, o);
+            if (lane >= o) ex += v;
+        }
+        ex -= run;   // exclusive: the runs of the lanes before this one
+        for (int c = lo; c < hi; ++c) s.ctiles[c] += ex;
+        if (lane == 0) s.ctiles[0] = 0;
     }
     __syncthreads();
     return s.ctiles[a.B];

@@ -108,7 +108,8 @@ struct Smem {
     int *wf;          // tensor-core VJP: [TPB] exponent field of each pivot's largest read
     int *wg;          // tensor-core VJP: per-warp [32] row exponents of the partial dL/dA
     int *idx;         // [M][TPB] box indices per pivot
-    int *tiles;       // [M + 2] tile prefix sums of the current phase
+    int *tiles;       // [M + 2] tile prefix sums of the current phase, then [M + 2] the
+                      // pivots of each segment
     int loaded_circ;
     int multi_key;    // several shapes: (group, level, kind) the tables hold, or -1
 };
@@ -208,7 +209,7 @@ struct Walk {
             }
             q.idx = n; n += (size_t)M * TPB * sizeof(int); al();
         }
-        q.tiles = n; n += (M + 2) * sizeof(int);
+        q.tiles = n; n += 2 * (M + 2) * sizeof(int);
         q.bytes = n + 64;
         return q;
     }
@@ -280,20 +281,31 @@ struct Walk {
     }
 
     // Offset of level `lev` in family K: sum over the levels below of the
-    // family's counts Pf(K, l, C_K - 1).  Thread 0 fills s.cum0 / s.cum1 /
-    // s.cum2 for the level of each phase, the one below and the one above.
+    // family's counts Pf(K, l, C_K - 1).  Warp 0 fills s.cum0 / s.cum1 /
+    // s.cum2 for the level of each phase, the one below and the one above:
+    // its lanes take the levels l = lane (mod 32) and a butterfly adds them,
+    // instead of one thread walking M x lev table entries in a row while the
+    // block waits.
     static __device__ void phase_offsets(const DiagShape &sh, Smem &s, int lev)
     {
+        const int lane = threadIdx.x & 31;
         for (int K = 0; K < sh.M; ++K) {
-            int64_t c0 = 0, c1 = 0;
-            for (int l = 0; l < lev; ++l) {
-                const int64_t n = Pf(s, K, l, sh.C[K] - 1);
+            long long c0 = 0, c1 = 0;
+            for (int l = lane; l < lev; l += 32) {
+                const long long n = Pf(s, K, l, sh.C[K] - 1);
                 c0 += n;
                 if (l + 1 < lev) c1 += n;
             }
-            s.cum0[K] = c0;
-            s.cum1[K] = c1;
-            s.cum2[K] = c0 + Pf(s, K, lev, sh.C[K] - 1);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                c0 += __shfl_xor_sync(0xffffffffu, c0, o);
+                c1 += __shfl_xor_sync(0xffffffffu, c1, o);
+            }
+            if (lane == 0) {
+                s.cum0[K] = c0;
+                s.cum1[K] = c1;
+                s.cum2[K] = c0 + Pf(s, K, lev, sh.C[K] - 1);
+            }
         }
     }
 
@@ -868,13 +880,14 @@ struct Walk {
     {
         const DiagShape &sh = a.sh;
         __syncthreads();
+        if (threadIdx.x < 32) phase_offsets(sh, s, lev);
         if (threadIdx.x == 0) {
-            phase_offsets(sh, s, lev);
             int acc = 0;
             const int nseg = (kind == 0) ? sh.M : 1;
             for (int k = 0; k < nseg; ++k) {
-                s.tiles[k] = acc;
                 const unsigned cnt = level_count(sh, s, kind == 0 ? k : 0, 1, lev);
+                s.tiles[k] = acc;
+                s.tiles[sh.M + 2 + k] = (int)cnt;
                 acc += (int)((cnt + TPB - 1) / TPB);
             }
             s.tiles[nseg] = acc;
@@ -895,7 +908,7 @@ struct Walk {
         while (k + 1 < nseg && r >= s.tiles[k + 1]) ++k;
         t.seg = k;
         t.rank0 = (unsigned)(r - s.tiles[k]) * TPB;
-        t.count = level_count(sh, s, kind == 0 ? k : 0, 1, lev);
+        t.count = (unsigned)s.tiles[sh.M + 2 + k];   // the segment's pivots, from phase_tiles
         return t;
     }
 
