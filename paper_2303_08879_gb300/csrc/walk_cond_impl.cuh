@@ -745,6 +745,12 @@ __device__ __forceinline__ void cond_products(const CSmem &s, int row0, int nrow
             }
         fm = max(fm, __shfl_xor_sync(0xffffffffu, fm, 1));
         fm = max(fm, __shfl_xor_sync(0xffffffffu, fm, 2));
+        // an N tile whose inputs all count as zero (points past the u-block's
+        // end) has zero products: write them without the MMAs
+        if (!__any_sync(0xffffffffu, fm >= 26)) {
+            for (int r = tig; r < nrow; r += 4) out[r * kCWBS + p] = 0.0;
+            continue;
+        }
         uint32_t bq[kNDig][KS][2];
 #pragma unroll
         for (int ks = 0; ks < KS; ++ks)

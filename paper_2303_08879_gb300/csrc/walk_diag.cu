@@ -307,6 +307,14 @@ int diag_grid_size(const DiagShape &sh, bool vjp, unsigned flags, int batch, int
     return FK_OK;
 }
 
+// A batch with at least two circuits per block walks circuit by circuit in
+// each block (block barriers between phases) rather than level by level over
+// the grid: small circuits then stop paying a grid barrier per level.
+static int circuit_per_block(int grid, int batch)
+{
+    return 2 * (int64_t)grid <= batch ? 1 : 0;
+}
+
 static int launch_coop(const void *fn, int grid, int tpb, size_t smem, DiagArgs *args, cudaStream_t st)
 {
     void *params[] = {args};
@@ -384,6 +392,7 @@ int launch_diag_forward(const DiagShape &sh, int batch, unsigned flags, const vo
     int rc = diag_grid_size(sh, false, flags, batch, &grid);
     if (rc) return rc;
     a.grid = grid;
+    a.pc = circuit_per_block(grid, batch);
     int bps = 0, tpb = 0, spb = 1;
     size_t smem = 0;
     const void *fn = nullptr;
@@ -451,6 +460,7 @@ int launch_diag_vjp(const DiagShape &sh, int batch, unsigned flags, const void *
         DiagArgs w = a;
         const int64_t useful = useful_blocks(sh, batch, wtpb, false);
         w.grid = (int)((int64_t)per * sms < useful ? (int64_t)per * sms : useful);
+        w.pc = circuit_per_block(w.grid, batch);
         if ((rc = launch_coop(wfn, w.grid, wtpb, wsmem, &w, st)) != 0) return rc;
         void *ev = nullptr;
         {
@@ -459,6 +469,7 @@ int launch_diag_vjp(const DiagShape &sh, int batch, unsigned flags, const void *
         }
         if (ev && cudaEventRecord((cudaEvent_t)ev, st) != cudaSuccess) return FK_ECUDA;
     }
+    a.pc = tc_engine_for(sh, tn) ? 0 : circuit_per_block(lay.grid_vjp, batch);   // the partial pass has no levels
     return launch_coop(fn, lay.grid_vjp, tpb, smem, &a, st);
 }
 

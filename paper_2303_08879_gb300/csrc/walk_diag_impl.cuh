@@ -83,6 +83,10 @@ struct DiagArgs {
     // debug-checks build: per-level timestamps (see trace_mark), or null
     unsigned long long *trace;
     int trace_cap;
+    // circuit-per-block mode (batches of at least twice as many circuits as
+    // blocks): each block walks whole circuits taken from a counter, with block
+    // barriers between its phases instead of grid barriers
+    int pc;
 };
 
 // ------------------------------------------------------------ shared memory
@@ -563,6 +567,12 @@ struct Walk {
                 }
             fm = max(fm, __shfl_xor_sync(0xffffffffu, fm, 1));
             fm = max(fm, __shfl_xor_sync(0xffffffffu, fm, 2));
+            // an N tile whose inputs all count as zero (inactive pivots at a
+            // tile's end) has zero products: write them without the MMAs
+            if (!__any_sync(0xffffffffu, fm >= 26)) {
+                for (int r = tig; r < n2; r += 4) out[r * WBS + p] = 0.0;
+                continue;
+            }
             uint32_t bq[NDIG][KS][2];
 #pragma unroll
             for (int ks = 0; ks < KS; ++ks)
@@ -679,6 +689,7 @@ struct Walk {
             for (int ks = 0; ks < 4; ++ks) {
                 const int t0 = 8 * ks + tig, t1 = t0 + 4;
                 const int e0 = ef[t0], e1 = ef[t1];
+                if (!__any_sync(0xffffffffu, e0 != 0 || e1 != 0)) continue;   // 8 pivots without reads
                 uint32_t aq[NDP][4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
@@ -867,6 +878,29 @@ struct Walk {
             __syncthreads();
             tile = s_next[k & 1];
             ++k;
+        }
+    }
+
+    // Circuit-per-block mode: the next circuit for this block (all threads
+    // get the same value), from the counter ctr, or a.B when none is left.
+    static __device__ int next_circuit(int *ctr)
+    {
+        __shared__ int s_c;
+        __syncthreads();
+        if (threadIdx.x == 0) s_c = atomicAdd(ctr, 1);
+        __syncthreads();
+        return s_c;
+    }
+
+    // The tiles of circuit c in a phase of nt tiles (circuit-major numbering),
+    // one after the other in this block.
+    template <class Fn>
+    static __device__ void circuit_tiles(const DiagArgs &a, int c, int nt, Fn fn)
+    {
+        const int per = nt / a.B;
+        for (int j = 0; j < per; ++j) {
+            fn(c * per + j);
+            __syncthreads();
         }
     }
 
@@ -1800,6 +1834,35 @@ struct Walk {
             if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&a.ctl->status, 0, (int)FK_EBZERO);
             return;
         }
+        if (a.pc) {
+            for (int c = next_circuit(a.ctr + 2 * sh.L); c < a.B; c = next_circuit(a.ctr + 2 * sh.L)) {
+                for (int lev = 0; lev < sh.L; ++lev) {
+                    if (hb) {
+                        circuit_tiles(a, c, phase_tiles(a, s, 1, lev), [&](int tile) {
+                            const TileId tl = decode_tile(a, s, 1, lev, tile);
+                            if (pivots_run(a, c, lev)) dp_forward_tile(a, s, tl, lev);
+                        });
+                    }
+                    circuit_tiles(a, c, phase_tiles(a, s, 0, lev), [&](int tile) {
+                        const TileId tl = decode_tile(a, s, 0, lev, tile);
+                        if (!pivots_run(a, c, lev)) return;
+                        if (a.early) {
+                            if (hb) ap_forward_tile<true, true>(a, s, tl, tl.seg, lev);
+                            else ap_forward_tile<false, true>(a, s, tl, tl.seg, lev);
+                        } else {
+                            if (hb) ap_forward_tile<true, false>(a, s, tl, tl.seg, lev);
+                            else ap_forward_tile<false, false>(a, s, tl, tl.seg, lev);
+                        }
+                    });
+                }
+                if (a.early && a.levels != nullptr && threadIdx.x == 0) {
+                    int n = 0;
+                    while (n < sh.L && pivots_run(a, c, n)) ++n;
+                    a.levels[c] = n + 1;
+                }
+            }
+            return;
+        }
         for (int lev = 0; lev < sh.L; ++lev) {
             if (hb) {
                 const int nt = phase_tiles(a, s, 1, lev);
@@ -1847,6 +1910,33 @@ struct Walk {
         const int hb = *(volatile int *)&a.ctl->has_b;
         if (hb && !sh.has_b) {
             if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&a.ctl->status, 0, (int)FK_EBZERO);
+            return;
+        }
+        if (a.pc) {
+            for (int c = next_circuit(a.ctr + 2 * sh.L); c < a.B; c = next_circuit(a.ctr + 2 * sh.L)) {
+                for (int lev = sh.L - 1; lev >= 0; --lev) {
+                    circuit_tiles(a, c, phase_tiles(a, s, 0, lev), [&](int tile) {
+                        const TileId tl = decode_tile(a, s, 0, lev, tile);
+                        if (!pivots_run_w(a, c, lev)) return;
+                        if constexpr (TC) {
+                            if (hb) ap_reverse_tile_tc<true>(a, s, tl, tl.seg, lev);
+                            else ap_reverse_tile_tc<false>(a, s, tl, tl.seg, lev);
+                        } else {
+                            if (hb) ap_reverse_tile<true>(a, s, tl, tl.seg, lev);
+                            else ap_reverse_tile<false>(a, s, tl, tl.seg, lev);
+                        }
+                    });
+                    if (hb) {
+                        circuit_tiles(a, c, phase_tiles(a, s, 1, lev), [&](int tile) {
+                            const TileId tl = decode_tile(a, s, 1, lev, tile);
+                            if (!pivots_run_w(a, c, lev)) return;
+                            if constexpr (TC) dp_reverse_tile_tc(a, s, tl, lev);
+                            else dp_reverse_tile(a, s, tl, lev);
+                        });
+                    }
+                }
+            }
+            if constexpr (!TC) finish_vjp(a, hb);
             return;
         }
         for (int lev = sh.L; lev >= 0; --lev) {
