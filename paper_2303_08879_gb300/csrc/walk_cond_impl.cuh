@@ -1109,7 +1109,7 @@ __device__ void pair_reverse_tc(const CondArgs &a, CSmem &s, const CTile &tl, in
 
 // KS = 0: the FP64 engine; KS = 1..3: the tensor engine with 16 KS real rows.
 template <int KS>
-__global__ void __launch_bounds__(TPB) cond_forward_kernel(const __grid_constant__ CondArgs a)
+__global__ void __launch_bounds__(TPB, (KS == 1 ? 4 : 1)) cond_forward_kernel(const __grid_constant__ CondArgs a)
 {
     FK_DBG_BEGIN(a.ctl);
     if (skip_walk(a.ctl)) return;   // the input scan found a NaN or Inf
@@ -1349,7 +1349,7 @@ __device__ void step1_reverse(const CondArgs &a, CSmem &s, int c, bool hb)
 }
 
 template <int KS>
-__global__ void __launch_bounds__(TPB) cond_vjp_kernel(const __grid_constant__ CondArgs a)
+__global__ void __launch_bounds__(TPB, (KS == 1 ? 4 : 1)) cond_vjp_kernel(const __grid_constant__ CondArgs a)
 {
     FK_DBG_BEGIN(a.ctl);
     if (skip_walk(a.ctl)) return;   // the input scan found a NaN or Inf

@@ -61,7 +61,9 @@ def gpu_cond(fd, A, b, c, cuts, mask):
 
 CASES = [((4, 3), (0, 1)), ((3, 4, 3), (0, 1, 1)), ((3, 2, 3, 3), (0, 0, 1, 1)),
          ((3, 4, 3), (1, 0, 1)), ((5, 4, 2), (1, 1, 0)), ((4, 1, 3), (1, 1, 0)),
-         ((3, 3), (0, 0)), ((1, 4, 3), (0, 1, 1)), ((4, 3, 1), (1, 1, 0)), ((6, 5), (1, 0))]
+         ((3, 3), (0, 0)), ((1, 4, 3), (0, 1, 1)), ((4, 3, 1), (1, 1, 0)), ((6, 5), (1, 0)),
+         # the tensor engine's two and three 16-row K steps (2 (2M + 1) real rows)
+         ((2, 3, 2, 2, 3), (1, 1, 0, 1, 0)), ((2, 2, 2, 2, 2, 2, 2, 3), (1, 1, 1, 1, 1, 1, 1, 0))]
 
 
 @pytest.mark.parametrize("cut,mask", CASES)
@@ -148,7 +150,8 @@ def oracle_cond_vjp(A, b, c, cut, mask, gbar):
 
 VJP_CASES = [((4, 3), (0, 1), True), ((3, 4, 3), (1, 1, 0), True), ((3, 4, 3), (1, 1, 0), False),
              ((3, 2, 3, 3), (0, 0, 1, 1), True), ((4, 1, 3), (1, 1, 0), True), ((3, 3), (0, 0), True),
-             ((5, 4), (1, 0), False)]
+             ((5, 4), (1, 0), False), ((2, 3, 2, 2, 3), (1, 1, 0, 1, 0), True),
+             ((2, 2, 2, 2, 2, 2, 2, 3), (1, 1, 1, 1, 1, 1, 1, 0), True)]
 
 
 @pytest.mark.parametrize("cut,mask,withb", VJP_CASES)
