@@ -48,10 +48,10 @@ NCIRC = 16
 # in proportion to them.  Valid only for the kernel source it was measured on
 # (sha256 prefix of csrc/walk_diag_impl.cuh + walk_digits.cuh) and the engine / tile shape; reported
 # as null once either differs.
-TRAFFIC = {"kernel_sha": "a373a76e12f053b1", "tuning": ["tensor", 128, 4, 0],
-           "bytes_per_launch": {"diag_forward_kernel": 8 * (495559680 + 854166784),
-                                "diag_vjp_kernel": 8 * (701991680 + 802892544),
-                                "diag_vjp_partials_kernel": 8 * (1731138816 + 133250560)}}
+TRAFFIC = {"kernel_sha": "c3afe7d126e57f2e", "tuning": ["tensor", 128, 4, 0],
+           "bytes_per_launch": {"diag_forward_kernel": 8 * (495795456 + 853985792),
+                                "diag_vjp_kernel": 8 * (702128384 + 803239424),
+                                "diag_vjp_partials_kernel": 8 * (1728069120 + 132130816)}}
 
 FALLBACK_HBM_GBS = 6800.0
 
