@@ -88,6 +88,8 @@ struct CSmem {
                                 // row exponents of the partial dL/dA
     PGeom *geo;                 // the current tile's pivot
     int *ctiles;                // [MAXB + 1] tile prefix over circuits
+    unsigned char *s1;          // the per-tile buffers, free while step 1 runs: its
+    size_t s1_bytes;            // staging area (amplitudes and levels of the u-block)
     int loaded;
 };
 
@@ -169,6 +171,9 @@ __device__ CSmem carve(const CondArgs &a, bool vjp, int KS)
     s.wg = (int *)at(q.wg);
     s.geo = (PGeom *)at(q.geo);
     s.ctiles = (int *)at(q.ctiles);
+    const size_t lo = KS > 0 ? q.wx : q.R3;   // per-tile buffers up to the tile's geometry
+    s.s1 = smem_raw + lo;
+    s.s1_bytes = q.geo - lo;
     s.loaded = -1;
     return s;
 }
@@ -310,41 +315,112 @@ __device__ void prologue(const CondArgs &a)
 // ------------------------------------------------------------ step 1
 // The zero-photon block (detected part 0): eq. (recrel) over the undetected
 // sub-lattice, written from the pivot u - 1_w with w its first nonzero index.
-__device__ void step1_forward(const CondArgs &a, CSmem &s, int c, bool hb)
+// One block per circuit, level by level.  When the u-block fits, its values
+// and levels are staged in the block's per-tile buffers (free during step 1),
+// so a level reads the two below it from shared memory; otherwise it reads
+// them from F.
+
+// Strides and cutoffs of the u-block positions, copied to shared memory.
+__device__ void stage_ubox(const CondCirc &cc, int *ust, int *ucu)
+{
+    __syncthreads();
+    if (threadIdx.x < 2 * cc.nU) {
+        ust[threadIdx.x] = cc.ustride[threadIdx.x];
+        ucu[threadIdx.x] = cc.CU[threadIdx.x >> 1];
+    }
+    __syncthreads();
+}
+
+// Whether the u-block's values (16 B) and levels (1 B) fit the staging area.
+__device__ __forceinline__ bool step1_staged(const CSmem &s, const CondCirc &cc)
+{
+    return cc.Lu < 256 && (size_t)cc.U2 * 17 <= s.s1_bytes;
+}
+
+template <bool SMEM>
+__device__ __forceinline__ double2 ld_u(const double2 *p)
+{
+    if constexpr (SMEM) return *p;
+    else return __ldcg(p);
+}
+
+// Digits of u (dig[0, tU)), their sum and the first nonzero position (tU: none).
+__device__ __forceinline__ int u_digits(int u, int tU, const int *ust, const int *ucu, int *dig, int *first)
+{
+    int sum = 0, f0 = tU;
+    for (int t = 0; t < tU; ++t) {
+        dig[t] = (u / ust[t]) % ucu[t];
+        sum += dig[t];
+        if (f0 == tU && dig[t] > 0) f0 = t;
+    }
+    *first = f0;
+    return sum;
+}
+
+// X: where the values live (shared staging area or F itself); lv: levels of
+// the staged u-block (SMEM only).
+template <bool SMEM>
+__device__ void step1_forward_levels(const CondArgs &a, CSmem &s, int c, bool hb, double2 *X,
+                                     const unsigned char *lv, const int *ust, const int *ucu)
 {
     const CondCirc &cc = a.plan[c];
-    load_circuit(a, s, c);
     double2 *F = a.F + cc.off_F;
-    const int tU = 2 * cc.nU, Db = 2 * cc.dsh.M;
-    for (int lev = 0; lev <= cc.Lu; ++lev) {
-        for (int u = threadIdx.x; u < cc.U2; u += blockDim.x) {
-            int dig[2 * FK_MAXU], sum = 0, w = -1;
-            for (int t = 0; t < tU; ++t) {
-                dig[t] = udigit(cc, u, t);
-                sum += dig[t];
-                if (w < 0 && dig[t] > 0) w = t;
-            }
+    const int tU = 2 * cc.nU, Db = 2 * cc.dsh.M, U2 = cc.U2, Lu = cc.Lu, nU = cc.nU;
+    for (int lev = 0; lev <= Lu; ++lev) {
+        for (int u = threadIdx.x; u < U2; u += blockDim.x) {
+            if (SMEM && lv[u] != lev) continue;
+            int dig[2 * FK_MAXU], w;
+            const int sum = u_digits(u, tU, ust, ucu, dig, &w);
             if (sum != lev) continue;
             double2 v;
             if (lev == 0) {
                 v = a.c[c];
             } else {
-                const int P = u - cc.ustride[w];
-                const int Pw = dig[w] - 1;
-                double2 acc = hb ? cmul(s.br[Db + w], __ldcg(F + fpos(cc, 0, P))) : czero();
+                const int P = u - ust[w];
+                double2 acc = hb ? cmul(s.br[Db + w], ld_u<SMEM>(X + (SMEM ? P : fpos(cc, 0, P)))) : czero();
                 for (int t = 0; t < tU; ++t) {
                     const int Pt = dig[t] - (t == w ? 1 : 0);
                     if (Pt <= 0) continue;
-                    acc = cfma(s.Ar[(Db + w) * a.Dmax + Db + t], __ldcg(F + fpos(cc, 0, P - cc.ustride[t])), acc);
+                    const int r = P - ust[t];
+                    acc = cfma(s.Ar[(Db + w) * a.Dmax + Db + t], ld_u<SMEM>(X + (SMEM ? r : fpos(cc, 0, r))), acc);
                 }
-                v = rscale(acc, s.inv[Pw + 1]);
+                v = rscale(acc, s.inv[dig[w]]);
             }
+            if (SMEM) X[u] = v;
             F[fpos(cc, 0, u)] = v;
-            int ket, bra;
-            const double f = uscale(cc, s, u, &ket, &bra);
+            // output (ket, bra) of u and sqrt(prod u_t!)
+            double f = 1.0;
+            int ket = 0, bra = 0;
+            for (int q = 0; q < nU; ++q) {
+                const int uk = dig[2 * q], ub = dig[2 * q + 1];
+                f *= s.sqf[uk] * s.sqf[ub];
+                ket = ket * ucu[2 * q] + uk;
+                bra = bra * ucu[2 * q] + ub;
+            }
             a.rho[rpos(cc, (int64_t)ket * cc.NUo + bra)] = rscale(v, f);
         }
         __syncthreads();
+    }
+}
+
+__device__ void step1_forward(const CondArgs &a, CSmem &s, int c, bool hb)
+{
+    __shared__ int ust[2 * FK_MAXU], ucu[2 * FK_MAXU];
+    const CondCirc &cc = a.plan[c];
+    load_circuit(a, s, c);
+    stage_ubox(cc, ust, ucu);
+    if (step1_staged(s, cc)) {
+        const int tU = 2 * cc.nU, U2 = cc.U2;
+        double2 *X = (double2 *)s.s1;
+        unsigned char *lv = (unsigned char *)(X + U2);
+        for (int u = threadIdx.x; u < U2; u += blockDim.x) {
+            int dig[2 * FK_MAXU], f0;
+            lv[u] = (unsigned char)u_digits(u, tU, ust, ucu, dig, &f0);
+        }
+        __syncthreads();
+        step1_forward_levels<true>(a, s, c, hb, X, lv, ust, ucu);
+    } else {
+        step1_forward_levels<false>(a, s, c, hb, a.F + cc.off_F, nullptr, ust, ucu);
     }
 }
 
@@ -529,27 +605,26 @@ __device__ __forceinline__ int64_t geo_index(const CondArgs &a, const CondCirc &
 }
 
 // The pivot geometry of every circuit, once per launch: one block per
-// circuit, a thread per pivot of each (kind, level, segment).
+// (circuit, kind, level), a thread per pivot of each segment.
 __device__ void build_geo(const CondArgs &a, const CSmem &s)
 {
-    for (int c = blockIdx.x; c < a.B; c += gridDim.x) {
+    const int nitem = a.B * 2 * a.Lmax;
+    for (int it = blockIdx.x; it < nitem; it += gridDim.x) {
+        const int c = it / (2 * a.Lmax), kind = (it / a.Lmax) & 1, lev = it % a.Lmax;
         const CondCirc &cc = a.plan[c];
         const DiagShape &ds = cc.dsh;
-        if (ds.M == 0) continue;
+        if (ds.M == 0 || lev >= ds.L) continue;
         const LevelTab W = ltab(a, cc);
-        for (int kind = 0; kind < 2; ++kind)
-            for (int lev = 0; lev < ds.L; ++lev) {
-                unsigned pb = 0;
-                const int nseg = kind == 0 ? ds.M : 1;
-                for (int k = 0; k < nseg; ++k) {
-                    const unsigned cnt = seg_count(a, cc, kind, k, lev);
-                    for (unsigned r = threadIdx.x; r < cnt; r += blockDim.x) {
-                        const Dig e = unrank(ds.C, ds.M, W, kind == 0 ? k : 0, 1, lev, r);
-                        a.geo[geo_index(a, cc, kind, lev, pb, r)] = kind == 0 ? ap_geom(ds, e, k, s) : dp_geom(ds, e);
-                    }
-                    pb += cnt;
-                }
+        unsigned pb = 0;
+        const int nseg = kind == 0 ? ds.M : 1;
+        for (int k = 0; k < nseg; ++k) {
+            const unsigned cnt = seg_count(a, cc, kind, k, lev);
+            for (unsigned r = threadIdx.x; r < cnt; r += blockDim.x) {
+                const Dig e = unrank(ds.C, ds.M, W, kind == 0 ? k : 0, 1, lev, r);
+                a.geo[geo_index(a, cc, kind, lev, pb, r)] = kind == 0 ? ap_geom(ds, e, k, s) : dp_geom(ds, e);
             }
+            pb += cnt;
+        }
     }
 }
 
@@ -1306,46 +1381,137 @@ __device__ void diag_reverse(const CondArgs &a, CSmem &s, const CTile &tl, int l
     *dst = cadd(__ldcg(dst), acc);
 }
 
-// Step 1 in reverse, one thread per circuit, u in decreasing flat order (every
-// reader of u has a larger flat index).
-__device__ void step1_reverse(const CondArgs &a, CSmem &s, int c, bool hb)
+// Sum of a double2 over the 32 lanes (xor butterfly: a fixed order, so the
+// result does not depend on timing).
+__device__ __forceinline__ double2 warp_sum(double2 v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+    return v;
+}
+
+// Sum of one double2 per thread over the block, in a fixed order; every
+// thread gets the result.
+__device__ double2 block_sum(double2 v)
+{
+    __shared__ double2 part[TPB / 32];
+    v = warp_sum(v);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double2 r = czero();
+    for (int k = 0; k < TPB / 32; ++k) r = cadd(r, part[k]);
+    return r;
+}
+
+// Step 1 in reverse, one block per circuit, the levels of the undetected
+// sub-lattice from the top down.  Every reader of a point v lies one level
+// above it (u = v + 1_w, the b term) or two (u = v + 1_t + 1_w with t >= w,
+// the A term), w being the first nonzero index of u, i.e. w <= the first
+// nonzero index of v.  Each thread owns the points of the level and pulls
+// their adjoint from those readers, whose adjoints are final; no two threads
+// write one point.  X holds the adjoints: the shared staging area (with the
+// levels lv) when the u-block fits it, else Fbar itself.
+template <bool SMEM>
+__device__ void step1_reverse_levels(const CondArgs &a, const CSmem &s, int c, bool hb, double2 *X,
+                                     const unsigned char *lv, const int *ust, const int *ucu)
 {
     const CondCirc &cc = a.plan[c];
+    const int tU = 2 * cc.nU, Db = 2 * cc.dsh.M, Dm = a.Dmax, U2 = cc.U2;
+    for (int lev = cc.Lu - 1; lev >= 0; --lev) {   // the top level has no readers
+        for (int v = threadIdx.x; v < U2; v += blockDim.x) {
+            if (SMEM && lv[v] != lev) continue;
+            int dv[2 * FK_MAXU], f0;
+            if (u_digits(v, tU, ust, ucu, dv, &f0) != lev) continue;
+            double2 acc = czero();
+            for (int w = 0; w < tU && w <= f0; ++w) {
+                if (dv[w] + 1 >= ucu[w]) continue;   // v + 1_w leaves the box
+                const int u1 = v + ust[w];
+                if (hb)
+                    acc = cfma_conj(s.br[Db + w],
+                                    rscale(ld_u<SMEM>(X + (SMEM ? u1 : fpos(cc, 0, u1))), s.inv[dv[w] + 1]), acc);
+                for (int t = w; t < tU; ++t) {
+                    const int dt = dv[t] + 1 + (t == w ? 1 : 0);   // digit t of u = v + 1_t + 1_w
+                    if (dt >= ucu[t]) continue;
+                    const int dw = dv[w] + 1 + (t == w ? 1 : 0);   // its digit w
+                    const int u2 = u1 + ust[t];
+                    acc = cfma_conj(s.Ar[(Db + w) * Dm + Db + t],
+                                    rscale(ld_u<SMEM>(X + (SMEM ? u2 : fpos(cc, 0, u2))), s.inv[dw]), acc);
+                }
+            }
+            double2 *dst = X + (SMEM ? v : fpos(cc, 0, v));
+            *dst = cadd(ld_u<SMEM>(dst), acc);
+        }
+        __syncthreads();
+    }
+}
+
+__device__ void step1_reverse(const CondArgs &a, CSmem &s, int c, bool hb)
+{
+    __shared__ int ust[2 * FK_MAXU], ucu[2 * FK_MAXU];
+    const CondCirc &cc = a.plan[c];
     load_circuit(a, s, c);
-    if (threadIdx.x != 0) return;
+    stage_ubox(cc, ust, ucu);
     const double2 *F = a.F + cc.off_F;
     double2 *Fb = a.Fbar + cc.off_F;
-    const int tU = 2 * cc.nU, Db = 2 * cc.dsh.M, Dm = a.Dmax;
-    double2 *pA = a.partA + ((size_t)c * a.slots + blockIdx.x * a.spb) * Dm * Dm;
-    double2 *pb = a.partb + ((size_t)c * a.slots + blockIdx.x * a.spb) * Dm;
-    if (cc.dsh.M == 0) {   // no detected mode: the upstream seed lands here
-        for (int u = 0; u < cc.U2; ++u) {
+    const int tU = 2 * cc.nU, Db = 2 * cc.dsh.M, Dm = a.Dmax, U2 = cc.U2;
+    const bool staged = step1_staged(s, cc);
+    double2 *X = staged ? (double2 *)s.s1 : Fb;
+    unsigned char *lv = staged ? (unsigned char *)(X + U2) : nullptr;
+    // the adjoints so far (and, with no detected mode, the upstream seed)
+    for (int u = threadIdx.x; u < U2; u += blockDim.x) {
+        int dig[2 * FK_MAXU], f0;
+        const int lev = u_digits(u, tU, ust, ucu, dig, &f0);
+        double2 y = __ldcg(Fb + fpos(cc, 0, u));
+        if (cc.dsh.M == 0) {
             int ket, bra;
             const double f = uscale(cc, s, u, &ket, &bra);
-            Fb[fpos(cc, 0, u)] = cadd(Fb[u], rscale(a.grho[rpos(cc, (int64_t)ket * cc.NUo + bra)], f));
+            y = cadd(y, rscale(a.grho[rpos(cc, (int64_t)ket * cc.NUo + bra)], f));
+        }
+        if (staged) {
+            X[u] = y;
+            lv[u] = (unsigned char)lev;
+        } else if (cc.dsh.M == 0) {
+            Fb[fpos(cc, 0, u)] = y;
         }
     }
-    for (int u = cc.U2 - 1; u >= 1; --u) {
-        int dig[2 * FK_MAXU], w = -1;
-        for (int q = 0; q < tU; ++q) {
-            dig[q] = udigit(cc, u, q);
-            if (w < 0 && dig[q] > 0) w = q;
-        }
-        const int P = u - cc.ustride[w];
-        const double2 y = rscale(Fb[u], s.inv[dig[w]]);
-        if (hb) {
-            Fb[fpos(cc, 0, P)] = cfma_conj(s.br[Db + w], y, Fb[P]);
-            pb[Db + w] = cfma_conj(F[P], y, pb[Db + w]);
-        }
-        for (int q = 0; q < tU; ++q) {
-            const int Pq = dig[q] - (q == w ? 1 : 0);
-            if (Pq <= 0) continue;
-            const int r = P - cc.ustride[q];
-            Fb[fpos(cc, 0, r)] = cfma_conj(s.Ar[(Db + w) * Dm + Db + q], y, Fb[r]);
-            double2 &dA = pA[(Db + w) * Dm + Db + q];
-            dA = cfma_conj(F[r], y, dA);
-        }
+    __syncthreads();
+    if (staged) {
+        step1_reverse_levels<true>(a, s, c, hb, X, lv, ust, ucu);
+        for (int u = threadIdx.x; u < U2; u += blockDim.x) Fb[fpos(cc, 0, u)] = X[u];
+    } else {
+        step1_reverse_levels<false>(a, s, c, hb, X, nullptr, ust, ucu);
     }
+    // partial sums: entry (w, t) with t >= w of dL/dA, t = tU the b term,
+    // each a sum over u formed in a fixed order
+    double2 *pA = a.partA + ((size_t)c * a.slots + blockIdx.x * a.spb) * Dm * Dm;
+    double2 *pb = a.partb + ((size_t)c * a.slots + blockIdx.x * a.spb) * Dm;
+    for (int w = 0; w < tU; ++w)
+        for (int t = w; t <= tU; ++t) {
+            if (t == tU && !hb) continue;
+            double2 acc = czero();
+            for (int u = threadIdx.x; u < U2; u += blockDim.x) {
+                int du[2 * FK_MAXU], f0;
+                u_digits(u, tU, ust, ucu, du, &f0);
+                if (f0 != w) continue;   // u = 0, or another first index
+                const int P = u - ust[w];
+                const double2 y = rscale(staged ? X[u] : __ldcg(Fb + fpos(cc, 0, u)), s.inv[du[w]]);
+                if (t == tU) {
+                    acc = cfma_conj(__ldcg(F + fpos(cc, 0, P)), y, acc);
+                } else if (du[t] - (t == w ? 1 : 0) > 0) {
+                    acc = cfma_conj(__ldcg(F + fpos(cc, 0, P - ust[t])), y, acc);
+                }
+            }
+            acc = block_sum(acc);
+            if (threadIdx.x == 0) {
+                double2 *dst = (t == tU) ? pb + Db + w : pA + (Db + w) * Dm + Db + t;
+                *dst = cadd(*dst, acc);
+            }
+        }
+    __syncthreads();
 }
 
 template <int KS>
@@ -1409,30 +1575,42 @@ __global__ void __launch_bounds__(TPB, (KS == 1 ? 4 : 1)) cond_vjp_kernel(const 
     for (int64_t e = gtid; e < (int64_t)a.B * Do * Do; e += gsz) a.gA[e] = czero();
     for (int64_t e = gtid; e < (int64_t)a.B * Do; e += gsz) a.gb[e] = czero();
     if (!grid_sync(a.ctl, gridDim.x, a.timeout_ns)) return;
-    for (int64_t e = gtid; e < (int64_t)a.B * Dm * Dm; e += gsz) {
-        const int c = (int)(e / (Dm * Dm));
-        const int w = (int)((e / Dm) % Dm), l = (int)(e % Dm);
-        const CondCirc &cc = a.plan[c];
-        if (w >= cc.Dred || l >= cc.Dred) continue;
-        double2 x = czero(), y = czero();
-        for (int blk = 0; blk < a.slots; ++blk) {
-            const double2 *pA = a.partA + ((size_t)c * a.slots + blk) * Dm * Dm;
-            x = cadd(x, pA[(size_t)w * Dm + l]);
-            y = cadd(y, pA[(size_t)l * Dm + w]);
+    // one warp per entry (w <= l of the symmetric dL/dA, then dL/db): the lanes
+    // sum interleaved subsets of the slots, a butterfly joins them
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = gtid >> 5, nw = gsz >> 5, nA = (int64_t)a.B * Dm * Dm;
+    for (int64_t e = gw; e < nA + (int64_t)a.B * Dm; e += nw) {
+        if (e < nA) {
+            const int c = (int)(e / (Dm * Dm));
+            const int w = (int)((e / Dm) % Dm), l = (int)(e % Dm);
+            const CondCirc &cc = a.plan[c];
+            if (w > l || l >= cc.Dred) continue;
+            double2 x = czero(), y = czero();
+            const double2 *pA = a.partA + (size_t)c * a.slots * Dm * Dm;
+            for (int blk = lane; blk < a.slots; blk += 32) {
+                x = cadd(x, __ldcg(pA + (size_t)blk * Dm * Dm + (size_t)w * Dm + l));
+                y = cadd(y, __ldcg(pA + (size_t)blk * Dm * Dm + (size_t)l * Dm + w));
+            }
+            x = warp_sum(x);
+            y = warp_sum(y);
+            if (lane == 0) {
+                const double2 g = make_double2(0.5 * (x.x + y.x), 0.5 * (x.y + y.y));
+                const int ow = cc.red_to_orig[w], ol = cc.red_to_orig[l];
+                a.gA[(size_t)c * Do * Do + (size_t)ow * Do + ol] = g;
+                a.gA[(size_t)c * Do * Do + (size_t)ol * Do + ow] = g;
+            }
+        } else {
+            const int c = (int)((e - nA) / Dm), w = (int)((e - nA) % Dm);
+            const CondCirc &cc = a.plan[c];
+            if (w >= cc.Dred) continue;
+            double2 x = czero();
+            for (int blk = lane; blk < a.slots; blk += 32)
+                x = cadd(x, __ldcg(a.partb + ((size_t)c * a.slots + blk) * Dm + w));
+            x = warp_sum(x);
+            if (lane == 0) a.gb[(size_t)c * Do + cc.red_to_orig[w]] = x;
         }
-        const int ow = cc.red_to_orig[w], ol = cc.red_to_orig[l];
-        a.gA[(size_t)c * Do * Do + (size_t)ow * Do + ol] =
-            make_double2(0.5 * (x.x + y.x), 0.5 * (x.y + y.y));
     }
-    for (int64_t e = gtid; e < (int64_t)a.B * Dm; e += gsz) {
-        const int c = (int)(e / Dm), w = (int)(e % Dm);
-        const CondCirc &cc = a.plan[c];
-        if (w >= cc.Dred) continue;
-        double2 x = czero();
-        for (int blk = 0; blk < a.slots; ++blk) x = cadd(x, a.partb[((size_t)c * a.slots + blk) * Dm + w]);
-        a.gb[(size_t)c * Do + cc.red_to_orig[w]] = x;
-    }
-    for (int64_t c = gtid; c < a.B; c += gsz) a.gc[c] = a.Fbar[a.plan[c].off_F];
+    for (int64_t c = gtid; c < a.B; c += gsz) a.gc[c] = __ldcg(a.Fbar + a.plan[c].off_F);
 }
 
 }  // namespace
