@@ -46,12 +46,12 @@ NCIRC = 16
 # each walk kernel on this 16-circuit workload, captured with ncu on a
 # 2-circuit launch and scaled by 8: circuits share no data, so traffic grows
 # in proportion to them.  Valid only for the kernel source it was measured on
-# (sha256 prefix of csrc/walk_diag_impl.cuh + walk_digits.cuh) and the engine / tile shape; reported
-# as null once either differs.
-TRAFFIC = {"kernel_sha": "c3afe7d126e57f2e", "tuning": ["tensor", 128, 4, 0],
-           "bytes_per_launch": {"diag_forward_kernel": 8 * (495795456 + 853985792),
-                                "diag_vjp_kernel": 8 * (702128384 + 803239424),
-                                "diag_vjp_partials_kernel": 8 * (1728069120 + 132130816)}}
+# (sha256 prefix of csrc/walk_diag_impl.cuh + walk_digits.cuh + walk_common.cuh)
+# and the engine / tile shape; reported as null once either differs.
+TRAFFIC = {"kernel_sha": "3d72219af4fdc118", "tuning": ["tensor", 128, 4, 0],
+           "bytes_per_launch": {"diag_forward_kernel": 8 * (495609856 + 853644800),
+                                "diag_vjp_kernel": 8 * (701247744 + 802786560),
+                                "diag_vjp_partials_kernel": 8 * (1728042240 + 131408384)}}
 
 FALLBACK_HBM_GBS = 6800.0
 
@@ -66,10 +66,11 @@ def measured_hbm_gbs():
 
 
 def kernel_sha():
-    """sha256 prefix of the walk kernels' source (csrc/walk_diag_impl.cuh and
-    the digit primitives of csrc/walk_digits.cuh)."""
+    """sha256 prefix of the walk kernels' source (csrc/walk_diag_impl.cuh, the
+    digit primitives of csrc/walk_digits.cuh and the grid barrier and helpers
+    of csrc/walk_common.cuh)."""
     h = hashlib.sha256()
-    for name in ("walk_diag_impl.cuh", "walk_digits.cuh"):
+    for name in ("walk_diag_impl.cuh", "walk_digits.cuh", "walk_common.cuh"):
         with open(os.path.join(ROOT, "paper_2303_08879_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
