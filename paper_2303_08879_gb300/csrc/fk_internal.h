@@ -25,7 +25,13 @@ struct Control {
     int dbg_site;        // source line of the first one
     long long dbg_index; // its index and the box [dbg_lo, dbg_hi) it had to lie in
     long long dbg_lo, dbg_hi;
-    int pad[50];
+    int pad[48];
+    // Key of the all-detected walk's pivot geometry table in this workspace,
+    // written by the forward after it built the table.  The forward clears
+    // the whole block before its launch; the VJP launch clears only the words
+    // before this one, so the reverse walk can tell that the table its
+    // workspace holds was built for its shape and reuse it.
+    unsigned long long geo_key;
 };
 static_assert(sizeof(Control) == 256, "control block is 256 bytes");
 

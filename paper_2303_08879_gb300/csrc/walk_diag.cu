@@ -5,6 +5,7 @@
 // kernels (vacuum problems, the input scan, the bounded-wait self-test).
 #include <cuda_runtime.h>
 
+#include <cstddef>
 #include <mutex>
 
 #include "walk_diag_impl.cuh"
@@ -322,6 +323,19 @@ static int launch_coop(const void *fn, int grid, int tpb, size_t smem, DiagArgs 
     return e == cudaSuccess ? FK_OK : FK_ECUDA;
 }
 
+// Key of the pivot geometry table: FNV-1a over the shape (a struct without
+// padding, zero-filled before it is built) and the table's address.
+static unsigned long long geometry_key(const DiagShape &sh, const int *geo)
+{
+    static_assert(sizeof(DiagShape) % 8 == 0, "DiagShape has no tail padding");
+    unsigned long long h = 0xcbf29ce484222325ull;
+    const unsigned char *p = (const unsigned char *)&sh;
+    for (size_t i = 0; i < sizeof(DiagShape); ++i) h = (h ^ p[i]) * 0x100000001b3ull;
+    const unsigned long long g = (unsigned long long)(uintptr_t)geo;
+    for (int i = 0; i < 8; ++i) h = (h ^ ((g >> (8 * i)) & 0xffu)) * 0x100000001b3ull;
+    return h | 1ull;   // never 0, the cleared value
+}
+
 static DiagArgs make_args(const DiagShape &sh, int batch, unsigned flags, const void *A,
                           const void *b, const void *c, void *ws, const DiagLayout &lay)
 {
@@ -339,6 +353,7 @@ static DiagArgs make_args(const DiagShape &sh, int batch, unsigned flags, const 
     a.dig = (unsigned char *)(w + lay.dig);
     a.ctr = (int *)(w + lay.ctr);
     a.geo = lay.geo != lay.F ? (int *)(w + lay.geo) : nullptr;
+    a.geo_key = a.geo != nullptr ? geometry_key(sh, a.geo) : 0ull;
     a.F = (double2 *)(w + lay.F);
     a.lvl = (unsigned long long *)(w + lay.lvl);
     a.timeout_ns = kBarrierTimeoutNs;
@@ -412,7 +427,9 @@ int launch_diag_vjp(const DiagShape &sh, int batch, unsigned flags, const void *
         return cudaGetLastError() == cudaSuccess ? FK_OK : FK_ECUDA;
     }
     char *w = (char *)ws;
-    if (cudaMemsetAsync(w + lay.ctl, 0, sizeof(Control), st) != cudaSuccess) return FK_ECUDA;
+    // the words before geo_key: the key the forward left says whether its
+    // pivot geometry table is still the one this walk needs
+    if (cudaMemsetAsync(w + lay.ctl, 0, offsetof(Control, geo_key), st) != cudaSuccess) return FK_ECUDA;
     // With b = 0 every adjoint the walk reads is stored before it is read (or
     // read as zero), so Fbar needs clearing only for the b != 0 sums.
     if (sh.has_b && cudaMemsetAsync(w + lay.Fbar, 0, lay.scratch - lay.Fbar, st) != cudaSuccess) return FK_ECUDA;
@@ -428,6 +445,7 @@ int launch_diag_vjp(const DiagShape &sh, int batch, unsigned flags, const void *
     a.gc = (double2 *)gc;
     a.grid = lay.grid_vjp;
     a.slots = lay.slots_vjp;
+    a.geo_reuse = 1;
     if (es) {
         a.early = 1;
         a.thr = stop_threshold(es->eps);

@@ -87,6 +87,12 @@ struct DiagArgs {
     // blocks): each block walks whole circuits taken from a counter, with block
     // barriers between its phases instead of grid barriers
     int pc;
+    // key of the pivot geometry table for this shape and workspace (0: none);
+    // geo_reuse: the table may be taken as built when the workspace's control
+    // block holds the same key (the reverse walk after its forward)
+    unsigned long long geo_key;
+    int geo_reuse;
+    int pad_geo;
 };
 
 // ------------------------------------------------------------ shared memory
@@ -1263,7 +1269,9 @@ struct Walk {
         if (clear_ctr)
             for (int64_t e = gtid; e < 4 * (int64_t)(sh.L + 1); e += gsz) a.ctr[e] = 0;
         if constexpr (TC) build_digits(a, s);
-        if (a.geo != nullptr) build_geometry(a, s);
+        if (a.geo != nullptr &&
+            !(a.geo_reuse && *(volatile const unsigned long long *)&a.ctl->geo_key == a.geo_key))
+            build_geometry(a, s);
         if (seed) {
             for (int64_t c = gtid; c < a.B; c += gsz) {
                 const double2 v = a.c[cix(a, (int)c)];
@@ -1829,6 +1837,7 @@ struct Walk {
         build_tables(sh, s);
         prologue(a, s, true);
         if (!grid_sync(a.ctl, gridDim.x, a.timeout_ns)) return;
+        if (a.geo != nullptr && blockIdx.x == 0 && threadIdx.x == 0) a.ctl->geo_key = a.geo_key;
         const int hb = *(volatile int *)&a.ctl->has_b;
         if (hb && !sh.has_b) {
             if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&a.ctl->status, 0, (int)FK_EBZERO);

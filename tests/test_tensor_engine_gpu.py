@@ -268,3 +268,31 @@ def test_tensor_vjp_gbs_m8_c6_batch16_matches_fp64_engine(fd):
         assert np.max(np.abs(gA[i] - rA[i])) <= 1e-10 * scale, i
         assert np.allclose(gA[i], gA[i].T, rtol=0, atol=1e-14 * scale)
     assert np.max(np.abs(gc - rc)) <= 1e-10 * np.max(np.abs(rc))
+
+
+def test_vjp_geometry_table_reused_or_rebuilt_alike(fd):
+    """The reverse walk takes the pivot-geometry table its forward built when
+    the workspace's control block holds the table's key (shape and address),
+    and rebuilds it otherwise.  A copy of the workspace lives at another
+    address, so its VJP rebuilds the table: both gradients must agree bit for
+    bit, and with the oracle's closed-form VJP."""
+    rng = np.random.default_rng(31)
+    cut = (3, 2, 2, 2, 2, 3)
+    A1, b1 = inputs.random_symmetric(2 * len(cut), rng, scale=0.12, with_b=False)
+    A, b, c = cuda(A1[None]), cuda(b1[None]), cuda(np.array([0.7 - 0.2j]))
+    w = rng.normal(size=(1,) + cut) + 1j * rng.normal(size=(1,) + cut)
+    flags = fd.FK_FLAG_B_ZERO
+    _, ws = fd.fock_diag_probs_batched(A, b, c, cut, flags=flags)
+    ws2 = ws.clone()
+    g_reuse = fd.fock_diag_probs_vjp_batched(A, b, c, cut, cuda(w), ws, flags=flags)
+    g_build = fd.fock_diag_probs_vjp_batched(A, b, c, cut, cuda(w), ws2, flags=flags)
+    for x, y in zip(g_reuse, g_build):
+        assert torch.equal(x, y)
+    G = oracle.full_lattice(A1, b1, 0.7 - 0.2j, oracle.dm_dims(cut))
+    gfull = np.zeros_like(G)
+    for n in np.ndindex(*cut):
+        gfull[tuple(v for a in n for v in (a, a))] = w[0][n]
+    rA, _, _ = ograd.vjp(G, gfull, 0.7 - 0.2j)
+    got = g_reuse[0][0].cpu().numpy()
+    big = np.abs(rA) > 1e-12 * max(1.0, float(np.max(np.abs(rA))))
+    assert np.max(np.abs(got - rA)[big] / np.abs(rA[big])) <= VJP_RTOL
