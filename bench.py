@@ -48,10 +48,10 @@ NCIRC = 16
 # in proportion to them.  Valid only for the kernel source it was measured on
 # (sha256 prefix of csrc/walk_diag_impl.cuh + walk_digits.cuh + walk_common.cuh)
 # and the engine / tile shape; reported as null once either differs.
-TRAFFIC = {"kernel_sha": "923a35d60ba7d32c", "tuning": ["tensor", 128, 4, 0],
-           "bytes_per_launch": {"diag_forward_kernel": 8 * (496057344 + 854129664),
-                                "diag_vjp_kernel": 8 * (707885568 + 722685440),
-                                "diag_vjp_partials_kernel": 8 * (1728098304 + 131586560)}}
+TRAFFIC = {"kernel_sha": "9b3fd66c1972b7e8", "tuning": ["tensor", 128, 4, 0],
+           "bytes_per_launch": {"diag_forward_kernel": 8 * (496652800 + 853942272),
+                                "diag_vjp_kernel": 8 * (707781888 + 722182144),
+                                "diag_vjp_partials_kernel": 8 * (1729087744 + 132293120)}}
 
 FALLBACK_HBM_GBS = 6800.0
 

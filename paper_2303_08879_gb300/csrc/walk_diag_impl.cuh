@@ -1105,27 +1105,34 @@ struct Walk {
         return ap_assemble<false>(sh, e, K, s, lev, (int64_t)r, q);
     }
 
-    // The table: every AP pivot of the pivot levels (one grid-stride pass per
-    // (K, level); every thread keeps the level offsets).
+    // The table: every AP pivot of the pivot levels.  The pivots (K, level, r)
+    // in that order are numbered densely and handed out grid-stride, so every
+    // thread gets the same share whatever the level sizes; a thread's numbers
+    // only grow, so it advances its (K, level) position instead of searching.
     static __device__ void build_geometry(const DiagArgs &a, const Smem &s)
     {
         const DiagShape &sh = a.sh;
-        const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
         const int64_t gsz = (int64_t)gridDim.x * blockDim.x;
-        for (int K = 0; K < sh.M; ++K) {
-            int64_t off = sh.off_ap[K];
-            for (int lev = 0; lev < sh.L; ++lev) {
-                const int64_t cnt = Pf(s, K, lev, sh.C[K] - 1);
-                for (int64_t r = gtid; r < cnt; r += gsz) {
-                    const Dig e = unrank(sh, s, K, 1, lev, (unsigned)r);
-                    const ApRel q = ap_rel(sh, e, K, s, lev, r);
-                    int4 *rec = (int4 *)(a.geo + (size_t)box_ap(sh, K, off + r) * kGeoInts);
-                    rec[0] = make_int4((int)(unsigned)e.lo, (int)(unsigned)(e.lo >> 32), q.idx[0], q.idx[1]);
-                    rec[1] = make_int4(q.idx[2], q.idx[3], q.idx[4], q.idx[5]);
-                    rec[2] = make_int4(q.idx[6], q.rt2, q.wdiag, 0);
+        int K = 0, lev = 0;
+        int64_t kbase = 0, lbase = 0;   // dense numbers of the first pivot of family K, of (K, lev)
+        int64_t cnt = Pf(s, 0, 0, sh.C[0] - 1);
+        for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;; t += gsz) {
+            while (t >= lbase + cnt) {
+                lbase += cnt;
+                if (++lev >= sh.L) {
+                    if (++K >= sh.M) return;
+                    lev = 0;
+                    kbase = lbase;
                 }
-                off += cnt;
+                cnt = Pf(s, K, lev, sh.C[K] - 1);
             }
+            const int64_t r = t - lbase;
+            const Dig e = unrank(sh, s, K, 1, lev, (unsigned)r);
+            const ApRel q = ap_rel(sh, e, K, s, lev, r);
+            int4 *rec = (int4 *)(a.geo + (size_t)box_ap(sh, K, sh.off_ap[K] + (lbase - kbase) + r) * kGeoInts);
+            rec[0] = make_int4((int)(unsigned)e.lo, (int)(unsigned)(e.lo >> 32), q.idx[0], q.idx[1]);
+            rec[1] = make_int4(q.idx[2], q.idx[3], q.idx[4], q.idx[5]);
+            rec[2] = make_int4(q.idx[6], q.rt2, q.wdiag, 0);
         }
     }
 
