@@ -177,6 +177,31 @@ def test_vjp_matches_oracle_gradient(fd, cut, mask, withb):
     assert_grad_close(gA2[0].cpu().numpy(), rA, "grad_A (recompute)")
 
 
+# Large undetected blocks: step 1 keeps its u-block in the block's shared
+# staging area only when the values and levels fit (17 bytes a point).  With
+# U2 = 34^2 the forward reads F directly and the VJP stages; with U2 = 50^2
+# both read global memory (for either engine's buffer sizes).
+LARGE_U_CASES = [((3, 34), (1, 0)), ((2, 50), (1, 0))]
+
+
+@pytest.mark.parametrize("cut,mask", LARGE_U_CASES)
+def test_large_undetected_block_forward_and_vjp(fd, cut, mask):
+    rng = np.random.default_rng(300 + sum(cut))
+    A, b = inputs.random_symmetric(2 * len(cut), rng, scale=0.12, with_b=True)
+    c = 0.5 - 0.2j
+    ref_rho = oracle.full_dm_conditional(A, b, c, cut, mask)
+    got, (Ad, bd, cd, ws) = gpu_cond(fd, A[None], b[None], c, [cut], mask)
+    assert_amp_close(got[0], ref_rho)
+    gbar = rng.normal(size=ref_rho.shape) + 1j * rng.normal(size=ref_rho.shape)
+    rA, rb, rc = oracle_cond_vjp(A, b, c, cut, mask, gbar)
+    gA, gb, gc = fd.fock_conditional_dm_vjp_batched(Ad, bd, cd, [cut], mask,
+                                                    cuda(gbar.reshape(-1)), ws, flags=FLAGS)
+    fd.check_workspace(ws)
+    assert_grad_close(gA[0].cpu().numpy(), rA, "grad_A")
+    assert_grad_close(gb[0].cpu().numpy(), rb, "grad_b")
+    assert abs(gc[0].item() - rc) <= VJP_RTOL * max(abs(rc), 1e-300)
+
+
 def test_vjp_batch_adjoint_and_homogeneity(fd):
     """Heterogeneous batch: every circuit's VJP satisfies the Euler identity
     sum conj(gbar)|k| G = sum 2 A conj(gA) + sum b conj(gb); one circuit is
