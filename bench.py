@@ -293,7 +293,7 @@ def _triples(fd, circs, dev):
     return A, b, c
 
 
-def config1_row(torch, fd, inputs, dev, fp64_peak):
+def small_circuit_row(torch, fd, inputs, dev, fp64_peak):
     """1 circuit, M = 2, C = 10, b = 0: latency of one forward and one
     forward + VJP call (launch-bound), and the same shape batched."""
     from paper_2303_08879_gb300 import counts
@@ -324,7 +324,7 @@ def config1_row(torch, fd, inputs, dev, fp64_peak):
     return out
 
 
-def config5_row(torch, fd, inputs, dev, fp64_peak, hbm):
+def large_circuit_row(torch, fd, inputs, dev, fp64_peak, hbm):
     """1 circuit, M = 12, C = 5 (4.63 G walk amplitudes, 244 M probabilities),
     forward + VJP with the forward's amplitudes kept (no checkpointing), on
     the default engine (the tensor engine up to 12 kept modes), with the
@@ -364,10 +364,10 @@ def config5_row(torch, fd, inputs, dev, fp64_peak, hbm):
             "engine": engine, "forward_ms": fwd, "vjp_ms": vjp,
             "probabilities_per_s": nout / ((fwd + vjp) * 1e-3), "walk_amplitudes": stored,
             "workspace_bytes": wsb,
-            "roofline": _config5_roofline(engine, f_fwd, fwd, vjp, by_fwd, by_vjp, fp64_peak, hbm)}
+            "roofline": _large_circuit_roofline(engine, f_fwd, fwd, vjp, by_fwd, by_vjp, fp64_peak, hbm)}
 
 
-def _config5_roofline(engine, f_fwd, fwd, vjp, by_fwd, by_vjp, fp64_peak, hbm):
+def _large_circuit_roofline(engine, f_fwd, fwd, vjp, by_fwd, by_vjp, fp64_peak, hbm):
     """The roof that binds the engine: HBM for the tensor engine (the digit
     products leave the FP64 pipe), the FP64 pipe for the FP64 engine; the
     other one beside it."""
@@ -405,7 +405,7 @@ def fig10_row(torch, fd):
 
 
 def learned_row():
-    """Config 4: dataset of 2^20 circuits from the batched conditional walk,
+    """Learned proposals: dataset of 2^20 circuits from the batched conditional walk,
     BF16 MLP training, then 32 MLP-proposed starts against 32 random starts,
     each refined by the same exact-gradient steps (wall times measured)."""
     from paper_2303_08879_gb300 import proposal
@@ -472,9 +472,9 @@ def secondary_rows(torch, fd, inputs, dev, fp64_peak, reps=5):
         "walk_amplitudes": n_amp,
         "outputs_per_s": n_out / ((fwd + vjp) * 1e-3),
         "circuits_per_s": 64 / ((fwd + vjp) * 1e-3),
-        # the slower of the two roofs the benchmark spec names binds here: the counted
-        # FP64 flops at the FP64 peak take 8x longer than the bytes at the HBM
-        # peak, and the tensor engine stays below the FP64 roof
+        # the slower of the two roofs (FP64 flops at the FP64 peak, bytes at
+        # the HBM peak) binds here: the counted FP64 flops take 8x longer than
+        # the bytes, and the tensor engine stays below the FP64 roof
         "roofline": {"bound": "alu", "achieved": f_fwd / (fwd * 1e-3) / 1e12, "peak": fp64_peak,
                      "unit": "TFLOP/s", "frac": f_fwd / (fwd * 1e-3) / 1e12 / fp64_peak,
                      "kernel": "cond_forward_kernel", "algorithmic_flops_forward": f_fwd,
@@ -524,9 +524,9 @@ def secondary_rows(torch, fd, inputs, dev, fp64_peak, reps=5):
         "roofline": {"bound": "tensor", "batch": 65536, "achieved": tf, "peak": peak,
                      "unit": "TFLOP/s", "frac": tf / peak, "peak_source": src}}
     torch.cuda.empty_cache()
-    rows["config1_latency"] = config1_row(torch, fd, inputs, dev, fp64_peak)
+    rows["m2_c10_latency"] = small_circuit_row(torch, fd, inputs, dev, fp64_peak)
     torch.cuda.empty_cache()
-    rows["config5_large"] = config5_row(torch, fd, inputs, dev, fp64_peak, hbm)
+    rows["m12_c5_large"] = large_circuit_row(torch, fd, inputs, dev, fp64_peak, hbm)
     rows["fig10b_time_vs_cutoff"] = fig10_row(torch, fd)
     torch.cuda.empty_cache()
     rows["learned_proposal"] = learned_row()
