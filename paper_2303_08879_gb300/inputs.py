@@ -89,34 +89,34 @@ def make_circuit(M, rng, *, r_range, eta_range, alpha_var=0.0,
 
 
 # ---------------------------------------------------------------------------
-# The five synthetic workloads (shapes and distributions of the paper's
-# GBS / conditional-state settings).  ``scale`` shrinks a workload for tests.
+# The synthetic workloads (shapes and distributions of the paper's
+# GBS / conditional-state settings); tests take the first few circuits of one.
 # ---------------------------------------------------------------------------
 
-def _cfg1(i, rng):
+def _gbs_m2_c10(i, rng):
     return make_circuit(2, rng, r_range=(0.0, 1.0), eta_range=(0.5, 1.0), cutoffs=(10, 10))
 
 
-def _cfg2(i, rng):
+def _cond_m3(i, rng):
     c0 = int(rng.integers(10, 21)); c1 = int(rng.integers(10, 21)); cu = int(rng.integers(20, 31))
     return make_circuit(3, rng, r_range=(0.0, 1.2), eta_range=(0.7, 1.0), alpha_var=0.5,
                         cutoffs=(c0, c1, cu), detected=(True, True, False))
 
 
-def _cfg3(i, rng):
+def _gbs_m8_c6(i, rng):
     return make_circuit(8, rng, r_range=(0.3, 1.0), eta_range=(0.6, 1.0), cutoffs=(6,) * 8)
 
 
-def _cfg5(i, rng):
+def _gbs_m12_c5(i, rng):
     return make_circuit(12, rng, r_range=(0.2, 0.8), eta_range=(0.8, 1.0), cutoffs=(5,) * 12)
 
 
 WORKLOADS = {
-    # name: (workload id, number of circuits, maker)
-    "gbs_m2_c10": (1, 1, _cfg1),
-    "cond_m3_batch64": (2, 64, _cfg2),
-    "gbs_m8_c6_batch16": (3, 16, _cfg3),
-    "gbs_m12_c5": (5, 1, _cfg5),
+    # name: (seed stream of the workload, number of circuits, maker)
+    "gbs_m2_c10": (1, 1, _gbs_m2_c10),
+    "cond_m3_batch64": (2, 64, _cond_m3),
+    "gbs_m8_c6_batch16": (3, 16, _gbs_m8_c6),
+    "gbs_m12_c5": (5, 1, _gbs_m12_c5),
 }
 
 
