@@ -172,7 +172,11 @@ int fock_diag_probs_batched(int batch, const fk_c128 *d_A, const fk_c128 *d_b, c
  *   d_grad_probs [batch][prod C_j]   upstream gradient (PyTorch convention)
  *   d_grad_A [batch][D][D], d_grad_b [batch][D], d_grad_c [batch]  outputs
  * Unless FK_FLAG_RECOMPUTE is set, d_ws must hold the state of a
- * fock_diag_probs[_batched] call with the same inputs, shape and flags.
+ * fock_diag_probs[_batched] call with the same inputs, shape and flags: its
+ * amplitudes, and the pivot-geometry table (up to 8 kept modes), which the
+ * reverse walk takes as built when the key that forward left in the
+ * workspace's control block matches this shape and address (it rebuilds the
+ * table otherwise, e.g. in a copy of the workspace).
  */
 int fock_diag_probs_vjp(const fk_c128 *d_A, const fk_c128 *d_b, const fk_c128 *d_c, int M,
                         const int *host_cutoffs, const fk_c128 *d_grad_probs, fk_c128 *d_grad_A,
